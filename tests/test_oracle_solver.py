@@ -1,0 +1,224 @@
+"""Oracle pins: mechanical laws (App. B), Jv (Eq. JF), J~ (Sec. 3.1), GMRES, Newton (Sec. 3.2-3.3),
+multigrid (structure only: parity unpinned beyond these properties)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_17217_gb300 import inputs as I
+
+
+def _rot(rng):
+    q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    return q * np.sign(np.linalg.det(q))
+
+
+def _one_cell_oracle(law, p1, p2):
+    m = I.hex_box(2, 2, 2)
+    return O.Oracle(m, I.Material(law, p1, p2))
+
+
+def test_neo_hookean_small_strain_limit_is_hooke():
+    """App. B: for |grad u| << 1 the neo-Hookean law reduces to linear elasticity."""
+    mu, kappa = 0.38e6, 8.3e6
+    lam = kappa - 2 * mu / 3
+    o = _one_cell_oracle(I.LAW_NEOHOOKEAN, mu, kappa)
+    rng = np.random.default_rng(1)
+    G0 = rng.standard_normal((3, 3))
+    for t in (1e-4, 1e-5, 1e-6):
+        G = t * G0
+        s = o.cauchy_stress(G)
+        hooke = mu * (G + G.T) + lam * np.trace(G) * np.eye(3)
+        err = np.abs(s - hooke).max() / np.abs(hooke).max()
+        assert err < 20 * t  # first-order agreement
+
+
+def test_neo_hookean_objectivity_and_rotation():
+    mu, kappa = 1.0e6, 5.0e6
+    o = _one_cell_oracle(I.LAW_NEOHOOKEAN, mu, kappa)
+    rng = np.random.default_rng(2)
+    F = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+    assert np.linalg.det(F) > 0
+    Q = _rot(rng)
+    s = o.cauchy_stress((F - np.eye(3)).T)
+    s_rot = o.cauchy_stress((Q @ F - np.eye(3)).T)
+    np.testing.assert_allclose(s_rot, Q @ s @ Q.T, atol=1e-8 * np.abs(s).max())
+    np.testing.assert_allclose(s, s.T, atol=1e-9 * np.abs(s).max())
+    # a pure rotation is stress free
+    s0 = o.cauchy_stress((Q - np.eye(3)).T)
+    assert np.abs(s0).max() < 1e-9 * mu
+    # pure dilatation J: sigma = kappa/2 (J^2 - 1)/J I
+    J = 1.2
+    sd = o.cauchy_stress((J ** (1 / 3) - 1) * np.eye(3))
+    np.testing.assert_allclose(sd, 0.5 * kappa * (J * J - 1) / J * np.eye(3), rtol=1e-12, atol=1e-6)
+
+
+def test_total_lagrangian_traction_operator():
+    """App. A: (J F^-T n) . sigma = n . T with T = J F^-1 sigma, checked against the first
+    Piola-Kirchhoff stress P = J sigma F^-T (P^T n)."""
+    o = _one_cell_oracle(I.LAW_NEOHOOKEAN, 1e6, 4e6)
+    rng = np.random.default_rng(3)
+    G = 0.2 * rng.standard_normal((3, 3))
+    F = np.eye(3) + G.T
+    grad = np.broadcast_to(G, (8, 3, 3)).copy()
+    T = o.traction_operator(grad)[0]
+    s = o.cauchy_stress(G)
+    Pk = np.linalg.det(F) * s @ np.linalg.inv(F).T
+    n = rng.standard_normal(3)
+    np.testing.assert_allclose(n @ T, Pk @ n, rtol=1e-12)
+
+
+def _fd_jacobian(o, u, h):
+    n = u.size
+    J = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n); e[j] = h
+        J[:, j] = (o.residual((u.ravel() + e).reshape(u.shape)) - o.residual((u.ravel() - e).reshape(u.shape))).ravel() / (2 * h)
+    return J
+
+
+def test_jv_matches_bruteforce_fd_jacobian_linear():
+    c = I.case_cantilever(4, 3, 3, (0.4, 0.3, 0.3), perturb=0.15, seed=2)  # 36 cells
+    o = O.Oracle.from_case(c)
+    u = I.random_field(1, c.mesh.n_cells, 1e-5)
+    K = _fd_jacobian(o, u, 1e-6)  # exact up to round-off: R is affine
+    for seed in (3, 4):
+        v = I.random_field(seed, c.mesh.n_cells, 1.0)
+        Jv = o.jv(u, v).ravel()
+        Kv = K @ v.ravel()
+        assert np.linalg.norm(Jv - Kv) < 1e-6 * np.linalg.norm(Kv)
+
+
+def test_jv_matches_bruteforce_fd_jacobian_neo_hookean():
+    c = I.case_nh_beam(5, 3, 3, (0.5, 0.3, 0.3), end_uy=0.05, perturb=0.1)  # 45 cells
+    o = O.Oracle.from_case(c)
+    u = I.random_field(1, c.mesh.n_cells, 2e-2)
+    J = _fd_jacobian(o, u, 1e-6)
+    v = I.random_field(5, c.mesh.n_cells, 1.0)
+    Jv = o.jv(u, v).ravel()
+    assert np.linalg.norm(Jv - J @ v.ravel()) < 1e-5 * np.linalg.norm(J @ v.ravel())
+    # zero direction
+    assert np.all(o.jv(u, np.zeros_like(v)) == 0)
+
+
+def test_jtilde_closed_form_on_uniform_box():
+    """Sec. 3.1 on an orthogonal uniform mesh: off-diagonals Kbar |Gamma| / h, so J~ is Kbar h
+    times the 7-point graph Laplacian; displacement faces add Kbar |Gamma| / (h/2)."""
+    nx, ny, nz, h = 4, 3, 3, 0.5
+    m = I.hex_box(nx, ny, nz, (nx * h, ny * h, nz * h))
+    m.patch("xmin").bc = I.BC_DISP
+    E, nu = 3.0, 0.2
+    Kbar = E / (1 + nu) + E * nu / ((1 + nu) * (1 - 2 * nu))
+    o = O.Oracle(m, I.Material(I.LAW_LINEAR, E, nu))
+    A = np.zeros((m.n_cells, m.n_cells))
+    for P, N in zip(m.owner[: m.n_internal], m.neighbour):
+        A[P, N] = A[N, P] = Kbar * h
+    D = -A.sum(1)
+    i = np.arange(m.n_cells) % nx
+    D[i == 0] -= Kbar * h * 2
+    A += np.diag(D)
+    np.testing.assert_allclose(o.jtilde_diag(), D, rtol=1e-14)
+    v = I.random_field(2, m.n_cells, 1.0)
+    np.testing.assert_allclose(o.jtilde_apply(v), A @ v, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(o.bjacobi(v), v / D[:, None], rtol=1e-14)
+
+
+def test_jtilde_symmetric_negative_definite_on_distorted_mesh():
+    c = I.case_cantilever(5, 3, 3, (0.5, 0.3, 0.3), perturb=0.15, seed=8)
+    o = O.Oracle.from_case(c)
+    n = c.mesh.n_cells
+    M = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros((n, 3)); e[j, 0] = 1.0
+        M[:, j] = o.jtilde_apply(e)[:, 0]
+    np.testing.assert_allclose(M, M.T, rtol=1e-13, atol=1e-13 * np.abs(M).max())
+    assert np.linalg.eigvalsh(M).max() < 0
+    # rows of cells without displacement faces sum to zero
+    rows = M.sum(1)
+    i = np.arange(n) % 5
+    assert np.abs(rows[i > 0]).max() < 1e-12 * np.abs(M).max()
+
+
+def test_gmres_full_krylov_solves_linear_system():
+    c = I.case_cantilever(4, 3, 3, (0.4, 0.3, 0.3), perturb=0.15, seed=2)
+    o = O.Oracle.from_case(c)
+    nc = c.mesh.n_cells
+    u = np.zeros((nc, 3))
+    K = _fd_jacobian(o, u, 1e-6)
+    b = I.random_field(3, nc, 1e3)
+    for pc in (O.PC_NONE, O.PC_BJACOBI):
+        x, rc, its, rel = o.gmres(u, b, m=3 * nc, eta=1e-10, max_restarts=2, pc=pc)
+        assert rc == 0
+        x_ref = np.linalg.solve(K, b.ravel())
+        assert np.linalg.norm(x.ravel() - x_ref) < 1e-7 * np.linalg.norm(x_ref)
+    # preconditioning reduces the iteration count
+    _, _, its_none, _ = o.gmres(u, b, m=3 * nc, eta=1e-6, pc=O.PC_NONE)
+    _, _, its_bj, _ = o.gmres(u, b, m=3 * nc, eta=1e-6, pc=O.PC_BJACOBI)
+    assert its_bj <= its_none
+
+
+def test_newton_linear_problem_and_preconditioner_independence():
+    """The converged discrete solution does not depend on the preconditioner (Sec. 3.1)."""
+    c = I.case_cantilever(6, 4, 4, (0.6, 0.4, 0.4), perturb=0.15, seed=2)
+    o = O.Oracle.from_case(c)
+    o.mg_setup(coarse_max=10)
+    sols = []
+    for pc in (O.PC_BJACOBI, O.PC_MG):
+        u, rc, st = o.newton(rtol=1e-11, eta=1e-6, pc=pc)
+        assert rc == 0
+        sols.append(u)
+    assert np.linalg.norm(sols[0] - sols[1]) < 1e-7 * np.linalg.norm(sols[0])
+
+
+def test_newton_quadratic_convergence_neo_hookean():
+    """Sec. 2.2: with an (almost) exact Jacobian action Newton converges quadratically:
+    log r_{k+1} / log r_k -> 2 until the finite-difference floor."""
+    c = I.case_nh_beam(8, 3, 3, (1.0, 0.125, 0.125), end_uy=0.15, load_steps=1)
+    o = O.Oracle.from_case(c)
+    u, rc, st = o.newton(rtol=1e-11, eta=1e-12, pc=O.PC_BJACOBI, max_newton=30)
+    assert rc == 0
+    o.set_load_factor(1.0)
+    r0 = np.linalg.norm(o.residual(np.zeros_like(u)))
+    r = np.array([st.hist[k] for k in range(st.n_hist)]) / r0
+    # find consecutive pairs in the asymptotic range (1e-1 > r_k > 1e-5)
+    orders = [np.log(r[k + 1]) / np.log(r[k]) for k in range(len(r) - 1) if 1e-5 < r[k] < 5e-2 and r[k + 1] > 1e-12]
+    assert orders, r
+    assert max(orders) > 1.8, (r, orders)
+
+
+def test_multigrid_aggregation_on_chain():
+    """Hand-worked pass-1/pass-2 aggregation of a uniform 6-cell chain:
+    {0,1} then {3,2,4}; 5 joins the aggregate of 4."""
+    m = I.hex_box(6, 1, 1, (6.0, 1.0, 1.0))
+    m.patch("xmin").bc = I.BC_DISP
+    o = O.Oracle(m, I.Material(I.LAW_LINEAR, 1.0, 0.3), prepare=False)
+    # a 1-cell-wide chain has a singular least-squares tensor; the multigrid set-up only
+    # needs J~, so use a 2-D slab instead
+    m2 = I.hex_box(6, 2, 1, (6.0, 2.0, 1.0), dim=2)
+    for p in m2.patches:
+        if p.name in ("ymin", "ymax"):
+            p.bc = I.BC_TRAC
+    m2.patch("xmin").bc = I.BC_DISP
+    o = O.Oracle(m2, I.Material(I.LAW_LINEAR, 1.0, 0.3))
+    o.mg_setup(theta=0.25, coarse_max=1)
+    agg = o.mg_aggregates(0)
+    # every row is assigned, aggregates are numbered 0..k-1
+    assert agg.min() == 0 and set(agg) == set(range(agg.max() + 1))
+    # cells (i, j) -> i + 6 j; row 0 takes its strong neighbours 1 and 6
+    assert agg[0] == agg[1] == agg[6]
+
+
+def test_multigrid_vcycle_is_symmetric_and_contracts():
+    c = I.case_cantilever(12, 4, 4, (1.0, 0.33, 0.33), perturb=0.15, seed=9)
+    o = O.Oracle.from_case(c)
+    L = o.mg_setup(coarse_max=20)
+    assert L >= 2
+    n = c.mesh.n_cells
+    a, b = I.random_field(1, n), I.random_field(2, n)
+    za, zb = o.mg_vcycle(a), o.mg_vcycle(b)
+    assert abs(np.vdot(za, b) - np.vdot(a, zb)) < 1e-10 * abs(np.vdot(za, b))
+    # as a preconditioner it beats Jacobi on GMRES iterations
+    u = np.zeros((n, 3))
+    rhs = I.random_field(3, n, 1.0)
+    _, _, its_bj, _ = o.gmres(u, rhs, eta=1e-6, pc=O.PC_BJACOBI)
+    _, _, its_mg, _ = o.gmres(u, rhs, eta=1e-6, pc=O.PC_MG)
+    assert its_mg < its_bj
