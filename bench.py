@@ -1,0 +1,303 @@
+"""Benchmark of the GB300 JFNK hot path.
+
+A step is one complete JFNK solve (residual, Jv, preconditioner, GMRES, Newton with line
+search) of the 3-D linear-elastic cantilever with 80,000 perturbed hex cells (200x20x20,
+1 x 0.1 x 0.1 m, interior nodes +-15% of the cell size, x-min clamped, 1 MPa shear traction
+on x-max; FP64 residual / Jv / Arnoldi / Newton update, FP32 multigrid V-cycle and FP32
+Krylov basis), from u = 0 to |R| <= 1e-8 |R(0)|.  The metric is Jv cell-updates per second
+of whole-solve time: cells x (Jv evaluations in the solve) / solve time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU): independent replicas of the same solve per rank (the
+method is not sharded; no collective on the data path); value = all ranks' cell-updates /
+the slowest rank's time.  `--impl reference` times the FP64 CPU oracle (the baseline of this
+project) on the host cores on a bounded sample of the same solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jv cell-updates/s"
+UNIT = "cell-updates/s"
+HBM_PEAK_FALLBACK = 6800.0
+# FP64 ALU roof: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": HBM_PEAK_FALLBACK}, "fallback"
+
+
+def workload_case():
+    from paper_2502_17217_gb300 import inputs as I
+    return I.case_cantilever(200, 20, 20, (1.0, 0.1, 0.1), perturb=0.15, seed=2)
+
+
+WORKLOAD = {"workload": "cantilever_200x20x20_perturbed15", "cells": 80000, "dofs": 240000,
+            "law": "linear elastic (E=200 GPa, nu=0.3)", "pc": "multigrid V-cycle (FP32)",
+            "krylov": "GMRES(30), FP32 basis, FP64 Arnoldi arithmetic", "tolerance": "|R|/|R0| < 1e-8",
+            "eta": 1e-3, "jv_eps": "1e-7 (1+|u|)/|v|"}
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                             parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 200.0] or rows
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in load:
+            for nm, val in zip(names, r[3:]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load),
+                "power_w_max": max(r[2] for r in rows)}
+
+
+# flops (FMA = 2) and algorithmic bytes per launch of the residual passes, from the mesh
+def kernel_costs(case):
+    m = case.mesh
+    nc, ni = m.n_cells, m.n_internal
+    nd = sum(p.size for p in m.patches if p.bc == 0)
+    slots = 2 * ni  # internal face sides
+    flux_flops = ni * 77 + nd * 53
+    grad_flops = slots * 21
+    # algorithmic bytes: each input read once, each output written once
+    flux_bytes = (ni + nd) * (11 * 8 + 4) + ni * 4 + 2 * 9 * 8 * nc + 2 * 3 * 8 * nc + (ni + nd) * 3 * 8
+    grad_bytes = slots * (4 + 3 * 8) + nc * 3 * 8 + nc * 9 * 8
+    finish_bytes = (ni + nd) * 3 * 8 + ni * 4 + nc * (3 * 8 + 3 * 8 + 3 * 8 + 4 * 4)
+    finish_flops = (2 * ni + nd) * 3 + nc * 9
+    return {"flux": (flux_flops, flux_bytes), "grad": (grad_flops, grad_bytes), "finish": (finish_flops, finish_bytes)}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2502_17217_gb300 import jfnk
+    import __graft_entry__ as g
+    g.build()
+    dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
+    torch.cuda.set_device(dev)
+    case = workload_case()
+    nc = case.mesh.n_cells
+    s = jfnk.Solver.from_case(case, device=dev.index, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED,
+                              newton_rtol=1e-8, gmres_restart=30, gmres_eta=1e-3)
+    s.setup()
+    u0 = torch.zeros((nc, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        u, st, rc = s.solve(u0)
+        if rc != 0:
+            raise RuntimeError(f"solve failed: status {rc}, rel res {st.final_rel_res:.3e}")
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = s.launch_count()
+    s.profile(True)
+    s.profile_reset()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    jv_total = 0
+    stats = []
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev[k][0].record()
+            st = step()
+            ev[k][1].record()
+            torch.cuda.synchronize()
+            jv_total += st.gmres_its
+            stats.append(st)
+    s.profile(False)
+    launches = s.launch_count() - launches0
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+        j = torch.tensor([jv_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(j)
+        jv_total = float(j.item())
+    value = nc * jv_total / (t_ms / 1e3)
+    # per-kernel times (events on the launch stream, inside the timed region)
+    kt = {}
+    for name in ("grad", "flux", "finish", "mdot", "update", "pc_mg"):
+        ms, n = s.profile_get(name)
+        kt[name] = {"ms": ms, "launches": n}
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    u_host = np.zeros((nc, 3))
+    s.solve(u_host)
+    t0 = time.perf_counter()
+    jv_e2e = 0
+    for _ in range(args.steps):
+        u, st, rc = s.solve(u_host)
+        jv_e2e += st.gmres_its
+    e2e_s = time.perf_counter() - t0
+    e2e_value = nc * jv_e2e / e2e_s * world
+    return {"value": value, "t_ms": t_ms, "stats": stats, "kernels": kt, "launches": launches, "clocks": clk.summary(),
+            "e2e": e2e_value, "case": case, "solver": s}
+
+
+def run_oracle_sample(case, seconds=10.0):
+    """The FP64 oracle on the host cores: GMRES(30) cycles of the first Newton iteration of the
+    same solve (block-Jacobi; the oracle's V-cycle is plain C too), bounded to ~`seconds`."""
+    import oracle as O
+    o = O.Oracle.from_case(case)
+    nc = case.mesh.n_cells
+    u = np.zeros((nc, 3))
+    R = o.residual(u)
+    its_total, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        _, _, its, _ = o.gmres(u, -R, m=30, eta=1e-3, max_restarts=1, pc=O.PC_BJACOBI, R_u=R)
+        its_total += its
+    dt = time.perf_counter() - t0
+    return nc * its_total / dt, its_total, dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        case = workload_case()
+        t_steps = []
+        vals = []
+        for _ in range(args.warmup):
+            run_oracle_sample(case, 1.0)
+        for _ in range(args.steps):
+            v, its, dt = run_oracle_sample(case, 3.0)
+            vals.append(v)
+            t_steps.append(dt)
+        value = float(np.mean(vals))
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(t_steps)),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": dict(WORKLOAD, sample="GMRES(30) cycles of the first Newton iteration, block-Jacobi, ~3 s per step"),
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": "~3 s of oracle GMRES(30) cycles per step on the same 80k-cell problem"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    case = r["case"]
+    nc = case.mesh.n_cells
+    peaks, src = measured_peaks()
+    costs = kernel_costs(case)
+    # dominant kernel by total time
+    top = max(("grad", "flux", "finish"), key=lambda k: r["kernels"][k]["ms"])
+    kt = r["kernels"][top]
+    avg_s = kt["ms"] / max(1, kt["launches"]) / 1e3
+    flops, nbytes = costs[top]
+    achieved = flops / avg_s / 1e12
+    roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "FP64 ALU: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe nominal 1.25 TFLOP/s)",
+            "hbm_achieved_gbs": nbytes / avg_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+            "hbm_frac": nbytes / avg_s / 1e9 / peaks.get("hbm_gbs", HBM_PEAK_FALLBACK), "hbm_peak_source": src,
+            "avg_launch_us": avg_s * 1e6}
+    st = r["stats"]
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["t_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism=f"replicas{world}", l2="flushed (256 MB write) before every step"),
+            "solve_time_s": r["t_ms"] / args.steps / 1e3,
+            "newton_its": st[-1].newton_its, "gmres_its": st[-1].gmres_its, "final_rel_res": st[-1].final_rel_res,
+            "roofline": roof,
+            "kernels": r["kernels"],
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": 24 * nc, "d2h_bytes_per_step": 24 * nc}}
+    if not args.no_cpu_baseline:
+        v, its, dt = run_oracle_sample(case, 12.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{its} oracle GMRES iterations (Jv + block-Jacobi + CGS2) of the first Newton step, {dt:.1f} s"}
+    print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * jfnk_gb300.h -- C ABI of the GB300 (sm_103a) Jacobian-free Newton-Krylov solver for
+ * cell-centred finite-volume solid mechanics (Cardiff, Armfield, Tukovic, Batistic, 2025).
+ *
+ * The library evaluates, on one GPU, the matrix-free momentum residual R(u) of Sec. 2.3
+ * (least-squares cell gradients, face tractions from the mechanical law, Rhie-Chow
+ * stabilisation, face-to-cell summation), the finite-difference Jacobian action of Eq. JF,
+ * the compact-stencil preconditioner of Sec. 3.1-3.2 (block-Jacobi or an aggregation
+ * multigrid V-cycle on J~), restarted right-preconditioned GMRES(m) and the Newton loop
+ * with line search and load stepping of Sec. 3.2-3.3.
+ *
+ * Conventions shared by every call
+ *  - Status: every function returns JFNK_OK (0) or a negative JFNK_E* / JFNK_* code.  No
+ *    call aborts, traps or exits; jfnk_last_error() gives a message owned by the context.
+ *  - Vectors (u, R, v, Jv, z) are blocked per cell as in Sec. 2.2: double [n_cells][3] in
+ *    the caller's cell numbering.  In 2-D (plane strain, one-cell-thick mesh) the z entry
+ *    is ignored on input and returned as zero.
+ *  - mem = JFNK_MEM_HOST: host pointers, copied in and out; the call returns when the result
+ *    is in the caller's buffer.  mem = JFNK_MEM_DEVICE: device pointers of the context's
+ *    device, borrowed for the duration of the work enqueued on `stream` (a cudaStream_t;
+ *    NULL means the context's own stream); the call returns once the work is enqueued and
+ *    the caller synchronises the stream before reading the result.
+ *  - One context is not thread-safe: calls on a context must not overlap in time (they
+ *    share device scratch buffers).  Distinct contexts are independent.
+ *  - Host arrays passed to set-up calls are caller-owned and copied; they may be freed on
+ *    return.  The context owns every device allocation it makes.
+ */
+#ifndef JFNK_GB300_H
+#define JFNK_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define JFNK_OK 0
+#define JFNK_EINVAL (-1)      /* invalid argument or mesh                                  */
+#define JFNK_ENOMEM (-2)      /* device or host allocation failed                          */
+#define JFNK_ECUDA (-3)       /* a CUDA runtime call failed                                */
+#define JFNK_ESTATE (-4)      /* call out of order (e.g. no mesh or material yet)          */
+#define JFNK_DIVERGED (-5)    /* NaN/Inf residual                                          */
+#define JFNK_MAXIT (-6)       /* Newton did not reach the tolerance in max iterations       */
+#define JFNK_LS_FAILED (-7)   /* the line search found no decrease                         */
+#define JFNK_GMRES_STAGNATED (-8) /* GMRES ran out of restarts (solution still returned)   */
+
+/* ---- enumerations ---------------------------------------------------------------------- */
+enum { JFNK_BC_DISP = 0, JFNK_BC_TRAC = 1, JFNK_BC_SYMM = 2, JFNK_BC_EMPTY = 3 };
+enum { JFNK_LAW_LINEAR = 0, JFNK_LAW_NEOHOOKEAN = 1 };
+enum { JFNK_PC_NONE = 0, JFNK_PC_BJACOBI = 1, JFNK_PC_MG = 2 };
+enum { JFNK_MEM_HOST = 0, JFNK_MEM_DEVICE = 1 };
+/* FP64: everything in double.  MIXED: preconditioner (matrix, smoother, V-cycle) and the
+ * Krylov basis in float; residual, the eps-difference of Jv, Arnoldi arithmetic, the
+ * Hessenberg/Givens data and the Newton update stay in double. */
+enum { JFNK_PREC_FP64 = 0, JFNK_PREC_MIXED = 1 };
+
+typedef struct jfnk_options {
+    int device;             /* CUDA device ordinal                                    (0)   */
+    int gmres_restart;      /* m of GMRES(m), 1..64 (Sec. 4.2 uses 30)                (30)  */
+    double gmres_eta;       /* inner tolerance: |r| <= eta |R(u)| (Sec. 3.2: 1e-3)    (1e-3)*/
+    int gmres_max_restarts; /* restarts per Newton iteration                           (100) */
+    double newton_rtol;     /* |R| <= rtol |R(u0)| per load step (Sec. 3.3)           (1e-8)*/
+    double newton_atol;     /* |R| <= atol (Sec. 3.3: 1e-50)                          (1e-50)*/
+    int newton_max_its;     /* Newton iterations per load step                         (50)  */
+    int line_search_max;    /* halvings of s in the backtracking line search           (10)  */
+    double alpha_residual;  /* Rhie-Chow alpha in R(u) (Eq. RhieChow)                  (1)   */
+    double alpha_pc;        /* alpha in the approximate Jacobian J~ (Sec. 3.1)         (1)   */
+    double jv_eps_scale;    /* eps = jv_eps_scale (1 + |u|) / |v| (Eq. JF)             (1e-7)*/
+    int pc;                 /* JFNK_PC_*                                         (BJACOBI)   */
+    int precision;          /* JFNK_PREC_*                                          (FP64)   */
+    int reorth;             /* 0: classical Gram-Schmidt twice when the norm drops by more
+                               than 1/sqrt(2) (selective); 1: always twice            (0)   */
+    int renumber;           /* 1: reverse Cuthill-McKee cell renumbering               (1)   */
+    int mg_max_levels;      /* multigrid levels (Sec. 4.2: up to 25)                   (25)  */
+    int mg_coarse_max;      /* rows of the coarsest (dense Cholesky) level             (2000)*/
+    double mg_theta;        /* strength threshold of the aggregation                   (0.25)*/
+    int mg_smooth_sweeps;   /* Jacobi sweeps before and after the coarse correction    (1)   */
+} jfnk_options;
+
+typedef struct jfnk_stats {
+    int newton_its;          /* Newton iterations over all load steps                       */
+    int gmres_its;           /* Arnoldi iterations over the whole solve                     */
+    int residual_evals;      /* R evaluations (Jv and line-search included)                 */
+    int load_steps_done;     /* load steps completed                                        */
+    int status;              /* JFNK_OK or the failure code                                 */
+    double final_rel_res;    /* |R| / |R(u0)| at the end of the last load step              */
+    double final_abs_res;    /* |R| at the end                                              */
+    double solve_ms;         /* wall time of the solve on the host clock                    */
+    double hist[64];         /* |R| after each Newton iteration (first 64)                  */
+    int n_hist;
+} jfnk_stats;
+
+typedef struct jfnk_ctx jfnk_ctx;
+
+/* ---- life cycle ------------------------------------------------------------------------ */
+/* Fills *opt with the defaults listed above. */
+void jfnk_default_options(jfnk_options* opt);
+/* Creates a context on opt->device (opt NULL = defaults).  *out is NULL on failure. */
+int jfnk_create(jfnk_ctx** out, const jfnk_options* opt);
+/* Frees every device and host resource of the context; NULL is accepted. */
+int jfnk_destroy(jfnk_ctx* ctx);
+/* Message of the last failure on this context (never NULL; owned by the context). */
+const char* jfnk_last_error(const jfnk_ctx* ctx);
+/* Replaces the options (takes effect at the next set-up or solve). */
+int jfnk_set_options(jfnk_ctx* ctx, const jfnk_options* opt);
+
+/* ---- problem definition (Sec. 2.3: face-addressed polyhedral mesh, three BC types) ----- */
+/* dim: 2 (plane strain, one-cell-thick mesh whose front/back faces form EMPTY patches) or 3.
+ * points [n_points][3]; faces as CSR face_ptr [n_faces+1] / face_pts; the right-hand normal
+ * of each face's point loop points out of its owner.  Internal faces (0..n_internal-1) have a
+ * neighbour; faces n_internal..n_faces-1 are boundary faces.  Every boundary face defaults to
+ * traction-free until jfnk_set_patch() says otherwise.  Errors: JFNK_EINVAL for out-of-range
+ * indices, an owner equal to its neighbour, non-positive cell volumes or a singular
+ * least-squares tensor (a cell without neighbours spanning dim directions). */
+int jfnk_set_mesh(jfnk_ctx* ctx, int dim, int32_t n_points, const double* points, int32_t n_faces,
+                  const int32_t* face_ptr, const int32_t* face_pts, const int32_t* owner,
+                  int32_t n_internal, const int32_t* neighbour, int32_t n_cells);
+/* Boundary faces [first_face, first_face + n_faces) get bc_type.  values [n_faces][3]:
+ * prescribed displacement (DISP) or traction per unit (reference) area (TRAC); NULL = zero.
+ * EMPTY faces are the front/back planes of 2-D meshes.  SYMM returns JFNK_EINVAL (not yet
+ * supported). */
+int jfnk_set_patch(jfnk_ctx* ctx, int32_t first_face, int32_t n_faces, int bc_type, const double* values);
+/* App. B.  LINEAR (small strain, Eq. momentum_lingeom): p1 = E, p2 = nu.
+ * NEOHOOKEAN (total Lagrangian, Eq. momentum_TL): p1 = mu, p2 = kappa.  Kbar = 4/3 mu + kappa. */
+int jfnk_set_material(jfnk_ctx* ctx, int law, double p1, double p2);
+/* Body force per unit volume [n_cells][3] (host, copied), NULL = none (Eq. volume_integral). */
+int jfnk_set_body_force(jfnk_ctx* ctx, const double* fb);
+/* Load factor lambda multiplying prescribed displacements, tractions and body forces. */
+int jfnk_set_load_factor(jfnk_ctx* ctx, double lambda);
+/* Builds everything the hot path needs (renumbering, geometry, coefficients, preconditioner).
+ * Called implicitly by the calls below when the problem changed. */
+int jfnk_setup(jfnk_ctx* ctx);
+
+/* ---- hot path -------------------------------------------------------------------------- */
+/* R(u), Eq. residual (static), with the paper's sign (surface forces + body force). */
+int jfnk_residual(jfnk_ctx* ctx, const double* u, double* R, int mem, void* stream);
+/* Jv ~ (R(u + eps v) - R(u)) / eps, eps = jv_eps_scale (1 + |u|_2) / |v|_2; Jv = 0 for v = 0
+ * (Eq. JF).  Evaluates R(u) too. */
+int jfnk_jv(jfnk_ctx* ctx, const double* u, const double* v, double* Jv, int mem, void* stream);
+/* z ~ P^-1 v with P = J~ (Sec. 3.2): JFNK_PC_BJACOBI (diagonal blocks of J~), JFNK_PC_MG
+ * (one V-cycle), JFNK_PC_NONE (copy).  Precision follows opt.precision. */
+int jfnk_precondition(jfnk_ctx* ctx, const double* v, double* z, int pc, int mem, void* stream);
+/* Newton solve (Sec. 3.2-3.3): u holds the initial guess on entry and the solution on exit;
+ * n_load_steps >= 1 ramps the load factor k / n_load_steps.  Returns JFNK_OK when every load
+ * step met |R| <= max(atol, rtol |R(u0)|), else the failure code (u holds the last iterate).
+ * The call synchronises the stream before returning. */
+int jfnk_solve(jfnk_ctx* ctx, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream);
+
+/* ---- inspection ------------------------------------------------------------------------ */
+/* Geometry in the caller's numbering (host arrays, any may be NULL): face area vectors
+ * Sf [n_faces][3] and centroids Cf [n_faces][3] (orientation of the input mesh), cell
+ * volumes V [n_cells] and centroids C [n_cells][3]. */
+int jfnk_get_geometry(jfnk_ctx* ctx, double* Sf, double* Cf, double* V, double* C);
+/* Cell gradient (grad u)_P [n_cells][3][3], entry (i, j) = d u_j / d x_i, of the last R
+ * evaluated (host array). */
+int jfnk_get_gradient(jfnk_ctx* ctx, double* grad);
+/* Internal cell order: new_to_old[n_cells] (host array). */
+int jfnk_get_permutation(jfnk_ctx* ctx, int32_t* new_to_old);
+/* Kernel timing: when enabled, CUDA events bracket every launch of the named kernels. */
+int jfnk_profile_enable(jfnk_ctx* ctx, int enable);
+/* Accumulated time (ms) and launch count of kernel `name` since the last reset; returns
+ * JFNK_EINVAL for unknown names.  Synchronises the context's last stream. */
+int jfnk_profile_get(jfnk_ctx* ctx, const char* name, double* total_ms, int64_t* launches);
+int jfnk_profile_reset(jfnk_ctx* ctx);
+/* Number of kernel launches made by the context since creation (every stream). */
+int64_t jfnk_launch_count(const jfnk_ctx* ctx);
+/* Device bytes held by the context. */
+int64_t jfnk_device_bytes(const jfnk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

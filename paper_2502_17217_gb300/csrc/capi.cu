@@ -1,0 +1,530 @@
+// The C ABI (include/jfnk_gb300.h): context life cycle, problem definition, hot-path calls,
+// inspection and kernel timing.  Argument marshalling and validation only; every step of
+// the method runs in the device kernels of the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "jfnk_internal.h"
+
+// ------------------------------------------------------------------ helpers
+int jfnk_fail(jfnk_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int jfnk_cuda_fail(jfnk_ctx* c, cudaError_t e, const char* what)
+{
+    std::string m = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return jfnk_fail(c, JFNK_ECUDA, m);
+}
+
+void* jfnk_dalloc(jfnk_ctx* c, size_t bytes)
+{
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemset(p, 0, bytes);
+    c->allocs.push_back(p);
+    c->dev_bytes += (int64_t)bytes;
+    return p;
+}
+
+int jfnk::Profiler::slot(const char* name)
+{
+    for (size_t i = 0; i < slots.size(); i++)
+        if (slots[i].name == name) return (int)i;
+    slots.push_back(Slot());
+    slots.back().name = name;
+    return (int)slots.size() - 1;
+}
+
+void jfnk_prof_begin(jfnk_ctx* c, int slot)
+{
+    if (slot < 0 || !c->prof.enabled) return;
+    auto& s = c->prof.slots[slot];
+    if (s.used + 2 > s.ev.size()) {
+        for (int q = 0; q < 64; q++) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            s.ev.push_back(e);
+        }
+    }
+    cudaEventRecord(s.ev[s.used], c->cur);
+}
+
+void jfnk_prof_end(jfnk_ctx* c, int slot)
+{
+    if (slot < 0 || !c->prof.enabled) return;
+    auto& s = c->prof.slots[slot];
+    cudaEventRecord(s.ev[s.used + 1], c->cur);
+    s.used += 2;
+    s.launches++;
+    if (s.used + 2 > 4096) {
+        // fold completed pairs into the running total to bound the event pool
+        cudaEventSynchronize(s.ev[s.used - 1]);
+        for (size_t q = 0; q < s.used; q += 2) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, s.ev[q], s.ev[q + 1]);
+            s.ms += ms;
+        }
+        s.used = 0;
+    }
+}
+
+static void free_device(jfnk_ctx* c)
+{
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    jfnk::mg_release(c);
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    c->dev_bytes = 0;
+    c->dm = jfnk::DevMesh();
+    c->u = c->Ru = c->w = c->R = c->z = c->x = c->bvec = c->wk = c->tmp = c->ext = nullptr;
+    c->G = c->T = c->F = c->partials = c->V = nullptr;
+    c->gd = nullptr;
+    c->scal = nullptr;
+    c->tickets = nullptr;
+    c->mg_ready = false;
+}
+
+static bool valid_options(const jfnk_options* o, std::string& why)
+{
+    if (o->gmres_restart < 1 || o->gmres_restart > jfnk::kMaxRestart) { why = "gmres_restart must be in [1, 64]"; return false; }
+    if (!(o->gmres_eta > 0 && o->gmres_eta < 1)) { why = "gmres_eta must be in (0, 1)"; return false; }
+    if (o->gmres_max_restarts < 1) { why = "gmres_max_restarts must be >= 1"; return false; }
+    if (!(o->newton_rtol >= 0) || !(o->newton_atol >= 0)) { why = "tolerances must be >= 0"; return false; }
+    if (o->pc < JFNK_PC_NONE || o->pc > JFNK_PC_MG) { why = "unknown preconditioner"; return false; }
+    if (o->precision != JFNK_PREC_FP64 && o->precision != JFNK_PREC_MIXED) { why = "unknown precision"; return false; }
+    if (!(o->jv_eps_scale > 0)) { why = "jv_eps_scale must be > 0"; return false; }
+    if (o->mg_coarse_max < 1 || o->mg_coarse_max > 8192) { why = "mg_coarse_max must be in [1, 8192]"; return false; }
+    return true;
+}
+
+extern "C" {
+
+void jfnk_default_options(jfnk_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->device = 0;
+    o->gmres_restart = 30;
+    o->gmres_eta = 1e-3;
+    o->gmres_max_restarts = 100;
+    o->newton_rtol = 1e-8;
+    o->newton_atol = 1e-50;
+    o->newton_max_its = 50;
+    o->line_search_max = 10;
+    o->alpha_residual = 1.0;
+    o->alpha_pc = 1.0;
+    o->jv_eps_scale = 1e-7;
+    o->pc = JFNK_PC_BJACOBI;
+    o->precision = JFNK_PREC_FP64;
+    o->reorth = 0;
+    o->renumber = 1;
+    o->mg_max_levels = 25;
+    o->mg_coarse_max = 1000;
+    o->mg_theta = 0.25;
+    o->mg_smooth_sweeps = 1;
+}
+
+int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
+{
+    if (!out) return JFNK_EINVAL;
+    *out = nullptr;
+    jfnk_ctx* c = new (std::nothrow) jfnk_ctx();
+    if (!c) return JFNK_ENOMEM;
+    if (opt) c->opt = *opt;
+    else jfnk_default_options(&c->opt);
+    std::string why;
+    if (!valid_options(&c->opt, why)) {
+        delete c;
+        return JFNK_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c->opt.device < 0 || c->opt.device >= ndev) {
+        cudaGetLastError();
+        delete c;
+        return JFNK_ECUDA;
+    }
+    if (cudaSetDevice(c->opt.device) != cudaSuccess || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return JFNK_ECUDA;
+    }
+    if (cudaMallocHost(&c->gh, sizeof(jfnk::GmresDev)) != cudaSuccess || cudaMallocHost(&c->scal_h, 16 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(c->stream);
+        delete c;
+        return JFNK_ENOMEM;
+    }
+    c->cur = c->stream;
+    *out = c;
+    return JFNK_OK;
+}
+
+int jfnk_destroy(jfnk_ctx* c)
+{
+    if (!c) return JFNK_OK;
+    cudaSetDevice(c->opt.device);
+    free_device(c);
+    for (auto& s : c->prof.slots)
+        for (auto e : s.ev) cudaEventDestroy(e);
+    if (c->gh) cudaFreeHost(c->gh);
+    if (c->scal_h) cudaFreeHost(c->scal_h);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return JFNK_OK;
+}
+
+const char* jfnk_last_error(const jfnk_ctx* c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+int jfnk_set_options(jfnk_ctx* c, const jfnk_options* opt)
+{
+    if (!c || !opt) return JFNK_EINVAL;
+    std::string why;
+    if (!valid_options(opt, why)) return jfnk_fail(c, JFNK_EINVAL, why);
+    if (opt->device != c->opt.device) return jfnk_fail(c, JFNK_EINVAL, "the device of a context cannot change");
+    c->opt = *opt;
+    c->dirty = true;
+    return JFNK_OK;
+}
+
+int jfnk_set_mesh(jfnk_ctx* c, int dim, int32_t n_points, const double* points, int32_t n_faces, const int32_t* face_ptr,
+                  const int32_t* face_pts, const int32_t* owner, int32_t n_internal, const int32_t* neighbour, int32_t n_cells)
+{
+    if (!c) return JFNK_EINVAL;
+    if ((dim != 2 && dim != 3) || n_points <= 0 || n_faces <= 0 || n_cells <= 0 || n_internal < 0 || n_internal > n_faces ||
+        !points || !face_ptr || !face_pts || !owner || (n_internal > 0 && !neighbour))
+        return jfnk_fail(c, JFNK_EINVAL, "jfnk_set_mesh: invalid sizes or null arrays");
+    if (face_ptr[0] != 0) return jfnk_fail(c, JFNK_EINVAL, "face_ptr[0] must be 0");
+    for (int32_t f = 0; f < n_faces; f++) {
+        if (face_ptr[f + 1] - face_ptr[f] < 3) return jfnk_fail(c, JFNK_EINVAL, "every face needs >= 3 points");
+        if (owner[f] < 0 || owner[f] >= n_cells) return jfnk_fail(c, JFNK_EINVAL, "owner index out of range");
+        if (f < n_internal && (neighbour[f] < 0 || neighbour[f] >= n_cells || neighbour[f] == owner[f]))
+            return jfnk_fail(c, JFNK_EINVAL, "neighbour index out of range or equal to the owner");
+    }
+    for (int64_t q = 0; q < face_ptr[n_faces]; q++)
+        if (face_pts[q] < 0 || face_pts[q] >= n_points) return jfnk_fail(c, JFNK_EINVAL, "face point index out of range");
+    jfnk::HostMesh& h = c->hm;
+    h.dim = dim; h.np = n_points; h.nf = n_faces; h.ni = n_internal; h.nc = n_cells;
+    h.pts.assign(points, points + 3 * (size_t)n_points);
+    h.fptr.assign(face_ptr, face_ptr + n_faces + 1);
+    h.fpts.assign(face_pts, face_pts + face_ptr[n_faces]);
+    h.own.assign(owner, owner + n_faces);
+    h.nei.assign(neighbour, neighbour + n_internal);
+    h.btype.assign(n_faces - n_internal, JFNK_BC_TRAC);
+    h.bval.assign((size_t)(n_faces - n_internal) * 3, 0.0);
+    c->fb_host.clear();
+    c->have_mesh = true;
+    c->dirty = true;
+    return JFNK_OK;
+}
+
+int jfnk_set_patch(jfnk_ctx* c, int32_t first_face, int32_t n_faces, int bc_type, const double* values)
+{
+    if (!c) return JFNK_EINVAL;
+    if (!c->have_mesh) return jfnk_fail(c, JFNK_ESTATE, "jfnk_set_patch before jfnk_set_mesh");
+    if (first_face < c->hm.ni || n_faces < 0 || first_face + n_faces > c->hm.nf)
+        return jfnk_fail(c, JFNK_EINVAL, "patch faces must be boundary faces");
+    if (bc_type == JFNK_BC_SYMM) return jfnk_fail(c, JFNK_EINVAL, "symmetry boundaries are not supported yet");
+    if (bc_type != JFNK_BC_DISP && bc_type != JFNK_BC_TRAC && bc_type != JFNK_BC_EMPTY)
+        return jfnk_fail(c, JFNK_EINVAL, "unknown boundary condition type");
+    for (int32_t k = 0; k < n_faces; k++) {
+        const int b = first_face - c->hm.ni + k;
+        c->hm.btype[b] = bc_type;
+        for (int q = 0; q < 3; q++) c->hm.bval[(size_t)b * 3 + q] = values ? values[(size_t)k * 3 + q] : 0.0;
+    }
+    c->dirty = true;
+    return JFNK_OK;
+}
+
+int jfnk_set_material(jfnk_ctx* c, int law, double p1, double p2)
+{
+    if (!c) return JFNK_EINVAL;
+    if (law == JFNK_LAW_LINEAR) {
+        if (!(p1 > 0) || !(p2 > -1.0 && p2 < 0.5)) return jfnk_fail(c, JFNK_EINVAL, "linear law needs E > 0 and -1 < nu < 1/2");
+        c->mu = p1 / (2.0 * (1.0 + p2));
+        c->lam = p1 * p2 / ((1.0 + p2) * (1.0 - 2.0 * p2));
+        c->kappa = c->lam + 2.0 * c->mu / 3.0;
+    } else if (law == JFNK_LAW_NEOHOOKEAN) {
+        if (!(p1 > 0) || !(p2 > 0)) return jfnk_fail(c, JFNK_EINVAL, "neo-Hookean law needs mu > 0 and kappa > 0");
+        c->mu = p1;
+        c->kappa = p2;
+        c->lam = p2 - 2.0 * p1 / 3.0;
+    } else {
+        return jfnk_fail(c, JFNK_EINVAL, "unknown material law");
+    }
+    c->law = law;
+    c->p1 = p1;
+    c->p2 = p2;
+    c->Kbar = 4.0 * c->mu / 3.0 + c->kappa;
+    c->have_material = true;
+    c->dirty = true;
+    return JFNK_OK;
+}
+
+int jfnk_set_body_force(jfnk_ctx* c, const double* fb)
+{
+    if (!c) return JFNK_EINVAL;
+    if (!c->have_mesh) return jfnk_fail(c, JFNK_ESTATE, "jfnk_set_body_force before jfnk_set_mesh");
+    if (fb) c->fb_host.assign(fb, fb + 3 * (size_t)c->hm.nc);
+    else c->fb_host.clear();
+    c->dirty = true;
+    return JFNK_OK;
+}
+
+int jfnk_set_load_factor(jfnk_ctx* c, double lambda)
+{
+    if (!c) return JFNK_EINVAL;
+    if (!std::isfinite(lambda)) return jfnk_fail(c, JFNK_EINVAL, "load factor must be finite");
+    c->load = lambda;
+    return JFNK_OK;
+}
+
+int jfnk_setup(jfnk_ctx* c)
+{
+    if (!c) return JFNK_EINVAL;
+    if (!c->have_mesh || !c->have_material) return jfnk_fail(c, JFNK_ESTATE, "mesh and material must be set before set-up");
+    if (cudaSetDevice(c->opt.device) != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    free_device(c);
+    c->cur = c->stream;
+    std::string e = jfnk::build_topology(c->hm, c->opt.renumber != 0, c->topo);
+    if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
+    int rc = jfnk::setup_device_mesh(c);
+    if (rc) return rc;
+    rc = jfnk::setup_material_coefficients(c);
+    if (rc) return rc;
+    const int nc = c->dm.nc;
+    const size_t v3 = 3 * (size_t)nc;
+    double** vecs[] = {&c->u, &c->Ru, &c->w, &c->R, &c->z, &c->x, &c->bvec, &c->wk, &c->tmp, &c->ext};
+    for (double** p : vecs) {
+        *p = (double*)jfnk_dalloc(c, sizeof(double) * v3);
+        if (!*p) return jfnk_fail(c, JFNK_ENOMEM, "device allocation of work vectors failed");
+    }
+    c->G = (double*)jfnk_dalloc(c, sizeof(double) * 9 * (size_t)nc);
+    c->T = (double*)jfnk_dalloc(c, sizeof(double) * (c->law == JFNK_LAW_NEOHOOKEAN ? 9 * (size_t)nc : 1));
+    c->F = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)std::max(1, c->dm.nflux));
+    c->partials = (double*)jfnk_dalloc(c, sizeof(double) * (size_t)jfnk::kRedBlocks * 2 * (jfnk::kMaxRestart + 2));
+    c->V_is_float = c->opt.precision == JFNK_PREC_MIXED;
+    c->V_ld = (v3 + 63) / 64 * 64;
+    const size_t vbytes = (c->V_is_float ? sizeof(float) : sizeof(double)) * c->V_ld * (size_t)(c->opt.gmres_restart + 1);
+    c->V = (double*)jfnk_dalloc(c, vbytes);
+    c->gd = (jfnk::GmresDev*)jfnk_dalloc(c, sizeof(jfnk::GmresDev));
+    c->scal = (double*)jfnk_dalloc(c, 16 * sizeof(double));
+    c->tickets = (unsigned*)jfnk_dalloc(c, 16 * sizeof(unsigned));
+    if (!c->G || !c->T || !c->F || !c->partials || !c->V || !c->gd || !c->scal || !c->tickets)
+        return jfnk_fail(c, JFNK_ENOMEM, "device allocation of solver buffers failed");
+    rc = jfnk::pc_setup(c);
+    if (rc) return rc;
+    if (cudaDeviceSynchronize() != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "set-up");
+    c->dirty = false;
+    return JFNK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ hot-path helpers
+static int begin_call(jfnk_ctx* c, void* stream)
+{
+    if (!c) return JFNK_EINVAL;
+    if (c->dirty) {
+        int rc = jfnk_setup(c);
+        if (rc) return rc;
+    }
+    if (cudaSetDevice(c->opt.device) != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    c->cur = stream ? (cudaStream_t)stream : c->stream;
+    return JFNK_OK;
+}
+
+static int load_vec(jfnk_ctx* c, const double* src, int mem, double* dst_int)
+{
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->dm.nc;
+    if (mem == JFNK_MEM_HOST) {
+        JF_CUDA(c, cudaMemcpyAsync(c->ext, src, bytes, cudaMemcpyHostToDevice, c->cur));
+        return jfnk::perm_in(c, c->ext, dst_int);
+    }
+    return jfnk::perm_in(c, src, dst_int);
+}
+
+static int store_vec(jfnk_ctx* c, const double* src_int, int mem, double* dst)
+{
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->dm.nc;
+    if (mem == JFNK_MEM_HOST) {
+        int rc = jfnk::perm_out(c, src_int, c->ext);
+        if (rc) return rc;
+        JF_CUDA(c, cudaMemcpyAsync(dst, c->ext, bytes, cudaMemcpyDeviceToHost, c->cur));
+        JF_CUDA(c, cudaStreamSynchronize(c->cur));
+        return JFNK_OK;
+    }
+    return jfnk::perm_out(c, src_int, dst);
+}
+
+extern "C" {
+
+int jfnk_residual(jfnk_ctx* c, const double* u, double* R, int mem, void* stream)
+{
+    int rc = begin_call(c, stream);
+    if (rc) return rc;
+    if (!u || !R || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE)) return jfnk_fail(c, JFNK_EINVAL, "jfnk_residual: bad arguments");
+    if ((rc = load_vec(c, u, mem, c->u))) return rc;
+    if ((rc = jfnk::residual(c, c->u, c->R, jfnk::OUT_R, nullptr))) return rc;
+    return store_vec(c, c->R, mem, R);
+}
+
+int jfnk_jv(jfnk_ctx* c, const double* u, const double* v, double* Jv, int mem, void* stream)
+{
+    int rc = begin_call(c, stream);
+    if (rc) return rc;
+    if (!u || !v || !Jv || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE)) return jfnk_fail(c, JFNK_EINVAL, "jfnk_jv: bad arguments");
+    const size_t n = 3 * (size_t)c->dm.nc;
+    if ((rc = load_vec(c, u, mem, c->u))) return rc;
+    if ((rc = load_vec(c, v, mem, c->z))) return rc;
+    if ((rc = jfnk::residual(c, c->u, c->Ru, jfnk::OUT_R, nullptr))) return rc;
+    if ((rc = jfnk::norm_mode(c, c->u, n, 2, nullptr))) return rc;
+    if ((rc = jfnk::norm_mode(c, c->z, n, 1, nullptr))) return rc;
+    if ((rc = jfnk::perturb(c, c->u, c->z, c->w, nullptr))) return rc;
+    if ((rc = jfnk::residual(c, c->w, c->tmp, jfnk::OUT_JV, &c->gd->eps))) return rc;
+    return store_vec(c, c->tmp, mem, Jv);
+}
+
+int jfnk_precondition(jfnk_ctx* c, const double* v, double* z, int pc, int mem, void* stream)
+{
+    int rc = begin_call(c, stream);
+    if (rc) return rc;
+    if (!v || !z || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE) || pc < JFNK_PC_NONE || pc > JFNK_PC_MG)
+        return jfnk_fail(c, JFNK_EINVAL, "jfnk_precondition: bad arguments");
+    if ((rc = load_vec(c, v, mem, c->tmp))) return rc;
+    if ((rc = jfnk::pc_apply(c, pc, c->tmp, c->z))) return rc;
+    return store_vec(c, c->z, mem, z);
+}
+
+int jfnk_solve(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream)
+{
+    int rc = begin_call(c, stream);
+    if (rc) return rc;
+    if (!u || n_load_steps < 1 || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE))
+        return jfnk_fail(c, JFNK_EINVAL, "jfnk_solve: bad arguments");
+    jfnk_stats local;
+    jfnk_stats* st = stats ? stats : &local;
+    std::memset(st, 0, sizeof *st);
+    if ((rc = load_vec(c, u, mem, c->u))) return rc;
+    const double saved_load = c->load;
+    int status = jfnk::newton(c, n_load_steps, st);
+    c->load = saved_load;
+    if (status == JFNK_ECUDA || status == JFNK_ENOMEM) return status;
+    if ((rc = store_vec(c, c->u, mem, u))) return rc;
+    JF_CUDA(c, cudaStreamSynchronize(c->cur));
+    if (status != JFNK_OK) {
+        const char* why = status == JFNK_MAXIT ? "Newton reached the iteration limit"
+                        : status == JFNK_LS_FAILED ? "line search found no decrease"
+                        : status == JFNK_DIVERGED ? "non-finite residual" : "solve failed";
+        return jfnk_fail(c, status, why);
+    }
+    return JFNK_OK;
+}
+
+int jfnk_get_geometry(jfnk_ctx* c, double* Sf, double* Cf, double* V, double* C)
+{
+    int rc = begin_call(c, nullptr);
+    if (rc) return rc;
+    const auto& t = c->topo;
+    const int nf = t.nf, nc = t.nc;
+    std::vector<double> a((size_t)3 * nf), b((size_t)3 * nf), v(nc), cc((size_t)3 * nc);
+    JF_CUDA(c, cudaMemcpy(a.data(), c->dm.Sf, sizeof(double) * a.size(), cudaMemcpyDeviceToHost));
+    JF_CUDA(c, cudaMemcpy(b.data(), c->dm.Cf, sizeof(double) * b.size(), cudaMemcpyDeviceToHost));
+    JF_CUDA(c, cudaMemcpy(v.data(), c->dm.V, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+    JF_CUDA(c, cudaMemcpy(cc.data(), c->dm.C, sizeof(double) * cc.size(), cudaMemcpyDeviceToHost));
+    for (int f = 0; f < nf; f++) {
+        const int o = t.face_src[f];
+        const double sg = t.face_flip[f] ? -1.0 : 1.0;
+        for (int k = 0; k < 3; k++) {
+            if (Sf) Sf[(size_t)o * 3 + k] = sg * a[(size_t)k * nf + f];
+            if (Cf) Cf[(size_t)o * 3 + k] = b[(size_t)k * nf + f];
+        }
+    }
+    for (int P = 0; P < nc; P++) {
+        const int o = t.n2o[P];
+        if (V) V[o] = v[P];
+        for (int k = 0; k < 3; k++)
+            if (C) C[(size_t)o * 3 + k] = cc[(size_t)k * nc + P];
+    }
+    return JFNK_OK;
+}
+
+int jfnk_get_gradient(jfnk_ctx* c, double* grad)
+{
+    int rc = begin_call(c, nullptr);
+    if (rc) return rc;
+    if (!grad) return jfnk_fail(c, JFNK_EINVAL, "null gradient buffer");
+    const int nc = c->dm.nc;
+    std::vector<double> g((size_t)9 * nc);
+    JF_CUDA(c, cudaDeviceSynchronize());
+    JF_CUDA(c, cudaMemcpy(g.data(), c->G, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
+    for (int P = 0; P < nc; P++)
+        for (int q = 0; q < 9; q++) grad[(size_t)c->topo.n2o[P] * 9 + q] = g[(size_t)q * nc + P];
+    return JFNK_OK;
+}
+
+int jfnk_get_permutation(jfnk_ctx* c, int32_t* new_to_old)
+{
+    int rc = begin_call(c, nullptr);
+    if (rc) return rc;
+    if (!new_to_old) return jfnk_fail(c, JFNK_EINVAL, "null buffer");
+    std::copy(c->topo.n2o.begin(), c->topo.n2o.end(), new_to_old);
+    return JFNK_OK;
+}
+
+int jfnk_profile_enable(jfnk_ctx* c, int enable)
+{
+    if (!c) return JFNK_EINVAL;
+    c->prof.enabled = enable != 0;
+    return JFNK_OK;
+}
+
+int jfnk_profile_get(jfnk_ctx* c, const char* name, double* total_ms, int64_t* launches)
+{
+    if (!c || !name) return JFNK_EINVAL;
+    for (auto& s : c->prof.slots) {
+        if (s.name != name) continue;
+        if (s.used) {
+            cudaEventSynchronize(s.ev[s.used - 1]);
+            for (size_t q = 0; q < s.used; q += 2) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, s.ev[q], s.ev[q + 1]);
+                s.ms += ms;
+            }
+            s.used = 0;
+        }
+        if (total_ms) *total_ms = s.ms;
+        if (launches) *launches = s.launches;
+        return JFNK_OK;
+    }
+    return jfnk_fail(c, JFNK_EINVAL, std::string("no kernel timed under the name ") + name);
+}
+
+int jfnk_profile_reset(jfnk_ctx* c)
+{
+    if (!c) return JFNK_EINVAL;
+    for (auto& s : c->prof.slots) {
+        if (s.used) cudaEventSynchronize(s.ev[s.used - 1]);
+        s.used = 0;
+        s.ms = 0;
+        s.launches = 0;
+    }
+    return JFNK_OK;
+}
+
+int64_t jfnk_launch_count(const jfnk_ctx* c) { return c ? c->launches : 0; }
+
+int64_t jfnk_device_bytes(const jfnk_ctx* c) { return c ? c->dev_bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// Device helpers shared by the library's kernels: deterministic warp/block reductions and the
+// last-block grid finalisation (fixed summation order, so every result is bitwise
+// reproducible run to run).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace jfnk {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  `sh` holds >= blockDim.x/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = (lane < nw) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// After every block stored partials[b + k * gridDim.x] (k < nvals), the last block to arrive
+// returns true; it must then reduce the partials (read with __ldcg) and reset *ticket.
+__device__ __forceinline__ bool last_block(unsigned* ticket)
+{
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return is_last;
+}
+
+// Deterministic sum of partials[0..n) by one block (fixed order); result in thread 0.
+__device__ __forceinline__ double reduce_partials(const double* partials, int n, double* sh)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(partials + i);
+    return block_sum(s, sh);
+}
+
+}  // namespace jfnk

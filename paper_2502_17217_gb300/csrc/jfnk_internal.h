@@ -1,0 +1,223 @@
+// Internal definitions of the GB300 JFNK library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/jfnk_gb300.h"
+
+namespace jfnk {
+
+constexpr int kMaxRestart = 64;   // largest m of GMRES(m)
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs: fixed grid of every reduction (deterministic)
+constexpr int kRedThreads = 256;
+
+// ------------------------------------------------------------------ host copy of the input
+struct HostMesh {
+    int dim = 3;
+    int np = 0, nf = 0, ni = 0, nc = 0;
+    std::vector<double> pts;                 // [np][3]
+    std::vector<int32_t> fptr, fpts, own, nei;
+    std::vector<int32_t> btype;              // [nf - ni]
+    std::vector<double> bval;                // [nf - ni][3]
+};
+
+// ------------------------------------------------------------------ host-built topology
+// Internal (device) numbering: cells renumbered, faces reordered into
+//   [0, ni)                internal faces, sorted by (owner, neighbour), owner < neighbour
+//   [ni, ni + nd)          displacement faces, sorted by owner
+//   [ni + nd, ni + nd + nt) traction faces, sorted by owner
+//   [.., nf)               empty faces
+struct Topology {
+    int nc = 0, ni = 0, nd = 0, nt = 0, ne = 0, nf = 0;
+    std::vector<int32_t> n2o, o2n;           // cell permutation
+    std::vector<int32_t> face_src;           // new face -> input face
+    std::vector<uint8_t> face_flip;          // 1 if the point loop was reversed
+    std::vector<int32_t> fptr, fpts;         // reordered (and flipped) face point lists
+    std::vector<int32_t> own, nei;           // own [nf], nei [ni]
+    std::vector<int32_t> fo_ptr;             // [nc+1] internal faces owned by each cell
+    std::vector<int32_t> fn_ptr, fn_face;    // [nc+1], [ni] internal faces whose neighbour is the cell
+    std::vector<int32_t> fd_ptr;             // [nc+1] displacement faces (absolute indices)
+    std::vector<int32_t> ft_ptr;             // [nc+1] traction faces (absolute indices)
+    std::vector<int32_t> ca_ptr, ca_face;    // all faces of each cell; ~f marks the neighbour side
+    // sliced-ELL (32 cells per slice) list of the internal neighbours of each cell
+    std::vector<int32_t> sell_off, sell_w;   // per slice: first slot, width (slots per lane)
+    std::vector<int32_t> sell_nbr, sell_face;// per slot: neighbour cell (-1 = padding), face
+    int n_slots = 0;
+    std::vector<double> bval;                // [nd + nt][3] boundary values in new face order
+    int bandwidth = 0;
+};
+
+// Builds the topology; returns "" on success or an error message.
+std::string build_topology(const HostMesh& hm, bool rcm, Topology& t);
+
+// ------------------------------------------------------------------ multigrid hierarchy (host)
+struct MgLevelHost {
+    int n = 0;
+    std::vector<int32_t> rp, col;
+    std::vector<double> val;
+    std::vector<int32_t> agg;   // aggregate of each row (all but the coarsest level)
+};
+// Aggregation hierarchy on A = -J~ given in CSR; returns "" on success.
+std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels, int coarse_max,
+                               std::vector<MgLevelHost>& levels, std::vector<double>& chol);
+
+// ------------------------------------------------------------------ device state
+struct DevMesh {
+    int dim = 3, nc = 0, ni = 0, nd = 0, nt = 0, nf = 0, nflux = 0, n_slots = 0, n_slices = 0;
+    double* pts = nullptr;
+    int32_t *fptr = nullptr, *fpts = nullptr;
+    int32_t *own = nullptr, *nei = nullptr;
+    int32_t *fo_ptr = nullptr, *fn_ptr = nullptr, *fn_face = nullptr, *fd_ptr = nullptr, *ft_ptr = nullptr;
+    int32_t *ca_ptr = nullptr, *ca_face = nullptr;
+    int32_t *sell_off = nullptr, *sell_w = nullptr, *sell_nbr = nullptr, *sell_face = nullptr;
+    double* sell_l = nullptr;        // [3][n_slots] least-squares vectors
+    double *Sf = nullptr, *Cf = nullptr;   // [3][nf]
+    double *V = nullptr, *C = nullptr;     // [nc], [3][nc]
+    double* coef = nullptr;          // [11][nflux] face coefficients of the residual
+    double* bval = nullptr;          // [3][nd + nt] boundary values (unscaled)
+    double* b0 = nullptr;            // [3][nc] body force + traction (unscaled)
+    double* fb = nullptr;            // [3][nc] body force density
+    double* jt_c = nullptr;          // [nflux] J~ face coefficients (internal and displacement)
+    double* jt_diag = nullptr;       // [nc]
+    double* jt_dinv = nullptr;       // [nc] 1 / diag
+    float* jt_dinv_f = nullptr;      // [nc]
+    int32_t* n2o = nullptr;
+    int32_t* err = nullptr;          // set-up error word
+};
+
+// Scalars of the GMRES cycle, resident on the device.
+struct GmresDev {
+    int j;            // Arnoldi index of the iteration being built
+    int k;            // iterations completed in this cycle
+    int done;         // converged / breakdown: later kernels of the cycle return at once
+    int reorth;       // second Gram-Schmidt pass needed for this column
+    unsigned ticket[8];
+    int pad[4];
+    double eps;       // Jv step for the current direction
+    double unorm;     // |u|
+    double beta;      // |r| at the start of the cycle
+    double target;    // eta |b|
+    double inv;       // 1 / |w|
+    double wn2;       // |w|^2 before orthogonalisation
+    double res;       // |g_{k}| current residual estimate
+    double scratch[8];
+    double h[kMaxRestart + 1];
+    double H[(kMaxRestart + 1) * kMaxRestart];  // column-major: H[i + (m+1) j]
+    double g[kMaxRestart + 1];
+    double cs[kMaxRestart], sn[kMaxRestart];
+    double y[kMaxRestart];
+};
+
+struct Profiler {
+    bool enabled = false;
+    struct Slot {
+        std::string name;
+        std::vector<cudaEvent_t> ev;   // pairs
+        size_t used = 0;
+        double ms = 0;
+        int64_t launches = 0;
+    };
+    std::vector<Slot> slots;
+    int slot(const char* name);
+};
+
+}  // namespace jfnk
+
+struct jfnk_ctx {
+    jfnk_options opt;
+    std::string err;
+    cudaStream_t stream = nullptr;      // context's own stream
+    cudaStream_t cur = nullptr;         // stream of the call in progress
+    jfnk::HostMesh hm;
+    bool have_mesh = false, have_material = false;
+    int law = JFNK_LAW_LINEAR;
+    double p1 = 0, p2 = 0, mu = 0, lam = 0, kappa = 0, Kbar = 0;
+    std::vector<double> fb_host;
+    double load = 1.0;
+    bool dirty = true;
+    jfnk::Topology topo;
+    jfnk::DevMesh dm;
+    // hot-path vectors, internal order, SoA [3][nc] unless noted
+    double *u = nullptr, *Ru = nullptr, *w = nullptr, *R = nullptr, *z = nullptr, *x = nullptr;
+    double *bvec = nullptr, *wk = nullptr, *tmp = nullptr, *ext = nullptr;
+    double *G = nullptr, *T = nullptr;  // [9][nc]
+    double* F = nullptr;                 // [3][nflux]
+    double* partials = nullptr;          // reduction partials
+    double* V = nullptr;                 // Krylov basis (double or float storage)
+    size_t V_ld = 0;                     // stride between basis vectors (elements)
+    int V_is_float = 0;
+    jfnk::GmresDev* gd = nullptr;        // device scalars
+    jfnk::GmresDev* gh = nullptr;        // pinned host mirror
+    double* scal = nullptr;              // device scalar scratch [16]
+    double* scal_h = nullptr;            // pinned [16]
+    unsigned* tickets = nullptr;         // [16]
+    // multigrid (precond.cu owns the hierarchy object)
+    void* mgs = nullptr;
+    int mg_coarse_n = 0;
+    bool mg_ready = false;
+    int64_t launches = 0;
+    int64_t dev_bytes = 0;
+    std::vector<void*> allocs;
+    jfnk::Profiler prof;
+};
+
+// ------------------------------------------------------------------ helpers (capi.cu)
+int jfnk_fail(jfnk_ctx* c, int code, const std::string& msg);
+int jfnk_cuda_fail(jfnk_ctx* c, cudaError_t e, const char* what);
+void* jfnk_dalloc(jfnk_ctx* c, size_t bytes);   // tracked cudaMalloc, zeroed; nullptr on failure
+
+#define JF_CUDA(ctx, call)                                         \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return jfnk_cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+#define JF_LAUNCHED(ctx)                                           \
+    do {                                                           \
+        (ctx)->launches++;                                         \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return jfnk_cuda_fail(ctx, e_, "kernel launch"); \
+    } while (0)
+
+// profiling brackets around a launch
+void jfnk_prof_begin(jfnk_ctx* c, int slot);
+void jfnk_prof_end(jfnk_ctx* c, int slot);
+
+// ------------------------------------------------------------------ module entry points
+namespace jfnk {
+// geometry.cu: device set-up (geometry, least-squares vectors, coefficients, J~)
+int setup_device_mesh(jfnk_ctx* c);
+int setup_material_coefficients(jfnk_ctx* c);
+// residual.cu
+enum ResidualOut { OUT_R = 0, OUT_JV = 1 };
+// R(u_int) into `out` (internal order); mode OUT_JV writes (R - Ru) * (1/eps) with eps read
+// from the device scalar `eps_dev`.
+int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev);
+int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate);
+// linalg.cu
+int perm_in(jfnk_ctx* c, const double* ext_aos, double* int_soa);
+int perm_out(jfnk_ctx* c, const double* int_soa, double* ext_aos);
+int norm2(jfnk_ctx* c, const double* x, size_t n, double* out_dev);          // out = |x|
+int axpby(jfnk_ctx* c, size_t n, double a, const double* x, double b, const double* y, double* out);
+int axpy_dev_scalar(jfnk_ctx* c, size_t n, const double* x, const double* a_dev, const double* y, double* out); // out = y + a x
+int norm_mode(jfnk_ctx* c, const double* x, size_t n, int mode, const int* gate);
+int perturb(jfnk_ctx* c, const double* u, const double* z, double* w, const int* gate);
+int cycle_init(jfnk_ctx* c, const double* r);
+int arnoldi_orthogonalise(jfnk_ctx* c, double* w);
+int arnoldi_finish_column(jfnk_ctx* c, const double* w, int j_host);
+int cycle_solution(jfnk_ctx* c, double* out);
+// precond.cu
+int pc_setup(jfnk_ctx* c);
+// z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
+int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);
+int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate);
+void mg_release(jfnk_ctx* c);
+int mg_levels_info(jfnk_ctx* c, std::vector<int>& sizes);
+// solver.cu
+int gmres(jfnk_ctx* c, const double* b, double* x, int* its, double* relres, int* status);
+int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st);
+}  // namespace jfnk

@@ -1,0 +1,485 @@
+// Preconditioners of Sec. 3.2 built from the compact-stencil approximate Jacobian J~ of
+// Sec. 3.1 (one scalar matrix shared by the displacement components):
+//   block-Jacobi  z_P = [J~]_PP^-1 v_P  (a scalar per cell without symmetry faces);
+//   multigrid     one V-cycle of an aggregation AMG on A = -J~ (the paper uses BoomerAMG,
+//                 one V-cycle per Krylov iteration with one pre- and one post-sweep;
+//                 Sec. 4.2).  The fine level is applied matrix-free from the per-face J~
+//                 coefficients; coarse levels are CSR; the coarsest is a dense inverse.
+//                 All three components go through each level in one pass.
+// Arithmetic: FP64 (precision FP64) or FP32 (precision MIXED: matrix, smoother, V-cycle).
+// FP32 runs on the wide FP32 pipe of GB300, FP64 on a pipe ~64x narrower.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device_common.cuh"
+#include "jfnk_internal.h"
+
+namespace jfnk {
+
+int norm_mode(jfnk_ctx* c, const double* x, size_t n, int mode, const int* gate);
+
+// ------------------------------------------------------------------ block-Jacobi
+template <typename TV, typename TP>
+__global__ void k_bjacobi(const int* gate, int nc, const TV* __restrict__ v, const TP* __restrict__ dinv,
+                          double* __restrict__ z)
+{
+    if (gate && *gate) return;
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= nc) return;
+    const TP d = dinv[P];
+#pragma unroll
+    for (int k = 0; k < 3; k++) z[(size_t)k * nc + P] = (double)((TP)v[(size_t)k * nc + P] * d);
+}
+
+template <typename TV>
+__global__ void k_copy_to_double(const int* gate, size_t n, const TV* __restrict__ v, double* __restrict__ z)
+{
+    if (gate && *gate) return;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        z[e] = (double)v[e];
+}
+
+// ------------------------------------------------------------------ multigrid kernels
+// Fine level (A = -J~, matrix-free):
+//   (A x)_P = -diag_P x_P - sum_{faces f of P} c_f x_other(f)
+template <typename T>
+__device__ __forceinline__ void a0_row(int P, int nc, const int32_t* __restrict__ fo_ptr, const int32_t* __restrict__ fn_ptr,
+                                       const int32_t* __restrict__ fn_face, const int32_t* __restrict__ own,
+                                       const int32_t* __restrict__ nei, const T* __restrict__ jc, const T* __restrict__ adiag,
+                                       const T* __restrict__ x, T out[3])
+{
+    const T d = adiag[P];
+    out[0] = d * x[P]; out[1] = d * x[nc + P]; out[2] = d * x[2 * (size_t)nc + P];
+    for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) {
+        const int N = nei[f];
+        const T cf = jc[f];
+        out[0] -= cf * x[N]; out[1] -= cf * x[nc + N]; out[2] -= cf * x[2 * (size_t)nc + N];
+    }
+    for (int k = fn_ptr[P]; k < fn_ptr[P + 1]; k++) {
+        const int f = fn_face[k];
+        const int N = own[f];
+        const T cf = jc[f];
+        out[0] -= cf * x[N]; out[1] -= cf * x[nc + N]; out[2] -= cf * x[2 * (size_t)nc + N];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void csr_row(int i, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                        const T* __restrict__ val, const T* __restrict__ x, T out[3])
+{
+    out[0] = out[1] = out[2] = (T)0;
+    for (int q = rp[i]; q < rp[i + 1]; q++) {
+        const int j = col[q];
+        const T a = val[q];
+        out[0] += a * x[j]; out[1] += a * x[n + j]; out[2] += a * x[2 * (size_t)n + j];
+    }
+}
+
+// level 0 entry: b = -v (so the cycle returns z = -A^-1 v = J~^-1 v), x = omega D^-1 b
+template <typename TV, typename T>
+__global__ void k_mg_pre0(const int* gate, int nc, const TV* __restrict__ v, const T* __restrict__ dinv, T omega,
+                          T* __restrict__ b, T* __restrict__ x)
+{
+    if (gate && *gate) return;
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= nc) return;
+    const T d = omega * dinv[P];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const T bb = -(T)v[(size_t)k * nc + P];
+        b[(size_t)k * nc + P] = bb;
+        x[(size_t)k * nc + P] = d * bb;
+    }
+}
+
+template <typename T>
+__global__ void k_mg_pre(const int* gate, int n, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
+                         T* __restrict__ x)
+{
+    if (gate && *gate) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T d = omega * dinv[i];
+#pragma unroll
+    for (int k = 0; k < 3; k++) x[(size_t)k * n + i] = d * b[(size_t)k * n + i];
+}
+
+// Extra Jacobi sweep x_out = x + omega D^-1 (b - A x) (sweeps > 1)
+template <typename T, bool FINE>
+__global__ void k_mg_jacobi(const int* gate, int n, const int32_t* __restrict__ p0, const int32_t* __restrict__ p1,
+                            const int32_t* __restrict__ p2, const int32_t* __restrict__ own, const int32_t* __restrict__ nei,
+                            const T* __restrict__ vals, const T* __restrict__ adiag, const T* __restrict__ dinv, T omega,
+                            const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo)
+{
+    if (gate && *gate) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T ax[3];
+    if (FINE) a0_row<T>(i, n, p0, p1, p2, own, nei, vals, adiag, x, ax);
+    else csr_row<T>(i, n, p0, p1, vals, x, ax);
+    const T d = omega * dinv[i];
+#pragma unroll
+    for (int k = 0; k < 3; k++) xo[(size_t)k * n + i] = x[(size_t)k * n + i] + d * (b[(size_t)k * n + i] - ax[k]);
+}
+
+// residual r = b - A x of the members of each aggregate, summed into the coarse right-hand side
+template <typename T, bool FINE>
+__global__ void k_mg_restrict(const int* gate, int nco, int n, const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
+                              const int32_t* __restrict__ p0, const int32_t* __restrict__ p1, const int32_t* __restrict__ p2,
+                              const int32_t* __restrict__ own, const int32_t* __restrict__ nei, const T* __restrict__ vals,
+                              const T* __restrict__ adiag, const T* __restrict__ b, const T* __restrict__ x,
+                              T* __restrict__ bc)
+{
+    if (gate && *gate) return;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nco) return;
+    T s[3] = {(T)0, (T)0, (T)0};
+    for (int q = mptr[I]; q < mptr[I + 1]; q++) {
+        const int i = midx[q];
+        T ax[3];
+        if (FINE) a0_row<T>(i, n, p0, p1, p2, own, nei, vals, adiag, x, ax);
+        else csr_row<T>(i, n, p0, p1, vals, x, ax);
+#pragma unroll
+        for (int k = 0; k < 3; k++) s[k] += b[(size_t)k * n + i] - ax[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) bc[(size_t)k * nco + I] = s[k];
+}
+
+// x' = x + P x_c (piecewise constant), then one Jacobi sweep: x_out = x' + omega D^-1 (b - A x').
+// FINE && TO_DOUBLE writes z (double) for the caller.
+template <typename T, bool FINE>
+__global__ void k_mg_post(const int* gate, int n, int nco, const int32_t* __restrict__ agg, const T* __restrict__ xc,
+                          const int32_t* __restrict__ p0, const int32_t* __restrict__ p1, const int32_t* __restrict__ p2,
+                          const int32_t* __restrict__ own, const int32_t* __restrict__ nei, const T* __restrict__ vals,
+                          const T* __restrict__ adiag, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
+                          const T* __restrict__ x, T* __restrict__ xo, double* __restrict__ zd)
+{
+    if (gate && *gate) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T ax[3] = {(T)0, (T)0, (T)0};
+    auto xp = [&](int j, int k) -> T { return x[(size_t)k * n + j] + xc[(size_t)k * nco + agg[j]]; };
+    if (FINE) {
+        const T d = adiag[i];
+        for (int k = 0; k < 3; k++) ax[k] = d * xp(i, k);
+        for (int f = p0[i]; f < p0[i + 1]; f++) {
+            const int N = nei[f];
+            const T cf = vals[f];
+            for (int k = 0; k < 3; k++) ax[k] -= cf * xp(N, k);
+        }
+        for (int q = p1[i]; q < p1[i + 1]; q++) {
+            const int f = p2[q];
+            const int N = own[f];
+            const T cf = vals[f];
+            for (int k = 0; k < 3; k++) ax[k] -= cf * xp(N, k);
+        }
+    } else {
+        for (int q = p0[i]; q < p0[i + 1]; q++) {
+            const int j = p1[q];
+            const T a = vals[q];
+            for (int k = 0; k < 3; k++) ax[k] += a * xp(j, k);
+        }
+    }
+    const T d = omega * dinv[i];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const T xn = xp(i, k) + d * (b[(size_t)k * n + i] - ax[k]);
+        if (zd) zd[(size_t)k * n + i] = (double)xn;
+        else xo[(size_t)k * n + i] = xn;
+    }
+}
+
+// coarsest level: x = A_c^-1 b with the (symmetric) dense inverse
+template <typename T>
+__global__ void k_mg_coarse(const int* gate, int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x)
+{
+    if (gate && *gate) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int k = 0; k < n; k++) {
+        const T a = Ainv[(size_t)k * n + i];
+        s0 += a * b[k]; s1 += a * b[n + k]; s2 += a * b[2 * (size_t)n + k];
+    }
+    x[i] = s0; x[n + i] = s1; x[2 * (size_t)n + i] = s2;
+}
+
+// ------------------------------------------------------------------ device hierarchy
+template <typename T>
+struct MgDev {
+    struct Level {
+        int n = 0, nco = 0;
+        int32_t *rp = nullptr, *col = nullptr;   // CSR (coarse levels)
+        T *val = nullptr, *adiag = nullptr, *dinv = nullptr;
+        int32_t *agg = nullptr, *mptr = nullptr, *midx = nullptr;  // to the next level
+        T *b = nullptr, *x = nullptr, *x2 = nullptr;
+    };
+    std::vector<Level> L;
+    T* Ainv = nullptr;
+    T* jc = nullptr;   // fine-level face coefficients in T
+};
+
+struct MgState {
+    MgDev<float> f;
+    MgDev<double> d;
+    bool ready = false;
+};
+
+static MgState& mg_state(jfnk_ctx* c);
+
+template <typename T>
+static T* upload_as(jfnk_ctx* c, const std::vector<double>& h)
+{
+    std::vector<T> t(h.begin(), h.end());
+    T* d = (T*)jfnk_dalloc(c, sizeof(T) * std::max<size_t>(1, t.size()));
+    if (d && !t.empty()) cudaMemcpy(d, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice);
+    return d;
+}
+static int32_t* upload_i(jfnk_ctx* c, const std::vector<int32_t>& h)
+{
+    int32_t* d = (int32_t*)jfnk_dalloc(c, sizeof(int32_t) * std::max<size_t>(1, h.size()));
+    if (d && !h.empty()) cudaMemcpy(d, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice);
+    return d;
+}
+
+template <typename T>
+static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& lv, const std::vector<double>& inv,
+                     const std::vector<double>& jc_h, const std::vector<double>& adiag0, const std::vector<int32_t>& agg0_new)
+{
+    const int nl = (int)lv.size();
+    M.L.assign(nl, typename MgDev<T>::Level());
+    M.jc = upload_as<T>(c, jc_h);
+    for (int l = 0; l < nl; l++) {
+        auto& D = M.L[l];
+        const MgLevelHost& H = lv[l];
+        D.n = H.n;
+        std::vector<double> ad(H.n), di(H.n);
+        if (l == 0) {
+            ad = adiag0;
+        } else {
+            for (int i = 0; i < H.n; i++)
+                for (int q = H.rp[i]; q < H.rp[i + 1]; q++)
+                    if (H.col[q] == i) ad[i] = H.val[q];
+            D.rp = upload_i(c, H.rp);
+            D.col = upload_i(c, H.col);
+            D.val = upload_as<T>(c, H.val);
+        }
+        for (int i = 0; i < H.n; i++) di[i] = 1.0 / ad[i];
+        D.adiag = upload_as<T>(c, ad);
+        D.dinv = upload_as<T>(c, di);
+        D.b = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
+        D.x = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
+        D.x2 = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
+        if (l < nl - 1) {
+            const std::vector<int32_t>& agg = (l == 0) ? agg0_new : H.agg;
+            int nco = lv[l + 1].n;
+            D.nco = nco;
+            std::vector<int32_t> mptr(nco + 1, 0), midx(H.n);
+            for (int i = 0; i < H.n; i++) mptr[agg[i] + 1]++;
+            for (int a = 0; a < nco; a++) mptr[a + 1] += mptr[a];
+            std::vector<int32_t> fill(mptr.begin(), mptr.end() - 1);
+            for (int i = 0; i < H.n; i++) midx[fill[agg[i]]++] = i;
+            D.agg = upload_i(c, agg);
+            D.mptr = upload_i(c, mptr);
+            D.midx = upload_i(c, midx);
+        }
+        if (!D.adiag || !D.dinv || !D.b || !D.x || !D.x2) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
+    }
+    M.Ainv = upload_as<T>(c, inv);
+    if (!M.Ainv || !M.jc) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
+    return JFNK_OK;
+}
+
+// ------------------------------------------------------------------ set-up
+static MgState& mg_state(jfnk_ctx* c)
+{
+    if (!c->mgs) c->mgs = new MgState();
+    return *(MgState*)c->mgs;
+}
+
+void mg_release(jfnk_ctx* c)
+{
+    delete (MgState*)c->mgs;
+    c->mgs = nullptr;
+}
+
+int pc_setup(jfnk_ctx* c)
+{
+    MgState& S = mg_state(c);
+    S.ready = false;
+    if (c->opt.pc != JFNK_PC_MG) return JFNK_OK;
+    const DevMesh& m = c->dm;
+    const Topology& t = c->topo;
+    const int nc = m.nc;
+    std::vector<double> jc(std::max(1, m.nflux)), diag(nc);
+    JF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (m.nflux) JF_CUDA(c, cudaMemcpy(jc.data(), m.jt_c, sizeof(double) * m.nflux, cudaMemcpyDeviceToHost));
+    JF_CUDA(c, cudaMemcpy(diag.data(), m.jt_diag, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    // level 0 in the caller's cell order (so the aggregation does not depend on the internal
+    // renumbering): rows by input index, columns ascending
+    MgLevelHost L0;
+    L0.n = nc;
+    std::vector<std::vector<std::pair<int32_t, double>>> rows(nc);
+    for (int P = 0; P < nc; P++) rows[t.n2o[P]].push_back({t.n2o[P], -diag[P]});
+    for (int f = 0; f < m.ni; f++) {
+        const int a = t.n2o[t.own[f]], b = t.n2o[t.nei[f]];
+        rows[a].push_back({b, -jc[f]});
+        rows[b].push_back({a, -jc[f]});
+    }
+    L0.rp.assign(nc + 1, 0);
+    for (int i = 0; i < nc; i++) {
+        std::sort(rows[i].begin(), rows[i].end(), [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
+        for (auto& e : rows[i]) { L0.col.push_back(e.first); L0.val.push_back(e.second); }
+        L0.rp[i + 1] = (int32_t)L0.col.size();
+    }
+    std::vector<MgLevelHost> lv;
+    std::vector<double> inv;
+    std::string e = mg_build_hierarchy(std::move(L0), c->opt.mg_theta, c->opt.mg_max_levels, c->opt.mg_coarse_max, lv, inv);
+    if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
+    std::vector<int32_t> agg0_new;
+    if (lv.size() > 1) {
+        agg0_new.resize(nc);
+        for (int P = 0; P < nc; P++) agg0_new[P] = lv[0].agg[t.n2o[P]];
+    }
+    std::vector<double> adiag0(nc);
+    for (int P = 0; P < nc; P++) adiag0[P] = -diag[P];
+    int rc = mg_upload<float>(c, S.f, lv, inv, jc, adiag0, agg0_new);
+    if (rc) return rc;
+    rc = mg_upload<double>(c, S.d, lv, inv, jc, adiag0, agg0_new);
+    if (rc) return rc;
+    c->mg_coarse_n = lv.back().n;
+    S.ready = true;
+    c->mg_ready = true;
+    return JFNK_OK;
+}
+
+int mg_levels_info(jfnk_ctx* c, std::vector<int>& sizes)
+{
+    MgState& S = mg_state(c);
+    sizes.clear();
+    if (!S.ready) return 0;
+    for (auto& l : S.f.L) sizes.push_back(l.n);
+    return (int)sizes.size();
+}
+
+static inline int nb(long n, int t) { return (int)std::max<long>(1, (n + t - 1) / t); }
+
+template <typename T, typename TV>
+static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* v, double* z, const int* gate)
+{
+    const DevMesh& m = c->dm;
+    cudaStream_t s = c->cur;
+    const T omega = (T)(2.0 / 3.0);
+    const int nl = (int)M.L.size();
+    const int sweeps = std::max(1, c->opt.mg_smooth_sweeps);
+    if (nl == 1) {
+        // a single level: the dense inverse applied to -v
+        auto& D = M.L[0];
+        k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, v, D.dinv, (T)0, D.b, D.x2);
+        JF_LAUNCHED(c);
+        k_mg_coarse<T><<<nb(D.n, 128), 128, 0, s>>>(gate, D.n, M.Ainv, D.b, D.x);
+        JF_LAUNCHED(c);
+        k_copy_to_double<T><<<nb(3L * D.n, 256), 256, 0, s>>>(gate, 3 * (size_t)D.n, D.x, z);
+        JF_LAUNCHED(c);
+        return JFNK_OK;
+    }
+    // downward
+    for (int l = 0; l < nl; l++) {
+        auto& D = M.L[l];
+        if (l == nl - 1) {
+            k_mg_coarse<T><<<nb(D.n, 128), 128, 0, s>>>(gate, D.n, M.Ainv, D.b, D.x);
+            JF_LAUNCHED(c);
+            break;
+        }
+        if (l == 0) k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, v, D.dinv, omega, D.b, D.x);
+        else k_mg_pre<T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.dinv, omega, D.b, D.x);
+        JF_LAUNCHED(c);
+        for (int sw = 1; sw < sweeps; sw++) {
+            if (l == 0)
+                k_mg_jacobi<T, true><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, m.fo_ptr, m.fn_ptr, m.fn_face, m.own, m.nei,
+                                                                   M.jc, D.adiag, D.dinv, omega, D.b, D.x, D.x2);
+            else
+                k_mg_jacobi<T, false><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, nullptr, nullptr, nullptr,
+                                                                    D.val, D.adiag, D.dinv, omega, D.b, D.x, D.x2);
+            JF_LAUNCHED(c);
+            std::swap(D.x, D.x2);
+        }
+        auto& Cn = M.L[l + 1];
+        if (l == 0)
+            k_mg_restrict<T, true><<<nb(D.nco, 128), 128, 0, s>>>(gate, D.nco, D.n, D.mptr, D.midx, m.fo_ptr, m.fn_ptr,
+                                                                    m.fn_face, m.own, m.nei, M.jc, D.adiag, D.b, D.x, Cn.b);
+        else
+            k_mg_restrict<T, false><<<nb(D.nco, 128), 128, 0, s>>>(gate, D.nco, D.n, D.mptr, D.midx, D.rp, D.col, nullptr,
+                                                                     nullptr, nullptr, D.val, D.adiag, D.b, D.x, Cn.b);
+        JF_LAUNCHED(c);
+    }
+    // upward
+    for (int l = nl - 2; l >= 0; l--) {
+        auto& D = M.L[l];
+        auto& Cn = M.L[l + 1];
+        double* zout = (l == 0 && sweeps == 1) ? z : nullptr;
+        if (l == 0)
+            k_mg_post<T, true><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.nco, D.agg, Cn.x, m.fo_ptr, m.fn_ptr, m.fn_face,
+                                                             m.own, m.nei, M.jc, D.adiag, D.dinv, omega, D.b, D.x, D.x2, zout);
+        else
+            k_mg_post<T, false><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.nco, D.agg, Cn.x, D.rp, D.col, nullptr, nullptr,
+                                                              nullptr, D.val, D.adiag, D.dinv, omega, D.b, D.x, D.x2, nullptr);
+        JF_LAUNCHED(c);
+        if (!zout) std::swap(D.x, D.x2);
+        for (int sw = 1; sw < sweeps; sw++) {
+            if (l == 0)
+                k_mg_jacobi<T, true><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, m.fo_ptr, m.fn_ptr, m.fn_face, m.own, m.nei,
+                                                                   M.jc, D.adiag, D.dinv, omega, D.b, D.x, D.x2);
+            else
+                k_mg_jacobi<T, false><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, nullptr, nullptr, nullptr,
+                                                                    D.val, D.adiag, D.dinv, omega, D.b, D.x, D.x2);
+            JF_LAUNCHED(c);
+            std::swap(D.x, D.x2);
+        }
+        if (l == 0 && sweeps > 1) {
+            k_copy_to_double<T><<<nb(3L * D.n, 256), 256, 0, s>>>(gate, 3 * (size_t)D.n, D.x, z);
+            JF_LAUNCHED(c);
+        }
+    }
+    return JFNK_OK;
+}
+
+// z = P^-1 v; v is double or float (basis storage); gate may be null
+int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate)
+{
+    const int nc = c->dm.nc;
+    const bool fp32 = c->opt.precision == JFNK_PREC_MIXED;
+    cudaStream_t s = c->cur;
+    int sl = c->prof.enabled ? c->prof.slot(pc == JFNK_PC_MG ? "pc_mg" : "pc_bjacobi") : -1;
+    jfnk_prof_begin(c, sl);
+    if (pc == JFNK_PC_BJACOBI) {
+        if (v_is_float) {
+            if (fp32) k_bjacobi<float, float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)v, c->dm.jt_dinv_f, z);
+            else k_bjacobi<float, double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)v, c->dm.jt_dinv, z);
+        } else {
+            if (fp32) k_bjacobi<double, float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)v, c->dm.jt_dinv_f, z);
+            else k_bjacobi<double, double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)v, c->dm.jt_dinv, z);
+        }
+        JF_LAUNCHED(c);
+    } else if (pc == JFNK_PC_MG) {
+        MgState& S = mg_state(c);
+        if (!S.ready) return jfnk_fail(c, JFNK_ESTATE, "multigrid preconditioner not set up (options.pc must be JFNK_PC_MG at set-up)");
+        int rc;
+        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)v, z, gate) : vcycle<float, double>(c, S.f, (const double*)v, z, gate);
+        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)v, z, gate) : vcycle<double, double>(c, S.d, (const double*)v, z, gate);
+        if (rc) return rc;
+    } else {
+        const size_t n = 3 * (size_t)nc;
+        if (v_is_float) k_copy_to_double<float><<<nb((long)n, 256), 256, 0, s>>>(gate, n, (const float*)v, z);
+        else k_copy_to_double<double><<<nb((long)n, 256), 256, 0, s>>>(gate, n, (const double*)v, z);
+        JF_LAUNCHED(c);
+    }
+    jfnk_prof_end(c, sl);
+    return JFNK_OK;
+}
+
+int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z) { return pc_apply_any(c, pc, v, 0, z, nullptr); }
+
+}  // namespace jfnk

@@ -1,0 +1,248 @@
+// The matrix-free momentum residual R(u) of Sec. 2.3 on the device, in three passes:
+//   k_grad    per cell: least-squares gradient (Eq. leastSquaresGrad) from the sliced-ELL
+//             neighbour table; neo-Hookean cells also form the total-Lagrangian traction
+//             operator T = J F^-1 sigma (App. A, App. B Eq. neoHook);
+//   k_flux    per internal and displacement face: the surface force of Eq. divStressDiscret
+//             with the interpolated stress of Eq. stressInterp plus the Rhie-Chow term of
+//             Eq. RhieChow, in owner-sorted face order;
+//   k_finish  per cell: owner faces added, neighbour faces (neighbour-sorted list)
+//             subtracted, plus the constant body/traction part; optionally the Jacobian
+//             action (R(u + eps v) - R(u)) / eps of Eq. JF.  No atomics, fixed summation
+//             order: the result is bitwise reproducible.
+// FP64 throughout (the difference in Eq. JF cancels catastrophically otherwise).  The FP64
+// pipe, not HBM, bounds these kernels on GB300, so the face coefficients are precomputed to
+// keep the FP64 instruction count per face low.
+#include "device_common.cuh"
+#include "jfnk_internal.h"
+
+namespace jfnk {
+
+template <int LAW>
+__global__ void __launch_bounds__(128) k_grad(const int* __restrict__ gate, int nc, int dim, const int32_t* __restrict__ sell_off,
+                                              const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
+                                              const double* __restrict__ sell_l, int n_slots,
+                                              const double* __restrict__ u, double* __restrict__ G,
+                                              double* __restrict__ T, double mu, double kappa)
+{
+    if (gate && *gate) return;
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= nc) return;
+    const int s = P >> 5, lane = P & 31, base = sell_off[s], w = sell_w[s];
+    const double u0 = u[P], u1 = u[nc + P], u2 = u[2 * nc + P];
+    double g[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) g[q] = 0.0;
+    for (int k = 0; k < w; k++) {
+        const int slot = base + 32 * k + lane;
+        const int N = sell_nbr[slot];
+        if (N < 0) break;
+        const double l0 = sell_l[slot], l1 = sell_l[n_slots + slot], l2 = sell_l[2 * n_slots + slot];
+        const double d0 = u[N] - u0, d1 = u[nc + N] - u1, d2 = u[2 * nc + N] - u2;
+        g[0] = fma(l0, d0, g[0]); g[1] = fma(l0, d1, g[1]); g[2] = fma(l0, d2, g[2]);
+        g[3] = fma(l1, d0, g[3]); g[4] = fma(l1, d1, g[4]); g[5] = fma(l1, d2, g[5]);
+        g[6] = fma(l2, d0, g[6]); g[7] = fma(l2, d1, g[7]); g[8] = fma(l2, d2, g[8]);
+    }
+#pragma unroll
+    for (int q = 0; q < 9; q++) G[(size_t)q * nc + P] = g[q];
+    if (LAW == JFNK_LAW_NEOHOOKEAN) {
+        // F = I + (grad u)^T: F_ij = delta_ij + g_ji
+        const double F00 = 1.0 + g[0], F01 = g[3], F02 = g[6];
+        const double F10 = g[1], F11 = 1.0 + g[4], F12 = g[7];
+        const double F20 = g[2], F21 = g[5], F22 = 1.0 + g[8];
+        // cofactor matrix: adj(F) = J F^-1
+        const double A00 = F11 * F22 - F12 * F21, A01 = F02 * F21 - F01 * F22, A02 = F01 * F12 - F02 * F11;
+        const double A10 = F12 * F20 - F10 * F22, A11 = F00 * F22 - F02 * F20, A12 = F02 * F10 - F00 * F12;
+        const double A20 = F10 * F21 - F11 * F20, A21 = F01 * F20 - F00 * F21, A22 = F00 * F11 - F01 * F10;
+        const double J = F00 * A00 + F01 * A10 + F02 * A20;
+        // b = F F^T (symmetric)
+        const double b00 = F00 * F00 + F01 * F01 + F02 * F02;
+        const double b01 = F00 * F10 + F01 * F11 + F02 * F12;
+        const double b02 = F00 * F20 + F01 * F21 + F02 * F22;
+        const double b11 = F10 * F10 + F11 * F11 + F12 * F12;
+        const double b12 = F10 * F20 + F11 * F21 + F12 * F22;
+        const double b22 = F20 * F20 + F21 * F21 + F22 * F22;
+        const double cj = cbrt(J);
+        const double Jm23 = 1.0 / (cj * cj);
+        const double rJ = 1.0 / J;
+        const double cm = mu * rJ * Jm23;                       // mu/J J^-2/3
+        const double tr3 = (b00 + b11 + b22) * (1.0 / 3.0);
+        const double p = 0.5 * kappa * (J * J - 1.0) * rJ;      // kappa/2 (J^2 - 1)/J
+        const double s00 = cm * (b00 - tr3) + p, s11 = cm * (b11 - tr3) + p, s22 = cm * (b22 - tr3) + p;
+        const double s01 = cm * b01, s02 = cm * b02, s12 = cm * b12;
+        // T = adj(F) sigma
+        double t[9];
+        t[0] = A00 * s00 + A01 * s01 + A02 * s02;
+        t[1] = A00 * s01 + A01 * s11 + A02 * s12;
+        t[2] = A00 * s02 + A01 * s12 + A02 * s22;
+        t[3] = A10 * s00 + A11 * s01 + A12 * s02;
+        t[4] = A10 * s01 + A11 * s11 + A12 * s12;
+        t[5] = A10 * s02 + A11 * s12 + A12 * s22;
+        t[6] = A20 * s00 + A21 * s01 + A22 * s02;
+        t[7] = A20 * s01 + A21 * s11 + A22 * s12;
+        t[8] = A20 * s02 + A21 * s12 + A22 * s22;
+#pragma unroll
+        for (int q = 0; q < 9; q++) T[(size_t)q * nc + P] = t[q];
+    }
+    (void)dim;
+}
+
+template <int LAW>
+__global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int ni, int nflux, int nc, const int32_t* __restrict__ own,
+                                              const int32_t* __restrict__ nei, const double* __restrict__ coef,
+                                              const double* __restrict__ u, const double* __restrict__ G,
+                                              const double* __restrict__ T, const double* __restrict__ bval,
+                                              double load, double* __restrict__ F)
+{
+    if (gate && *gate) return;
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nflux) return;
+    const int P = own[f];
+    const bool internal = f < ni;
+    const int N = internal ? nei[f] : P;
+    const double w = coef[f], kc = coef[nflux + f];
+    double gf[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) {
+        const double gp = G[(size_t)q * nc + P];
+        if (internal) {
+            const double gn = G[(size_t)q * nc + N];
+            gf[q] = fma(w, gp - gn, gn);
+        } else {
+            gf[q] = gp;
+        }
+    }
+    double du[3];
+    if (internal) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) du[c] = u[(size_t)c * nc + N] - u[(size_t)c * nc + P];
+    } else {
+        const int k = f - ni;
+#pragma unroll
+        for (int c = 0; c < 3; c++) du[c] = load * bval[(size_t)k * 3 + c] - u[(size_t)c * nc + P];
+    }
+    const double c0 = coef[2 * nflux + f], c1 = coef[3 * nflux + f], c2 = coef[4 * nflux + f];
+    const double c3 = coef[5 * nflux + f], c4 = coef[6 * nflux + f], c5 = coef[7 * nflux + f];
+    double t[3];
+    if (LAW == JFNK_LAW_LINEAR) {
+        // t_j = p . G_:j + q . G_j: + r_j tr(G) + kc du_j
+        const double r0 = coef[8 * nflux + f], r1 = coef[9 * nflux + f], r2 = coef[10 * nflux + f];
+        const double tr = gf[0] + gf[4] + gf[8];
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            double a = c0 * gf[j];
+            a = fma(c1, gf[3 + j], a);
+            a = fma(c2, gf[6 + j], a);
+            a = fma(c3, gf[3 * j], a);
+            a = fma(c4, gf[3 * j + 1], a);
+            a = fma(c5, gf[3 * j + 2], a);
+            a = fma((j == 0 ? r0 : (j == 1 ? r1 : r2)), tr, a);
+            t[j] = fma(kc, du[j], a);
+        }
+    } else {
+        // t_j = Gamma . T_f:j - a . G_f:j + kc du_j
+        double tf[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) {
+            const double tp = T[(size_t)q * nc + P];
+            if (internal) {
+                const double tn = T[(size_t)q * nc + N];
+                tf[q] = fma(w, tp - tn, tn);
+            } else {
+                tf[q] = tp;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            double a = c0 * tf[j];
+            a = fma(c1, tf[3 + j], a);
+            a = fma(c2, tf[6 + j], a);
+            a = fma(-c3, gf[j], a);
+            a = fma(-c4, gf[3 + j], a);
+            a = fma(-c5, gf[6 + j], a);
+            t[j] = fma(kc, du[j], a);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) F[(size_t)c * nflux + f] = t[c];
+}
+
+// mode 0: out = R;  mode 1: out = (R - Ru) / eps  (eps from device memory; 0 -> out = 0)
+__global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int dim, const int32_t* __restrict__ fo_ptr,
+                                                const int32_t* __restrict__ fn_ptr, const int32_t* __restrict__ fn_face,
+                                                const int32_t* __restrict__ fd_ptr, const double* __restrict__ F,
+                                                const double* __restrict__ b0, double load, int mode,
+                                                const double* __restrict__ Ru, const double* __restrict__ eps_dev,
+                                                const int* __restrict__ gate, double* __restrict__ out)
+{
+    if (gate && *gate) return;
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= nc) return;
+    double r0 = load * b0[P], r1 = load * b0[nc + P], r2 = load * b0[2 * nc + P];
+    for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) {
+        r0 += F[f]; r1 += F[nflux + f]; r2 += F[2 * (size_t)nflux + f];
+    }
+    for (int k = fn_ptr[P]; k < fn_ptr[P + 1]; k++) {
+        const int f = fn_face[k];
+        r0 -= F[f]; r1 -= F[nflux + f]; r2 -= F[2 * (size_t)nflux + f];
+    }
+    for (int f = fd_ptr[P]; f < fd_ptr[P + 1]; f++) {
+        r0 += F[f]; r1 += F[nflux + f]; r2 += F[2 * (size_t)nflux + f];
+    }
+    if (dim == 2) r2 = 0.0;
+    if (mode == 1) {
+        const double eps = *eps_dev;
+        if (eps == 0.0) {
+            r0 = r1 = r2 = 0.0;
+        } else {
+            const double ie = 1.0 / eps;
+            r0 = (r0 - Ru[P]) * ie;
+            r1 = (r1 - Ru[nc + P]) * ie;
+            r2 = (r2 - Ru[2 * nc + P]) * ie;
+        }
+    }
+    out[P] = r0; out[nc + P] = r1; out[2 * nc + P] = r2;
+}
+
+static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
+
+int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate)
+{
+    const DevMesh& m = c->dm;
+    cudaStream_t s = c->cur;
+    static const char* const kNames[3] = {"grad", "flux", "finish"};
+    int sl[3];
+    for (int q = 0; q < 3; q++) sl[q] = c->prof.enabled ? c->prof.slot(kNames[q]) : -1;
+    jfnk_prof_begin(c, sl[0]);
+    if (c->law == JFNK_LAW_LINEAR)
+        k_grad<JFNK_LAW_LINEAR><<<nblk(m.nc, 128), 128, 0, s>>>(gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr,
+                                                                 m.sell_l, m.n_slots, u_int, c->G, c->T, c->mu, c->kappa);
+    else
+        k_grad<JFNK_LAW_NEOHOOKEAN><<<nblk(m.nc, 128), 128, 0, s>>>(gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr,
+                                                                     m.sell_l, m.n_slots, u_int, c->G, c->T, c->mu, c->kappa);
+    JF_LAUNCHED(c);
+    jfnk_prof_end(c, sl[0]);
+    if (m.nflux > 0) {
+        jfnk_prof_begin(c, sl[1]);
+        if (c->law == JFNK_LAW_LINEAR)
+            k_flux<JFNK_LAW_LINEAR><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
+                                                                        u_int, c->G, c->T, m.bval, c->load, c->F);
+        else
+            k_flux<JFNK_LAW_NEOHOOKEAN><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
+                                                                            u_int, c->G, c->T, m.bval, c->load, c->F);
+        JF_LAUNCHED(c);
+        jfnk_prof_end(c, sl[1]);
+    }
+    jfnk_prof_begin(c, sl[2]);
+    k_finish<<<nblk(m.nc, 256), 256, 0, s>>>(m.nc, m.nflux, m.dim, m.fo_ptr, m.fn_ptr, m.fn_face, m.fd_ptr, c->F, m.b0,
+                                            c->load, mode, c->Ru, eps_dev, gate, out);
+    JF_LAUNCHED(c);
+    jfnk_prof_end(c, sl[2]);
+    return JFNK_OK;
+}
+
+int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev)
+{
+    return residual_gated(c, u_int, out, mode, eps_dev, nullptr);
+}
+
+}  // namespace jfnk

@@ -1,0 +1,328 @@
+// Host-side set-up of the mesh topology: validation, reverse Cuthill-McKee cell numbering,
+// face reordering (owner-sorted internal faces with owner < neighbour, boundary faces grouped
+// by condition), the cell-to-face lists and the sliced-ELL neighbour table of the gradient
+// kernel; plus the aggregation multigrid hierarchy on -J~.  Runs once per mesh (off the hot
+// path); everything it builds is uploaded and used by the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+
+#include "jfnk_internal.h"
+
+namespace jfnk {
+
+static std::vector<int32_t> rcm_order(int nc, const std::vector<std::vector<int32_t>>& adj)
+{
+    // Reverse Cuthill-McKee (Cuthill & McKee 1969; George 1971): breadth-first search from a
+    // minimum-degree cell of each component, visiting neighbours by increasing degree (then
+    // index), and the final order reversed.
+    std::vector<int32_t> deg(nc);
+    for (int i = 0; i < nc; i++) deg[i] = (int32_t)adj[i].size();
+    std::vector<int32_t> cand(nc);
+    std::iota(cand.begin(), cand.end(), 0);
+    std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return deg[a] < deg[b]; });
+    std::vector<char> seen(nc, 0);
+    std::vector<int32_t> order;
+    order.reserve(nc);
+    std::vector<int32_t> nb;
+    for (int s : cand) {
+        if (seen[s]) continue;
+        size_t head = order.size();
+        order.push_back(s);
+        seen[s] = 1;
+        while (head < order.size()) {
+            int v = order[head++];
+            nb.clear();
+            for (int w : adj[v])
+                if (!seen[w]) nb.push_back(w);
+            std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
+            for (int w : nb) {
+                seen[w] = 1;
+                order.push_back(w);
+            }
+        }
+    }
+    std::reverse(order.begin(), order.end());
+    return order;
+}
+
+std::string build_topology(const HostMesh& hm, bool rcm, Topology& t)
+{
+    const int nc = hm.nc, ni = hm.ni, nf = hm.nf;
+    t = Topology();
+    t.nc = nc;
+    // --- cell numbering
+    if (rcm) {
+        std::vector<std::vector<int32_t>> adj(nc);
+        for (int f = 0; f < ni; f++) {
+            adj[hm.own[f]].push_back(hm.nei[f]);
+            adj[hm.nei[f]].push_back(hm.own[f]);
+        }
+        t.n2o = rcm_order(nc, adj);
+    } else {
+        t.n2o.resize(nc);
+        std::iota(t.n2o.begin(), t.n2o.end(), 0);
+    }
+    t.o2n.assign(nc, -1);
+    for (int i = 0; i < nc; i++) t.o2n[t.n2o[i]] = i;
+    // --- face order
+    struct FK { int32_t a, b, src; uint8_t flip; };
+    std::vector<FK> in(ni);
+    for (int f = 0; f < ni; f++) {
+        int a = t.o2n[hm.own[f]], b = t.o2n[hm.nei[f]];
+        uint8_t flip = 0;
+        if (a > b) { std::swap(a, b); flip = 1; }
+        in[f] = {a, b, f, flip};
+    }
+    std::sort(in.begin(), in.end(), [](const FK& x, const FK& y) {
+        return x.a != y.a ? x.a < y.a : (x.b != y.b ? x.b < y.b : x.src < y.src);
+    });
+    std::vector<FK> bd[3];  // disp, trac, empty
+    for (int f = ni; f < nf; f++) {
+        int bt = hm.btype[f - ni];
+        int cls = bt == JFNK_BC_DISP ? 0 : (bt == JFNK_BC_TRAC ? 1 : 2);
+        bd[cls].push_back({t.o2n[hm.own[f]], -1, f, 0});
+    }
+    for (auto& v : bd)
+        std::sort(v.begin(), v.end(), [](const FK& x, const FK& y) { return x.a != y.a ? x.a < y.a : x.src < y.src; });
+    t.ni = ni;
+    t.nd = (int)bd[0].size();
+    t.nt = (int)bd[1].size();
+    t.ne = (int)bd[2].size();
+    t.nf = nf;
+    std::vector<FK> all;
+    all.reserve(nf);
+    all.insert(all.end(), in.begin(), in.end());
+    for (auto& v : bd) all.insert(all.end(), v.begin(), v.end());
+    t.face_src.resize(nf);
+    t.face_flip.resize(nf);
+    t.own.resize(nf);
+    t.nei.resize(ni);
+    t.fptr.assign(nf + 1, 0);
+    t.fpts.clear();
+    t.fpts.reserve(hm.fpts.size());
+    for (int f = 0; f < nf; f++) {
+        const FK& k = all[f];
+        t.face_src[f] = k.src;
+        t.face_flip[f] = k.flip;
+        t.own[f] = k.a;
+        if (f < ni) t.nei[f] = k.b;
+        int s0 = hm.fptr[k.src], s1 = hm.fptr[k.src + 1];
+        if (!k.flip)
+            for (int q = s0; q < s1; q++) t.fpts.push_back(hm.fpts[q]);
+        else
+            for (int q = s1 - 1; q >= s0; q--) t.fpts.push_back(hm.fpts[q]);
+        t.fptr[f + 1] = (int32_t)t.fpts.size();
+    }
+    int bw = 0;
+    for (int f = 0; f < ni; f++) bw = std::max(bw, t.nei[f] - t.own[f]);
+    t.bandwidth = bw;
+    // --- per-cell ranges
+    auto ranges = [&](int lo, int hi, std::vector<int32_t>& ptr) {
+        ptr.assign(nc + 1, 0);
+        for (int f = lo; f < hi; f++) ptr[t.own[f] + 1]++;
+        for (int P = 0; P < nc; P++) ptr[P + 1] += ptr[P];
+        for (int P = 0; P <= nc; P++) ptr[P] += lo;
+    };
+    ranges(0, ni, t.fo_ptr);
+    ranges(ni, ni + t.nd, t.fd_ptr);
+    ranges(ni + t.nd, ni + t.nd + t.nt, t.ft_ptr);
+    // neighbour-sorted internal faces
+    t.fn_ptr.assign(nc + 1, 0);
+    for (int f = 0; f < ni; f++) t.fn_ptr[t.nei[f] + 1]++;
+    for (int P = 0; P < nc; P++) t.fn_ptr[P + 1] += t.fn_ptr[P];
+    t.fn_face.resize(ni);
+    {
+        std::vector<int32_t> fill(t.fn_ptr.begin(), t.fn_ptr.end() - 1);
+        for (int f = 0; f < ni; f++) t.fn_face[fill[t.nei[f]]++] = f;
+    }
+    // all faces of each cell (geometry): owner side f, neighbour side ~f, by face index
+    t.ca_ptr.assign(nc + 1, 0);
+    for (int f = 0; f < nf; f++) {
+        t.ca_ptr[t.own[f] + 1]++;
+        if (f < ni) t.ca_ptr[t.nei[f] + 1]++;
+    }
+    for (int P = 0; P < nc; P++) t.ca_ptr[P + 1] += t.ca_ptr[P];
+    t.ca_face.resize(t.ca_ptr[nc]);
+    {
+        std::vector<int32_t> fill(t.ca_ptr.begin(), t.ca_ptr.end() - 1);
+        for (int f = 0; f < nf; f++) {
+            t.ca_face[fill[t.own[f]]++] = f;
+            if (f < ni) t.ca_face[fill[t.nei[f]]++] = ~f;
+        }
+    }
+    // sliced ELL of internal neighbours (32 cells per slice), faces in increasing index
+    std::vector<int32_t> cnt(nc, 0);
+    for (int f = 0; f < ni; f++) { cnt[t.own[f]]++; cnt[t.nei[f]]++; }
+    const int ns = (nc + 31) / 32;
+    t.sell_off.resize(ns + 1);
+    t.sell_w.resize(ns);
+    int off = 0;
+    for (int s = 0; s < ns; s++) {
+        int w = 0;
+        for (int l = 0; l < 32 && 32 * s + l < nc; l++) w = std::max(w, cnt[32 * s + l]);
+        t.sell_off[s] = off;
+        t.sell_w[s] = w;
+        off += 32 * w;
+    }
+    t.sell_off[ns] = off;
+    t.n_slots = off;
+    t.sell_nbr.assign(off, -1);
+    t.sell_face.assign(off, -1);
+    std::vector<int32_t> k(nc, 0);
+    // walk each cell's internal faces in increasing face index: merge owner and neighbour lists
+    for (int P = 0; P < nc; P++) {
+        int a = t.fo_ptr[P], ae = t.fo_ptr[P + 1];
+        int b = t.fn_ptr[P], be = t.fn_ptr[P + 1];
+        int s = P / 32, lane = P % 32;
+        while (a < ae || b < be) {
+            int f, N;
+            if (b >= be || (a < ae && a < t.fn_face[b])) { f = a; N = t.nei[a]; a++; }
+            else { f = t.fn_face[b]; N = t.own[f]; b++; }
+            int slot = t.sell_off[s] + 32 * k[P] + lane;
+            t.sell_nbr[slot] = N;
+            t.sell_face[slot] = f;
+            k[P]++;
+        }
+    }
+    // boundary values in the new face order
+    t.bval.assign((size_t)(t.nd + t.nt) * 3, 0.0);
+    for (int f = ni; f < ni + t.nd + t.nt; f++)
+        for (int c = 0; c < 3; c++) t.bval[(size_t)(f - ni) * 3 + c] = hm.bval[(size_t)(t.face_src[f] - ni) * 3 + c];
+    return "";
+}
+
+// ------------------------------------------------------------------ aggregation multigrid
+// Plain aggregation on A = -J~, rows visited in the input cell order:
+//   strong(i, j):  -a_ij >= theta * max_k(-a_ik), values within a relative 1e-10 counting as
+//                  equal so that rounding does not decide ties;
+//   pass 1:        a free row whose strong neighbours are all free starts an aggregate;
+//   pass 2:        a remaining row joins the aggregate of its strongest aggregated neighbour
+//                  (lowest index among equals), else forms a singleton;
+//   P piecewise constant, A_c = P^T A P, until coarse_max rows, max_levels, or < 10% shrink.
+static int aggregate(const MgLevelHost& L, double theta, std::vector<int32_t>& agg)
+{
+    const double tie = 1e-10;
+    const int n = L.n;
+    agg.assign(n, -1);
+    std::vector<char> strong(L.col.size(), 0);
+    for (int i = 0; i < n; i++) {
+        double mx = 0;
+        for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
+            if (L.col[q] != i) mx = std::max(mx, -L.val[q]);
+        for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
+            strong[q] = (L.col[q] != i && mx > 0 && -L.val[q] >= theta * mx * (1.0 - tie));
+    }
+    int na = 0;
+    for (int i = 0; i < n; i++) {
+        if (agg[i] >= 0) continue;
+        bool ok = true;
+        int ns = 0;
+        for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
+            if (strong[q]) {
+                ns++;
+                if (agg[L.col[q]] >= 0) ok = false;
+            }
+        if (!ok || ns == 0) continue;
+        agg[i] = na;
+        for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
+            if (strong[q]) agg[L.col[q]] = na;
+        na++;
+    }
+    for (int i = 0; i < n; i++) {
+        if (agg[i] >= 0) continue;
+        double mx = 0;
+        for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
+            if (L.col[q] != i && agg[L.col[q]] >= 0) mx = std::max(mx, -L.val[q]);
+        int best = -1;
+        if (mx > 0)
+            for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
+                if (L.col[q] != i && agg[L.col[q]] >= 0 && -L.val[q] >= mx * (1.0 - tie)) { best = L.col[q]; break; }
+        agg[i] = best >= 0 ? agg[best] : na++;
+    }
+    return na;
+}
+
+std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels, int coarse_max,
+                               std::vector<MgLevelHost>& levels, std::vector<double>& chol)
+{
+    levels.clear();
+    levels.push_back(std::move(fine));
+    const int cap = max_levels > 0 ? max_levels : 25;
+    while ((int)levels.size() < cap && levels.back().n > coarse_max) {
+        MgLevelHost& F = levels.back();
+        std::vector<int32_t> agg;
+        int nco = aggregate(F, theta, agg);
+        if (nco > 0.9 * F.n) break;
+        F.agg = agg;
+        MgLevelHost Cl;
+        Cl.n = nco;
+        std::vector<int32_t> aptr(nco + 1, 0), arow(F.n);
+        for (int i = 0; i < F.n; i++) aptr[agg[i] + 1]++;
+        for (int a = 0; a < nco; a++) aptr[a + 1] += aptr[a];
+        {
+            std::vector<int32_t> fill(aptr.begin(), aptr.end() - 1);
+            for (int i = 0; i < F.n; i++) arow[fill[agg[i]]++] = i;
+        }
+        std::vector<double> acc(nco, 0.0);
+        std::vector<int32_t> mark(nco, -1), list;
+        Cl.rp.assign(nco + 1, 0);
+        for (int a = 0; a < nco; a++) {
+            list.clear();
+            for (int t = aptr[a]; t < aptr[a + 1]; t++) {
+                int i = arow[t];
+                for (int q = F.rp[i]; q < F.rp[i + 1]; q++) {
+                    int b = agg[F.col[q]];
+                    if (mark[b] != a) { mark[b] = a; acc[b] = 0.0; list.push_back(b); }
+                    acc[b] += F.val[q];
+                }
+            }
+            std::sort(list.begin(), list.end());
+            for (int b : list) { Cl.col.push_back(b); Cl.val.push_back(acc[b]); }
+            Cl.rp[a + 1] = (int32_t)Cl.col.size();
+        }
+        levels.push_back(std::move(Cl));
+    }
+    // explicit inverse of the coarsest matrix via its Cholesky factor
+    const MgLevelHost& Lc = levels.back();
+    const int n = Lc.n;
+    std::vector<double> A((size_t)n * n, 0.0);
+    for (int i = 0; i < n; i++)
+        for (int q = Lc.rp[i]; q < Lc.rp[i + 1]; q++) A[(size_t)i * n + Lc.col[q]] = Lc.val[q];
+    for (int j = 0; j < n; j++) {
+        double s = A[(size_t)j * n + j];
+        for (int q = 0; q < j; q++) s -= A[(size_t)j * n + q] * A[(size_t)j * n + q];
+        if (!(s > 0)) {
+            char buf[96];
+            snprintf(buf, sizeof buf, "coarse multigrid matrix not positive definite at row %d", j);
+            return buf;
+        }
+        double d = std::sqrt(s);
+        A[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; i++) {
+            double t = A[(size_t)i * n + j];
+            for (int q = 0; q < j; q++) t -= A[(size_t)i * n + q] * A[(size_t)j * n + q];
+            A[(size_t)i * n + j] = t / d;
+        }
+    }
+    // inverse: solve L L^T X = I column by column
+    chol.assign((size_t)n * n, 0.0);
+    std::vector<double> y(n);
+    for (int c = 0; c < n; c++) {
+        for (int i = 0; i < n; i++) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int q = 0; q < i; q++) s -= A[(size_t)i * n + q] * y[q];
+            y[i] = s / A[(size_t)i * n + i];
+        }
+        for (int i = n - 1; i >= 0; i--) {
+            double s = y[i];
+            for (int q = i + 1; q < n; q++) s -= A[(size_t)q * n + i] * y[q];
+            y[i] = s / A[(size_t)i * n + i];
+        }
+        for (int i = 0; i < n; i++) chol[(size_t)i * n + c] = y[i];
+    }
+    return "";
+}
+
+}  // namespace jfnk

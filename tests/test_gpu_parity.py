@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP64 both sides, different summation orders):
+  * geometry, gradient, residual: |x_gpu - x_orc| / |x_orc| <= 1e-12 at generic u;
+  * Jv: the finite-difference quotient amplifies the ~1e-16 relative difference of the two
+    residual evaluations by |R| / (eps |Jv|):  tol = 1e-12 (|R(u)| / (eps |Jv|) + 1);
+  * solutions of Newton solves run on both sides to |R| <= 1e-11 |R0|: relative difference
+    <= 1e-8 (the stated displacement tolerance).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_17217_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _solver(case, **kw):
+    from paper_2502_17217_gb300 import jfnk
+    return jfnk.Solver.from_case(case, **kw)
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+CASES = {
+    "mms2d_32": lambda: I.case_mms2d(32),
+    "mms2d_24_perturbed": lambda: I.case_mms2d(24, perturb=0.15, seed=4),
+    "cantilever_40x8x8": lambda: I.case_cantilever(40, 8, 8, (1.0, 0.2, 0.2), perturb=0.15, seed=2),
+    "cantilever_ragged_37x5x3": lambda: I.case_cantilever(37, 5, 3, (1.0, 0.14, 0.08), perturb=0.15, seed=7),
+    "nh_beam_24x6x6": lambda: I.case_nh_beam(24, 6, 6, (1.0, 0.25, 0.25), end_uy=0.2, perturb=0.1, seed=3),
+}
+
+
+@pytest.mark.parametrize("renumber", [1, 0])
+@pytest.mark.parametrize("name", list(CASES))
+def test_geometry_and_residual_parity(name, renumber):
+    case = CASES[name]()
+    s = _solver(case, renumber=renumber)
+    o = O.Oracle.from_case(case)
+    for a, b in zip(s.geometry(), o.geometry()):
+        assert _rel(a, b) <= 1e-13
+    scale = 0.05 if case.material.law == I.LAW_NEOHOOKEAN else 1e-4
+    for seed in (1, 2):
+        u = I.random_field(seed, case.mesh.n_cells, scale, dim=case.mesh.dim)
+        R = s.residual(u)
+        Ro = o.residual(u)
+        assert _rel(R, Ro) <= 1e-12, _rel(R, Ro)
+        g = s.gradient()
+        assert _rel(g, o.gradient(u)) <= 1e-12
+    # load factor scales prescribed values and body force
+    s.set_load_factor(0.37)
+    o.set_load_factor(0.37)
+    u = I.random_field(3, case.mesh.n_cells, scale, dim=case.mesh.dim)
+    assert _rel(s.residual(u), o.residual(u)) <= 1e-12
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_jv_parity(name):
+    case = CASES[name]()
+    s = _solver(case)
+    o = O.Oracle.from_case(case)
+    scale = 0.05 if case.material.law == I.LAW_NEOHOOKEAN else 1e-4
+    u = I.random_field(4, case.mesh.n_cells, scale, dim=case.mesh.dim)
+    v = I.random_field(5, case.mesh.n_cells, 1.0, dim=case.mesh.dim)
+    Jv = s.jv(u, v)
+    Jo = o.jv(u, v)
+    Ru = o.residual(u)
+    eps = 1e-7 * (1 + np.linalg.norm(u)) / np.linalg.norm(v)
+    tol = 1e-12 * (np.linalg.norm(Ru) / (eps * np.linalg.norm(Jo)) + 1.0)
+    assert _rel(Jv, Jo) <= tol, (_rel(Jv, Jo), tol)
+    # zero direction
+    assert np.all(s.jv(u, np.zeros_like(v)) == 0)
+
+
+@pytest.mark.parametrize("name", ["cantilever_40x8x8", "mms2d_24_perturbed"])
+def test_block_jacobi_parity(name):
+    from paper_2502_17217_gb300 import jfnk
+    case = CASES[name]()
+    s = _solver(case)
+    o = O.Oracle.from_case(case)
+    v = I.random_field(8, case.mesh.n_cells, 1.0, dim=case.mesh.dim)
+    assert _rel(s.precondition(v, jfnk.PC_BJACOBI), o.bjacobi(v)) <= 1e-14
+    assert _rel(s.precondition(v, jfnk.PC_NONE), v) == 0.0
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 2e-5)])
+def test_multigrid_vcycle_parity(precision, tol):
+    """Same hierarchy on both sides (aggregation in the caller's cell order); FP64 V-cycle
+    agrees to round-off, the FP32 V-cycle to single precision."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(40, 8, 8, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
+    s = _solver(case, pc=jfnk.PC_MG, precision=precision, mg_coarse_max=200)
+    o = O.Oracle.from_case(case)
+    o.mg_setup(theta=0.25, max_levels=25, coarse_max=200)
+    v = I.random_field(9, case.mesh.n_cells, 1.0)
+    z = s.precondition(v, jfnk.PC_MG)
+    zo = o.mg_vcycle(v)
+    assert _rel(z, zo) <= tol, _rel(z, zo)
+
+
+def _solve_both(case, pc=1, load_steps=1, **kw):
+    from paper_2502_17217_gb300 import jfnk
+    s = _solver(case, pc=pc, newton_rtol=1e-11, **kw)
+    ug, st, rc = s.solve(load_steps=load_steps)
+    assert rc == 0, (rc, st.final_rel_res, st.newton_its, st.gmres_its)
+    o = O.Oracle.from_case(case)
+    if pc == jfnk.PC_MG:
+        o.mg_setup(coarse_max=s.options.mg_coarse_max)
+    uo, rco, sto = o.newton(load_steps=load_steps, rtol=1e-11, pc=pc)
+    assert rco == 0
+    return ug, uo, st, sto
+
+
+def test_solve_parity_config1_mms2d():
+    """2-D plane-strain MMS, 32x32, JFNK + GMRES(30) + block-Jacobi, eps = 1e-7 (1+|u|)/|v|."""
+    ug, uo, st, sto = _solve_both(I.case_mms2d(32))
+    assert _rel(ug, uo) <= 1e-8
+    assert st.newton_its <= 10
+
+
+def test_solve_parity_multigrid_and_mixed_precision():
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(20, 4, 4, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
+    ug, uo, st, _ = _solve_both(case, pc=jfnk.PC_MG, mg_coarse_max=50)
+    assert _rel(ug, uo) <= 1e-8
+    ugm, _, stm, _ = _solve_both(case, pc=jfnk.PC_MG, mg_coarse_max=50, precision=jfnk.PREC_MIXED)
+    assert _rel(ugm, uo) <= 1e-8
+
+
+def test_solve_parity_neo_hookean_load_steps():
+    case = I.case_nh_beam(16, 4, 4, (1.0, 0.25, 0.25), end_uy=0.25, load_steps=3)
+    ug, uo, st, _ = _solve_both(case, load_steps=3)
+    assert _rel(ug, uo) <= 1e-8
+    assert st.load_steps_done == 3
+
+
+def test_device_pointer_path_matches_host_path():
+    import torch
+    case = CASES["cantilever_ragged_37x5x3"]()
+    s = _solver(case)
+    u = I.random_field(1, case.mesh.n_cells, 1e-4)
+    v = I.random_field(2, case.mesh.n_cells, 1.0)
+    Rh = s.residual(u)
+    Rd = s.residual(torch.from_numpy(u).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(Rh, Rd.cpu().numpy())
+    Jh = s.jv(u, v)
+    Jd = s.jv(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(Jh, Jd.cpu().numpy())
+
+
+def test_bitwise_deterministic():
+    case = CASES["nh_beam_24x6x6"]()
+    s = _solver(case)
+    u = I.random_field(3, case.mesh.n_cells, 0.05)
+    a, b = s.residual(u), s.residual(u)
+    assert np.array_equal(a, b)
+    u1, st1, _ = s.solve()
+    u2, st2, _ = s.solve()
+    assert np.array_equal(u1, u2) and st1.gmres_its == st2.gmres_its
+
+
+def test_invalid_inputs_fail_cleanly():
+    from paper_2502_17217_gb300 import jfnk
+    m = I.hex_box(4, 3, 3)
+    with pytest.raises(jfnk.JfnkError):
+        bad = I.hex_box(4, 3, 3)
+        bad.neighbour = bad.neighbour.copy()
+        bad.neighbour[0] = bad.owner[0]
+        jfnk.Solver(bad, I.Material(I.LAW_LINEAR, 1.0, 0.3))
+    s = jfnk.Solver(m, I.Material(I.LAW_LINEAR, 1.0, 0.3))
+    with pytest.raises(jfnk.JfnkError):
+        s._check(s.L.jfnk_set_patch(s.h, m.patch("xmin").start, 3, jfnk.BC_SYMM, None))
+    with pytest.raises(jfnk.JfnkError):
+        s._check(s.L.jfnk_set_material(s.h, jfnk.LAW_LINEAR, -1.0, 0.3))
+    # a one-cell-wide direction gives a singular least-squares tensor
+    thin = I.hex_box(5, 1, 3)
+    s2 = jfnk.Solver(thin, I.Material(I.LAW_LINEAR, 1.0, 0.3))
+    with pytest.raises(jfnk.JfnkError, match="singular"):
+        s2.setup()
+    # the context stays usable after an error
+    s.setup()
+    assert s.residual(np.zeros((m.n_cells, 3))).shape == (m.n_cells, 3)
+
+
+def test_all_traction_problem_and_zero_load():
+    case = I.case_cantilever(10, 4, 4, (1.0, 0.4, 0.4), perturb=0.1, seed=5)
+    for p in case.mesh.patches:
+        p.bc = I.BC_TRAC
+        p.values = None
+    s = _solver(case)
+    o = O.Oracle.from_case(case)
+    u = I.random_field(1, case.mesh.n_cells, 1e-4)
+    assert _rel(s.residual(u), o.residual(u)) <= 1e-12
+    # zero residual at u = 0 and zero load: Newton returns at once
+    case0 = I.case_cantilever(10, 4, 4, (1.0, 0.4, 0.4), traction=(0.0, 0.0, 0.0))
+    s0 = _solver(case0)
+    u0, st, rc = s0.solve()
+    assert rc == 0 and st.newton_its == 0 and np.all(u0 == 0)
