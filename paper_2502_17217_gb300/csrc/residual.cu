@@ -61,8 +61,10 @@ __global__ void __launch_bounds__(128) k_grad(const int* __restrict__ gate, int 
         const double b11 = F10 * F10 + F11 * F11 + F12 * F12;
         const double b12 = F10 * F20 + F11 * F21 + F12 * F22;
         const double b22 = F20 * F20 + F21 * F21 + F22 * F22;
+        // an inverted cell (J <= 0) has no stress: NaN makes the residual non-finite so the
+        // line search rejects the state
         const double cj = cbrt(J);
-        const double Jm23 = 1.0 / (cj * cj);
+        const double Jm23 = (J > 0.0) ? 1.0 / (cj * cj) : __longlong_as_double(0x7ff8000000000000LL);
         const double rJ = 1.0 / J;
         const double cm = mu * rJ * Jm23;                       // mu/J J^-2/3
         const double tr3 = (b00 + b11 + b22) * (1.0 / 3.0);
