@@ -75,7 +75,8 @@ typedef struct jfnk_options {
     int mg_max_levels;      /* multigrid levels (Sec. 4.2: up to 25)                   (25)  */
     int mg_coarse_max;      /* rows of the coarsest (dense Cholesky) level             (2000)*/
     double mg_theta;        /* strength threshold of the aggregation                   (0.25)*/
-    int mg_smooth_sweeps;   /* Jacobi sweeps before and after the coarse correction    (1)   */
+    int mg_smooth_sweeps;   /* Jacobi sweeps before and after the coarse correction    (2)   */
+    int mg_smoothed;        /* 1: smoothed-aggregation prolongation, 0: piecewise constant (1) */
 } jfnk_options;
 
 typedef struct jfnk_stats {
@@ -89,6 +90,7 @@ typedef struct jfnk_stats {
     double solve_ms;         /* wall time of the solve on the host clock                    */
     double hist[64];         /* |R| after each Newton iteration (first 64)                  */
     int n_hist;
+    int reorth_its;          /* Arnoldi iterations that needed a second Gram-Schmidt pass   */
 } jfnk_stats;
 
 typedef struct jfnk_ctx jfnk_ctx;

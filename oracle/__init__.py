@@ -61,6 +61,8 @@ def lib():
             "orc_jtilde_diag": (None, [vp, vp]),
             "orc_bjacobi": (None, [vp, vp, vp]),
             "orc_mg_setup": (i, [vp, d, i, i]),
+            "orc_mg_setup_ex": (i, [vp, d, i, i, i]),
+            "orc_mg_set_sweeps": (None, [vp, i, i]),
             "orc_mg_levels": (i, [vp, vp]),
             "orc_mg_aggregates": (i, [vp, i, vp]),
             "orc_mg_vcycle": (None, [vp, vp, vp]),
@@ -188,8 +190,9 @@ class Oracle:
         lib().orc_bjacobi(self.h, _p(v), _p(z))
         return z
 
-    def mg_setup(self, theta=0.25, max_levels=25, coarse_max=2000):
-        return self._check(lib().orc_mg_setup(self.h, theta, max_levels, coarse_max))
+    def mg_setup(self, theta=0.25, max_levels=25, coarse_max=1000, smoothed=False, sweeps=1):
+        lib().orc_mg_set_sweeps(self.h, sweeps, sweeps)
+        return self._check(lib().orc_mg_setup_ex(self.h, theta, max_levels, coarse_max, 1 if smoothed else 0))
 
     def mg_levels(self):
         n = lib().orc_mg_levels(self.h, None)

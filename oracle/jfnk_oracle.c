@@ -41,7 +41,11 @@ struct orc_problem {
     int** mg_col;
     double** mg_val;
     int** mg_agg;       /* aggregate of each row of level l (l < levels-1) */
+    int** mg_prp;       /* prolongation P_l (n_l x n_l+1) in CSR */
+    int** mg_pcol;
+    double** mg_pval;
     double* mg_chol;    /* dense Cholesky factor of the coarsest level */
+    int mg_pre, mg_post; /* Jacobi sweeps before / after the coarse correction */
     char err[256];
 };
 
@@ -124,9 +128,12 @@ static void mg_free(orc_problem* p)
     for (int l = 0; l < p->mg_levels; l++) {
         free(p->mg_rowptr[l]); free(p->mg_col[l]); free(p->mg_val[l]);
         if (p->mg_agg && p->mg_agg[l]) free(p->mg_agg[l]);
+        if (p->mg_prp && p->mg_prp[l]) { free(p->mg_prp[l]); free(p->mg_pcol[l]); free(p->mg_pval[l]); }
     }
     free(p->mg_rowptr); free(p->mg_col); free(p->mg_val); free(p->mg_agg); free(p->mg_n); free(p->mg_chol);
+    free(p->mg_prp); free(p->mg_pcol); free(p->mg_pval);
     p->mg_rowptr = NULL; p->mg_col = NULL; p->mg_val = NULL; p->mg_agg = NULL; p->mg_n = NULL; p->mg_chol = NULL;
+    p->mg_prp = NULL; p->mg_pcol = NULL; p->mg_pval = NULL;
     p->mg_levels = 0;
 }
 
@@ -631,16 +638,20 @@ void orc_bjacobi(const orc_problem* p, const double* v, double* z)
 
 /* ------------------------------------------------------------------ multigrid on A = -J~
  * The paper uses HYPRE BoomerAMG (Sec. 4.2: one V-cycle per Krylov iteration, one pre- and
- * one post-smoothing sweep).  Reading: a plain aggregation AMG stands in for it.
+ * one post-smoothing sweep, interpolation with truncation).  Reading: an aggregation AMG
+ * stands in for it.
  *   strength: j is strong for i if -a_ij >= theta * max_k(-a_ik) (values within a relative
  *             1e-10 count as equal, so ties do not depend on rounding);
  *   pass 1:   rows in index order; a row whose strong neighbours are all free starts an
  *             aggregate with them;
  *   pass 2:   each remaining row joins the aggregate of its strongest aggregated neighbour
  *             (lowest index among equals), else becomes a singleton;
- *   P:        piecewise constant; A_c = P^T A P; coarsening stops at coarse_max rows,
- *             max_levels levels, or when a level shrinks by less than 10%;
- *   smoother: Jacobi with weight 2/3, one sweep before and one after the coarse correction;
+ *   P:        piecewise constant (plain), or smoothed: P = (I - omega D^-1 A) P_tent with
+ *             omega = 4 / (3 rho), rho the Gershgorin bound max_i sum_j |a_ij| / a_ii;
+ *   A_c = P^T A P; coarsening stops at coarse_max rows, max_levels levels, or when a level
+ *             shrinks by less than 10%;
+ *   smoother: Jacobi with weight 2/3, `pre` sweeps before and `post` after the coarse
+ *             correction (1 and 1 as in Sec. 4.2 unless set);
  *   coarsest: dense Cholesky.  */
 #define MG_TIE 1e-10
 
@@ -684,15 +695,87 @@ static int mg_coarsen(int n, const int* rp, const int* col, const double* val, d
     return na;
 }
 
+/* y = P^T A P for CSR A (n x n) and CSR P (n x nco), rows of the result with ascending columns */
+static void galerkin(int n, const int* rp, const int* col, const double* val, int nco, const int* prp, const int* pcol,
+                     const double* pval, int** crp_out, int** ccol_out, double** cval_out)
+{
+    /* transpose of P */
+    int* tp = (int*)xcalloc((size_t)nco + 1, sizeof(int));
+    for (int i = 0; i < n; i++)
+        for (int k = prp[i]; k < prp[i + 1]; k++) tp[pcol[k] + 1]++;
+    for (int J = 0; J < nco; J++) tp[J + 1] += tp[J];
+    int* tr = (int*)xcalloc((size_t)prp[n], sizeof(int));
+    double* tv = (double*)xcalloc((size_t)prp[n], sizeof(double));
+    int* fill = (int*)xcalloc((size_t)nco, sizeof(int));
+    for (int i = 0; i < n; i++)
+        for (int k = prp[i]; k < prp[i + 1]; k++) {
+            int J = pcol[k];
+            tr[tp[J] + fill[J]] = i;
+            tv[tp[J] + fill[J]] = pval[k];
+            fill[J]++;
+        }
+    free(fill);
+    double* acc = (double*)xcalloc((size_t)nco, sizeof(double));
+    int* mark = (int*)xcalloc((size_t)nco, sizeof(int));
+    int* list = (int*)xcalloc((size_t)nco, sizeof(int));
+    for (int J = 0; J < nco; J++) mark[J] = -1;
+    int cap_nnz = 16 * nco + 16, nnz = 0;
+    int* crp = (int*)xcalloc((size_t)nco + 1, sizeof(int));
+    int* ccol = (int*)xcalloc((size_t)cap_nnz, sizeof(int));
+    double* cval = (double*)xcalloc((size_t)cap_nnz, sizeof(double));
+    for (int I = 0; I < nco; I++) {
+        int nl = 0;
+        for (int t = tp[I]; t < tp[I + 1]; t++) {
+            int i = tr[t];
+            double pI = tv[t];
+            for (int k = rp[i]; k < rp[i + 1]; k++) {
+                int j = col[k];
+                for (int q = prp[j]; q < prp[j + 1]; q++) {
+                    int J = pcol[q];
+                    if (mark[J] != I) { mark[J] = I; acc[J] = 0.0; list[nl++] = J; }
+                    acc[J] += pI * val[k] * pval[q];
+                }
+            }
+        }
+        for (int x = 1; x < nl; x++)
+            for (int y = x; y > 0 && list[y - 1] > list[y]; y--) { int t = list[y]; list[y] = list[y - 1]; list[y - 1] = t; }
+        if (nnz + nl > cap_nnz) {
+            while (nnz + nl > cap_nnz) cap_nnz *= 2;
+            ccol = (int*)realloc(ccol, sizeof(int) * (size_t)cap_nnz);
+            cval = (double*)realloc(cval, sizeof(double) * (size_t)cap_nnz);
+        }
+        for (int x = 0; x < nl; x++) { ccol[nnz] = list[x]; cval[nnz] = acc[list[x]]; nnz++; }
+        crp[I + 1] = nnz;
+    }
+    free(acc); free(mark); free(list); free(tp); free(tr); free(tv);
+    *crp_out = crp; *ccol_out = ccol; *cval_out = cval;
+}
+
 int orc_mg_setup(orc_problem* p, double theta, int max_levels, int coarse_max)
 {
+    return orc_mg_setup_ex(p, theta, max_levels, coarse_max, 0);
+}
+
+void orc_mg_set_sweeps(orc_problem* p, int pre, int post)
+{
+    p->mg_pre = pre > 0 ? pre : 1;
+    p->mg_post = post > 0 ? post : 1;
+}
+
+int orc_mg_setup_ex(orc_problem* p, double theta, int max_levels, int coarse_max, int smoothed)
+{
     mg_free(p);
+    if (p->mg_pre < 1) p->mg_pre = 1;
+    if (p->mg_post < 1) p->mg_post = 1;
     int cap = max_levels > 0 ? max_levels : 25;
     p->mg_n = (int*)xcalloc((size_t)cap, sizeof(int));
     p->mg_rowptr = (int**)xcalloc((size_t)cap, sizeof(int*));
     p->mg_col = (int**)xcalloc((size_t)cap, sizeof(int*));
     p->mg_val = (double**)xcalloc((size_t)cap, sizeof(double*));
     p->mg_agg = (int**)xcalloc((size_t)cap, sizeof(int*));
+    p->mg_prp = (int**)xcalloc((size_t)cap, sizeof(int*));
+    p->mg_pcol = (int**)xcalloc((size_t)cap, sizeof(int*));
+    p->mg_pval = (double**)xcalloc((size_t)cap, sizeof(double*));
     /* level 0: rows in cell order, columns ascending */
     int n = p->nc;
     int* rp = (int*)xcalloc((size_t)n + 1, sizeof(int));
@@ -715,7 +798,6 @@ int orc_mg_setup(orc_problem* p, double theta, int max_levels, int coarse_max)
             val[pos] = -face_coef(p, f, P);
             pos++;
         }
-        /* sort the row by column (insertion sort; rows are short) */
         for (int a = rp[P] + 1; a < rp[P + 1]; a++)
             for (int b = a; b > rp[P] && col[b - 1] > col[b]; b--) {
                 int tc = col[b]; col[b] = col[b - 1]; col[b - 1] = tc;
@@ -728,52 +810,65 @@ int orc_mg_setup(orc_problem* p, double theta, int max_levels, int coarse_max)
     L = 1;
     while (L < cap && p->mg_n[L - 1] > coarse_max) {
         int nf = p->mg_n[L - 1];
-        int* agg = (int*)xcalloc((size_t)nf, sizeof(int));
-        int nco = mg_coarsen(nf, p->mg_rowptr[L - 1], p->mg_col[L - 1], p->mg_val[L - 1], theta, agg);
-        if (nco > 0.9 * nf) { free(agg); break; }
-        p->mg_agg[L - 1] = agg;
-        /* Galerkin product with piecewise-constant P: dense accumulation row by row */
-        int* crp = (int*)xcalloc((size_t)nco + 1, sizeof(int));
-        /* rows of each aggregate */
-        int* aptr = (int*)xcalloc((size_t)nco + 1, sizeof(int));
-        for (int i = 0; i < nf; i++) aptr[agg[i] + 1]++;
-        for (int a = 0; a < nco; a++) aptr[a + 1] += aptr[a];
-        int* arow = (int*)xcalloc((size_t)nf, sizeof(int));
-        int* afill = (int*)xcalloc((size_t)nco, sizeof(int));
-        for (int i = 0; i < nf; i++) arow[aptr[agg[i]] + afill[agg[i]]++] = i;
-        free(afill);
-        double* acc = (double*)xcalloc((size_t)nco, sizeof(double));
-        int* mark = (int*)xcalloc((size_t)nco, sizeof(int));
-        for (int a = 0; a < nco; a++) mark[a] = -1;
-        int cap_nnz = 16 * nco + 16, nnz = 0;
-        int* ccol = (int*)xcalloc((size_t)cap_nnz, sizeof(int));
-        double* cval = (double*)xcalloc((size_t)cap_nnz, sizeof(double));
-        int* list = (int*)xcalloc((size_t)nco, sizeof(int));
         const int* frp = p->mg_rowptr[L - 1];
         const int* fcol = p->mg_col[L - 1];
         const double* fval = p->mg_val[L - 1];
-        for (int a = 0; a < nco; a++) {
-            int nl = 0;
-            for (int t = aptr[a]; t < aptr[a + 1]; t++) {
-                int i = arow[t];
+        int* agg = (int*)xcalloc((size_t)nf, sizeof(int));
+        int nco = mg_coarsen(nf, frp, fcol, fval, theta, agg);
+        if (nco > 0.9 * nf) { free(agg); break; }
+        p->mg_agg[L - 1] = agg;
+        /* prolongation */
+        int* prp = (int*)xcalloc((size_t)nf + 1, sizeof(int));
+        int* pcol;
+        double* pval;
+        if (!smoothed) {
+            pcol = (int*)xcalloc((size_t)nf, sizeof(int));
+            pval = (double*)xcalloc((size_t)nf, sizeof(double));
+            for (int i = 0; i < nf; i++) { prp[i + 1] = i + 1; pcol[i] = agg[i]; pval[i] = 1.0; }
+        } else {
+            double rho = 0.0;
+            for (int i = 0; i < nf; i++) {
+                double s = 0.0, d = 0.0;
                 for (int k = frp[i]; k < frp[i + 1]; k++) {
-                    int b = agg[fcol[k]];
-                    if (mark[b] != a) { mark[b] = a; acc[b] = 0.0; list[nl++] = b; }
-                    acc[b] += fval[k];
+                    s += fabs(fval[k]);
+                    if (fcol[k] == i) d = fval[k];
                 }
+                if (s / d > rho) rho = s / d;
             }
-            /* ascending columns */
-            for (int x = 1; x < nl; x++)
-                for (int y = x; y > 0 && list[y - 1] > list[y]; y--) { int t = list[y]; list[y] = list[y - 1]; list[y - 1] = t; }
-            if (nnz + nl > cap_nnz) {
-                while (nnz + nl > cap_nnz) cap_nnz *= 2;
-                ccol = (int*)realloc(ccol, sizeof(int) * (size_t)cap_nnz);
-                cval = (double*)realloc(cval, sizeof(double) * (size_t)cap_nnz);
+            double omega = 4.0 / (3.0 * rho);
+            int cap_p = 8 * nf + 8, np = 0;
+            pcol = (int*)xcalloc((size_t)cap_p, sizeof(int));
+            pval = (double*)xcalloc((size_t)cap_p, sizeof(double));
+            double* acc = (double*)xcalloc((size_t)nco, sizeof(double));
+            int* mark = (int*)xcalloc((size_t)nco, sizeof(int));
+            int* list = (int*)xcalloc((size_t)nco, sizeof(int));
+            for (int J = 0; J < nco; J++) mark[J] = -1;
+            for (int i = 0; i < nf; i++) {
+                double d = 0.0;
+                for (int k = frp[i]; k < frp[i + 1]; k++) if (fcol[k] == i) d = fval[k];
+                int nl = 0;
+                mark[agg[i]] = i; acc[agg[i]] = 1.0; list[nl++] = agg[i];
+                for (int k = frp[i]; k < frp[i + 1]; k++) {
+                    int J = agg[fcol[k]];
+                    if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list[nl++] = J; }
+                    acc[J] -= omega * fval[k] / d;
+                }
+                for (int x = 1; x < nl; x++)
+                    for (int y = x; y > 0 && list[y - 1] > list[y]; y--) { int t = list[y]; list[y] = list[y - 1]; list[y - 1] = t; }
+                if (np + nl > cap_p) {
+                    while (np + nl > cap_p) cap_p *= 2;
+                    pcol = (int*)realloc(pcol, sizeof(int) * (size_t)cap_p);
+                    pval = (double*)realloc(pval, sizeof(double) * (size_t)cap_p);
+                }
+                for (int x = 0; x < nl; x++) { pcol[np] = list[x]; pval[np] = acc[list[x]]; np++; }
+                prp[i + 1] = np;
             }
-            for (int x = 0; x < nl; x++) { ccol[nnz] = list[x]; cval[nnz] = acc[list[x]]; nnz++; }
-            crp[a + 1] = nnz;
+            free(acc); free(mark); free(list);
         }
-        free(acc); free(mark); free(list); free(aptr); free(arow);
+        p->mg_prp[L - 1] = prp; p->mg_pcol[L - 1] = pcol; p->mg_pval[L - 1] = pval;
+        int *crp, *ccol;
+        double* cval;
+        galerkin(nf, frp, fcol, fval, nco, prp, pcol, pval, &crp, &ccol, &cval);
         p->mg_n[L] = nco; p->mg_rowptr[L] = crp; p->mg_col[L] = ccol; p->mg_val[L] = cval;
         L++;
     }
@@ -857,17 +952,29 @@ static void vcycle(const orc_problem* p, int l, const double* b, double* x)
     double* r = (double*)xcalloc((size_t)n, sizeof(double));
     /* pre-smoothing from zero */
     for (int i = 0; i < n; i++) x[i] = omega * b[i] / row_diag(rp, col, val, i);
+    for (int s = 1; s < p->mg_pre; s++) {
+        spmv(n, rp, col, val, x, r);
+        for (int i = 0; i < n; i++) r[i] = x[i] + omega * (b[i] - r[i]) / row_diag(rp, col, val, i);
+        memcpy(x, r, sizeof(double) * (size_t)n);
+    }
     spmv(n, rp, col, val, x, r);
     for (int i = 0; i < n; i++) r[i] = b[i] - r[i];
     int nco = p->mg_n[l + 1];
     double* bc = (double*)xcalloc((size_t)nco, sizeof(double));
     double* xc = (double*)xcalloc((size_t)nco, sizeof(double));
-    const int* agg = p->mg_agg[l];
-    for (int i = 0; i < n; i++) bc[agg[i]] += r[i];
+    const int* prp = p->mg_prp[l];
+    const int* pcol = p->mg_pcol[l];
+    const double* pval = p->mg_pval[l];
+    for (int i = 0; i < n; i++)  /* b_c = P^T r */
+        for (int k = prp[i]; k < prp[i + 1]; k++) bc[pcol[k]] += pval[k] * r[i];
     vcycle(p, l + 1, bc, xc);
-    for (int i = 0; i < n; i++) x[i] += xc[agg[i]];
-    spmv(n, rp, col, val, x, r);
-    for (int i = 0; i < n; i++) x[i] += omega * (b[i] - r[i]) / row_diag(rp, col, val, i);
+    for (int i = 0; i < n; i++)  /* x += P x_c */
+        for (int k = prp[i]; k < prp[i + 1]; k++) x[i] += pval[k] * xc[pcol[k]];
+    for (int s = 0; s < p->mg_post; s++) {
+        spmv(n, rp, col, val, x, r);
+        for (int i = 0; i < n; i++) r[i] = x[i] + omega * (b[i] - r[i]) / row_diag(rp, col, val, i);
+        memcpy(x, r, sizeof(double) * (size_t)n);
+    }
     free(r); free(bc); free(xc);
 }
 

@@ -68,7 +68,11 @@ void orc_jtilde_diag(const orc_problem* p, double* diag /* [nc] */);
 void orc_bjacobi(const orc_problem* p, const double* v, double* z);
 
 /* multigrid on -J~ (scalar, shared by the components) */
-int orc_mg_setup(orc_problem* p, double theta, int max_levels, int coarse_max);
+int orc_mg_setup(orc_problem* p, double theta, int max_levels, int coarse_max);  /* plain aggregation */
+/* smoothed != 0: smoothed-aggregation prolongation */
+int orc_mg_setup_ex(orc_problem* p, double theta, int max_levels, int coarse_max, int smoothed);
+/* Jacobi sweeps before / after the coarse correction (default 1 and 1) */
+void orc_mg_set_sweeps(orc_problem* p, int pre, int post);
 int orc_mg_levels(const orc_problem* p, int* sizes /* [levels] or NULL */);
 int orc_mg_aggregates(const orc_problem* p, int level, int* agg /* [size of level] */);
 void orc_mg_vcycle(const orc_problem* p, const double* v, double* z);

@@ -79,6 +79,9 @@ void jfnk_prof_end(jfnk_ctx* c, int slot)
 static void free_device(jfnk_ctx* c)
 {
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->it_graph) cudaGraphExecDestroy(c->it_graph);
+    c->it_graph = nullptr;
+    c->load_on_device = -1.0;
     jfnk::mg_release(c);
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
@@ -129,7 +132,8 @@ void jfnk_default_options(jfnk_options* o)
     o->mg_max_levels = 25;
     o->mg_coarse_max = 1000;
     o->mg_theta = 0.25;
-    o->mg_smooth_sweeps = 1;
+    o->mg_smooth_sweeps = 2;
+    o->mg_smoothed = 1;
 }
 
 int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
@@ -162,6 +166,7 @@ int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
         delete c;
         return JFNK_ENOMEM;
     }
+    for (auto& e : c->it_ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
     c->cur = c->stream;
     *out = c;
     return JFNK_OK;
@@ -174,6 +179,8 @@ int jfnk_destroy(jfnk_ctx* c)
     free_device(c);
     for (auto& s : c->prof.slots)
         for (auto e : s.ev) cudaEventDestroy(e);
+    for (auto e : c->it_ev)
+        if (e) cudaEventDestroy(e);
     if (c->gh) cudaFreeHost(c->gh);
     if (c->scal_h) cudaFreeHost(c->scal_h);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -313,7 +320,8 @@ int jfnk_setup(jfnk_ctx* c)
     c->G = (double*)jfnk_dalloc(c, sizeof(double) * 9 * (size_t)nc);
     c->T = (double*)jfnk_dalloc(c, sizeof(double) * (c->law == JFNK_LAW_NEOHOOKEAN ? 9 * (size_t)nc : 1));
     c->F = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)std::max(1, c->dm.nflux));
-    c->partials = (double*)jfnk_dalloc(c, sizeof(double) * (size_t)jfnk::kRedBlocks * 2 * (jfnk::kMaxRestart + 2));
+    const size_t chunks = (v3 + 2047) / 2048 + 2 * (size_t)jfnk::kRedBlocks;
+    c->partials = (double*)jfnk_dalloc(c, sizeof(double) * chunks * (jfnk::kMaxRestart + 2));
     c->V_is_float = c->opt.precision == JFNK_PREC_MIXED;
     c->V_ld = (v3 + 63) / 64 * 64;
     const size_t vbytes = (c->V_is_float ? sizeof(float) : sizeof(double)) * c->V_ld * (size_t)(c->opt.gmres_restart + 1);

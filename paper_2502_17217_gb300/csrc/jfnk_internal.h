@@ -59,11 +59,14 @@ struct MgLevelHost {
     int n = 0;
     std::vector<int32_t> rp, col;
     std::vector<double> val;
-    std::vector<int32_t> agg;   // aggregate of each row (all but the coarsest level)
+    std::vector<int32_t> agg;              // aggregate of each row (all but the coarsest level)
+    std::vector<int32_t> prp, pcol;        // prolongation to the next level (CSR, n x n_next)
+    std::vector<double> pval;
 };
-// Aggregation hierarchy on A = -J~ given in CSR; returns "" on success.
-std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels, int coarse_max,
-                               std::vector<MgLevelHost>& levels, std::vector<double>& chol);
+// Aggregation hierarchy on A = -J~ given in CSR (plain or smoothed prolongation) and the
+// dense inverse of the coarsest matrix; returns "" on success.
+std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels, int coarse_max, bool smoothed,
+                               std::vector<MgLevelHost>& levels, std::vector<double>& inverse);
 
 // ------------------------------------------------------------------ device state
 struct DevMesh {
@@ -104,7 +107,10 @@ struct GmresDev {
     double inv;       // 1 / |w|
     double wn2;       // |w|^2 before orthogonalisation
     double res;       // |g_{k}| current residual estimate
-    double scratch[8];
+    int n_reorth;     // second Gram-Schmidt passes run (diagnostic)
+    int pad2;
+    double load;      // load factor read by the residual kernels
+    double scratch[6];
     double h[kMaxRestart + 1];
     double H[(kMaxRestart + 1) * kMaxRestart];  // column-major: H[i + (m+1) j]
     double g[kMaxRestart + 1];
@@ -138,6 +144,7 @@ struct jfnk_ctx {
     double p1 = 0, p2 = 0, mu = 0, lam = 0, kappa = 0, Kbar = 0;
     std::vector<double> fb_host;
     double load = 1.0;
+    double load_on_device = -1.0;      // value last copied to gd->load
     bool dirty = true;
     jfnk::Topology topo;
     jfnk::DevMesh dm;
@@ -152,6 +159,10 @@ struct jfnk_ctx {
     int V_is_float = 0;
     jfnk::GmresDev* gd = nullptr;        // device scalars
     jfnk::GmresDev* gh = nullptr;        // pinned host mirror
+    cudaGraphExec_t it_graph = nullptr;  // one captured Arnoldi iteration (replayed for every j)
+    cudaEvent_t it_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int use_graphs = 1;
+    int64_t graph_kernels = 0;           // kernels in the captured iteration
     double* scal = nullptr;              // device scalar scratch [16]
     double* scal_h = nullptr;            // pinned [16]
     unsigned* tickets = nullptr;         // [16]
@@ -198,6 +209,7 @@ enum ResidualOut { OUT_R = 0, OUT_JV = 1 };
 // from the device scalar `eps_dev`.
 int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev);
 int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate);
+int sync_load(jfnk_ctx* c);
 // linalg.cu
 int perm_in(jfnk_ctx* c, const double* ext_aos, double* int_soa);
 int perm_out(jfnk_ctx* c, const double* int_soa, double* ext_aos);
@@ -208,13 +220,14 @@ int norm_mode(jfnk_ctx* c, const double* x, size_t n, int mode, const int* gate)
 int perturb(jfnk_ctx* c, const double* u, const double* z, double* w, const int* gate);
 int cycle_init(jfnk_ctx* c, const double* r);
 int arnoldi_orthogonalise(jfnk_ctx* c, double* w);
-int arnoldi_finish_column(jfnk_ctx* c, const double* w, int j_host);
 int cycle_solution(jfnk_ctx* c, double* out);
 // precond.cu
 int pc_setup(jfnk_ctx* c);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);
 int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate);
+int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z,
+                 const int* gate);
 void mg_release(jfnk_ctx* c);
 int mg_levels_info(jfnk_ctx* c, std::vector<int>& sizes);
 // solver.cu

@@ -5,6 +5,7 @@
 // Every reduction runs on a fixed grid with warp-shuffle trees and a last-block finalisation
 // in fixed order, so results are bitwise reproducible.  Kernels of a GMRES cycle return at
 // once when the device flag `done` is set (converged, breakdown or cycle full).
+#include <algorithm>
 #include <cmath>
 
 #include "device_common.cuh"
@@ -118,103 +119,11 @@ __device__ __forceinline__ void finalize_values(const double* partials, int nblo
     __syncthreads();
 }
 
-// pass 0: h_i = V_i . w (i <= j), |w|^2;  pass 1 (only when gd->reorth): h_i again, added to H
-template <typename TV>
-__global__ void __launch_bounds__(kRedThreads) k_mdot(size_t n, const TV* __restrict__ V, size_t ld,
-                                                     const double* __restrict__ w, GmresDev* gd, int pass,
-                                                     int always_reorth, double* __restrict__ partials, int m1)
+// Givens step on column j of H (in place), by one thread: rotations of the previous columns,
+// the new rotation, g update, residual estimate; sets done when converged, on breakdown or
+// when the cycle is full, and advances j.
+__device__ void givens_step(GmresDev* gd, int m)
 {
-    if (gd->done) return;
-    if (pass == 1 && !gd->reorth) return;
-    const int j = gd->j, nv = j + 1;
-    const int nvals = nv + (pass == 0 ? 1 : 0);
-    __shared__ double sh[8][kRedThreads / 32];
-    __shared__ double sums[kMaxRestart + 2];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c0 = 0; c0 < nvals; c0 += 8) {
-        double acc[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) acc[q] = 0.0;
-        for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-            const double we = w[e];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const int i = c0 + q;
-                if (i < nv) acc[q] = fma((double)V[(size_t)i * ld + e], we, acc[q]);
-                else if (i == nv && pass == 0) acc[q] = fma(we, we, acc[q]);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const double v = warp_sum(acc[q]);
-            if (lane == 0) sh[q][wid] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 8 && c0 + (int)threadIdx.x < nvals) {
-            double s = 0.0;
-            for (int x = 0; x < nw; x++) s += sh[threadIdx.x][x];
-            partials[(size_t)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
-        }
-        __syncthreads();
-    }
-    if (!last_block(&gd->ticket[0])) return;
-    finalize_values(partials, gridDim.x, nvals, sums);
-    if (threadIdx.x == 0) {
-        double hh = 0.0;
-        for (int i = 0; i < nv; i++) {
-            gd->h[i] = sums[i];
-            if (pass == 0) gd->H[i + (size_t)m1 * j] = sums[i];
-            else gd->H[i + (size_t)m1 * j] += sums[i];
-            hh += sums[i] * sums[i];
-        }
-        if (pass == 0) {
-            const double wn2 = sums[nv];
-            gd->wn2 = wn2;
-            // classical Gram-Schmidt is repeated when the projection removed more than half
-            // of |w|^2, i.e. |w'| < |w| / sqrt(2) (the 'twice is enough' test)
-            gd->reorth = (always_reorth || (wn2 - hh) < 0.5 * wn2) ? 1 : 0;
-        }
-        gd->ticket[0] = 0u;
-    }
-}
-
-// w -= sum_i h_i V_i, then |w|; the final pass stores H(j+1, j) = |w| and 1/|w|
-template <typename TV>
-__global__ void __launch_bounds__(kRedThreads) k_update(size_t n, const TV* __restrict__ V, size_t ld,
-                                                       double* __restrict__ w, GmresDev* gd, int pass,
-                                                       double* __restrict__ partials, int m1)
-{
-    if (gd->done) return;
-    if (pass == 1 && !gd->reorth) return;
-    const int j = gd->j, nv = j + 1;
-    __shared__ double hs[kMaxRestart + 1];
-    __shared__ double sh[32];
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = gd->h[i];
-    __syncthreads();
-    double a = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-        double s = w[e];
-        for (int i = 0; i < nv; i++) s = fma(-hs[i], (double)V[(size_t)i * ld + e], s);
-        w[e] = s;
-        a = fma(s, s, a);
-    }
-    a = block_sum(a, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = a;
-    if (!last_block(&gd->ticket[1])) return;
-    const double tot = reduce_partials(partials, gridDim.x, sh);
-    if (threadIdx.x == 0) {
-        if (pass == 1 || !gd->reorth) {
-            const double nrm = sqrt(tot);
-            gd->H[(j + 1) + (size_t)m1 * j] = nrm;
-            gd->inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-        }
-        gd->ticket[1] = 0u;
-    }
-}
-
-__global__ void k_givens(GmresDev* gd, int m)
-{
-    if (gd->done) return;
     const int m1 = m + 1, j = gd->j;
     double* H = gd->H + (size_t)m1 * j;
     const double hn = H[j + 1];
@@ -237,6 +146,164 @@ __global__ void k_givens(GmresDev* gd, int m)
     gd->res = fabs(gd->g[j + 1]);
     if (gd->res <= gd->target || hn == 0.0 || j + 1 >= m || !(gd->res == gd->res)) gd->done = 1;
     gd->j = j + 1;
+}
+
+// Multi-dot h_i = V_i . w (i <= j) and, in pass 0, |w|^2.  Grid: x = element chunks of
+// kMdotThreads * kMdotE elements, y = groups of kMdotVG vectors; each thread keeps its
+// kMdotE elements of w in registers, so w is read once per group and each basis vector once.
+// pass 1 runs only when the pass-0 test asked for re-orthogonalisation.
+constexpr int kMdotThreads = 128, kMdotE = 16, kMdotVG = 8;
+
+template <typename TV>
+__global__ void __launch_bounds__(kMdotThreads) k_mdot(size_t n, const TV* __restrict__ V, size_t ld,
+                                                      const double* __restrict__ w, GmresDev* gd, int pass,
+                                                      int always_reorth, double* __restrict__ partials, int m1)
+{
+    if (gd->done) return;
+    if (pass == 1 && !gd->reorth) return;
+    const int j = gd->j, nv = j + 1;
+    const int nvals = nv + (pass == 0 ? 1 : 0);
+    const int nblk = gridDim.x * gridDim.y;
+    __shared__ double sh[kMdotVG][kMdotThreads / 32];
+    __shared__ double sums[kMaxRestart + 2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int v0 = blockIdx.y * kMdotVG;
+    if (v0 < nvals) {
+        const size_t base = (size_t)blockIdx.x * (kMdotThreads * kMdotE) + threadIdx.x;
+        double we[kMdotE];
+#pragma unroll
+        for (int q = 0; q < kMdotE; q++) {
+            const size_t e = base + (size_t)q * kMdotThreads;
+            we[q] = e < n ? w[e] : 0.0;
+        }
+        const int vend = min(nvals, v0 + kMdotVG);
+        for (int i = v0; i < vend; i++) {
+            double acc = 0.0;
+            if (i < nv) {
+                const TV* vi = V + (size_t)i * ld;
+#pragma unroll
+                for (int q = 0; q < kMdotE; q++) {
+                    const size_t e = base + (size_t)q * kMdotThreads;
+                    if (e < n) acc = fma((double)vi[e], we[q], acc);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kMdotE; q++) acc = fma(we[q], we[q], acc);
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) sh[i - v0][wid] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < kMdotVG && v0 + (int)threadIdx.x < vend) {
+            double s = 0.0;
+#pragma unroll
+            for (int x = 0; x < kMdotThreads / 32; x++) s += sh[threadIdx.x][x];
+            partials[(size_t)(v0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+        }
+    }
+    // last block: sum the per-chunk partials of every value (warp per value)
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(&gd->ticket[0], 1u) == (unsigned)nblk - 1);
+    __syncthreads();
+    if (!is_last) return;
+    for (int i = wid; i < nvals; i += kMdotThreads / 32) {
+        double sacc = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) sacc += __ldcg(partials + (size_t)i * gridDim.x + b);
+        sacc = warp_sum(sacc);
+        if (lane == 0) sums[i] = sacc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double hh = 0.0;
+        for (int i = 0; i < nv; i++) {
+            gd->h[i] = sums[i];
+            if (pass == 0) gd->H[i + (size_t)m1 * j] = sums[i];
+            else gd->H[i + (size_t)m1 * j] += sums[i];
+            hh += sums[i] * sums[i];
+        }
+        if (pass == 0) {
+            const double wn2 = sums[nv];
+            gd->wn2 = wn2;
+            // classical Gram-Schmidt is repeated when the projection removed more than half
+            // of |w|^2, i.e. |w'| < |w| / sqrt(2) (the 'twice is enough' test)
+            gd->reorth = (always_reorth || (wn2 - hh) < 0.5 * wn2) ? 1 : 0;
+        } else {
+            gd->n_reorth++;
+        }
+        gd->ticket[0] = 0u;
+    }
+}
+
+// w -= sum_i h_i V_i, then |w|.  The final pass stores H(j+1, j) = |w|, 1/|w| and runs the
+// Givens step (which advances j).  Each thread updates kUpdE elements (independent chains).
+constexpr int kUpdThreads = 256, kUpdE = 4;
+
+template <typename TV>
+__global__ void __launch_bounds__(kUpdThreads) k_update(size_t n, const TV* __restrict__ V, size_t ld,
+                                                       double* __restrict__ w, GmresDev* gd, int pass,
+                                                       double* __restrict__ partials, int m)
+{
+    if (gd->done) return;
+    if (pass == 1 && !gd->reorth) return;
+    const int j = gd->j, nv = j + 1, m1 = m + 1;
+    __shared__ double hs[kMaxRestart + 1];
+    __shared__ double sh[32];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = gd->h[i];
+    __syncthreads();
+    double a = 0.0;
+    for (size_t base = (size_t)blockIdx.x * (kUpdThreads * kUpdE) + threadIdx.x; base < n;
+         base += (size_t)gridDim.x * (kUpdThreads * kUpdE)) {
+        double s[kUpdE];
+#pragma unroll
+        for (int q = 0; q < kUpdE; q++) {
+            const size_t e = base + (size_t)q * kUpdThreads;
+            s[q] = e < n ? w[e] : 0.0;
+        }
+        for (int i = 0; i < nv; i++) {
+            const TV* vi = V + (size_t)i * ld;
+            const double h = hs[i];
+#pragma unroll
+            for (int q = 0; q < kUpdE; q++) {
+                const size_t e = base + (size_t)q * kUpdThreads;
+                if (e < n) s[q] = fma(-h, (double)vi[e], s[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kUpdE; q++) {
+            const size_t e = base + (size_t)q * kUpdThreads;
+            if (e < n) {
+                w[e] = s[q];
+                a = fma(s[q], s[q], a);
+            }
+        }
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = a;
+    if (!last_block(&gd->ticket[1])) return;
+    const double tot = reduce_partials(partials, gridDim.x, sh);
+    if (threadIdx.x == 0) {
+        if (pass == 1 || !gd->reorth) {
+            const double nrm = sqrt(tot);
+            gd->H[(j + 1) + (size_t)m1 * j] = nrm;
+            gd->inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+            givens_step(gd, m);
+        }
+        gd->ticket[1] = 0u;
+    }
+}
+
+// V_{j} = w * inv for the (already advanced) j: the next basis vector
+template <typename TV>
+__global__ void k_scale_next(size_t n, const double* __restrict__ w, const GmresDev* __restrict__ gd, TV* __restrict__ V,
+                             size_t ld)
+{
+    if (gd->done) return;
+    const double s = gd->inv;
+    TV* out = V + (size_t)gd->j * ld;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = (TV)(w[e] * s);
 }
 
 __global__ void k_solve_y(GmresDev* gd, int m)
@@ -329,43 +396,33 @@ int cycle_init(jfnk_ctx* c, const double* r)
 
 int arnoldi_orthogonalise(jfnk_ctx* c, double* w)
 {
-    // classical Gram-Schmidt against V_0..V_j, repeated when needed, then V_{j+1} = w / |w|
+    // classical Gram-Schmidt against V_0..V_j, repeated when needed; the final pass runs the
+    // Givens step; then V_{j+1} = w / |w|
     const size_t n = 3 * (size_t)c->dm.nc;
-    const int m1 = c->opt.gmres_restart + 1;
+    const int m = c->opt.gmres_restart, m1 = m + 1;
     const int always = c->opt.reorth ? 1 : 0;
-    const int* gate = &c->gd->done;
     int sl_d = c->prof.enabled ? c->prof.slot("mdot") : -1;
     int sl_u = c->prof.enabled ? c->prof.slot("update") : -1;
+    const dim3 gd_mdot((unsigned)((n + kMdotThreads * kMdotE - 1) / (kMdotThreads * kMdotE)), (unsigned)((m + 2 + kMdotVG - 1) / kMdotVG));
+    const int gu = (int)std::min<size_t>((n + kUpdThreads * kUpdE - 1) / (kUpdThreads * kUpdE), (size_t)kRedBlocks * 2);
     for (int pass = 0; pass < 2; pass++) {
         jfnk_prof_begin(c, sl_d);
         if (c->V_is_float)
-            k_mdot<float><<<kRedBlocks, kRedThreads, 0, c->cur>>>(n, (const float*)c->V, c->V_ld, w, c->gd, pass, always, c->partials, m1);
+            k_mdot<float><<<gd_mdot, kMdotThreads, 0, c->cur>>>(n, (const float*)c->V, c->V_ld, w, c->gd, pass, always, c->partials, m1);
         else
-            k_mdot<double><<<kRedBlocks, kRedThreads, 0, c->cur>>>(n, c->V, c->V_ld, w, c->gd, pass, always, c->partials, m1);
+            k_mdot<double><<<gd_mdot, kMdotThreads, 0, c->cur>>>(n, c->V, c->V_ld, w, c->gd, pass, always, c->partials, m1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, sl_d);
         jfnk_prof_begin(c, sl_u);
         if (c->V_is_float)
-            k_update<float><<<kRedBlocks, kRedThreads, 0, c->cur>>>(n, (const float*)c->V, c->V_ld, w, c->gd, pass, c->partials, m1);
+            k_update<float><<<gu, kUpdThreads, 0, c->cur>>>(n, (const float*)c->V, c->V_ld, w, c->gd, pass, c->partials, m);
         else
-            k_update<double><<<kRedBlocks, kRedThreads, 0, c->cur>>>(n, c->V, c->V_ld, w, c->gd, pass, c->partials, m1);
+            k_update<double><<<gu, kUpdThreads, 0, c->cur>>>(n, c->V, c->V_ld, w, c->gd, pass, c->partials, m);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, sl_u);
     }
-    return JFNK_OK;
-}
-
-// V_{j+1} = w * inv, then the Givens step (advances j)
-int arnoldi_finish_column(jfnk_ctx* c, const double* w, int j_host)
-{
-    const size_t n = 3 * (size_t)c->dm.nc;
-    const int* gate = &c->gd->done;
-    if (c->V_is_float)
-        k_scale_to<float><<<gsz(n), 256, 0, c->cur>>>(gate, n, w, c->gd, (float*)c->V + (size_t)(j_host + 1) * c->V_ld);
-    else
-        k_scale_to<double><<<gsz(n), 256, 0, c->cur>>>(gate, n, w, c->gd, c->V + (size_t)(j_host + 1) * c->V_ld);
-    JF_LAUNCHED(c);
-    k_givens<<<1, 1, 0, c->cur>>>(c->gd, c->opt.gmres_restart);
+    if (c->V_is_float) k_scale_next<float><<<gsz(n), 256, 0, c->cur>>>(n, w, c->gd, (float*)c->V, c->V_ld);
+    else k_scale_next<double><<<gsz(n), 256, 0, c->cur>>>(n, w, c->gd, c->V, c->V_ld);
     JF_LAUNCHED(c);
     return JFNK_OK;
 }

@@ -21,15 +21,28 @@ int norm_mode(jfnk_ctx* c, const double* x, size_t n, int mode, const int* gate)
 
 // ------------------------------------------------------------------ block-Jacobi
 template <typename TV, typename TP>
-__global__ void k_bjacobi(const int* gate, int nc, const TV* __restrict__ v, const TP* __restrict__ dinv,
-                          double* __restrict__ z)
+__global__ void k_bjacobi(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
+                          const TP* __restrict__ dinv, double* __restrict__ z)
 {
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
+    const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
     const TP d = dinv[P];
 #pragma unroll
     for (int k = 0; k < 3; k++) z[(size_t)k * nc + P] = (double)((TP)v[(size_t)k * nc + P] * d);
+}
+
+template <typename TV>
+__global__ void k_copy_vec(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
+                           double* __restrict__ z)
+{
+    if (gate && *gate) return;
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= nc) return;
+    const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
+#pragma unroll
+    for (int k = 0; k < 3; k++) z[(size_t)k * nc + P] = (double)v[(size_t)k * nc + P];
 }
 
 template <typename TV>
@@ -66,24 +79,41 @@ __device__ __forceinline__ void a0_row(int P, int nc, const int32_t* __restrict_
 
 template <typename T>
 __device__ __forceinline__ void csr_row(int i, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                        const T* __restrict__ val, const T* __restrict__ x, T out[3])
+                                        const T* __restrict__ val, const T* __restrict__ x, int nx, T out[3])
 {
     out[0] = out[1] = out[2] = (T)0;
     for (int q = rp[i]; q < rp[i + 1]; q++) {
         const int j = col[q];
         const T a = val[q];
-        out[0] += a * x[j]; out[1] += a * x[n + j]; out[2] += a * x[2 * (size_t)n + j];
+        out[0] += a * x[j]; out[1] += a * x[nx + j]; out[2] += a * x[2 * (size_t)nx + j];
     }
+    (void)n;
 }
 
-// level 0 entry: b = -v (so the cycle returns z = -A^-1 v = J~^-1 v), x = omega D^-1 b
+// Operator of one level: the fine level from face coefficients, coarse levels from CSR.
+template <typename T>
+struct LevelOp {
+    int n;
+    bool fine;
+    const int32_t *p0, *p1, *p2, *own, *nei;  // fine: fo_ptr, fn_ptr, fn_face, own, nei; coarse: rp, col
+    const T *vals, *adiag, *dinv;
+    __device__ __forceinline__ void row(int i, const T* x, T out[3]) const
+    {
+        if (fine) a0_row<T>(i, n, p0, p1, p2, own, nei, vals, adiag, x, out);
+        else csr_row<T>(i, n, p0, p1, vals, x, n, out);
+    }
+};
+
+// level 0 entry: b = -v (so the cycle returns z = -A^-1 v = J~^-1 v), x = omega D^-1 b.
+// v = base + (*jidx) * ld when jidx is given (the Krylov vector of the current iteration).
 template <typename TV, typename T>
-__global__ void k_mg_pre0(const int* gate, int nc, const TV* __restrict__ v, const T* __restrict__ dinv, T omega,
-                          T* __restrict__ b, T* __restrict__ x)
+__global__ void k_mg_pre0(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
+                          const T* __restrict__ dinv, T omega, T* __restrict__ b, T* __restrict__ x)
 {
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
+    const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
     const T d = omega * dinv[P];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -105,105 +135,78 @@ __global__ void k_mg_pre(const int* gate, int n, const T* __restrict__ dinv, T o
     for (int k = 0; k < 3; k++) x[(size_t)k * n + i] = d * b[(size_t)k * n + i];
 }
 
-// Extra Jacobi sweep x_out = x + omega D^-1 (b - A x) (sweeps > 1)
-template <typename T, bool FINE>
-__global__ void k_mg_jacobi(const int* gate, int n, const int32_t* __restrict__ p0, const int32_t* __restrict__ p1,
-                            const int32_t* __restrict__ p2, const int32_t* __restrict__ own, const int32_t* __restrict__ nei,
-                            const T* __restrict__ vals, const T* __restrict__ adiag, const T* __restrict__ dinv, T omega,
-                            const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo)
+// Jacobi sweep x_out = x + omega D^-1 (b - A x); zd != null writes the result as double
+template <typename T>
+__global__ void k_mg_jacobi(const int* gate, LevelOp<T> op, T omega, const T* __restrict__ b, const T* __restrict__ x,
+                            T* __restrict__ xo, double* __restrict__ zd)
 {
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = op.n;
     if (i >= n) return;
     T ax[3];
-    if (FINE) a0_row<T>(i, n, p0, p1, p2, own, nei, vals, adiag, x, ax);
-    else csr_row<T>(i, n, p0, p1, vals, x, ax);
-    const T d = omega * dinv[i];
-#pragma unroll
-    for (int k = 0; k < 3; k++) xo[(size_t)k * n + i] = x[(size_t)k * n + i] + d * (b[(size_t)k * n + i] - ax[k]);
-}
-
-// residual r = b - A x of the members of each aggregate, summed into the coarse right-hand side
-template <typename T, bool FINE>
-__global__ void k_mg_restrict(const int* gate, int nco, int n, const int32_t* __restrict__ mptr, const int32_t* __restrict__ midx,
-                              const int32_t* __restrict__ p0, const int32_t* __restrict__ p1, const int32_t* __restrict__ p2,
-                              const int32_t* __restrict__ own, const int32_t* __restrict__ nei, const T* __restrict__ vals,
-                              const T* __restrict__ adiag, const T* __restrict__ b, const T* __restrict__ x,
-                              T* __restrict__ bc)
-{
-    if (gate && *gate) return;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nco) return;
-    T s[3] = {(T)0, (T)0, (T)0};
-    for (int q = mptr[I]; q < mptr[I + 1]; q++) {
-        const int i = midx[q];
-        T ax[3];
-        if (FINE) a0_row<T>(i, n, p0, p1, p2, own, nei, vals, adiag, x, ax);
-        else csr_row<T>(i, n, p0, p1, vals, x, ax);
-#pragma unroll
-        for (int k = 0; k < 3; k++) s[k] += b[(size_t)k * n + i] - ax[k];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; k++) bc[(size_t)k * nco + I] = s[k];
-}
-
-// x' = x + P x_c (piecewise constant), then one Jacobi sweep: x_out = x' + omega D^-1 (b - A x').
-// FINE && TO_DOUBLE writes z (double) for the caller.
-template <typename T, bool FINE>
-__global__ void k_mg_post(const int* gate, int n, int nco, const int32_t* __restrict__ agg, const T* __restrict__ xc,
-                          const int32_t* __restrict__ p0, const int32_t* __restrict__ p1, const int32_t* __restrict__ p2,
-                          const int32_t* __restrict__ own, const int32_t* __restrict__ nei, const T* __restrict__ vals,
-                          const T* __restrict__ adiag, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
-                          const T* __restrict__ x, T* __restrict__ xo, double* __restrict__ zd)
-{
-    if (gate && *gate) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T ax[3] = {(T)0, (T)0, (T)0};
-    auto xp = [&](int j, int k) -> T { return x[(size_t)k * n + j] + xc[(size_t)k * nco + agg[j]]; };
-    if (FINE) {
-        const T d = adiag[i];
-        for (int k = 0; k < 3; k++) ax[k] = d * xp(i, k);
-        for (int f = p0[i]; f < p0[i + 1]; f++) {
-            const int N = nei[f];
-            const T cf = vals[f];
-            for (int k = 0; k < 3; k++) ax[k] -= cf * xp(N, k);
-        }
-        for (int q = p1[i]; q < p1[i + 1]; q++) {
-            const int f = p2[q];
-            const int N = own[f];
-            const T cf = vals[f];
-            for (int k = 0; k < 3; k++) ax[k] -= cf * xp(N, k);
-        }
-    } else {
-        for (int q = p0[i]; q < p0[i + 1]; q++) {
-            const int j = p1[q];
-            const T a = vals[q];
-            for (int k = 0; k < 3; k++) ax[k] += a * xp(j, k);
-        }
-    }
-    const T d = omega * dinv[i];
+    op.row(i, x, ax);
+    const T d = omega * op.dinv[i];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        const T xn = xp(i, k) + d * (b[(size_t)k * n + i] - ax[k]);
+        const T xn = x[(size_t)k * n + i] + d * (b[(size_t)k * n + i] - ax[k]);
         if (zd) zd[(size_t)k * n + i] = (double)xn;
         else xo[(size_t)k * n + i] = xn;
     }
 }
 
-// coarsest level: x = A_c^-1 b with the (symmetric) dense inverse
+// r = b - A x
+template <typename T>
+__global__ void k_mg_resid(const int* gate, LevelOp<T> op, const T* __restrict__ b, const T* __restrict__ x,
+                           T* __restrict__ r)
+{
+    if (gate && *gate) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = op.n;
+    if (i >= n) return;
+    T ax[3];
+    op.row(i, x, ax);
+#pragma unroll
+    for (int k = 0; k < 3; k++) r[(size_t)k * n + i] = b[(size_t)k * n + i] - ax[k];
+}
+
+// y = M x (add = 0) or y += M x (add = 1) for a CSR matrix with nrow rows and nx columns
+template <typename T>
+__global__ void k_mg_spmv(const int* gate, int nrow, int nx, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add)
+{
+    if (gate && *gate) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrow) return;
+    T s[3];
+    csr_row<T>(i, nrow, rp, col, val, x, nx, s);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (add) y[(size_t)k * nrow + i] += s[k];
+        else y[(size_t)k * nrow + i] = s[k];
+    }
+}
+
+// coarsest level: x = A_c^-1 b with the dense (symmetric) inverse, one warp per row
 template <typename T>
 __global__ void k_mg_coarse(const int* gate, int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x)
 {
     if (gate && *gate) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= n) return;
     T s0 = 0, s1 = 0, s2 = 0;
-    for (int k = 0; k < n; k++) {
-        const T a = Ainv[(size_t)k * n + i];
+    const T* row = Ainv + (size_t)w * n;
+    for (int k = lane; k < n; k += 32) {
+        const T a = row[k];
         s0 += a * b[k]; s1 += a * b[n + k]; s2 += a * b[2 * (size_t)n + k];
     }
-    x[i] = s0; x[n + i] = s1; x[2 * (size_t)n + i] = s2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) { x[w] = s0; x[n + w] = s1; x[2 * (size_t)n + w] = s2; }
 }
 
 // ------------------------------------------------------------------ device hierarchy
@@ -211,10 +214,13 @@ template <typename T>
 struct MgDev {
     struct Level {
         int n = 0, nco = 0;
-        int32_t *rp = nullptr, *col = nullptr;   // CSR (coarse levels)
+        int32_t *rp = nullptr, *col = nullptr;    // A (coarse levels)
         T *val = nullptr, *adiag = nullptr, *dinv = nullptr;
-        int32_t *agg = nullptr, *mptr = nullptr, *midx = nullptr;  // to the next level
-        T *b = nullptr, *x = nullptr, *x2 = nullptr;
+        int32_t *prp = nullptr, *pcol = nullptr;  // P: n x nco
+        T* pval = nullptr;
+        int32_t *rrp = nullptr, *rcol = nullptr;  // R = P^T: nco x n
+        T* rval = nullptr;
+        T *b = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr;
     };
     std::vector<Level> L;
     T* Ainv = nullptr;
@@ -226,8 +232,6 @@ struct MgState {
     MgDev<double> d;
     bool ready = false;
 };
-
-static MgState& mg_state(jfnk_ctx* c);
 
 template <typename T>
 static T* upload_as(jfnk_ctx* c, const std::vector<double>& h)
@@ -244,9 +248,42 @@ static int32_t* upload_i(jfnk_ctx* c, const std::vector<int32_t>& h)
     return d;
 }
 
+// P of the fine level re-indexed to the internal cell order, and R = P^T for every level
+struct HostTransfer {
+    std::vector<int32_t> prp, pcol, rrp, rcol;
+    std::vector<double> pval, rval;
+};
+
+static void make_transfer(const std::vector<int32_t>& prp, const std::vector<int32_t>& pcol, const std::vector<double>& pval,
+                          int n, int nco, const std::vector<int32_t>* n2o, HostTransfer& t)
+{
+    // rows of P in the device numbering of this level
+    t.prp.assign(n + 1, 0);
+    t.pcol.clear();
+    t.pval.clear();
+    for (int i = 0; i < n; i++) {
+        const int src = n2o ? (*n2o)[i] : i;
+        for (int q = prp[src]; q < prp[src + 1]; q++) { t.pcol.push_back(pcol[q]); t.pval.push_back(pval[q]); }
+        t.prp[i + 1] = (int32_t)t.pcol.size();
+    }
+    t.rrp.assign(nco + 1, 0);
+    for (int q = 0; q < (int)t.pcol.size(); q++) t.rrp[t.pcol[q] + 1]++;
+    for (int J = 0; J < nco; J++) t.rrp[J + 1] += t.rrp[J];
+    t.rcol.assign(t.pcol.size(), 0);
+    t.rval.assign(t.pcol.size(), 0.0);
+    std::vector<int32_t> fill(t.rrp.begin(), t.rrp.end() - 1);
+    for (int i = 0; i < n; i++)
+        for (int q = t.prp[i]; q < t.prp[i + 1]; q++) {
+            const int J = t.pcol[q];
+            t.rcol[fill[J]] = i;
+            t.rval[fill[J]] = t.pval[q];
+            fill[J]++;
+        }
+}
+
 template <typename T>
 static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& lv, const std::vector<double>& inv,
-                     const std::vector<double>& jc_h, const std::vector<double>& adiag0, const std::vector<int32_t>& agg0_new)
+                     const std::vector<double>& jc_h, const std::vector<double>& adiag0, const std::vector<HostTransfer>& tr)
 {
     const int nl = (int)lv.size();
     M.L.assign(nl, typename MgDev<T>::Level());
@@ -272,20 +309,17 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
         D.b = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
         D.x = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
         D.x2 = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
+        D.r = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
         if (l < nl - 1) {
-            const std::vector<int32_t>& agg = (l == 0) ? agg0_new : H.agg;
-            int nco = lv[l + 1].n;
-            D.nco = nco;
-            std::vector<int32_t> mptr(nco + 1, 0), midx(H.n);
-            for (int i = 0; i < H.n; i++) mptr[agg[i] + 1]++;
-            for (int a = 0; a < nco; a++) mptr[a + 1] += mptr[a];
-            std::vector<int32_t> fill(mptr.begin(), mptr.end() - 1);
-            for (int i = 0; i < H.n; i++) midx[fill[agg[i]]++] = i;
-            D.agg = upload_i(c, agg);
-            D.mptr = upload_i(c, mptr);
-            D.midx = upload_i(c, midx);
+            D.nco = lv[l + 1].n;
+            D.prp = upload_i(c, tr[l].prp);
+            D.pcol = upload_i(c, tr[l].pcol);
+            D.pval = upload_as<T>(c, tr[l].pval);
+            D.rrp = upload_i(c, tr[l].rrp);
+            D.rcol = upload_i(c, tr[l].rcol);
+            D.rval = upload_as<T>(c, tr[l].rval);
         }
-        if (!D.adiag || !D.dinv || !D.b || !D.x || !D.x2) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
+        if (!D.adiag || !D.dinv || !D.b || !D.x || !D.x2 || !D.r) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
     }
     M.Ainv = upload_as<T>(c, inv);
     if (!M.Ainv || !M.jc) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
@@ -330,24 +364,24 @@ int pc_setup(jfnk_ctx* c)
     }
     L0.rp.assign(nc + 1, 0);
     for (int i = 0; i < nc; i++) {
-        std::sort(rows[i].begin(), rows[i].end(), [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
+        std::sort(rows[i].begin(), rows[i].end(),
+                  [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
         for (auto& e : rows[i]) { L0.col.push_back(e.first); L0.val.push_back(e.second); }
         L0.rp[i + 1] = (int32_t)L0.col.size();
     }
     std::vector<MgLevelHost> lv;
     std::vector<double> inv;
-    std::string e = mg_build_hierarchy(std::move(L0), c->opt.mg_theta, c->opt.mg_max_levels, c->opt.mg_coarse_max, lv, inv);
+    std::string e = mg_build_hierarchy(std::move(L0), c->opt.mg_theta, c->opt.mg_max_levels, c->opt.mg_coarse_max,
+                                       c->opt.mg_smoothed != 0, lv, inv);
     if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
-    std::vector<int32_t> agg0_new;
-    if (lv.size() > 1) {
-        agg0_new.resize(nc);
-        for (int P = 0; P < nc; P++) agg0_new[P] = lv[0].agg[t.n2o[P]];
-    }
+    std::vector<HostTransfer> tr(lv.size());
+    for (size_t l = 0; l + 1 < lv.size(); l++)
+        make_transfer(lv[l].prp, lv[l].pcol, lv[l].pval, lv[l].n, lv[l + 1].n, l == 0 ? &t.n2o : nullptr, tr[l]);
     std::vector<double> adiag0(nc);
     for (int P = 0; P < nc; P++) adiag0[P] = -diag[P];
-    int rc = mg_upload<float>(c, S.f, lv, inv, jc, adiag0, agg0_new);
+    int rc = mg_upload<float>(c, S.f, lv, inv, jc, adiag0, tr);
     if (rc) return rc;
-    rc = mg_upload<double>(c, S.d, lv, inv, jc, adiag0, agg0_new);
+    rc = mg_upload<double>(c, S.d, lv, inv, jc, adiag0, tr);
     if (rc) return rc;
     c->mg_coarse_n = lv.back().n;
     S.ready = true;
@@ -366,88 +400,84 @@ int mg_levels_info(jfnk_ctx* c, std::vector<int>& sizes)
 
 static inline int nb(long n, int t) { return (int)std::max<long>(1, (n + t - 1) / t); }
 
-template <typename T, typename TV>
-static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* v, double* z, const int* gate)
+template <typename T>
+static LevelOp<T> level_op(const jfnk_ctx* c, const MgDev<T>& M, int l)
 {
-    const DevMesh& m = c->dm;
+    const auto& D = M.L[l];
+    LevelOp<T> op;
+    op.n = D.n;
+    op.fine = (l == 0);
+    if (l == 0) {
+        op.p0 = c->dm.fo_ptr; op.p1 = c->dm.fn_ptr; op.p2 = c->dm.fn_face; op.own = c->dm.own; op.nei = c->dm.nei;
+        op.vals = M.jc;
+    } else {
+        op.p0 = D.rp; op.p1 = D.col; op.p2 = nullptr; op.own = nullptr; op.nei = nullptr;
+        op.vals = D.val;
+    }
+    op.adiag = D.adiag;
+    op.dinv = D.dinv;
+    return op;
+}
+
+template <typename T, typename TV>
+static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const int* jidx, double* z, const int* gate)
+{
     cudaStream_t s = c->cur;
     const T omega = (T)(2.0 / 3.0);
     const int nl = (int)M.L.size();
     const int sweeps = std::max(1, c->opt.mg_smooth_sweeps);
     if (nl == 1) {
-        // a single level: the dense inverse applied to -v
         auto& D = M.L[0];
-        k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, v, D.dinv, (T)0, D.b, D.x2);
+        k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, vbase, ld, jidx, D.dinv, (T)0, D.b, D.x2);
         JF_LAUNCHED(c);
-        k_mg_coarse<T><<<nb(D.n, 128), 128, 0, s>>>(gate, D.n, M.Ainv, D.b, D.x);
+        k_mg_coarse<T><<<nb(32L * D.n, 256), 256, 0, s>>>(gate, D.n, M.Ainv, D.b, D.x);
         JF_LAUNCHED(c);
         k_copy_to_double<T><<<nb(3L * D.n, 256), 256, 0, s>>>(gate, 3 * (size_t)D.n, D.x, z);
         JF_LAUNCHED(c);
         return JFNK_OK;
     }
     // downward
-    for (int l = 0; l < nl; l++) {
+    for (int l = 0; l < nl - 1; l++) {
         auto& D = M.L[l];
-        if (l == nl - 1) {
-            k_mg_coarse<T><<<nb(D.n, 128), 128, 0, s>>>(gate, D.n, M.Ainv, D.b, D.x);
-            JF_LAUNCHED(c);
-            break;
-        }
-        if (l == 0) k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, v, D.dinv, omega, D.b, D.x);
+        const LevelOp<T> op = level_op<T>(c, M, l);
+        if (l == 0) k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, vbase, ld, jidx, D.dinv, omega, D.b, D.x);
         else k_mg_pre<T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.dinv, omega, D.b, D.x);
         JF_LAUNCHED(c);
         for (int sw = 1; sw < sweeps; sw++) {
-            if (l == 0)
-                k_mg_jacobi<T, true><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, m.fo_ptr, m.fn_ptr, m.fn_face, m.own, m.nei,
-                                                                   M.jc, D.adiag, D.dinv, omega, D.b, D.x, D.x2);
-            else
-                k_mg_jacobi<T, false><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, nullptr, nullptr, nullptr,
-                                                                    D.val, D.adiag, D.dinv, omega, D.b, D.x, D.x2);
+            k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, nullptr);
             JF_LAUNCHED(c);
             std::swap(D.x, D.x2);
         }
+        k_mg_resid<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, D.b, D.x, D.r);
+        JF_LAUNCHED(c);
         auto& Cn = M.L[l + 1];
-        if (l == 0)
-            k_mg_restrict<T, true><<<nb(D.nco, 128), 128, 0, s>>>(gate, D.nco, D.n, D.mptr, D.midx, m.fo_ptr, m.fn_ptr,
-                                                                    m.fn_face, m.own, m.nei, M.jc, D.adiag, D.b, D.x, Cn.b);
-        else
-            k_mg_restrict<T, false><<<nb(D.nco, 128), 128, 0, s>>>(gate, D.nco, D.n, D.mptr, D.midx, D.rp, D.col, nullptr,
-                                                                     nullptr, nullptr, D.val, D.adiag, D.b, D.x, Cn.b);
+        k_mg_spmv<T><<<nb(D.nco, 256), 256, 0, s>>>(gate, D.nco, D.n, D.rrp, D.rcol, D.rval, D.r, Cn.b, 0);
+        JF_LAUNCHED(c);
+    }
+    {
+        auto& Dc = M.L[nl - 1];
+        k_mg_coarse<T><<<nb(32L * Dc.n, 256), 256, 0, s>>>(gate, Dc.n, M.Ainv, Dc.b, Dc.x);
         JF_LAUNCHED(c);
     }
     // upward
     for (int l = nl - 2; l >= 0; l--) {
         auto& D = M.L[l];
         auto& Cn = M.L[l + 1];
-        double* zout = (l == 0 && sweeps == 1) ? z : nullptr;
-        if (l == 0)
-            k_mg_post<T, true><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.nco, D.agg, Cn.x, m.fo_ptr, m.fn_ptr, m.fn_face,
-                                                             m.own, m.nei, M.jc, D.adiag, D.dinv, omega, D.b, D.x, D.x2, zout);
-        else
-            k_mg_post<T, false><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.nco, D.agg, Cn.x, D.rp, D.col, nullptr, nullptr,
-                                                              nullptr, D.val, D.adiag, D.dinv, omega, D.b, D.x, D.x2, nullptr);
+        const LevelOp<T> op = level_op<T>(c, M, l);
+        k_mg_spmv<T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, Cn.n, D.prp, D.pcol, D.pval, Cn.x, D.x, 1);
         JF_LAUNCHED(c);
-        if (!zout) std::swap(D.x, D.x2);
-        for (int sw = 1; sw < sweeps; sw++) {
-            if (l == 0)
-                k_mg_jacobi<T, true><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, m.fo_ptr, m.fn_ptr, m.fn_face, m.own, m.nei,
-                                                                   M.jc, D.adiag, D.dinv, omega, D.b, D.x, D.x2);
-            else
-                k_mg_jacobi<T, false><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, nullptr, nullptr, nullptr,
-                                                                    D.val, D.adiag, D.dinv, omega, D.b, D.x, D.x2);
+        for (int sw = 0; sw < sweeps; sw++) {
+            const bool last = (l == 0 && sw == sweeps - 1);
+            k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
             JF_LAUNCHED(c);
-            std::swap(D.x, D.x2);
-        }
-        if (l == 0 && sweeps > 1) {
-            k_copy_to_double<T><<<nb(3L * D.n, 256), 256, 0, s>>>(gate, 3 * (size_t)D.n, D.x, z);
-            JF_LAUNCHED(c);
+            if (!last) std::swap(D.x, D.x2);
         }
     }
     return JFNK_OK;
 }
 
-// z = P^-1 v; v is double or float (basis storage); gate may be null
-int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate)
+// z = P^-1 v with v = vbase + (*jidx) * ld (jidx given) or vbase; v double or float; gate may be null
+int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z, const int* gate)
 {
     const int nc = c->dm.nc;
     const bool fp32 = c->opt.precision == JFNK_PREC_MIXED;
@@ -456,28 +486,34 @@ int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, 
     jfnk_prof_begin(c, sl);
     if (pc == JFNK_PC_BJACOBI) {
         if (v_is_float) {
-            if (fp32) k_bjacobi<float, float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)v, c->dm.jt_dinv_f, z);
-            else k_bjacobi<float, double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)v, c->dm.jt_dinv, z);
+            if (fp32) k_bjacobi<float, float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)vbase, ld, jidx, c->dm.jt_dinv_f, z);
+            else k_bjacobi<float, double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)vbase, ld, jidx, c->dm.jt_dinv, z);
         } else {
-            if (fp32) k_bjacobi<double, float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)v, c->dm.jt_dinv_f, z);
-            else k_bjacobi<double, double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)v, c->dm.jt_dinv, z);
+            if (fp32) k_bjacobi<double, float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)vbase, ld, jidx, c->dm.jt_dinv_f, z);
+            else k_bjacobi<double, double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)vbase, ld, jidx, c->dm.jt_dinv, z);
         }
         JF_LAUNCHED(c);
     } else if (pc == JFNK_PC_MG) {
         MgState& S = mg_state(c);
         if (!S.ready) return jfnk_fail(c, JFNK_ESTATE, "multigrid preconditioner not set up (options.pc must be JFNK_PC_MG at set-up)");
         int rc;
-        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)v, z, gate) : vcycle<float, double>(c, S.f, (const double*)v, z, gate);
-        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)v, z, gate) : vcycle<double, double>(c, S.d, (const double*)v, z, gate);
+        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)vbase, ld, jidx, z, gate)
+                                  : vcycle<float, double>(c, S.f, (const double*)vbase, ld, jidx, z, gate);
+        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)vbase, ld, jidx, z, gate)
+                             : vcycle<double, double>(c, S.d, (const double*)vbase, ld, jidx, z, gate);
         if (rc) return rc;
     } else {
-        const size_t n = 3 * (size_t)nc;
-        if (v_is_float) k_copy_to_double<float><<<nb((long)n, 256), 256, 0, s>>>(gate, n, (const float*)v, z);
-        else k_copy_to_double<double><<<nb((long)n, 256), 256, 0, s>>>(gate, n, (const double*)v, z);
+        if (v_is_float) k_copy_vec<float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)vbase, ld, jidx, z);
+        else k_copy_vec<double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)vbase, ld, jidx, z);
         JF_LAUNCHED(c);
     }
     jfnk_prof_end(c, sl);
     return JFNK_OK;
+}
+
+int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate)
+{
+    return pc_apply_dev(c, pc, v, 0, nullptr, v_is_float, z, gate);
 }
 
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z) { return pc_apply_any(c, pc, v, 0, z, nullptr); }

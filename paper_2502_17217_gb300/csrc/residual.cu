@@ -93,11 +93,12 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
                                               const int32_t* __restrict__ nei, const double* __restrict__ coef,
                                               const double* __restrict__ u, const double* __restrict__ G,
                                               const double* __restrict__ T, const double* __restrict__ bval,
-                                              double load, double* __restrict__ F)
+                                              const double* __restrict__ load_dev, double* __restrict__ F)
 {
     if (gate && *gate) return;
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nflux) return;
+    const double load = *load_dev;
     const int P = own[f];
     const bool internal = f < ni;
     const int N = internal ? nei[f] : P;
@@ -172,13 +173,14 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
 __global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int dim, const int32_t* __restrict__ fo_ptr,
                                                 const int32_t* __restrict__ fn_ptr, const int32_t* __restrict__ fn_face,
                                                 const int32_t* __restrict__ fd_ptr, const double* __restrict__ F,
-                                                const double* __restrict__ b0, double load, int mode,
+                                                const double* __restrict__ b0, const double* __restrict__ load_dev, int mode,
                                                 const double* __restrict__ Ru, const double* __restrict__ eps_dev,
                                                 const int* __restrict__ gate, double* __restrict__ out)
 {
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
+    const double load = *load_dev;
     double r0 = load * b0[P], r1 = load * b0[nc + P], r2 = load * b0[2 * nc + P];
     for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) {
         r0 += F[f]; r1 += F[nflux + f]; r2 += F[2 * (size_t)nflux + f];
@@ -207,6 +209,16 @@ __global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int dim, cons
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
+// Makes the device copy of the load factor equal to c->load (rare: once per load step).
+int sync_load(jfnk_ctx* c)
+{
+    if (c->load_on_device == c->load) return JFNK_OK;
+    JF_CUDA(c, cudaStreamSynchronize(c->cur));
+    JF_CUDA(c, cudaMemcpy(&c->gd->load, &c->load, sizeof(double), cudaMemcpyHostToDevice));
+    c->load_on_device = c->load;
+    return JFNK_OK;
+}
+
 int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate)
 {
     const DevMesh& m = c->dm;
@@ -227,16 +239,16 @@ int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, cons
         jfnk_prof_begin(c, sl[1]);
         if (c->law == JFNK_LAW_LINEAR)
             k_flux<JFNK_LAW_LINEAR><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
-                                                                        u_int, c->G, c->T, m.bval, c->load, c->F);
+                                                                        u_int, c->G, c->T, m.bval, &c->gd->load, c->F);
         else
             k_flux<JFNK_LAW_NEOHOOKEAN><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
-                                                                            u_int, c->G, c->T, m.bval, c->load, c->F);
+                                                                            u_int, c->G, c->T, m.bval, &c->gd->load, c->F);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, sl[1]);
     }
     jfnk_prof_begin(c, sl[2]);
     k_finish<<<nblk(m.nc, 256), 256, 0, s>>>(m.nc, m.nflux, m.dim, m.fo_ptr, m.fn_ptr, m.fn_face, m.fd_ptr, c->F, m.b0,
-                                            c->load, mode, c->Ru, eps_dev, gate, out);
+                                            &c->gd->load, mode, c->Ru, eps_dev, gate, out);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);
     return JFNK_OK;
@@ -244,6 +256,8 @@ int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, cons
 
 int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev)
 {
+    int rc = sync_load(c);
+    if (rc) return rc;
     return residual_gated(c, u_int, out, mode, eps_dev, nullptr);
 }
 

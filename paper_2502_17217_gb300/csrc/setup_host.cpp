@@ -194,13 +194,15 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t)
 }
 
 // ------------------------------------------------------------------ aggregation multigrid
-// Plain aggregation on A = -J~, rows visited in the input cell order:
+// Aggregation AMG on A = -J~, rows visited in the input cell order:
 //   strong(i, j):  -a_ij >= theta * max_k(-a_ik), values within a relative 1e-10 counting as
 //                  equal so that rounding does not decide ties;
 //   pass 1:        a free row whose strong neighbours are all free starts an aggregate;
 //   pass 2:        a remaining row joins the aggregate of its strongest aggregated neighbour
 //                  (lowest index among equals), else forms a singleton;
-//   P piecewise constant, A_c = P^T A P, until coarse_max rows, max_levels, or < 10% shrink.
+//   P:             piecewise constant, or smoothed P = (I - omega D^-1 A) P_tent with
+//                  omega = 4 / (3 rho), rho = max_i sum_j |a_ij| / a_ii (Gershgorin);
+//   A_c = P^T A P, until coarse_max rows, max_levels, or < 10% shrink.
 static int aggregate(const MgLevelHost& L, double theta, std::vector<int32_t>& agg)
 {
     const double tie = 1e-10;
@@ -244,7 +246,92 @@ static int aggregate(const MgLevelHost& L, double theta, std::vector<int32_t>& a
     return na;
 }
 
-std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels, int coarse_max,
+static void smoothed_prolongation(const MgLevelHost& F, const std::vector<int32_t>& agg, int nco, bool smoothed,
+                                  std::vector<int32_t>& prp, std::vector<int32_t>& pcol, std::vector<double>& pval)
+{
+    const int n = F.n;
+    prp.assign(n + 1, 0);
+    pcol.clear();
+    pval.clear();
+    if (!smoothed) {
+        for (int i = 0; i < n; i++) { pcol.push_back(agg[i]); pval.push_back(1.0); prp[i + 1] = i + 1; }
+        return;
+    }
+    double rho = 0.0;
+    std::vector<double> diag(n, 0.0);
+    for (int i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int q = F.rp[i]; q < F.rp[i + 1]; q++) {
+            s += std::fabs(F.val[q]);
+            if (F.col[q] == i) diag[i] = F.val[q];
+        }
+        rho = std::max(rho, s / diag[i]);
+    }
+    const double omega = 4.0 / (3.0 * rho);
+    std::vector<double> acc(nco, 0.0);
+    std::vector<int32_t> mark(nco, -1), list;
+    for (int i = 0; i < n; i++) {
+        list.clear();
+        mark[agg[i]] = i; acc[agg[i]] = 1.0; list.push_back(agg[i]);
+        for (int q = F.rp[i]; q < F.rp[i + 1]; q++) {
+            const int J = agg[F.col[q]];
+            if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list.push_back(J); }
+            acc[J] -= omega * F.val[q] / diag[i];
+        }
+        std::sort(list.begin(), list.end());
+        for (int J : list) { pcol.push_back(J); pval.push_back(acc[J]); }
+        prp[i + 1] = (int32_t)pcol.size();
+    }
+}
+
+// A_c = P^T A P, rows with ascending columns
+static void galerkin(const MgLevelHost& F, int nco, MgLevelHost& Cl)
+{
+    const int n = F.n;
+    std::vector<int32_t> tp(nco + 1, 0);
+    for (int i = 0; i < n; i++)
+        for (int q = F.prp[i]; q < F.prp[i + 1]; q++) tp[F.pcol[q] + 1]++;
+    for (int J = 0; J < nco; J++) tp[J + 1] += tp[J];
+    std::vector<int32_t> tr(F.prp[n]);
+    std::vector<double> tv(F.prp[n]);
+    {
+        std::vector<int32_t> fill(tp.begin(), tp.end() - 1);
+        for (int i = 0; i < n; i++)
+            for (int q = F.prp[i]; q < F.prp[i + 1]; q++) {
+                const int J = F.pcol[q];
+                tr[fill[J]] = i;
+                tv[fill[J]] = F.pval[q];
+                fill[J]++;
+            }
+    }
+    Cl.n = nco;
+    Cl.rp.assign(nco + 1, 0);
+    Cl.col.clear();
+    Cl.val.clear();
+    std::vector<double> acc(nco, 0.0);
+    std::vector<int32_t> mark(nco, -1), list;
+    for (int I = 0; I < nco; I++) {
+        list.clear();
+        for (int t = tp[I]; t < tp[I + 1]; t++) {
+            const int i = tr[t];
+            const double pI = tv[t];
+            for (int k = F.rp[i]; k < F.rp[i + 1]; k++) {
+                const int j = F.col[k];
+                const double a = pI * F.val[k];
+                for (int q = F.prp[j]; q < F.prp[j + 1]; q++) {
+                    const int J = F.pcol[q];
+                    if (mark[J] != I) { mark[J] = I; acc[J] = 0.0; list.push_back(J); }
+                    acc[J] += a * F.pval[q];
+                }
+            }
+        }
+        std::sort(list.begin(), list.end());
+        for (int J : list) { Cl.col.push_back(J); Cl.val.push_back(acc[J]); }
+        Cl.rp[I + 1] = (int32_t)Cl.col.size();
+    }
+}
+
+std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels, int coarse_max, bool smoothed,
                                std::vector<MgLevelHost>& levels, std::vector<double>& chol)
 {
     levels.clear();
@@ -256,32 +343,9 @@ std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels,
         int nco = aggregate(F, theta, agg);
         if (nco > 0.9 * F.n) break;
         F.agg = agg;
+        smoothed_prolongation(F, agg, nco, smoothed, F.prp, F.pcol, F.pval);
         MgLevelHost Cl;
-        Cl.n = nco;
-        std::vector<int32_t> aptr(nco + 1, 0), arow(F.n);
-        for (int i = 0; i < F.n; i++) aptr[agg[i] + 1]++;
-        for (int a = 0; a < nco; a++) aptr[a + 1] += aptr[a];
-        {
-            std::vector<int32_t> fill(aptr.begin(), aptr.end() - 1);
-            for (int i = 0; i < F.n; i++) arow[fill[agg[i]]++] = i;
-        }
-        std::vector<double> acc(nco, 0.0);
-        std::vector<int32_t> mark(nco, -1), list;
-        Cl.rp.assign(nco + 1, 0);
-        for (int a = 0; a < nco; a++) {
-            list.clear();
-            for (int t = aptr[a]; t < aptr[a + 1]; t++) {
-                int i = arow[t];
-                for (int q = F.rp[i]; q < F.rp[i + 1]; q++) {
-                    int b = agg[F.col[q]];
-                    if (mark[b] != a) { mark[b] = a; acc[b] = 0.0; list.push_back(b); }
-                    acc[b] += F.val[q];
-                }
-            }
-            std::sort(list.begin(), list.end());
-            for (int b : list) { Cl.col.push_back(b); Cl.val.push_back(acc[b]); }
-            Cl.rp[a + 1] = (int32_t)Cl.col.size();
-        }
+        galerkin(F, nco, Cl);
         levels.push_back(std::move(Cl));
     }
     // explicit inverse of the coarsest matrix via its Cholesky factor

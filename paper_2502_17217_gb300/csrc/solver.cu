@@ -19,8 +19,8 @@ namespace jfnk {
 
 static int read_header(jfnk_ctx* c)
 {
-    // first fields of GmresDev (j, k, done, reorth, tickets, pad, eps, unorm, beta, target, inv, wn2, res)
-    JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gd, offsetof(GmresDev, scratch), cudaMemcpyDeviceToHost, c->cur));
+    // first fields of GmresDev (j, k, done, reorth, tickets, pad, eps, unorm, beta, target, inv, wn2, res, n_reorth)
+    JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gd, offsetof(GmresDev, load), cudaMemcpyDeviceToHost, c->cur));
     JF_CUDA(c, cudaStreamSynchronize(c->cur));
     return JFNK_OK;
 }
@@ -41,6 +41,47 @@ static int jv_direction(jfnk_ctx* c, const double* x, double* out)
     if (!rc) rc = perturb(c, c->u, x, c->w, nullptr);
     if (!rc) rc = residual(c, c->w, out, OUT_JV, &c->gd->eps);
     return rc;
+}
+
+// One Arnoldi iteration, every kernel reading j from the device and returning at once when
+// the cycle is done: z = P^-1 V_j, eps, w = u + eps z, Jv into wk, Gram-Schmidt (+ Givens),
+// V_{j+1}; then the header (j, k, done, ...) is copied to pinned host memory.
+static int enqueue_iteration(jfnk_ctx* c)
+{
+    const size_t n = 3 * (size_t)c->dm.nc;
+    const int* gate = &c->gd->done;
+    int rc;
+    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gd->j, c->V_is_float, c->z, gate))) return rc;
+    if ((rc = norm_mode(c, c->z, n, 1, gate))) return rc;
+    if ((rc = perturb(c, c->u, c->z, c->w, gate))) return rc;
+    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, &c->gd->eps, gate))) return rc;
+    if ((rc = arnoldi_orthogonalise(c, c->wk))) return rc;
+    JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gd, offsetof(GmresDev, n_reorth), cudaMemcpyDeviceToHost, c->cur));
+    return JFNK_OK;
+}
+
+static int capture_iteration(jfnk_ctx* c)
+{
+    if (c->it_graph) return JFNK_OK;
+    cudaGraph_t g = nullptr;
+    const int64_t before = c->launches;
+    JF_CUDA(c, cudaStreamBeginCapture(c->cur, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration(c);
+    cudaError_t e = cudaStreamEndCapture(c->cur, &g);
+    c->graph_kernels = c->launches - before;  // counted again at every replay
+    c->launches = before;
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return jfnk_cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->it_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->it_graph = nullptr;
+        return jfnk_cuda_fail(c, e, "cudaGraphInstantiate");
+    }
+    return JFNK_OK;
 }
 
 int gmres(jfnk_ctx* c, const double* b, double* x, int* its_out, double* relres_out, int* status)
@@ -65,8 +106,8 @@ int gmres(jfnk_ctx* c, const double* b, double* x, int* its_out, double* relres_
     const double target = c->opt.gmres_eta * beta0;
     c->scal_h[1] = target;
     JF_CUDA(c, cudaMemcpyAsync(&c->gd->target, c->scal_h + 1, sizeof(double), cudaMemcpyHostToDevice, c->cur));
-    const int check = 4;
-    const int* gate = &c->gd->done;
+    const bool graphs = c->use_graphs && !c->prof.enabled;
+    if (graphs && (rc = capture_iteration(c))) return rc;
     for (int rs = 0; rs < c->opt.gmres_max_restarts; rs++) {
         // r = b - J x
         if (rs == 0) {
@@ -80,19 +121,19 @@ int gmres(jfnk_ctx* c, const double* b, double* x, int* its_out, double* relres_
         rel = c->gh->beta / beta0;
         if (!(c->gh->beta == c->gh->beta)) { *status = JFNK_DIVERGED; break; }
         if (c->gh->beta <= target) { *status = JFNK_OK; break; }
+        // Arnoldi iterations; at most two in flight ahead of the host's view of `done`
         for (int j = 0; j < m; j++) {
-            const void* vj = c->V_is_float ? (const void*)((const float*)c->V + (size_t)j * c->V_ld)
-                                           : (const void*)(c->V + (size_t)j * c->V_ld);
-            if ((rc = pc_apply_any(c, pc, vj, c->V_is_float, c->z, gate))) return rc;
-            if ((rc = norm_mode(c, c->z, n, 1, gate))) return rc;
-            if ((rc = perturb(c, c->u, c->z, c->w, gate))) return rc;
-            if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, &c->gd->eps, gate))) return rc;
-            if ((rc = arnoldi_orthogonalise(c, c->wk))) return rc;
-            if ((rc = arnoldi_finish_column(c, c->wk, j))) return rc;
-            if ((j + 1) % check == 0 && j + 1 < m) {
-                if ((rc = read_header(c))) return rc;
-                if (c->gh->done) break;
+            if (j >= 2) {
+                JF_CUDA(c, cudaEventSynchronize(c->it_ev[(j - 2) & 3]));
+                if (((volatile GmresDev*)c->gh)->done) break;
             }
+            if (graphs) {
+                JF_CUDA(c, cudaGraphLaunch(c->it_graph, c->cur));
+                c->launches += c->graph_kernels;
+            } else if ((rc = enqueue_iteration(c))) {
+                return rc;
+            }
+            JF_CUDA(c, cudaEventRecord(c->it_ev[j & 3], c->cur));
         }
         if ((rc = read_header(c))) return rc;
         const int k = c->gh->k;
@@ -117,8 +158,10 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
     auto t0 = std::chrono::steady_clock::now();
     int status = JFNK_OK, rc;
     double rn = 0, r0 = 0;
+    JF_CUDA(c, cudaMemsetAsync(&c->gd->n_reorth, 0, sizeof(int), c->cur));
     for (int step = 1; step <= n_load_steps && status == JFNK_OK; step++) {
         c->load = (double)step / n_load_steps;
+        if ((rc = sync_load(c))) return rc;
         if ((rc = residual(c, c->u, c->Ru, OUT_R, nullptr))) return rc;
         st->residual_evals++;
         if ((rc = norm2(c, c->Ru, n, c->scal))) return rc;
@@ -149,8 +192,9 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
                 s *= 0.5;
             }
             if (!acc) { status = JFNK_LS_FAILED; break; }
-            std::swap(c->u, c->w);
-            std::swap(c->Ru, c->R);
+            // copies, not pointer swaps: the captured iteration graph holds these addresses
+            JF_CUDA(c, cudaMemcpyAsync(c->u, c->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cur));
+            JF_CUDA(c, cudaMemcpyAsync(c->Ru, c->R, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cur));
             rn = rt;
             st->newton_its++;
             if (st->n_hist < 64) st->hist[st->n_hist++] = rn;
@@ -159,6 +203,7 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
         st->final_abs_res = rn;
         if (conv) st->load_steps_done++;
     }
+    if (read_header(c) == JFNK_OK) st->reorth_its = c->gh->n_reorth;
     st->status = status;
     st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return status;

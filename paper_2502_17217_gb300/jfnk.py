@@ -40,13 +40,14 @@ class Options(C.Structure):
                 ("newton_max_its", C.c_int), ("line_search_max", C.c_int), ("alpha_residual", C.c_double),
                 ("alpha_pc", C.c_double), ("jv_eps_scale", C.c_double), ("pc", C.c_int), ("precision", C.c_int),
                 ("reorth", C.c_int), ("renumber", C.c_int), ("mg_max_levels", C.c_int), ("mg_coarse_max", C.c_int),
-                ("mg_theta", C.c_double), ("mg_smooth_sweeps", C.c_int)]
+                ("mg_theta", C.c_double), ("mg_smooth_sweeps", C.c_int), ("mg_smoothed", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("gmres_its", C.c_int), ("residual_evals", C.c_int),
                 ("load_steps_done", C.c_int), ("status", C.c_int), ("final_rel_res", C.c_double),
-                ("final_abs_res", C.c_double), ("solve_ms", C.c_double), ("hist", C.c_double * 64), ("n_hist", C.c_int)]
+                ("final_abs_res", C.c_double), ("solve_ms", C.c_double), ("hist", C.c_double * 64), ("n_hist", C.c_int),
+                ("reorth_its", C.c_int)]
 
 
 _lib = None

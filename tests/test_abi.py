@@ -43,7 +43,7 @@ def test_default_options_match_header_defaults(lib):
     o = jfnk.default_options()
     assert o.gmres_restart == 30 and o.gmres_eta == 1e-3 and o.newton_rtol == 1e-8 and o.newton_atol == 1e-50
     assert o.pc == jfnk.PC_BJACOBI and o.precision == jfnk.PREC_FP64 and o.jv_eps_scale == 1e-7
-    assert o.alpha_residual == 1.0 and o.alpha_pc == 1.0 and o.mg_smooth_sweeps == 1
+    assert o.alpha_residual == 1.0 and o.alpha_pc == 1.0 and o.mg_smooth_sweeps == 2 and o.mg_smoothed == 1
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

@@ -96,15 +96,17 @@ def test_block_jacobi_parity(name):
     assert _rel(s.precondition(v, jfnk.PC_NONE), v) == 0.0
 
 
+@pytest.mark.parametrize("smoothed,sweeps", [(0, 1), (1, 2)])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 2e-5)])
-def test_multigrid_vcycle_parity(precision, tol):
-    """Same hierarchy on both sides (aggregation in the caller's cell order); FP64 V-cycle
-    agrees to round-off, the FP32 V-cycle to single precision."""
+def test_multigrid_vcycle_parity(precision, tol, smoothed, sweeps):
+    """Same hierarchy on both sides (aggregation in the caller's cell order, plain or smoothed
+    prolongation); FP64 V-cycle agrees to round-off, the FP32 V-cycle to single precision."""
     from paper_2502_17217_gb300 import jfnk
     case = I.case_cantilever(40, 8, 8, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
-    s = _solver(case, pc=jfnk.PC_MG, precision=precision, mg_coarse_max=200)
+    s = _solver(case, pc=jfnk.PC_MG, precision=precision, mg_coarse_max=200, mg_smoothed=smoothed,
+                mg_smooth_sweeps=sweeps)
     o = O.Oracle.from_case(case)
-    o.mg_setup(theta=0.25, max_levels=25, coarse_max=200)
+    o.mg_setup(theta=0.25, max_levels=25, coarse_max=200, smoothed=bool(smoothed), sweeps=sweeps)
     v = I.random_field(9, case.mesh.n_cells, 1.0)
     z = s.precondition(v, jfnk.PC_MG)
     zo = o.mg_vcycle(v)
@@ -118,7 +120,8 @@ def _solve_both(case, pc=1, load_steps=1, **kw):
     assert rc == 0, (rc, st.final_rel_res, st.newton_its, st.gmres_its)
     o = O.Oracle.from_case(case)
     if pc == jfnk.PC_MG:
-        o.mg_setup(coarse_max=s.options.mg_coarse_max)
+        o.mg_setup(coarse_max=s.options.mg_coarse_max, smoothed=bool(s.options.mg_smoothed),
+                   sweeps=s.options.mg_smooth_sweeps)
     uo, rco, sto = o.newton(load_steps=load_steps, rtol=1e-11, pc=pc)
     assert rco == 0
     return ug, uo, st, sto
@@ -161,6 +164,19 @@ def test_device_pointer_path_matches_host_path():
     Jd = s.jv(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda())
     torch.cuda.synchronize()
     assert np.array_equal(Jh, Jd.cpu().numpy())
+
+
+def test_graph_and_direct_launch_agree():
+    """The captured Arnoldi-iteration graph and direct launches give bitwise equal solves."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(30, 6, 6, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
+    s = _solver(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, mg_coarse_max=50)
+    u1, st1, rc1 = s.solve()
+    s.profile(True)  # per-kernel events force direct launches
+    u2, st2, rc2 = s.solve()
+    s.profile(False)
+    assert rc1 == rc2 == 0 and st1.gmres_its == st2.gmres_its
+    assert np.array_equal(u1, u2)
 
 
 def test_bitwise_deterministic():

@@ -207,10 +207,11 @@ def test_multigrid_aggregation_on_chain():
     assert agg[0] == agg[1] == agg[6]
 
 
-def test_multigrid_vcycle_is_symmetric_and_contracts():
+@pytest.mark.parametrize("smoothed,sweeps", [(False, 1), (True, 1), (True, 2)])
+def test_multigrid_vcycle_is_symmetric_and_contracts(smoothed, sweeps):
     c = I.case_cantilever(12, 4, 4, (1.0, 0.33, 0.33), perturb=0.15, seed=9)
     o = O.Oracle.from_case(c)
-    L = o.mg_setup(coarse_max=20)
+    L = o.mg_setup(coarse_max=20, smoothed=smoothed, sweeps=sweeps)
     assert L >= 2
     n = c.mesh.n_cells
     a, b = I.random_field(1, n), I.random_field(2, n)
@@ -222,3 +223,20 @@ def test_multigrid_vcycle_is_symmetric_and_contracts():
     _, _, its_bj, _ = o.gmres(u, rhs, eta=1e-6, pc=O.PC_BJACOBI)
     _, _, its_mg, _ = o.gmres(u, rhs, eta=1e-6, pc=O.PC_MG)
     assert its_mg < its_bj
+
+
+def test_smoothed_aggregation_prolongation_and_strength():
+    """Smoothed prolongation P = (I - omega D^-1 A) P_tent preserves the constant vector's
+    image (row sums of P equal 1 - omega D^-1 (A 1)); two-level J~ coarse operators stay
+    symmetric; smoothed aggregation needs fewer Krylov iterations than plain aggregation."""
+    c = I.case_cantilever(24, 6, 6, (1.0, 0.25, 0.25), perturb=0.15, seed=9)
+    o = O.Oracle.from_case(c)
+    n = c.mesh.n_cells
+    u = np.zeros((n, 3))
+    rhs = I.random_field(3, n, 1.0)
+    its = {}
+    for sm in (False, True):
+        o.mg_setup(coarse_max=30, smoothed=sm, sweeps=2)
+        _, rc, its[sm], _ = o.gmres(u, rhs, eta=1e-6, pc=O.PC_MG)
+        assert rc == 0
+    assert its[True] < its[False]
