@@ -142,6 +142,10 @@ def run_ours(args, rank, world):
     s = jfnk.Solver.from_case(case, device=dev.index, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED,
                               newton_rtol=1e-8, gmres_restart=30, gmres_eta=1e-3)
     s.setup()
+    # the library launches on the caller's stream: a dedicated stream, current for every call,
+    # so the CUDA events below sit on the launching stream
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     u0 = torch.zeros((nc, 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
@@ -164,9 +168,9 @@ def run_ours(args, rank, world):
         for k in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
-            ev[k][0].record()
+            ev[k][0].record(stream)
             st = step()
-            ev[k][1].record()
+            ev[k][1].record(stream)
             torch.cuda.synchronize()
             jv_total += st.gmres_its
             stats.append(st)
