@@ -196,7 +196,8 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     s.profile(False)
     kt = {}
-    for name in ("grad", "flux", "finish", "mdot", "update", "pc_mg"):
+    for name in ("grad", "flux", "finish", "mdot", "update", "pc_mg", "mg_smooth", "mg_resid", "mg_restrict",
+                 "mg_prolong", "mg_coarse"):
         ms, n = s.profile_get(name)
         kt[name] = {"ms": ms, "launches": n}
     # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -236,7 +237,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu", action="store_true", help="untimed solves only, for an ncu capture of the same kernels")
     args = ap.parse_args()
+    if args.ncu:
+        import torch
+        from paper_2502_17217_gb300 import jfnk
+        import __graft_entry__ as g
+        g.build()
+        case = workload_case()
+        s = jfnk.Solver.from_case(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-8)
+        for _ in range(args.warmup + args.steps):
+            u, st, rc = s.solve()
+            if rc != 0:
+                raise SystemExit(f"solve failed: {rc}")
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_driver": True, "gmres_its": st.gmres_its, "newton_its": st.newton_its}))
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
 

@@ -88,7 +88,7 @@ static void free_device(jfnk_ctx* c)
     c->dev_bytes = 0;
     c->dm = jfnk::DevMesh();
     c->u = c->Ru = c->w = c->R = c->z = c->x = c->bvec = c->wk = c->tmp = c->ext = nullptr;
-    c->G = c->T = c->F = c->partials = c->V = nullptr;
+    c->G = c->T = c->F = c->Fn = c->partials = c->V = nullptr;
     c->gd = nullptr;
     c->scal = nullptr;
     c->tickets = nullptr;
@@ -320,6 +320,7 @@ int jfnk_setup(jfnk_ctx* c)
     c->G = (double*)jfnk_dalloc(c, sizeof(double) * 9 * (size_t)nc);
     c->T = (double*)jfnk_dalloc(c, sizeof(double) * (c->law == JFNK_LAW_NEOHOOKEAN ? 9 * (size_t)nc : 1));
     c->F = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)std::max(1, c->dm.nflux));
+    c->Fn = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)std::max(1, c->dm.ni));
     const size_t chunks = (v3 + 2047) / 2048 + 2 * (size_t)jfnk::kRedBlocks;
     c->partials = (double*)jfnk_dalloc(c, sizeof(double) * chunks * (jfnk::kMaxRestart + 2));
     c->V_is_float = c->opt.precision == JFNK_PREC_MIXED;
@@ -329,7 +330,7 @@ int jfnk_setup(jfnk_ctx* c)
     c->gd = (jfnk::GmresDev*)jfnk_dalloc(c, sizeof(jfnk::GmresDev));
     c->scal = (double*)jfnk_dalloc(c, 16 * sizeof(double));
     c->tickets = (unsigned*)jfnk_dalloc(c, 16 * sizeof(unsigned));
-    if (!c->G || !c->T || !c->F || !c->partials || !c->V || !c->gd || !c->scal || !c->tickets)
+    if (!c->G || !c->T || !c->F || !c->Fn || !c->partials || !c->V || !c->gd || !c->scal || !c->tickets)
         return jfnk_fail(c, JFNK_ENOMEM, "device allocation of solver buffers failed");
     rc = jfnk::pc_setup(c);
     if (rc) return rc;

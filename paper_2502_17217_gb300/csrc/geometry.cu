@@ -279,6 +279,11 @@ int setup_device_mesh(jfnk_ctx* c)
     m.fo_ptr = upload(c, t.fo_ptr);
     m.fn_ptr = upload(c, t.fn_ptr);
     m.fn_face = upload(c, t.fn_face);
+    {
+        std::vector<int32_t> pos(std::max(1, t.ni), 0);
+        for (int k = 0; k < t.ni; k++) pos[t.fn_face[k]] = k;
+        m.fn_pos = upload(c, pos);
+    }
     m.fd_ptr = upload(c, t.fd_ptr);
     m.ft_ptr = upload(c, t.ft_ptr);
     m.ca_ptr = upload(c, t.ca_ptr);
@@ -303,7 +308,7 @@ int setup_device_mesh(jfnk_ctx* c)
     m.jt_dinv = (double*)jfnk_dalloc(c, sizeof(double) * (size_t)nc);
     m.jt_dinv_f = (float*)jfnk_dalloc(c, sizeof(float) * (size_t)nc);
     m.err = (int32_t*)jfnk_dalloc(c, sizeof(int32_t));
-    if (!m.pts || !m.fptr || !m.fpts || !m.own || !m.nei || !m.fo_ptr || !m.fn_ptr || !m.fn_face || !m.fd_ptr ||
+    if (!m.pts || !m.fptr || !m.fpts || !m.own || !m.nei || !m.fo_ptr || !m.fn_ptr || !m.fn_face || !m.fn_pos || !m.fd_ptr ||
         !m.ft_ptr || !m.ca_ptr || !m.ca_face || !m.sell_off || !m.sell_w || !m.sell_nbr || !m.sell_face || !m.n2o ||
         !m.bval || !m.sell_l || !m.Sf || !m.Cf || !m.V || !m.C || !m.coef || !m.b0 || !m.fb || !m.jt_c ||
         !m.jt_diag || !m.jt_dinv || !m.jt_dinv_f || !m.err)

@@ -75,6 +75,7 @@ struct DevMesh {
     int32_t *fptr = nullptr, *fpts = nullptr;
     int32_t *own = nullptr, *nei = nullptr;
     int32_t *fo_ptr = nullptr, *fn_ptr = nullptr, *fn_face = nullptr, *fd_ptr = nullptr, *ft_ptr = nullptr;
+    int32_t* fn_pos = nullptr;       // [ni] position of each internal face in the neighbour-sorted list
     int32_t *ca_ptr = nullptr, *ca_face = nullptr;
     int32_t *sell_off = nullptr, *sell_w = nullptr, *sell_nbr = nullptr, *sell_face = nullptr;
     double* sell_l = nullptr;        // [3][n_slots] least-squares vectors
@@ -152,7 +153,8 @@ struct jfnk_ctx {
     double *u = nullptr, *Ru = nullptr, *w = nullptr, *R = nullptr, *z = nullptr, *x = nullptr;
     double *bvec = nullptr, *wk = nullptr, *tmp = nullptr, *ext = nullptr;
     double *G = nullptr, *T = nullptr;  // [9][nc]
-    double* F = nullptr;                 // [3][nflux]
+    double* F = nullptr;                 // [3][nflux] face fluxes, owner-sorted
+    double* Fn = nullptr;                // [3][ni] the same fluxes, neighbour-sorted
     double* partials = nullptr;          // reduction partials
     double* V = nullptr;                 // Krylov basis (double or float storage)
     size_t V_ld = 0;                     // stride between basis vectors (elements)

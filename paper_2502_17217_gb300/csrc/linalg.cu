@@ -149,10 +149,11 @@ __device__ void givens_step(GmresDev* gd, int m)
 }
 
 // Multi-dot h_i = V_i . w (i <= j) and, in pass 0, |w|^2.  Grid: x = element chunks of
-// kMdotThreads * kMdotE elements, y = groups of kMdotVG vectors; each thread keeps its
-// kMdotE elements of w in registers, so w is read once per group and each basis vector once.
-// pass 1 runs only when the pass-0 test asked for re-orthogonalisation.
-constexpr int kMdotThreads = 128, kMdotE = 16, kMdotVG = 8;
+// kMdotThreads * kMdotE elements, y = one basis vector per block (so the GPU has many
+// independent blocks in flight); each thread keeps kMdotE elements of w in registers and
+// accumulates kMdotE products before the FP64 warp reduction.  Pass 1 runs only when the
+// pass-0 test asked for re-orthogonalisation.
+constexpr int kMdotThreads = 128, kMdotE = 32;
 
 template <typename TV>
 __global__ void __launch_bounds__(kMdotThreads) k_mdot(size_t n, const TV* __restrict__ V, size_t ld,
@@ -163,65 +164,65 @@ __global__ void __launch_bounds__(kMdotThreads) k_mdot(size_t n, const TV* __res
     if (pass == 1 && !gd->reorth) return;
     const int j = gd->j, nv = j + 1;
     const int nvals = nv + (pass == 0 ? 1 : 0);
-    const int nblk = gridDim.x * gridDim.y;
-    __shared__ double sh[kMdotVG][kMdotThreads / 32];
+    const unsigned nblk = gridDim.x * gridDim.y;
+    __shared__ double sh[kMdotThreads / 32];
     __shared__ double sums[kMaxRestart + 2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int v0 = blockIdx.y * kMdotVG;
-    if (v0 < nvals) {
+    const int i = blockIdx.y;
+    if (i < nvals) {
         const size_t base = (size_t)blockIdx.x * (kMdotThreads * kMdotE) + threadIdx.x;
-        double we[kMdotE];
+        double acc = 0.0;
+        if (i < nv) {
+            const TV* vi = V + (size_t)i * ld;
+            TV vv[kMdotE];
 #pragma unroll
-        for (int q = 0; q < kMdotE; q++) {
-            const size_t e = base + (size_t)q * kMdotThreads;
-            we[q] = e < n ? w[e] : 0.0;
-        }
-        const int vend = min(nvals, v0 + kMdotVG);
-        for (int i = v0; i < vend; i++) {
-            double acc = 0.0;
-            if (i < nv) {
-                const TV* vi = V + (size_t)i * ld;
-#pragma unroll
-                for (int q = 0; q < kMdotE; q++) {
-                    const size_t e = base + (size_t)q * kMdotThreads;
-                    if (e < n) acc = fma((double)vi[e], we[q], acc);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < kMdotE; q++) acc = fma(we[q], we[q], acc);
+            for (int q = 0; q < kMdotE; q++) {
+                const size_t e = base + (size_t)q * kMdotThreads;
+                vv[q] = e < n ? vi[e] : (TV)0;
             }
-            acc = warp_sum(acc);
-            if (lane == 0) sh[i - v0][wid] = acc;
+#pragma unroll
+            for (int q = 0; q < kMdotE; q++) {
+                const size_t e = base + (size_t)q * kMdotThreads;
+                if (e < n) acc = fma((double)vv[q], w[e], acc);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kMdotE; q++) {
+                const size_t e = base + (size_t)q * kMdotThreads;
+                if (e < n) { const double x = w[e]; acc = fma(x, x, acc); }
+            }
         }
+        acc = warp_sum(acc);
+        if (lane == 0) sh[wid] = acc;
         __syncthreads();
-        if (threadIdx.x < kMdotVG && v0 + (int)threadIdx.x < vend) {
+        if (threadIdx.x == 0) {
             double s = 0.0;
 #pragma unroll
-            for (int x = 0; x < kMdotThreads / 32; x++) s += sh[threadIdx.x][x];
-            partials[(size_t)(v0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+            for (int x = 0; x < kMdotThreads / 32; x++) s += sh[x];
+            partials[(size_t)i * gridDim.x + blockIdx.x] = s;
         }
     }
     // last block: sum the per-chunk partials of every value (warp per value)
     __shared__ bool is_last;
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&gd->ticket[0], 1u) == (unsigned)nblk - 1);
+    if (threadIdx.x == 0) is_last = (atomicAdd(&gd->ticket[0], 1u) == nblk - 1);
     __syncthreads();
     if (!is_last) return;
-    for (int i = wid; i < nvals; i += kMdotThreads / 32) {
+    for (int v = wid; v < nvals; v += kMdotThreads / 32) {
         double sacc = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) sacc += __ldcg(partials + (size_t)i * gridDim.x + b);
+        for (int b = lane; b < (int)gridDim.x; b += 32) sacc += __ldcg(partials + (size_t)v * gridDim.x + b);
         sacc = warp_sum(sacc);
-        if (lane == 0) sums[i] = sacc;
+        if (lane == 0) sums[v] = sacc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double hh = 0.0;
-        for (int i = 0; i < nv; i++) {
-            gd->h[i] = sums[i];
-            if (pass == 0) gd->H[i + (size_t)m1 * j] = sums[i];
-            else gd->H[i + (size_t)m1 * j] += sums[i];
-            hh += sums[i] * sums[i];
+        for (int v = 0; v < nv; v++) {
+            gd->h[v] = sums[v];
+            if (pass == 0) gd->H[v + (size_t)m1 * j] = sums[v];
+            else gd->H[v + (size_t)m1 * j] += sums[v];
+            hh += sums[v] * sums[v];
         }
         if (pass == 0) {
             const double wn2 = sums[nv];
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kMdotThreads) k_mdot(size_t n, const TV* __res
 
 // w -= sum_i h_i V_i, then |w|.  The final pass stores H(j+1, j) = |w|, 1/|w| and runs the
 // Givens step (which advances j).  Each thread updates kUpdE elements (independent chains).
-constexpr int kUpdThreads = 256, kUpdE = 4;
+constexpr int kUpdThreads = 256, kUpdE = 2;
 
 template <typename TV>
 __global__ void __launch_bounds__(kUpdThreads) k_update(size_t n, const TV* __restrict__ V, size_t ld,
@@ -261,6 +262,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(size_t n, const TV* __re
             const size_t e = base + (size_t)q * kUpdThreads;
             s[q] = e < n ? w[e] : 0.0;
         }
+#pragma unroll 4
         for (int i = 0; i < nv; i++) {
             const TV* vi = V + (size_t)i * ld;
             const double h = hs[i];
@@ -403,8 +405,8 @@ int arnoldi_orthogonalise(jfnk_ctx* c, double* w)
     const int always = c->opt.reorth ? 1 : 0;
     int sl_d = c->prof.enabled ? c->prof.slot("mdot") : -1;
     int sl_u = c->prof.enabled ? c->prof.slot("update") : -1;
-    const dim3 gd_mdot((unsigned)((n + kMdotThreads * kMdotE - 1) / (kMdotThreads * kMdotE)), (unsigned)((m + 2 + kMdotVG - 1) / kMdotVG));
-    const int gu = (int)std::min<size_t>((n + kUpdThreads * kUpdE - 1) / (kUpdThreads * kUpdE), (size_t)kRedBlocks * 2);
+    const dim3 gd_mdot((unsigned)((n + kMdotThreads * kMdotE - 1) / (kMdotThreads * kMdotE)), (unsigned)(m + 1));
+    const int gu = (int)std::min<size_t>((n + kUpdThreads * kUpdE - 1) / (kUpdThreads * kUpdE), (size_t)kRedBlocks * 4);
     for (int pass = 0; pass < 2; pass++) {
         jfnk_prof_begin(c, sl_d);
         if (c->V_is_float)

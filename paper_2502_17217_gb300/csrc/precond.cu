@@ -10,6 +10,8 @@
 // FP32 runs on the wide FP32 pipe of GB300, FP64 on a pipe ~64x narrower.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "device_common.cuh"
@@ -384,6 +386,11 @@ int pc_setup(jfnk_ctx* c)
     rc = mg_upload<double>(c, S.d, lv, inv, jc, adiag0, tr);
     if (rc) return rc;
     c->mg_coarse_n = lv.back().n;
+    if (getenv("JFNK_VERBOSE")) {
+        for (size_t l = 0; l < lv.size(); l++)
+            fprintf(stderr, "[jfnk] multigrid level %zu: %d rows, %zu nonzeros, P nonzeros %zu\n", l, lv[l].n,
+                    lv[l].col.size(), lv[l].pcol.size());
+    }
     S.ready = true;
     c->mg_ready = true;
     return JFNK_OK;
@@ -423,6 +430,10 @@ template <typename T, typename TV>
 static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const int* jidx, double* z, const int* gate)
 {
     cudaStream_t s = c->cur;
+    const bool pf = c->prof.enabled;
+    const int s_sm = pf ? c->prof.slot("mg_smooth") : -1, s_re = pf ? c->prof.slot("mg_resid") : -1;
+    const int s_rs = pf ? c->prof.slot("mg_restrict") : -1, s_pr = pf ? c->prof.slot("mg_prolong") : -1;
+    const int s_co = pf ? c->prof.slot("mg_coarse") : -1;
     const T omega = (T)(2.0 / 3.0);
     const int nl = (int)M.L.size();
     const int sweeps = std::max(1, c->opt.mg_smooth_sweeps);
@@ -440,6 +451,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     for (int l = 0; l < nl - 1; l++) {
         auto& D = M.L[l];
         const LevelOp<T> op = level_op<T>(c, M, l);
+        jfnk_prof_begin(c, s_sm);
         if (l == 0) k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, vbase, ld, jidx, D.dinv, omega, D.b, D.x);
         else k_mg_pre<T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.dinv, omega, D.b, D.x);
         JF_LAUNCHED(c);
@@ -448,30 +460,41 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
             JF_LAUNCHED(c);
             std::swap(D.x, D.x2);
         }
+        jfnk_prof_end(c, s_sm);
+        jfnk_prof_begin(c, s_re);
         k_mg_resid<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, D.b, D.x, D.r);
         JF_LAUNCHED(c);
+        jfnk_prof_end(c, s_re);
         auto& Cn = M.L[l + 1];
+        jfnk_prof_begin(c, s_rs);
         k_mg_spmv<T><<<nb(D.nco, 256), 256, 0, s>>>(gate, D.nco, D.n, D.rrp, D.rcol, D.rval, D.r, Cn.b, 0);
         JF_LAUNCHED(c);
+        jfnk_prof_end(c, s_rs);
     }
     {
         auto& Dc = M.L[nl - 1];
+        jfnk_prof_begin(c, s_co);
         k_mg_coarse<T><<<nb(32L * Dc.n, 256), 256, 0, s>>>(gate, Dc.n, M.Ainv, Dc.b, Dc.x);
         JF_LAUNCHED(c);
+        jfnk_prof_end(c, s_co);
     }
     // upward
     for (int l = nl - 2; l >= 0; l--) {
         auto& D = M.L[l];
         auto& Cn = M.L[l + 1];
         const LevelOp<T> op = level_op<T>(c, M, l);
+        jfnk_prof_begin(c, s_pr);
         k_mg_spmv<T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, Cn.n, D.prp, D.pcol, D.pval, Cn.x, D.x, 1);
         JF_LAUNCHED(c);
+        jfnk_prof_end(c, s_pr);
+        jfnk_prof_begin(c, s_sm);
         for (int sw = 0; sw < sweeps; sw++) {
             const bool last = (l == 0 && sw == sweeps - 1);
             k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
             JF_LAUNCHED(c);
             if (!last) std::swap(D.x, D.x2);
         }
+        jfnk_prof_end(c, s_sm);
     }
     return JFNK_OK;
 }

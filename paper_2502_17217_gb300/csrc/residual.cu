@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(128) k_grad(const int* __restrict__ gate, int 
     double g[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) g[q] = 0.0;
+#pragma unroll 2
     for (int k = 0; k < w; k++) {
         const int slot = base + 32 * k + lane;
         const int N = sell_nbr[slot];
@@ -93,7 +94,8 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
                                               const int32_t* __restrict__ nei, const double* __restrict__ coef,
                                               const double* __restrict__ u, const double* __restrict__ G,
                                               const double* __restrict__ T, const double* __restrict__ bval,
-                                              const double* __restrict__ load_dev, double* __restrict__ F)
+                                              const double* __restrict__ load_dev, const int32_t* __restrict__ fn_pos,
+                                              double* __restrict__ F, double* __restrict__ Fn)
 {
     if (gate && *gate) return;
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -167,11 +169,17 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
     }
 #pragma unroll
     for (int c = 0; c < 3; c++) F[(size_t)c * nflux + f] = t[c];
+    if (internal) {
+        // the same flux in the neighbour-sorted order, so the cell pass reads contiguous ranges
+        const int q = fn_pos[f];
+#pragma unroll
+        for (int c = 0; c < 3; c++) Fn[(size_t)c * ni + q] = t[c];
+    }
 }
 
 // mode 0: out = R;  mode 1: out = (R - Ru) / eps  (eps from device memory; 0 -> out = 0)
-__global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int dim, const int32_t* __restrict__ fo_ptr,
-                                                const int32_t* __restrict__ fn_ptr, const int32_t* __restrict__ fn_face,
+__global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int ni, int dim, const int32_t* __restrict__ fo_ptr,
+                                                const int32_t* __restrict__ fn_ptr, const double* __restrict__ Fn,
                                                 const int32_t* __restrict__ fd_ptr, const double* __restrict__ F,
                                                 const double* __restrict__ b0, const double* __restrict__ load_dev, int mode,
                                                 const double* __restrict__ Ru, const double* __restrict__ eps_dev,
@@ -186,8 +194,7 @@ __global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int dim, cons
         r0 += F[f]; r1 += F[nflux + f]; r2 += F[2 * (size_t)nflux + f];
     }
     for (int k = fn_ptr[P]; k < fn_ptr[P + 1]; k++) {
-        const int f = fn_face[k];
-        r0 -= F[f]; r1 -= F[nflux + f]; r2 -= F[2 * (size_t)nflux + f];
+        r0 -= Fn[k]; r1 -= Fn[ni + k]; r2 -= Fn[2 * (size_t)ni + k];
     }
     for (int f = fd_ptr[P]; f < fd_ptr[P + 1]; f++) {
         r0 += F[f]; r1 += F[nflux + f]; r2 += F[2 * (size_t)nflux + f];
@@ -239,15 +246,15 @@ int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, cons
         jfnk_prof_begin(c, sl[1]);
         if (c->law == JFNK_LAW_LINEAR)
             k_flux<JFNK_LAW_LINEAR><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
-                                                                        u_int, c->G, c->T, m.bval, &c->gd->load, c->F);
+                                                                        u_int, c->G, c->T, m.bval, &c->gd->load, m.fn_pos, c->F, c->Fn);
         else
             k_flux<JFNK_LAW_NEOHOOKEAN><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
-                                                                            u_int, c->G, c->T, m.bval, &c->gd->load, c->F);
+                                                                            u_int, c->G, c->T, m.bval, &c->gd->load, m.fn_pos, c->F, c->Fn);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, sl[1]);
     }
     jfnk_prof_begin(c, sl[2]);
-    k_finish<<<nblk(m.nc, 256), 256, 0, s>>>(m.nc, m.nflux, m.dim, m.fo_ptr, m.fn_ptr, m.fn_face, m.fd_ptr, c->F, m.b0,
+    k_finish<<<nblk(m.nc, 256), 256, 0, s>>>(m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, c->Fn, m.fd_ptr, c->F, m.b0,
                                             &c->gd->load, mode, c->Ru, eps_dev, gate, out);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);
