@@ -70,7 +70,7 @@ typedef struct jfnk_options {
     int pc;                 /* JFNK_PC_*                                         (BJACOBI)   */
     int precision;          /* JFNK_PREC_*                                          (FP64)   */
     int reorth;             /* 0: classical Gram-Schmidt twice when the norm drops by more
-                               than 1/sqrt(2) (selective); 1: always twice            (0)   */
+                               than 1/sqrt(2) (selective); 1: always twice; 2: once   (0)   */
     int renumber;           /* 1: reverse Cuthill-McKee cell renumbering               (1)   */
     int mg_max_levels;      /* multigrid levels (Sec. 4.2: up to 25)                   (25)  */
     int mg_coarse_max;      /* rows of the coarsest (dense Cholesky) level             (2000)*/
@@ -169,6 +169,11 @@ int jfnk_profile_reset(jfnk_ctx* ctx);
 int64_t jfnk_launch_count(const jfnk_ctx* ctx);
 /* Device bytes held by the context. */
 int64_t jfnk_device_bytes(const jfnk_ctx* ctx);
+/* The float -> double conversion the FP32 Krylov basis is read through (integer operations,
+ * so it does not occupy the narrow FP64 pipe): out[i] = in[i] exactly for normal floats and
+ * zeros; float subnormals give zero; Inf/NaN give NaN.  in/out are device arrays of n
+ * elements; the work is enqueued on `stream` (a cudaStream_t, NULL = legacy default). */
+int jfnk_convert_f32_to_f64(const float* in, double* out, int64_t n, void* stream);
 
 #ifdef __cplusplus
 }

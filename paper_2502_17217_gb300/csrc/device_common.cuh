@@ -55,4 +55,20 @@ __device__ __forceinline__ double reduce_partials(const double* partials, int n,
     return block_sum(s, sh);
 }
 
+// float -> double without the FP64 pipe (on GB300 a conversion costs as much as a DFMA):
+// the exponent is re-biased and the mantissa shifted with integer operations.  Exact for
+// normal floats and zero; float subnormals (|x| < 1.2e-38) become zero; Inf/NaN become NaN.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned a = u & 0x7fffffffu;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    unsigned long long bits = sign | (((unsigned long long)a << 29) + (896ull << 52));
+    bits = (a < 0x00800000u) ? sign : bits;                       // zero and subnormals
+    bits = (a >= 0x7f800000u) ? 0x7ff8000000000000ull : bits;     // Inf, NaN
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double to_f64(float f) { return f2d(f); }
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
 }  // namespace jfnk

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kMdotThreads) k_mdot(size_t n, const TV* __res
 #pragma unroll
             for (int q = 0; q < kMdotE; q++) {
                 const size_t e = base + (size_t)q * kMdotThreads;
-                if (e < n) acc = fma((double)vv[q], w[e], acc);
+                if (e < n) acc = fma(to_f64(vv[q]), w[e], acc);
             }
         } else {
 #pragma unroll
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kMdotThreads) k_mdot(size_t n, const TV* __res
             gd->wn2 = wn2;
             // classical Gram-Schmidt is repeated when the projection removed more than half
             // of |w|^2, i.e. |w'| < |w| / sqrt(2) (the 'twice is enough' test)
-            gd->reorth = (always_reorth || (wn2 - hh) < 0.5 * wn2) ? 1 : 0;
+            gd->reorth = (always_reorth == 1 || (always_reorth == 0 && (wn2 - hh) < 0.5 * wn2)) ? 1 : 0;
         } else {
             gd->n_reorth++;
         }
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(size_t n, const TV* __re
 #pragma unroll
             for (int q = 0; q < kUpdE; q++) {
                 const size_t e = base + (size_t)q * kUpdThreads;
-                if (e < n) s[q] = fma(-h, (double)vi[e], s[q]);
+                if (e < n) s[q] = fma(-h, to_f64(vi[e]), s[q]);
             }
         }
 #pragma unroll
@@ -329,9 +329,15 @@ __global__ void k_combine(size_t n, const TV* __restrict__ V, size_t ld, const G
     __syncthreads();
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int i = 0; i < k; i++) s = fma(ys[i], (double)V[(size_t)i * ld + e], s);
+        for (int i = 0; i < k; i++) s = fma(ys[i], to_f64(V[(size_t)i * ld + e]), s);
         out[e] = s;
     }
+}
+
+__global__ void k_f2d(size_t n, const float* __restrict__ in, double* __restrict__ out)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = f2d(in[e]);
 }
 
 // ------------------------------------------------------------------ host wrappers
@@ -402,7 +408,7 @@ int arnoldi_orthogonalise(jfnk_ctx* c, double* w)
     // Givens step; then V_{j+1} = w / |w|
     const size_t n = 3 * (size_t)c->dm.nc;
     const int m = c->opt.gmres_restart, m1 = m + 1;
-    const int always = c->opt.reorth ? 1 : 0;
+    const int always = c->opt.reorth;  // 0 selective, 1 always, 2 never
     int sl_d = c->prof.enabled ? c->prof.slot("mdot") : -1;
     int sl_u = c->prof.enabled ? c->prof.slot("update") : -1;
     const dim3 gd_mdot((unsigned)((n + kMdotThreads * kMdotE - 1) / (kMdotThreads * kMdotE)), (unsigned)(m + 1));
@@ -441,3 +447,11 @@ int cycle_solution(jfnk_ctx* c, double* out)
 }
 
 }  // namespace jfnk
+
+extern "C" int jfnk_convert_f32_to_f64(const float* in, double* out, int64_t n, void* stream)
+{
+    if ((!in || !out) && n > 0) return JFNK_EINVAL;
+    if (n <= 0) return JFNK_OK;
+    jfnk::k_f2d<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>((size_t)n, in, out);
+    return cudaGetLastError() == cudaSuccess ? JFNK_OK : JFNK_ECUDA;
+}

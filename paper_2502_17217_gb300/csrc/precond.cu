@@ -32,7 +32,7 @@ __global__ void k_bjacobi(const int* gate, int nc, const TV* __restrict__ base, 
     const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
     const TP d = dinv[P];
 #pragma unroll
-    for (int k = 0; k < 3; k++) z[(size_t)k * nc + P] = (double)((TP)v[(size_t)k * nc + P] * d);
+    for (int k = 0; k < 3; k++) z[(size_t)k * nc + P] = to_f64((TP)v[(size_t)k * nc + P] * d);
 }
 
 template <typename TV>
@@ -44,7 +44,7 @@ __global__ void k_copy_vec(const int* gate, int nc, const TV* __restrict__ base,
     if (P >= nc) return;
     const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
 #pragma unroll
-    for (int k = 0; k < 3; k++) z[(size_t)k * nc + P] = (double)v[(size_t)k * nc + P];
+    for (int k = 0; k < 3; k++) z[(size_t)k * nc + P] = to_f64(v[(size_t)k * nc + P]);
 }
 
 template <typename TV>
@@ -52,7 +52,7 @@ __global__ void k_copy_to_double(const int* gate, size_t n, const TV* __restrict
 {
     if (gate && *gate) return;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-        z[e] = (double)v[e];
+        z[e] = to_f64(v[e]);
 }
 
 // ------------------------------------------------------------------ multigrid kernels
@@ -152,7 +152,7 @@ __global__ void k_mg_jacobi(const int* gate, LevelOp<T> op, T omega, const T* __
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         const T xn = x[(size_t)k * n + i] + d * (b[(size_t)k * n + i] - ax[k]);
-        if (zd) zd[(size_t)k * n + i] = (double)xn;
+        if (zd) zd[(size_t)k * n + i] = to_f64(xn);
         else xo[(size_t)k * n + i] = xn;
     }
 }
@@ -186,6 +186,64 @@ __global__ void k_mg_spmv(const int* gate, int nrow, int nx, const int32_t* __re
     for (int k = 0; k < 3; k++) {
         if (add) y[(size_t)k * nrow + i] += s[k];
         else y[(size_t)k * nrow + i] = s[k];
+    }
+}
+
+// y = M x (add = 0) or y += M x (add = 1), one warp per row (long rows: P^T and coarse A)
+template <typename T>
+__global__ void k_mg_spmv_warp(const int* gate, int nrow, int nx, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add)
+{
+    if (gate && *gate) return;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= nrow) return;
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+        const int j = col[q];
+        const T a = val[q];
+        s0 += a * x[j]; s1 += a * x[nx + j]; s2 += a * x[2 * (size_t)nx + j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        if (add) { y[i] += s0; y[nrow + i] += s1; y[2 * (size_t)nrow + i] += s2; }
+        else { y[i] = s0; y[nrow + i] = s1; y[2 * (size_t)nrow + i] = s2; }
+    }
+}
+
+// Jacobi sweep or residual on a coarse (CSR) level, one warp per row:
+// mode 0: xo = x + omega D^-1 (b - A x);  mode 1: xo = b - A x
+template <typename T>
+__global__ void k_mg_csr_warp(const int* gate, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const T* __restrict__ val, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
+                              const T* __restrict__ x, T* __restrict__ xo, int mode)
+{
+    if (gate && *gate) return;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (i >= n) return;
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+        const int j = col[q];
+        const T a = val[q];
+        s0 += a * x[j]; s1 += a * x[n + j]; s2 += a * x[2 * (size_t)n + j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        const T r0 = b[i] - s0, r1 = b[n + i] - s1, r2 = b[2 * (size_t)n + i] - s2;
+        if (mode == 1) { xo[i] = r0; xo[n + i] = r1; xo[2 * (size_t)n + i] = r2; }
+        else {
+            const T d = omega * dinv[i];
+            xo[i] = x[i] + d * r0; xo[n + i] = x[n + i] + d * r1; xo[2 * (size_t)n + i] = x[2 * (size_t)n + i] + d * r2;
+        }
     }
 }
 
@@ -456,18 +514,20 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         else k_mg_pre<T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.dinv, omega, D.b, D.x);
         JF_LAUNCHED(c);
         for (int sw = 1; sw < sweeps; sw++) {
-            k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, nullptr);
+            if (l == 0) k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, nullptr);
+            else k_mg_csr_warp<T><<<nb(32L * D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.x2, 0);
             JF_LAUNCHED(c);
             std::swap(D.x, D.x2);
         }
         jfnk_prof_end(c, s_sm);
         jfnk_prof_begin(c, s_re);
-        k_mg_resid<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, D.b, D.x, D.r);
+        if (l == 0) k_mg_resid<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, D.b, D.x, D.r);
+        else k_mg_csr_warp<T><<<nb(32L * D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.r, 1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_re);
         auto& Cn = M.L[l + 1];
         jfnk_prof_begin(c, s_rs);
-        k_mg_spmv<T><<<nb(D.nco, 256), 256, 0, s>>>(gate, D.nco, D.n, D.rrp, D.rcol, D.rval, D.r, Cn.b, 0);
+        k_mg_spmv_warp<T><<<nb(32L * D.nco, 256), 256, 0, s>>>(gate, D.nco, D.n, D.rrp, D.rcol, D.rval, D.r, Cn.b, 0);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_rs);
     }
@@ -490,7 +550,8 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         jfnk_prof_begin(c, s_sm);
         for (int sw = 0; sw < sweeps; sw++) {
             const bool last = (l == 0 && sw == sweeps - 1);
-            k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
+            if (l == 0) k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
+            else k_mg_csr_warp<T><<<nb(32L * D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.x2, 0);
             JF_LAUNCHED(c);
             if (!last) std::swap(D.x, D.x2);
         }

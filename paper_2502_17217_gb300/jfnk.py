@@ -30,7 +30,7 @@ EXPORTS = [
     "jfnk_set_mesh", "jfnk_set_patch", "jfnk_set_material", "jfnk_set_body_force", "jfnk_set_load_factor",
     "jfnk_setup", "jfnk_residual", "jfnk_jv", "jfnk_precondition", "jfnk_solve", "jfnk_get_geometry",
     "jfnk_get_gradient", "jfnk_get_permutation", "jfnk_profile_enable", "jfnk_profile_get", "jfnk_profile_reset",
-    "jfnk_launch_count", "jfnk_device_bytes",
+    "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64",
 ]
 
 
@@ -86,6 +86,7 @@ def load():
         "jfnk_profile_reset": (i, [vp]),
         "jfnk_launch_count": (C.c_int64, [vp]),
         "jfnk_device_bytes": (C.c_int64, [vp]),
+        "jfnk_convert_f32_to_f64": (i, [vp, vp, C.c_int64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -179,6 +179,30 @@ def test_graph_and_direct_launch_agree():
     assert np.array_equal(u1, u2)
 
 
+def test_f32_to_f64_conversion_matches_ieee():
+    """The integer float->double conversion equals the IEEE widening (numpy) for normal
+    floats and signed zeros; subnormals flush to zero; Inf/NaN give NaN."""
+    import torch
+    from paper_2502_17217_gb300 import jfnk
+    L = jfnk.load()
+    rng = np.random.default_rng(0)
+    vals = np.concatenate([
+        (rng.standard_normal(100000) * 10.0 ** rng.uniform(-37, 37, 100000)).astype(np.float32),
+        np.array([0.0, -0.0, 1.0, -1.0, np.finfo(np.float32).max, np.finfo(np.float32).tiny,
+                  -np.finfo(np.float32).tiny, 3.0e-39, -1.0e-45, np.inf, -np.inf, np.nan], np.float32)])
+    x = torch.from_numpy(vals).cuda()
+    y = torch.empty(vals.size, dtype=torch.float64, device="cuda")
+    assert L.jfnk_convert_f32_to_f64(x.data_ptr(), y.data_ptr(), vals.size, None) == 0
+    torch.cuda.synchronize()
+    out = y.cpu().numpy()
+    ref = vals.astype(np.float64)
+    normal = np.isfinite(vals) & ((np.abs(vals) >= np.finfo(np.float32).tiny) | (vals == 0))
+    assert np.array_equal(out[normal].view(np.int64), ref[normal].view(np.int64))  # bitwise, incl. -0
+    sub = np.isfinite(vals) & (np.abs(vals) < np.finfo(np.float32).tiny) & (vals != 0)
+    assert np.all(out[sub] == 0)
+    assert np.all(np.isnan(out[~np.isfinite(vals)]))
+
+
 def test_bitwise_deterministic():
     case = CASES["nh_beam_24x6x6"]()
     s = _solver(case)
