@@ -21,7 +21,7 @@ def lib():
 
 def _declared():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"\b(jfnk_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(jfnk_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_and_binding_agree():
@@ -31,7 +31,7 @@ def test_header_and_binding_agree():
 
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (jfnk_[a-z_]+)\b", out))
+    exported = set(re.findall(r"\bT (jfnk_[a-z0-9_]+)\b", out))
     missing = [f for f in _declared() if f not in exported]
     assert not missing, missing
     for f in _declared():
