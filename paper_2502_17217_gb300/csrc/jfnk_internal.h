@@ -212,6 +212,8 @@ enum ResidualOut { OUT_R = 0, OUT_JV = 1 };
 int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev);
 int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate);
 int sync_load(jfnk_ctx* c);
+int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate,
+                  double* G, double* T, double* F, double* Fn);
 // linalg.cu
 int perm_in(jfnk_ctx* c, const double* ext_aos, double* int_soa);
 int perm_out(jfnk_ctx* c, const double* int_soa, double* ext_aos);

@@ -228,6 +228,12 @@ int sync_load(jfnk_ctx* c)
 
 int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate)
 {
+    return residual_bufs(c, u_int, out, mode, eps_dev, gate, c->G, c->T, c->F, c->Fn);
+}
+
+int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate,
+                  double* G, double* T, double* F, double* Fn)
+{
     const DevMesh& m = c->dm;
     cudaStream_t s = c->cur;
     static const char* const kNames[3] = {"grad", "flux", "finish"};
@@ -236,25 +242,25 @@ int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, cons
     jfnk_prof_begin(c, sl[0]);
     if (c->law == JFNK_LAW_LINEAR)
         k_grad<JFNK_LAW_LINEAR><<<nblk(m.nc, 128), 128, 0, s>>>(gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr,
-                                                                 m.sell_l, m.n_slots, u_int, c->G, c->T, c->mu, c->kappa);
+                                                                 m.sell_l, m.n_slots, u_int, G, T, c->mu, c->kappa);
     else
         k_grad<JFNK_LAW_NEOHOOKEAN><<<nblk(m.nc, 128), 128, 0, s>>>(gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr,
-                                                                     m.sell_l, m.n_slots, u_int, c->G, c->T, c->mu, c->kappa);
+                                                                     m.sell_l, m.n_slots, u_int, G, T, c->mu, c->kappa);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[0]);
     if (m.nflux > 0) {
         jfnk_prof_begin(c, sl[1]);
         if (c->law == JFNK_LAW_LINEAR)
             k_flux<JFNK_LAW_LINEAR><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
-                                                                        u_int, c->G, c->T, m.bval, &c->gd->load, m.fn_pos, c->F, c->Fn);
+                                                                        u_int, G, T, m.bval, &c->gd->load, m.fn_pos, F, Fn);
         else
             k_flux<JFNK_LAW_NEOHOOKEAN><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
-                                                                            u_int, c->G, c->T, m.bval, &c->gd->load, m.fn_pos, c->F, c->Fn);
+                                                                            u_int, G, T, m.bval, &c->gd->load, m.fn_pos, F, Fn);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, sl[1]);
     }
     jfnk_prof_begin(c, sl[2]);
-    k_finish<<<nblk(m.nc, 256), 256, 0, s>>>(m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, c->Fn, m.fd_ptr, c->F, m.b0,
+    k_finish<<<nblk(m.nc, 256), 256, 0, s>>>(m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr, F, m.b0,
                                             &c->gd->load, mode, c->Ru, eps_dev, gate, out);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);

@@ -28,7 +28,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 EXPORTS = [
     "jfnk_default_options", "jfnk_create", "jfnk_destroy", "jfnk_last_error", "jfnk_set_options",
     "jfnk_set_mesh", "jfnk_set_patch", "jfnk_set_material", "jfnk_set_body_force", "jfnk_set_load_factor",
-    "jfnk_setup", "jfnk_residual", "jfnk_jv", "jfnk_precondition", "jfnk_solve", "jfnk_get_geometry",
+    "jfnk_setup", "jfnk_residual", "jfnk_residual_noalloc", "jfnk_jv", "jfnk_precondition", "jfnk_solve", "jfnk_get_geometry",
     "jfnk_get_gradient", "jfnk_get_permutation", "jfnk_profile_enable", "jfnk_profile_get", "jfnk_profile_reset",
     "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64",
 ]
@@ -75,6 +75,7 @@ def load():
         "jfnk_set_load_factor": (i, [vp, d]),
         "jfnk_setup": (i, [vp]),
         "jfnk_residual": (i, [vp, dp, dp, i, vp]),
+        "jfnk_residual_noalloc": (i, [vp, dp, dp, vp]),
         "jfnk_jv": (i, [vp, dp, dp, dp, i, vp]),
         "jfnk_precondition": (i, [vp, dp, dp, i, i, vp]),
         "jfnk_solve": (i, [vp, dp, i, i, C.POINTER(Stats), vp]),
@@ -214,6 +215,13 @@ class Solver:
         R = self._out_like(u) if out is None else out
         mem, s = self._io(u)
         self._check(self.L.jfnk_residual(self.h, _ptr(u), _ptr(R), mem, s))
+        return R
+
+    def residual_noalloc(self, u, out=None):
+        """R(u) for torch CUDA tensors, through the entry point that allocates nothing."""
+        u = self._in(u)
+        R = self._out_like(u) if out is None else out
+        self._check(self.L.jfnk_residual_noalloc(self.h, _ptr(u), _ptr(R), _stream(u)))
         return R
 
     def jv(self, u, v, out=None):
