@@ -160,8 +160,31 @@ int jfnk_precondition(jfnk_ctx* ctx, const double* v, double* z, int pc, int mem
 /* Newton solve (Sec. 3.2-3.3): u holds the initial guess on entry and the solution on exit;
  * n_load_steps >= 1 ramps the load factor k / n_load_steps.  Returns JFNK_OK when every load
  * step met |R| <= max(atol, rtol |R(u0)|), else the failure code (u holds the last iterate).
- * The call synchronises the stream before returning. */
+ * For a batch every problem runs its own Newton loop; stats aggregates them (maximum Newton
+ * count, summed Krylov counts, worst status and relative residual) and jfnk_batch_stats
+ * gives each one.  The call synchronises the stream before returning. */
 int jfnk_solve(jfnk_ctx* ctx, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream);
+
+/* ---- batches of independent problems in one index space -------------------------------- */
+/* A context becomes a batch when problems are added to it instead of calling jfnk_set_mesh.
+ * Each problem is defined in its own context (jfnk_set_mesh, jfnk_set_patch,
+ * jfnk_set_material, jfnk_set_body_force; no set-up needed) and copied in; that context may be
+ * destroyed afterwards.  The batch's cells are the problems' cells concatenated in the order
+ * added, so every vector passed to jfnk_residual / jfnk_jv / jfnk_precondition / jfnk_solve on
+ * the batch is [sum of n_cells][3].  All problems share the options, dimension, load factor
+ * and load-step schedule; each keeps its own material, body force, Jv step eps, GMRES
+ * iteration, line search and convergence test, so a problem's iterates do not depend on the
+ * other problems except through the multigrid hierarchy, whose coarsest levels are built for
+ * the whole batch.  *index receives the problem's position.  Errors: JFNK_ESTATE if the
+ * context already holds a single mesh or the problem has no mesh/material; JFNK_EINVAL if the
+ * dimensions differ. */
+int jfnk_batch_add(jfnk_ctx* batch, const jfnk_ctx* problem, int32_t* index);
+/* Number of problems (1 for a single-mesh context). */
+int jfnk_batch_size(const jfnk_ctx* ctx);
+/* First cell (in the concatenated numbering) and cell count of problem `index`. */
+int jfnk_batch_problem_cells(const jfnk_ctx* ctx, int32_t index, int32_t* first_cell, int32_t* n_cells);
+/* Per-problem statistics of the last jfnk_solve: per_problem [jfnk_batch_size(ctx)]. */
+int jfnk_batch_stats(const jfnk_ctx* ctx, jfnk_stats* per_problem);
 
 /* ---- inspection ------------------------------------------------------------------------ */
 /* Geometry in the caller's numbering (host arrays, any may be NULL): face area vectors

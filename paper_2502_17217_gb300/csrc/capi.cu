@@ -2,6 +2,7 @@
 // inspection and kernel timing.  Argument marshalling and validation only; every step of
 // the method runs in the device kernels of the other translation units.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -89,9 +90,12 @@ static void free_device(jfnk_ctx* c)
     c->dm = jfnk::DevMesh();
     c->u = c->Ru = c->w = c->R = c->z = c->x = c->bvec = c->wk = c->tmp = c->ext = nullptr;
     c->G = c->T = c->F = c->Fn = c->partials = c->V = nullptr;
-    c->gd = nullptr;
-    c->scal = nullptr;
-    c->tickets = nullptr;
+    c->pd = nullptr;
+    c->gdev = nullptr;
+    c->ch_beg = nullptr;
+    c->ch_len = c->ch_prob = c->pch_beg = c->pch_cnt = c->cell_prob = c->pmask = nullptr;
+    c->mat = MatDev{};
+    c->n_chunks = 0;
     c->mg_ready = false;
 }
 
@@ -160,7 +164,7 @@ int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
         delete c;
         return JFNK_ECUDA;
     }
-    if (cudaMallocHost(&c->gh, sizeof(jfnk::GmresDev)) != cudaSuccess || cudaMallocHost(&c->scal_h, 16 * sizeof(double)) != cudaSuccess) {
+    if (cudaMallocHost(&c->gh, sizeof(jfnk::GlobalDev)) != cudaSuccess || cudaMallocHost(&c->scal_h, 16 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         cudaStreamDestroy(c->stream);
         delete c;
@@ -182,6 +186,7 @@ int jfnk_destroy(jfnk_ctx* c)
     for (auto e : c->it_ev)
         if (e) cudaEventDestroy(e);
     if (c->gh) cudaFreeHost(c->gh);
+    if (c->ph) cudaFreeHost(c->ph);
     if (c->scal_h) cudaFreeHost(c->scal_h);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -212,6 +217,7 @@ int jfnk_set_mesh(jfnk_ctx* c, int dim, int32_t n_points, const double* points, 
     if ((dim != 2 && dim != 3) || n_points <= 0 || n_faces <= 0 || n_cells <= 0 || n_internal < 0 || n_internal > n_faces ||
         !points || !face_ptr || !face_pts || !owner || (n_internal > 0 && !neighbour))
         return jfnk_fail(c, JFNK_EINVAL, "jfnk_set_mesh: invalid sizes or null arrays");
+    if (c->is_batch) return jfnk_fail(c, JFNK_ESTATE, "jfnk_set_mesh on a batch context (problems are added with jfnk_batch_add)");
     if (face_ptr[0] != 0) return jfnk_fail(c, JFNK_EINVAL, "face_ptr[0] must be 0");
     for (int32_t f = 0; f < n_faces; f++) {
         if (face_ptr[f + 1] - face_ptr[f] < 3) return jfnk_fail(c, JFNK_EINVAL, "every face needs >= 3 points");
@@ -300,17 +306,118 @@ int jfnk_set_load_factor(jfnk_ctx* c, double lambda)
 int jfnk_setup(jfnk_ctx* c)
 {
     if (!c) return JFNK_EINVAL;
-    if (!c->have_mesh || !c->have_material) return jfnk_fail(c, JFNK_ESTATE, "mesh and material must be set before set-up");
+    if (c->is_batch ? c->batch.empty() : (!c->have_mesh || !c->have_material))
+        return jfnk_fail(c, JFNK_ESTATE, "mesh and material (or batch problems) must be set before set-up");
     if (cudaSetDevice(c->opt.device) != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
     free_device(c);
     c->cur = c->stream;
-    std::string e = jfnk::build_topology(c->hm, c->opt.renumber != 0, c->topo);
+    // problems: the single mesh, or the batch concatenated into one mesh
+    std::vector<int32_t> group;
+    std::vector<std::array<double, 3>> mats;  // (law, p1, p2) per problem
+    if (c->is_batch) {
+        jfnk::HostMesh& h = c->hm;
+        h = jfnk::HostMesh();
+        h.dim = c->batch[0].hm.dim;
+        int np = 0, nc = 0, nf = 0, ni = 0;
+        for (auto& q : c->batch) { np += q.hm.np; nc += q.hm.nc; nf += q.hm.nf; ni += q.hm.ni; }
+        h.np = np; h.nc = nc; h.nf = nf; h.ni = ni;
+        h.pts.reserve(3 * (size_t)np);
+        h.fptr.assign(1, 0);
+        c->fb_host.assign(3 * (size_t)nc, 0.0);
+        c->prob_first_cell.clear();
+        // internal faces of all problems first, then boundary faces
+        int poff = 0, coff = 0;
+        std::vector<int32_t> bf_src;  // (problem, face) of each boundary face, in order
+        for (size_t p = 0; p < c->batch.size(); p++) {
+            const jfnk::HostMesh& q = c->batch[p].hm;
+            c->prob_first_cell.push_back(coff);
+            h.pts.insert(h.pts.end(), q.pts.begin(), q.pts.end());
+            for (int f = 0; f < q.ni; f++) {
+                for (int k = q.fptr[f]; k < q.fptr[f + 1]; k++) h.fpts.push_back(q.fpts[k] + poff);
+                h.fptr.push_back((int32_t)h.fpts.size());
+                h.own.push_back(q.own[f] + coff);
+                h.nei.push_back(q.nei[f] + coff);
+            }
+            if (!c->batch[p].fb.empty())
+                std::copy(c->batch[p].fb.begin(), c->batch[p].fb.end(), c->fb_host.begin() + 3 * (size_t)coff);
+            for (int i = 0; i < q.nc; i++) group.push_back((int32_t)p);
+            mats.push_back({(double)c->batch[p].law, c->batch[p].p1, c->batch[p].p2});
+            poff += q.np;
+            coff += q.nc;
+        }
+        poff = 0; coff = 0;
+        for (size_t p = 0; p < c->batch.size(); p++) {
+            const jfnk::HostMesh& q = c->batch[p].hm;
+            for (int f = q.ni; f < q.nf; f++) {
+                for (int k = q.fptr[f]; k < q.fptr[f + 1]; k++) h.fpts.push_back(q.fpts[k] + poff);
+                h.fptr.push_back((int32_t)h.fpts.size());
+                h.own.push_back(q.own[f] + coff);
+                h.btype.push_back(q.btype[f - q.ni]);
+                for (int k = 0; k < 3; k++) h.bval.push_back(q.bval[(size_t)(f - q.ni) * 3 + k]);
+            }
+            poff += q.np;
+            coff += q.nc;
+        }
+        c->nprob = (int)c->batch.size();
+    } else {
+        c->nprob = 1;
+        c->prob_first_cell.assign(1, 0);
+        mats.push_back({(double)c->law, c->p1, c->p2});
+    }
+    // material table: law, mu, lambda, kappa, alpha Kbar, alpha_pc Kbar per problem
+    const int P = c->nprob;
+    c->mat_host.assign(6 * (size_t)P, 0.0);
+    int n_lin = 0;
+    for (int p = 0; p < P; p++) {
+        const int law = (int)mats[p][0];
+        double mu, lam, kappa;
+        if (law == JFNK_LAW_LINEAR) {
+            mu = mats[p][1] / (2.0 * (1.0 + mats[p][2]));
+            lam = mats[p][1] * mats[p][2] / ((1.0 + mats[p][2]) * (1.0 - 2.0 * mats[p][2]));
+            kappa = lam + 2.0 * mu / 3.0;
+            n_lin++;
+        } else {
+            mu = mats[p][1];
+            kappa = mats[p][2];
+            lam = kappa - 2.0 * mu / 3.0;
+        }
+        const double Kbar = 4.0 * mu / 3.0 + kappa;
+        c->mat_host[p] = law;
+        c->mat_host[P + p] = mu;
+        c->mat_host[2 * P + p] = lam;
+        c->mat_host[3 * P + p] = kappa;
+        c->mat_host[4 * P + p] = c->opt.alpha_residual * Kbar;
+        c->mat_host[5 * P + p] = c->opt.alpha_pc * Kbar;
+    }
+    c->law_mode = (n_lin == P) ? 0 : (n_lin == 0 ? 1 : 2);
+    std::string e = jfnk::build_topology(c->hm, c->opt.renumber != 0, c->topo, c->is_batch ? &group : nullptr);
     if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
+    const int nc = c->hm.nc;
+    // problems' internal cell ranges and the internal cell -> problem map
+    std::vector<int32_t> cell_prob(nc, 0);
+    c->prob_c0.assign(P, 0);
+    c->prob_c1.assign(P, 0);
+    for (int i = 0; i < nc; i++) cell_prob[i] = c->is_batch ? group[c->topo.n2o[i]] : 0;
+    for (int i = nc - 1; i >= 0; i--) c->prob_c0[cell_prob[i]] = i;
+    for (int i = 0; i < nc; i++) c->prob_c1[cell_prob[i]] = i + 1;
+    {
+        std::vector<int32_t> lawv(P);
+        for (int p = 0; p < P; p++) lawv[p] = (int32_t)c->mat_host[p];
+        int32_t* dl = (int32_t*)jfnk_dalloc(c, sizeof(int32_t) * P);
+        double* dm = (double*)jfnk_dalloc(c, sizeof(double) * 5 * (size_t)P);
+        c->cell_prob = (int32_t*)jfnk_dalloc(c, sizeof(int32_t) * (size_t)nc);
+        if (!dl || !dm || !c->cell_prob) return jfnk_fail(c, JFNK_ENOMEM, "device allocation of the material table failed");
+        JF_CUDA(c, cudaMemcpy(dl, lawv.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice));
+        JF_CUDA(c, cudaMemcpy(dm, c->mat_host.data() + P, sizeof(double) * 5 * (size_t)P, cudaMemcpyHostToDevice));
+        JF_CUDA(c, cudaMemcpy(c->cell_prob, cell_prob.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice));
+        c->mat = MatDev{dl, dm, dm + P, dm + 2 * (size_t)P, dm + 3 * (size_t)P, dm + 4 * (size_t)P};
+    }
     int rc = jfnk::setup_device_mesh(c);
     if (rc) return rc;
     rc = jfnk::setup_material_coefficients(c);
     if (rc) return rc;
-    const int nc = c->dm.nc;
+    rc = jfnk::build_chunks(c);
+    if (rc) return rc;
     const size_t v3 = 3 * (size_t)nc;
     double** vecs[] = {&c->u, &c->Ru, &c->w, &c->R, &c->z, &c->x, &c->bvec, &c->wk, &c->tmp, &c->ext};
     for (double** p : vecs) {
@@ -318,24 +425,82 @@ int jfnk_setup(jfnk_ctx* c)
         if (!*p) return jfnk_fail(c, JFNK_ENOMEM, "device allocation of work vectors failed");
     }
     c->G = (double*)jfnk_dalloc(c, sizeof(double) * 9 * (size_t)nc);
-    c->T = (double*)jfnk_dalloc(c, sizeof(double) * (c->law == JFNK_LAW_NEOHOOKEAN ? 9 * (size_t)nc : 1));
+    c->T = (double*)jfnk_dalloc(c, sizeof(double) * (c->law_mode != 0 ? 9 * (size_t)nc : 1));
     c->F = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)std::max(1, c->dm.nflux));
     c->Fn = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)std::max(1, c->dm.ni));
-    const size_t chunks = (v3 + 2047) / 2048 + 2 * (size_t)jfnk::kRedBlocks;
-    c->partials = (double*)jfnk_dalloc(c, sizeof(double) * chunks * (jfnk::kMaxRestart + 2));
+    c->partials = (double*)jfnk_dalloc(c, sizeof(double) * ((size_t)c->n_chunks + 64) * (jfnk::kMaxRestart + 2));
     c->V_is_float = c->opt.precision == JFNK_PREC_MIXED;
     c->V_ld = (v3 + 63) / 64 * 64;
     const size_t vbytes = (c->V_is_float ? sizeof(float) : sizeof(double)) * c->V_ld * (size_t)(c->opt.gmres_restart + 1);
     c->V = (double*)jfnk_dalloc(c, vbytes);
-    c->gd = (jfnk::GmresDev*)jfnk_dalloc(c, sizeof(jfnk::GmresDev));
-    c->scal = (double*)jfnk_dalloc(c, 16 * sizeof(double));
-    c->tickets = (unsigned*)jfnk_dalloc(c, 16 * sizeof(unsigned));
-    if (!c->G || !c->T || !c->F || !c->Fn || !c->partials || !c->V || !c->gd || !c->scal || !c->tickets)
+    c->pd = (jfnk::ProbDev*)jfnk_dalloc(c, sizeof(jfnk::ProbDev) * (size_t)P);
+    c->gdev = (jfnk::GlobalDev*)jfnk_dalloc(c, sizeof(jfnk::GlobalDev));
+    c->pmask = (int32_t*)jfnk_dalloc(c, sizeof(int32_t) * (size_t)P);
+    if (!c->G || !c->T || !c->F || !c->Fn || !c->partials || !c->V || !c->pd || !c->gdev || !c->pmask)
         return jfnk_fail(c, JFNK_ENOMEM, "device allocation of solver buffers failed");
+    if (c->ph_count < (size_t)P) {
+        if (c->ph) cudaFreeHost(c->ph);
+        c->ph = nullptr;
+        if (cudaMallocHost(&c->ph, sizeof(jfnk::ProbDev) * (size_t)P) != cudaSuccess) {
+            c->ph_count = 0;
+            return jfnk_fail(c, JFNK_ENOMEM, "pinned host allocation failed");
+        }
+        c->ph_count = P;
+    }
+    std::memset(c->ph, 0, sizeof(jfnk::ProbDev) * (size_t)P);
+    c->pmask_h_store.assign(P, 0);
+    c->pmask_h = c->pmask_h_store.data();
     rc = jfnk::pc_setup(c);
     if (rc) return rc;
     if (cudaDeviceSynchronize() != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "set-up");
     c->dirty = false;
+    return JFNK_OK;
+}
+
+int jfnk_batch_add(jfnk_ctx* c, const jfnk_ctx* q, int32_t* index)
+{
+    if (!c || !q) return JFNK_EINVAL;
+    if (c->have_mesh) return jfnk_fail(c, JFNK_ESTATE, "jfnk_batch_add on a context that holds a single mesh");
+    if (!q->have_mesh || !q->have_material || q->is_batch)
+        return jfnk_fail(c, JFNK_ESTATE, "jfnk_batch_add: the problem needs a mesh and a material");
+    if (!c->batch.empty() && c->batch[0].hm.dim != q->hm.dim)
+        return jfnk_fail(c, JFNK_EINVAL, "jfnk_batch_add: all problems of a batch share the dimension");
+    ProblemDef d;
+    d.hm = q->hm;
+    d.law = q->law;
+    d.p1 = q->p1;
+    d.p2 = q->p2;
+    d.fb = q->fb_host;
+    c->batch.push_back(std::move(d));
+    c->is_batch = true;
+    c->dirty = true;
+    if (index) *index = (int32_t)c->batch.size() - 1;
+    return JFNK_OK;
+}
+
+int jfnk_batch_size(const jfnk_ctx* c)
+{
+    if (!c) return JFNK_EINVAL;
+    return c->is_batch ? (int)c->batch.size() : 1;
+}
+
+int jfnk_batch_problem_cells(const jfnk_ctx* c, int32_t index, int32_t* first_cell, int32_t* n_cells)
+{
+    if (!c) return JFNK_EINVAL;
+    const int P = c->is_batch ? (int)c->batch.size() : 1;
+    if (index < 0 || index >= P) return JFNK_EINVAL;
+    int32_t first = 0;
+    for (int p = 0; p < index; p++) first += c->batch[p].hm.nc;
+    if (first_cell) *first_cell = first;
+    if (n_cells) *n_cells = c->is_batch ? c->batch[index].hm.nc : c->hm.nc;
+    return JFNK_OK;
+}
+
+int jfnk_batch_stats(const jfnk_ctx* c, jfnk_stats* per_problem)
+{
+    if (!c || !per_problem) return JFNK_EINVAL;
+    if (c->pstats.empty()) return JFNK_ESTATE;
+    std::memcpy(per_problem, c->pstats.data(), sizeof(jfnk_stats) * c->pstats.size());
     return JFNK_OK;
 }
 
@@ -394,14 +559,13 @@ int jfnk_jv(jfnk_ctx* c, const double* u, const double* v, double* Jv, int mem, 
     int rc = begin_call(c, stream);
     if (rc) return rc;
     if (!u || !v || !Jv || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE)) return jfnk_fail(c, JFNK_EINVAL, "jfnk_jv: bad arguments");
-    const size_t n = 3 * (size_t)c->dm.nc;
     if ((rc = load_vec(c, u, mem, c->u))) return rc;
     if ((rc = load_vec(c, v, mem, c->z))) return rc;
     if ((rc = jfnk::residual(c, c->u, c->Ru, jfnk::OUT_R, nullptr))) return rc;
-    if ((rc = jfnk::norm_mode(c, c->u, n, 2, nullptr))) return rc;
-    if ((rc = jfnk::norm_mode(c, c->z, n, 1, nullptr))) return rc;
-    if ((rc = jfnk::perturb(c, c->u, c->z, c->w, nullptr))) return rc;
-    if ((rc = jfnk::residual(c, c->w, c->tmp, jfnk::OUT_JV, &c->gd->eps))) return rc;
+    if ((rc = jfnk::pnorm(c, c->u, 2, false))) return rc;
+    if ((rc = jfnk::pnorm(c, c->z, 1, false))) return rc;
+    if ((rc = jfnk::perturb(c, c->u, c->z, c->w, false))) return rc;
+    if ((rc = jfnk::residual(c, c->w, c->tmp, jfnk::OUT_JV, nullptr))) return rc;
     return store_vec(c, c->tmp, mem, Jv);
 }
 

@@ -166,7 +166,7 @@ __global__ void k_cell_ls(int nc, int nf, int dim, const int32_t* __restrict__ s
 //   t_j = sum_i p_i G_ij + sum_i q_i G_ji + r_j tr(G),  p = mu Gamma - a, q = mu Gamma, r = lambda Gamma.
 // Neo-Hookean (total Lagrangian) keeps Gamma and a:  t = Gamma . T_f - a . G_f.
 // slots: 0 w | 1 kc | 2-4 p (or Gamma) | 5-7 q (or a) | 8-10 r.  J~ gets alpha_pc Kbar |Delta||Gamma|/|d|.
-__global__ void k_flux_coef(int ni, int nflux, int nf, int nc, int law, double mu, double lam, double aK, double aKpc,
+__global__ void k_flux_coef(int ni, int nflux, int nf, int nc, MatDev mat, const int32_t* __restrict__ cell_prob,
                             const int32_t* __restrict__ own, const int32_t* __restrict__ nei,
                             const double* __restrict__ Sf, const double* __restrict__ Cf, const double* __restrict__ C,
                             double* __restrict__ coef, double* __restrict__ jt_c)
@@ -174,6 +174,10 @@ __global__ void k_flux_coef(int ni, int nflux, int nf, int nc, int law, double m
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nflux) return;
     const int P = own[f];
+    // material of the face's problem (both cells of an internal face belong to one problem)
+    const int pr = cell_prob[P];
+    const int law = mat.law[pr];
+    const double mu = mat.mu[pr], lam = mat.lam[pr], aK = mat.aK[pr], aKpc = mat.aKpc[pr];
     const double Gx = Sf[f], Gy = Sf[nf + f], Gz = Sf[2 * nf + f];
     const double mG = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
     const double nx = Gx / mG, ny = Gy / mG, nz = Gz / mG;
@@ -339,10 +343,9 @@ int setup_material_coefficients(jfnk_ctx* c)
         for (int P = 0; P < m.nc; P++)
             for (int k = 0; k < 3; k++) fbs[(size_t)k * m.nc + P] = c->fb_host[(size_t)c->topo.n2o[P] * 3 + k];
     JF_CUDA(c, cudaMemcpyAsync(m.fb, fbs.data(), sizeof(double) * fbs.size(), cudaMemcpyHostToDevice, s));
-    const double aK = c->opt.alpha_residual * c->Kbar, aKpc = c->opt.alpha_pc * c->Kbar;
     if (m.nflux > 0) {
-        k_flux_coef<<<blocks(m.nflux, 256), 256, 0, s>>>(m.ni, m.nflux, m.nf, m.nc, c->law, c->mu, c->lam, aK, aKpc,
-                                                         m.own, m.nei, m.Sf, m.Cf, m.C, m.coef, m.jt_c);
+        k_flux_coef<<<blocks(m.nflux, 256), 256, 0, s>>>(m.ni, m.nflux, m.nf, m.nc, c->mat, c->cell_prob, m.own, m.nei,
+                                                         m.Sf, m.Cf, m.C, m.coef, m.jt_c);
         JF_LAUNCHED(c);
     }
     k_cell_b0<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.nf, m.ni, m.nd, m.ft_ptr, m.Sf, m.bval, m.V, m.fb, m.dim, m.b0);

@@ -51,8 +51,9 @@ struct Topology {
     int bandwidth = 0;
 };
 
-// Builds the topology; returns "" on success or an error message.
-std::string build_topology(const HostMesh& hm, bool rcm, Topology& t);
+// Builds the topology; returns "" on success or an error message.  With `group` (one entry
+// per input cell) the cells of each group stay contiguous, groups in increasing order.
+std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std::vector<int32_t>* group = nullptr);
 
 // ------------------------------------------------------------------ multigrid hierarchy (host)
 struct MgLevelHost {
@@ -93,30 +94,44 @@ struct DevMesh {
     int32_t* err = nullptr;          // set-up error word
 };
 
-// Scalars of the GMRES cycle, resident on the device.
-struct GmresDev {
+// Chunks of the SoA vectors for per-problem (segmented) reductions: every chunk lies inside
+// one problem's range of one displacement component.
+constexpr int kChunk = 2048;
+constexpr int kChunkThreads = 128;   // kChunk / kChunkThreads = 16 elements per thread
+
+// Per-problem scalars of the GMRES cycle and the Newton step, resident on the device.
+struct ProbDev {
     int j;            // Arnoldi index of the iteration being built
     int k;            // iterations completed in this cycle
-    int done;         // converged / breakdown: later kernels of the cycle return at once
+    int done;         // this problem's cycle is finished (converged, breakdown, full, inactive)
     int reorth;       // second Gram-Schmidt pass needed for this column
-    unsigned ticket[8];
-    int pad[4];
+    int active;       // takes part in the current Newton step
+    int n_reorth;     // second passes run (diagnostic)
+    unsigned ticket[4];
     double eps;       // Jv step for the current direction
-    double unorm;     // |u|
-    double beta;      // |r| at the start of the cycle
-    double target;    // eta |b|
-    double inv;       // 1 / |w|
-    double wn2;       // |w|^2 before orthogonalisation
-    double res;       // |g_{k}| current residual estimate
-    int n_reorth;     // second Gram-Schmidt passes run (diagnostic)
-    int pad2;
-    double load;      // load factor read by the residual kernels
-    double scratch[6];
+    double unorm;     // |u_p|
+    double beta;      // |r_p| at the start of the cycle
+    double target;    // eta |b_p|
+    double inv;       // 1 / |w_p| (or 1 / beta at the cycle start)
+    double wn2;       // |w_p|^2 before orthogonalisation
+    double res;       // |g_k| current residual estimate
+    double step;      // line-search step s_p
+    double nrm;       // output of plain per-problem norms
+    double pad2[7];
     double h[kMaxRestart + 1];
     double H[(kMaxRestart + 1) * kMaxRestart];  // column-major: H[i + (m+1) j]
     double g[kMaxRestart + 1];
     double cs[kMaxRestart], sn[kMaxRestart];
     double y[kMaxRestart];
+};
+
+// Scalars shared by all problems of a context.
+struct GlobalDev {
+    int jg;           // index of the lockstep Arnoldi iteration (all active problems share it)
+    int all_done;     // every problem's cycle is finished: the iteration's kernels return at once
+    int n_active;     // problems whose cycle is still running
+    int pad;
+    double load;      // load factor read by the residual kernels
 };
 
 struct Profiler {
@@ -134,6 +149,20 @@ struct Profiler {
 
 }  // namespace jfnk
 
+// A problem copied into a batch: mesh, boundary data, material, body force.
+struct ProblemDef {
+    jfnk::HostMesh hm;
+    int law = JFNK_LAW_LINEAR;
+    double p1 = 0, p2 = 0;
+    std::vector<double> fb;
+};
+
+// Per-problem material constants on the device (arrays over problems).
+struct MatDev {
+    const int32_t* law;
+    const double *mu, *lam, *kappa, *aK, *aKpc;
+};
+
 struct jfnk_ctx {
     jfnk_options opt;
     std::string err;
@@ -141,11 +170,21 @@ struct jfnk_ctx {
     cudaStream_t cur = nullptr;         // stream of the call in progress
     jfnk::HostMesh hm;
     bool have_mesh = false, have_material = false;
+    bool is_batch = false;
+    std::vector<ProblemDef> batch;       // problems of a batch, in the order added
+    std::vector<int32_t> prob_first_cell;// caller numbering: first cell of each problem
+    std::vector<double> mat_host;        // [6][nprob]: law, mu, lam, kappa, Kbar(alpha), Kbar(alpha_pc)
+    int law_mode = 0;                    // 0 all Hooke, 1 all neo-Hookean, 2 mixed
+    MatDev mat{};                        // device copies
+    std::vector<jfnk_stats> pstats;      // per-problem statistics of the last solve
+    int32_t* pmask = nullptr;            // device [nprob]
+    std::vector<int32_t> pmask_h_store;
+    int32_t* pmask_h = nullptr;
     int law = JFNK_LAW_LINEAR;
     double p1 = 0, p2 = 0, mu = 0, lam = 0, kappa = 0, Kbar = 0;
     std::vector<double> fb_host;
     double load = 1.0;
-    double load_on_device = -1.0;      // value last copied to gd->load
+    double load_on_device = -1.0;      // value last copied to gdev->load
     bool dirty = true;
     jfnk::Topology topo;
     jfnk::DevMesh dm;
@@ -159,15 +198,24 @@ struct jfnk_ctx {
     double* V = nullptr;                 // Krylov basis (double or float storage)
     size_t V_ld = 0;                     // stride between basis vectors (elements)
     int V_is_float = 0;
-    jfnk::GmresDev* gd = nullptr;        // device scalars
-    jfnk::GmresDev* gh = nullptr;        // pinned host mirror
+    // problems (P >= 1) in one concatenated index space
+    int nprob = 1;
+    std::vector<int32_t> prob_c0, prob_c1;   // internal cell range of each problem
+    int n_chunks = 0;
+    int64_t* ch_beg = nullptr;           // device chunk table
+    int32_t *ch_len = nullptr, *ch_prob = nullptr;
+    int32_t *pch_beg = nullptr, *pch_cnt = nullptr;  // per problem: first chunk, chunk count
+    int32_t* cell_prob = nullptr;        // [nc] problem of each internal cell
+    jfnk::ProbDev* pd = nullptr;         // device per-problem scalars [nprob]
+    jfnk::ProbDev* ph = nullptr;         // pinned host mirror (header fields only are refreshed)
+    jfnk::GlobalDev* gdev = nullptr;     // device global scalars
+    jfnk::GlobalDev* gh = nullptr;       // pinned host mirror
+    size_t ph_count = 0;                 // problems the pinned mirror can hold
     cudaGraphExec_t it_graph = nullptr;  // one captured Arnoldi iteration (replayed for every j)
     cudaEvent_t it_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int use_graphs = 1;
     int64_t graph_kernels = 0;           // kernels in the captured iteration
-    double* scal = nullptr;              // device scalar scratch [16]
     double* scal_h = nullptr;            // pinned [16]
-    unsigned* tickets = nullptr;         // [16]
     // multigrid (precond.cu owns the hierarchy object)
     void* mgs = nullptr;
     int mg_coarse_n = 0;
@@ -216,15 +264,19 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
                   double* G, double* T, double* F, double* Fn);
 // linalg.cu
 int perm_in(jfnk_ctx* c, const double* ext_aos, double* int_soa);
+int build_chunks(jfnk_ctx* c);
 int perm_out(jfnk_ctx* c, const double* int_soa, double* ext_aos);
-int norm2(jfnk_ctx* c, const double* x, size_t n, double* out_dev);          // out = |x|
 int axpby(jfnk_ctx* c, size_t n, double a, const double* x, double b, const double* y, double* out);
 int axpy_dev_scalar(jfnk_ctx* c, size_t n, const double* x, const double* a_dev, const double* y, double* out); // out = y + a x
-int norm_mode(jfnk_ctx* c, const double* x, size_t n, int mode, const int* gate);
-int perturb(jfnk_ctx* c, const double* u, const double* z, double* w, const int* gate);
+// per-problem norms: mode 0 -> pd[p].nrm, 1 -> pd[p].eps (Jv step), 2 -> pd[p].unorm,
+// 3 -> pd[p].beta and inv; gated = skip problems that are inactive or whose cycle is done
+int pnorm(jfnk_ctx* c, const double* x, int mode, bool gated);
+int perturb(jfnk_ctx* c, const double* u, const double* z, double* w, bool gated);
 int cycle_init(jfnk_ctx* c, const double* r);
 int arnoldi_orthogonalise(jfnk_ctx* c, double* w);
 int cycle_solution(jfnk_ctx* c, double* out);
+int line_trial(jfnk_ctx* c, const double* u, const double* x, double* w);       // w = u + s_p x (active)
+int accept_masked(jfnk_ctx* c, const int32_t* mask_dev, double* u, const double* w, double* Ru, const double* R);
 // precond.cu
 int pc_setup(jfnk_ctx* c);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*

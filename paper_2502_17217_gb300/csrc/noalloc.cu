@@ -58,11 +58,11 @@ double* scratch_address(int device, cudaError_t* err)
 extern "C" int jfnk_residual_noalloc(jfnk_ctx* c, const double* u, double* R, void* stream)
 {
     if (!c || !u || !R) return JFNK_EINVAL;
-    if (c->dirty || !c->gd)
+    if (c->dirty || !c->gdev)
         return jfnk_fail(c, JFNK_ESTATE, "jfnk_residual_noalloc: call jfnk_setup() first (this entry point never allocates)");
     const jfnk::DevMesh& m = c->dm;
     const size_t nc = (size_t)m.nc;
-    const size_t need = 3 * nc + 9 * nc + (c->law == JFNK_LAW_NEOHOOKEAN ? 9 * nc : 0) + 3 * (size_t)m.nflux +
+    const size_t need = 3 * nc + 9 * nc + (c->law_mode != 0 ? 9 * nc : 0) + 3 * (size_t)m.nflux +
                         3 * (size_t)m.ni + 3 * nc;
     if (need > kNoallocScratchDoubles)
         return jfnk_fail(c, JFNK_EINVAL,
@@ -76,7 +76,7 @@ extern "C" int jfnk_residual_noalloc(jfnk_ctx* c, const double* u, double* R, vo
     double* u_int = base;
     double* G = u_int + 3 * nc;
     double* T = G + 9 * nc;
-    double* F = T + (c->law == JFNK_LAW_NEOHOOKEAN ? 9 * nc : 0);
+    double* F = T + (c->law_mode != 0 ? 9 * nc : 0);
     double* Fn = F + 3 * (size_t)m.nflux;
     double* R_int = Fn + 3 * (size_t)m.ni;
     int rc = jfnk::sync_load(c);

@@ -19,7 +19,6 @@
 
 namespace jfnk {
 
-int norm_mode(jfnk_ctx* c, const double* x, size_t n, int mode, const int* gate);
 
 // ------------------------------------------------------------------ block-Jacobi
 template <typename TV, typename TP>

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(128) k_grad(const int* __restrict__ gate, int 
                                               const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
                                               const double* __restrict__ sell_l, int n_slots,
                                               const double* __restrict__ u, double* __restrict__ G,
-                                              double* __restrict__ T, double mu, double kappa)
+                                              double* __restrict__ T, MatDev mat, const int32_t* __restrict__ cell_prob)
 {
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,7 +45,9 @@ __global__ void __launch_bounds__(128) k_grad(const int* __restrict__ gate, int 
     }
 #pragma unroll
     for (int q = 0; q < 9; q++) G[(size_t)q * nc + P] = g[q];
-    if (LAW == JFNK_LAW_NEOHOOKEAN) {
+    const int pr = (LAW == JFNK_LAW_LINEAR) ? 0 : cell_prob[P];
+    if (LAW == JFNK_LAW_NEOHOOKEAN || (LAW == 2 && mat.law[pr] == JFNK_LAW_NEOHOOKEAN)) {
+        const double mu = mat.mu[pr], kappa = mat.kappa[pr];
         // F = I + (grad u)^T: F_ij = delta_ij + g_ji
         const double F00 = 1.0 + g[0], F01 = g[3], F02 = g[6];
         const double F10 = g[1], F11 = 1.0 + g[4], F12 = g[7];
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
                                               const double* __restrict__ u, const double* __restrict__ G,
                                               const double* __restrict__ T, const double* __restrict__ bval,
                                               const double* __restrict__ load_dev, const int32_t* __restrict__ fn_pos,
+                                              MatDev mat, const int32_t* __restrict__ cell_prob,
                                               double* __restrict__ F, double* __restrict__ Fn)
 {
     if (gate && *gate) return;
@@ -128,7 +131,8 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
     const double c0 = coef[2 * nflux + f], c1 = coef[3 * nflux + f], c2 = coef[4 * nflux + f];
     const double c3 = coef[5 * nflux + f], c4 = coef[6 * nflux + f], c5 = coef[7 * nflux + f];
     double t[3];
-    if (LAW == JFNK_LAW_LINEAR) {
+    const bool hooke = (LAW == JFNK_LAW_LINEAR) || (LAW == 2 && mat.law[cell_prob[P]] == JFNK_LAW_LINEAR);
+    if (hooke) {
         // t_j = p . G_:j + q . G_j: + r_j tr(G) + kc du_j
         const double r0 = coef[8 * nflux + f], r1 = coef[9 * nflux + f], r2 = coef[10 * nflux + f];
         const double tr = gf[0] + gf[4] + gf[8];
@@ -177,13 +181,15 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
     }
 }
 
-// mode 0: out = R;  mode 1: out = (R - Ru) / eps  (eps from device memory; 0 -> out = 0)
+// mode 0: out = R;  mode 1: out = (R - Ru) / eps_p with eps_p the Jv step of the cell's
+// problem (0 -> out = 0)
 __global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int ni, int dim, const int32_t* __restrict__ fo_ptr,
                                                 const int32_t* __restrict__ fn_ptr, const double* __restrict__ Fn,
                                                 const int32_t* __restrict__ fd_ptr, const double* __restrict__ F,
                                                 const double* __restrict__ b0, const double* __restrict__ load_dev, int mode,
-                                                const double* __restrict__ Ru, const double* __restrict__ eps_dev,
-                                                const int* __restrict__ gate, double* __restrict__ out)
+                                                const double* __restrict__ Ru, const ProbDev* __restrict__ pd,
+                                                const int32_t* __restrict__ cell_prob, const int* __restrict__ gate,
+                                                double* __restrict__ out)
 {
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
@@ -201,7 +207,7 @@ __global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int ni, int d
     }
     if (dim == 2) r2 = 0.0;
     if (mode == 1) {
-        const double eps = *eps_dev;
+        const double eps = pd[cell_prob[P]].eps;
         if (eps == 0.0) {
             r0 = r1 = r2 = 0.0;
         } else {
@@ -221,7 +227,7 @@ int sync_load(jfnk_ctx* c)
 {
     if (c->load_on_device == c->load) return JFNK_OK;
     JF_CUDA(c, cudaStreamSynchronize(c->cur));
-    JF_CUDA(c, cudaMemcpy(&c->gd->load, &c->load, sizeof(double), cudaMemcpyHostToDevice));
+    JF_CUDA(c, cudaMemcpy(&c->gdev->load, &c->load, sizeof(double), cudaMemcpyHostToDevice));
     c->load_on_device = c->load;
     return JFNK_OK;
 }
@@ -240,28 +246,30 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     int sl[3];
     for (int q = 0; q < 3; q++) sl[q] = c->prof.enabled ? c->prof.slot(kNames[q]) : -1;
     jfnk_prof_begin(c, sl[0]);
-    if (c->law == JFNK_LAW_LINEAR)
-        k_grad<JFNK_LAW_LINEAR><<<nblk(m.nc, 128), 128, 0, s>>>(gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr,
-                                                                 m.sell_l, m.n_slots, u_int, G, T, c->mu, c->kappa);
-    else
-        k_grad<JFNK_LAW_NEOHOOKEAN><<<nblk(m.nc, 128), 128, 0, s>>>(gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr,
-                                                                     m.sell_l, m.n_slots, u_int, G, T, c->mu, c->kappa);
+#define JF_GRAD(LAW_)                                                                                                  \
+    k_grad<LAW_><<<nblk(m.nc, 128), 128, 0, s>>>(gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr, m.sell_l,        \
+                                                 m.n_slots, u_int, G, T, c->mat, c->cell_prob)
+    if (c->law_mode == 0) JF_GRAD(JFNK_LAW_LINEAR);
+    else if (c->law_mode == 1) JF_GRAD(JFNK_LAW_NEOHOOKEAN);
+    else JF_GRAD(2);
+#undef JF_GRAD
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[0]);
     if (m.nflux > 0) {
         jfnk_prof_begin(c, sl[1]);
-        if (c->law == JFNK_LAW_LINEAR)
-            k_flux<JFNK_LAW_LINEAR><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
-                                                                        u_int, G, T, m.bval, &c->gd->load, m.fn_pos, F, Fn);
-        else
-            k_flux<JFNK_LAW_NEOHOOKEAN><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef,
-                                                                            u_int, G, T, m.bval, &c->gd->load, m.fn_pos, F, Fn);
+#define JF_FLUX(LAW_)                                                                                                  \
+    k_flux<LAW_><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef, u_int, G, T,     \
+                                                    m.bval, &c->gdev->load, m.fn_pos, c->mat, c->cell_prob, F, Fn)
+        if (c->law_mode == 0) JF_FLUX(JFNK_LAW_LINEAR);
+        else if (c->law_mode == 1) JF_FLUX(JFNK_LAW_NEOHOOKEAN);
+        else JF_FLUX(2);
+#undef JF_FLUX
         JF_LAUNCHED(c);
         jfnk_prof_end(c, sl[1]);
     }
     jfnk_prof_begin(c, sl[2]);
     k_finish<<<nblk(m.nc, 256), 256, 0, s>>>(m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr, F, m.b0,
-                                            &c->gd->load, mode, c->Ru, eps_dev, gate, out);
+                                            &c->gdev->load, mode, c->Ru, c->pd, c->cell_prob, gate, out);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);
     return JFNK_OK;

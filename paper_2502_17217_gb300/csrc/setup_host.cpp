@@ -47,7 +47,7 @@ static std::vector<int32_t> rcm_order(int nc, const std::vector<std::vector<int3
     return order;
 }
 
-std::string build_topology(const HostMesh& hm, bool rcm, Topology& t)
+std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std::vector<int32_t>* group)
 {
     const int nc = hm.nc, ni = hm.ni, nf = hm.nf;
     t = Topology();
@@ -64,6 +64,8 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t)
         t.n2o.resize(nc);
         std::iota(t.n2o.begin(), t.n2o.end(), 0);
     }
+    if (group)
+        std::stable_sort(t.n2o.begin(), t.n2o.end(), [&](int a, int b) { return (*group)[a] < (*group)[b]; });
     t.o2n.assign(nc, -1);
     for (int i = 0; i < nc; i++) t.o2n[t.n2o[i]] = i;
     // --- face order

@@ -1,14 +1,18 @@
-// Host orchestration of the device-resident Jacobian-free Newton-Krylov loop (Sec. 3.2-3.3).
-//   gmres():  restarted right-preconditioned GMRES(m) on J(u) x = b, x0 = 0.  Each Arnoldi
-//             iteration j enqueues: z = P^-1 V_j with eps = s (1 + |u|) / |z|; w = u + eps z;
-//             the three residual passes ending in Jv = (R(w) - R(u)) / eps; Gram-Schmidt
-//             (twice when needed); V_{j+1} = w / |w|; a Givens step.  Every scalar lives on
-//             the device; the host only polls the `done` flag every few iterations.  At the
-//             end of a cycle x += P^-1 (V y).
-//   newton(): J du = -R per Newton iteration with inner tolerance eta (Sec. 3.2: three
-//             orders), backtracking line search on |R| (s = 1, 1/2, ...; accepted when
-//             |R(u + s du)| <= (1 - 1e-4 s) |R(u)|), convergence |R| <= max(atol, rtol |R(u0)|)
-//             per load step with the load factor ramped k / n (Sec. 3.3).
+// Host orchestration of the device-resident Jacobian-free Newton-Krylov loop (Sec. 3.2-3.3)
+// for P >= 1 independent problems advancing together.
+//   gmres():  restarted right-preconditioned GMRES(m) on J_p(u_p) x_p = b_p for every active
+//             problem, x0 = 0.  One Arnoldi iteration enqueues: z = P^-1 V_j; eps_p =
+//             s (1 + |u_p|) / |z_p|; w = u + eps z; the three residual passes ending in
+//             Jv = (R(w) - R(u)) / eps_p; Gram-Schmidt (twice when needed) with each problem's
+//             Givens step; V_{j+1} = w / |w|.  The iteration is captured once as a CUDA graph
+//             and replayed; every scalar lives on the device and the host keeps two iterations
+//             in flight ahead of its view of the `all done` flag.  At the end of a cycle
+//             x += P^-1 (V y) per problem.
+//   newton(): per problem, J du = -R with inner tolerance eta (Sec. 3.2: three orders), a
+//             backtracking line search on |R_p| (s = 1, 1/2, ...; accepted when
+//             |R(u + s du)| <= (1 - 1e-4 s) |R(u)|), convergence |R_p| <= max(atol, rtol |R_p(u0)|)
+//             per load step with the load factor ramped k / n (Sec. 3.3).  Problems that
+//             converge (or fail) leave the active set; the others continue.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -17,46 +21,51 @@
 
 namespace jfnk {
 
-static int read_header(jfnk_ctx* c)
+// per-problem header fields (everything before the h array) to the pinned mirror
+static int read_problems(jfnk_ctx* c)
 {
-    // first fields of GmresDev (j, k, done, reorth, tickets, pad, eps, unorm, beta, target, inv, wn2, res, n_reorth)
-    JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gd, offsetof(GmresDev, load), cudaMemcpyDeviceToHost, c->cur));
+    JF_CUDA(c, cudaMemcpy2DAsync(c->ph, sizeof(ProbDev), c->pd, sizeof(ProbDev), offsetof(ProbDev, h), c->nprob,
+                                 cudaMemcpyDeviceToHost, c->cur));
     JF_CUDA(c, cudaStreamSynchronize(c->cur));
     return JFNK_OK;
 }
 
-static int read_scalar(jfnk_ctx* c, const double* dev, double* out)
+// copies field `off` (a double) of every problem's host mirror to the device
+static int write_problem_doubles(jfnk_ctx* c, size_t off)
 {
-    JF_CUDA(c, cudaMemcpyAsync(c->scal_h, dev, sizeof(double), cudaMemcpyDeviceToHost, c->cur));
-    JF_CUDA(c, cudaStreamSynchronize(c->cur));
-    *out = c->scal_h[0];
+    JF_CUDA(c, cudaMemcpy2DAsync((char*)c->pd + off, sizeof(ProbDev), (const char*)c->ph + off, sizeof(ProbDev),
+                                 sizeof(double), c->nprob, cudaMemcpyHostToDevice, c->cur));
     return JFNK_OK;
 }
 
-// Jx = (R(u + eps x) - R(u)) / eps into out (direction x, eps from |x|)
+static int write_problem_ints(jfnk_ctx* c, size_t off)
+{
+    JF_CUDA(c, cudaMemcpy2DAsync((char*)c->pd + off, sizeof(ProbDev), (const char*)c->ph + off, sizeof(ProbDev),
+                                 sizeof(int), c->nprob, cudaMemcpyHostToDevice, c->cur));
+    return JFNK_OK;
+}
+
+// Jx = (R(u + eps x) - R(u)) / eps_p into out (direction x, eps_p from |x_p|)
 static int jv_direction(jfnk_ctx* c, const double* x, double* out)
 {
-    const size_t n = 3 * (size_t)c->dm.nc;
-    int rc = norm_mode(c, x, n, 1, nullptr);
-    if (!rc) rc = perturb(c, c->u, x, c->w, nullptr);
-    if (!rc) rc = residual(c, c->w, out, OUT_JV, &c->gd->eps);
+    int rc = pnorm(c, x, 1, false);
+    if (!rc) rc = perturb(c, c->u, x, c->w, false);
+    if (!rc) rc = residual(c, c->w, out, OUT_JV, nullptr);
     return rc;
 }
 
-// One Arnoldi iteration, every kernel reading j from the device and returning at once when
-// the cycle is done: z = P^-1 V_j, eps, w = u + eps z, Jv into wk, Gram-Schmidt (+ Givens),
-// V_{j+1}; then the header (j, k, done, ...) is copied to pinned host memory.
+// One lockstep Arnoldi iteration; kernels read the iteration index and the per-problem flags
+// from the device and return at once when every cycle is done.
 static int enqueue_iteration(jfnk_ctx* c)
 {
-    const size_t n = 3 * (size_t)c->dm.nc;
-    const int* gate = &c->gd->done;
+    const int* gate = &c->gdev->all_done;
     int rc;
-    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gd->j, c->V_is_float, c->z, gate))) return rc;
-    if ((rc = norm_mode(c, c->z, n, 1, gate))) return rc;
-    if ((rc = perturb(c, c->u, c->z, c->w, gate))) return rc;
-    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, &c->gd->eps, gate))) return rc;
+    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate))) return rc;
+    if ((rc = pnorm(c, c->z, 1, true))) return rc;
+    if ((rc = perturb(c, c->u, c->z, c->w, true))) return rc;
+    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, nullptr, gate))) return rc;
     if ((rc = arnoldi_orthogonalise(c, c->wk))) return rc;
-    JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gd, offsetof(GmresDev, n_reorth), cudaMemcpyDeviceToHost, c->cur));
+    JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
     return JFNK_OK;
 }
 
@@ -84,31 +93,36 @@ static int capture_iteration(jfnk_ctx* c)
     return JFNK_OK;
 }
 
-int gmres(jfnk_ctx* c, const double* b, double* x, int* its_out, double* relres_out, int* status)
+// GMRES for every problem whose ph[p].active is set on entry (uploaded here).  its[p] gains
+// the Arnoldi iterations of problem p; conv[p] tells whether its tolerance was met.
+int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, std::vector<int>& conv)
 {
     const size_t n = 3 * (size_t)c->dm.nc;
-    const int m = c->opt.gmres_restart;
-    const int pc = c->opt.pc;
-    int its = 0;
-    *status = JFNK_GMRES_STAGNATED;
+    const int m = c->opt.gmres_restart, P = c->nprob;
+    int rc;
     JF_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->cur));
-    int rc = norm2(c, b, n, c->scal);
-    if (rc) return rc;
-    double beta0 = 0;
-    if ((rc = read_scalar(c, c->scal, &beta0))) return rc;
-    double rel = 0.0;
-    if (!(beta0 > 0.0)) {
-        *status = (beta0 == 0.0) ? JFNK_OK : JFNK_DIVERGED;
-        if (its_out) *its_out = 0;
-        if (relres_out) *relres_out = 0;
-        return JFNK_OK;
+    if ((rc = pnorm(c, b, 0, false))) return rc;
+    std::vector<int> act(P);
+    for (int p = 0; p < P; p++) act[p] = c->ph[p].active;
+    if ((rc = read_problems(c))) return rc;
+    for (int p = 0; p < P; p++) {
+        conv[p] = 0;
+        const double b0 = c->ph[p].nrm;
+        if (act[p] && !(b0 > 0.0)) {  // zero right-hand side: x = 0 solves it; NaN: not converged
+            conv[p] = (b0 == 0.0);
+            act[p] = 0;
+        }
+        c->ph[p].target = c->opt.gmres_eta * b0;
+        c->ph[p].active = act[p];
     }
-    const double target = c->opt.gmres_eta * beta0;
-    c->scal_h[1] = target;
-    JF_CUDA(c, cudaMemcpyAsync(&c->gd->target, c->scal_h + 1, sizeof(double), cudaMemcpyHostToDevice, c->cur));
+    if ((rc = write_problem_doubles(c, offsetof(ProbDev, target)))) return rc;
+    if ((rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
     const bool graphs = c->use_graphs && !c->prof.enabled;
     if (graphs && (rc = capture_iteration(c))) return rc;
     for (int rs = 0; rs < c->opt.gmres_max_restarts; rs++) {
+        int n_act = 0;
+        for (int p = 0; p < P; p++) n_act += act[p];
+        if (!n_act) break;
         // r = b - J x
         if (rs == 0) {
             JF_CUDA(c, cudaMemcpyAsync(c->wk, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cur));
@@ -117,96 +131,169 @@ int gmres(jfnk_ctx* c, const double* b, double* x, int* its_out, double* relres_
             if ((rc = axpby(c, n, 1.0, b, -1.0, c->tmp, c->wk))) return rc;
         }
         if ((rc = cycle_init(c, c->wk))) return rc;
-        if ((rc = read_header(c))) return rc;
-        rel = c->gh->beta / beta0;
-        if (!(c->gh->beta == c->gh->beta)) { *status = JFNK_DIVERGED; break; }
-        if (c->gh->beta <= target) { *status = JFNK_OK; break; }
-        // Arnoldi iterations; at most two in flight ahead of the host's view of `done`
-        for (int j = 0; j < m; j++) {
-            if (j >= 2) {
-                JF_CUDA(c, cudaEventSynchronize(c->it_ev[(j - 2) & 3]));
-                if (((volatile GmresDev*)c->gh)->done) break;
+        JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
+        JF_CUDA(c, cudaStreamSynchronize(c->cur));
+        if (!c->gh->all_done) {
+            // Arnoldi iterations; at most two in flight ahead of the host's view of `all done`
+            for (int j = 0; j < m; j++) {
+                if (j >= 2) {
+                    JF_CUDA(c, cudaEventSynchronize(c->it_ev[(j - 2) & 3]));
+                    if (((volatile GlobalDev*)c->gh)->all_done) break;
+                }
+                if (graphs) {
+                    JF_CUDA(c, cudaGraphLaunch(c->it_graph, c->cur));
+                    c->launches += c->graph_kernels;
+                } else if ((rc = enqueue_iteration(c))) {
+                    return rc;
+                }
+                JF_CUDA(c, cudaEventRecord(c->it_ev[j & 3], c->cur));
             }
-            if (graphs) {
-                JF_CUDA(c, cudaGraphLaunch(c->it_graph, c->cur));
-                c->launches += c->graph_kernels;
-            } else if ((rc = enqueue_iteration(c))) {
-                return rc;
-            }
-            JF_CUDA(c, cudaEventRecord(c->it_ev[j & 3], c->cur));
-        }
-        if ((rc = read_header(c))) return rc;
-        const int k = c->gh->k;
-        its += k;
-        rel = c->gh->res / beta0;
-        if (k > 0) {
             if ((rc = cycle_solution(c, c->tmp))) return rc;
-            if ((rc = pc_apply_any(c, pc, c->tmp, 0, c->z, nullptr))) return rc;
+            if ((rc = pc_apply_any(c, c->opt.pc, c->tmp, 0, c->z, nullptr))) return rc;
             if ((rc = axpby(c, n, 1.0, x, 1.0, c->z, x))) return rc;
         }
-        if (!(c->gh->res == c->gh->res)) { *status = JFNK_DIVERGED; break; }
-        if (c->gh->res <= target) { *status = JFNK_OK; break; }
+        if ((rc = read_problems(c))) return rc;
+        bool any_change = false;
+        for (int p = 0; p < P; p++) {
+            if (!act[p]) continue;
+            const ProbDev& Q = c->ph[p];
+            its[p] += Q.k;
+            const bool nan = !(Q.beta == Q.beta) || !(Q.res == Q.res);
+            if (Q.beta <= Q.target || (Q.k > 0 && Q.res <= Q.target) || nan) {
+                conv[p] = !nan;
+                act[p] = 0;
+                c->ph[p].active = 0;
+                any_change = true;
+            }
+        }
+        if (any_change && (rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
     }
-    if (its_out) *its_out = its;
-    if (relres_out) *relres_out = rel;
     return JFNK_OK;
 }
 
 int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
 {
     const size_t n = 3 * (size_t)c->dm.nc;
+    const int P = c->nprob;
     auto t0 = std::chrono::steady_clock::now();
-    int status = JFNK_OK, rc;
-    double rn = 0, r0 = 0;
-    JF_CUDA(c, cudaMemsetAsync(&c->gd->n_reorth, 0, sizeof(int), c->cur));
-    for (int step = 1; step <= n_load_steps && status == JFNK_OK; step++) {
+    int rc;
+    std::vector<jfnk_stats>& S = c->pstats;
+    S.assign(P, jfnk_stats());
+    for (auto& s : S) std::memset(&s, 0, sizeof s);
+    std::vector<int> status(P, JFNK_OK), act(P), its(P), conv(P), newton_its(P);
+    std::vector<double> rn(P), r0(P);
+    if ((rc = read_problems(c))) return rc;
+    for (int p = 0; p < P; p++) { c->ph[p].n_reorth = 0; c->ph[p].active = 0; }
+    if ((rc = write_problem_ints(c, offsetof(ProbDev, n_reorth)))) return rc;
+    if ((rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
+    for (int step = 1; step <= n_load_steps; step++) {
         c->load = (double)step / n_load_steps;
         if ((rc = sync_load(c))) return rc;
         if ((rc = residual(c, c->u, c->Ru, OUT_R, nullptr))) return rc;
-        st->residual_evals++;
-        if ((rc = norm2(c, c->Ru, n, c->scal))) return rc;
-        if ((rc = read_scalar(c, c->scal, &rn))) return rc;
-        r0 = rn;
-        bool conv = false;
-        for (int it = 0;; it++) {
-            if (!std::isfinite(rn)) { status = JFNK_DIVERGED; break; }
-            if (rn <= std::max(c->opt.newton_atol, c->opt.newton_rtol * r0)) { conv = true; break; }
-            if (it >= c->opt.newton_max_its) { status = JFNK_MAXIT; break; }
-            if ((rc = axpby(c, n, -1.0, c->Ru, 0.0, c->Ru, c->bvec))) return rc;
-            if ((rc = norm_mode(c, c->u, n, 2, nullptr))) return rc;
-            int gits = 0, gst = 0;
-            double grel = 0;
-            if ((rc = gmres(c, c->bvec, c->x, &gits, &grel, &gst))) return rc;
-            st->gmres_its += gits;
-            st->residual_evals += gits;
-            if (gst == JFNK_DIVERGED) { status = JFNK_DIVERGED; break; }
-            double s = 1.0, rt = 0.0;
-            bool acc = false;
-            for (int ls = 0; ls <= c->opt.line_search_max; ls++) {
-                if ((rc = axpby(c, n, s, c->x, 1.0, c->u, c->w))) return rc;
-                if ((rc = residual(c, c->w, c->R, OUT_R, nullptr))) return rc;
-                st->residual_evals++;
-                if ((rc = norm2(c, c->R, n, c->scal))) return rc;
-                if ((rc = read_scalar(c, c->scal, &rt))) return rc;
-                if (rt <= (1.0 - 1e-4 * s) * rn) { acc = true; break; }
-                s *= 0.5;
-            }
-            if (!acc) { status = JFNK_LS_FAILED; break; }
-            // copies, not pointer swaps: the captured iteration graph holds these addresses
-            JF_CUDA(c, cudaMemcpyAsync(c->u, c->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cur));
-            JF_CUDA(c, cudaMemcpyAsync(c->Ru, c->R, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cur));
-            rn = rt;
-            st->newton_its++;
-            if (st->n_hist < 64) st->hist[st->n_hist++] = rn;
+        if ((rc = pnorm(c, c->Ru, 0, false))) return rc;
+        if ((rc = read_problems(c))) return rc;
+        for (int p = 0; p < P; p++) {
+            rn[p] = r0[p] = c->ph[p].nrm;
+            S[p].residual_evals++;
+            act[p] = status[p] == JFNK_OK;
+            newton_its[p] = 0;
         }
-        st->final_rel_res = r0 > 0 ? rn / r0 : 0.0;
-        st->final_abs_res = rn;
-        if (conv) st->load_steps_done++;
+        for (;;) {
+            int n_act = 0;
+            for (int p = 0; p < P; p++) {
+                if (!act[p]) continue;
+                if (!std::isfinite(rn[p])) { status[p] = JFNK_DIVERGED; act[p] = 0; }
+                else if (rn[p] <= std::max(c->opt.newton_atol, c->opt.newton_rtol * r0[p])) { act[p] = 0; S[p].load_steps_done++; }
+                else if (newton_its[p] >= c->opt.newton_max_its) { status[p] = JFNK_MAXIT; act[p] = 0; }
+                n_act += act[p];
+            }
+            if (!n_act) break;
+            if ((rc = axpby(c, n, -1.0, c->Ru, 0.0, c->Ru, c->bvec))) return rc;
+            if ((rc = pnorm(c, c->u, 2, false))) return rc;
+            for (int p = 0; p < P; p++) { c->ph[p].active = act[p]; its[p] = 0; }
+            if ((rc = gmres_batch(c, c->bvec, c->x, its, conv))) return rc;
+            for (int p = 0; p < P; p++) {
+                if (!act[p]) continue;
+                S[p].gmres_its += its[p];
+                S[p].residual_evals += its[p];
+            }
+            // backtracking line search, per problem
+            std::vector<int> acc(P, 0), trial(act);
+            std::vector<double> s(P, 1.0), rt(P, 0.0);
+            for (int ls = 0; ls <= c->opt.line_search_max; ls++) {
+                int n_trial = 0;
+                for (int p = 0; p < P; p++) {
+                    c->ph[p].active = trial[p];
+                    c->ph[p].step = s[p];
+                    n_trial += trial[p];
+                }
+                if (!n_trial) break;
+                if ((rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
+                if ((rc = write_problem_doubles(c, offsetof(ProbDev, step)))) return rc;
+                if ((rc = line_trial(c, c->u, c->x, c->w))) return rc;
+                if ((rc = residual(c, c->w, c->R, OUT_R, nullptr))) return rc;
+                if ((rc = pnorm(c, c->R, 0, false))) return rc;
+                if ((rc = read_problems(c))) return rc;
+                bool any = false;
+                for (int p = 0; p < P; p++) {
+                    c->pmask_h[p] = 0;
+                    if (!trial[p]) continue;
+                    S[p].residual_evals++;
+                    rt[p] = c->ph[p].nrm;
+                    if (rt[p] <= (1.0 - 1e-4 * s[p]) * rn[p]) {
+                        acc[p] = 1;
+                        trial[p] = 0;
+                        c->pmask_h[p] = 1;
+                        any = true;
+                    } else {
+                        s[p] *= 0.5;
+                    }
+                }
+                if (any) {
+                    JF_CUDA(c, cudaMemcpyAsync(c->pmask, c->pmask_h, sizeof(int32_t) * P, cudaMemcpyHostToDevice, c->cur));
+                    if ((rc = accept_masked(c, c->pmask, c->u, c->w, c->Ru, c->R))) return rc;
+                }
+            }
+            JF_CUDA(c, cudaStreamSynchronize(c->cur));
+            for (int p = 0; p < P; p++) {
+                if (!act[p]) continue;
+                if (!acc[p]) { status[p] = JFNK_LS_FAILED; act[p] = 0; continue; }
+                rn[p] = rt[p];
+                newton_its[p]++;
+                S[p].newton_its++;
+                if (S[p].n_hist < 64) S[p].hist[S[p].n_hist++] = rn[p];
+            }
+        }
+        for (int p = 0; p < P; p++) {
+            S[p].final_rel_res = r0[p] > 0 ? rn[p] / r0[p] : 0.0;
+            S[p].final_abs_res = rn[p];
+        }
     }
-    if (read_header(c) == JFNK_OK) st->reorth_its = c->gh->n_reorth;
-    st->status = status;
-    st->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    return status;
+    if ((rc = read_problems(c))) return rc;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    // aggregate: maximum Newton count, sums of Krylov counts, worst status and residual
+    std::memset(st, 0, sizeof *st);
+    st->status = JFNK_OK;
+    st->load_steps_done = n_load_steps;
+    for (int p = 0; p < P; p++) {
+        S[p].status = status[p];
+        S[p].reorth_its = c->ph[p].n_reorth;
+        S[p].solve_ms = ms;
+        st->newton_its = std::max(st->newton_its, S[p].newton_its);
+        st->gmres_its += S[p].gmres_its;
+        st->residual_evals += S[p].residual_evals;
+        st->reorth_its += S[p].reorth_its;
+        st->load_steps_done = std::min(st->load_steps_done, S[p].load_steps_done);
+        st->final_rel_res = std::max(st->final_rel_res, S[p].final_rel_res);
+        st->final_abs_res = std::max(st->final_abs_res, S[p].final_abs_res);
+        if (status[p] != JFNK_OK && st->status == JFNK_OK) st->status = status[p];
+    }
+    if (P == 1) {
+        st->n_hist = S[0].n_hist;
+        std::memcpy(st->hist, S[0].hist, sizeof st->hist);
+    }
+    st->solve_ms = ms;
+    return st->status;
 }
 
 }  // namespace jfnk

@@ -30,7 +30,8 @@ EXPORTS = [
     "jfnk_set_mesh", "jfnk_set_patch", "jfnk_set_material", "jfnk_set_body_force", "jfnk_set_load_factor",
     "jfnk_setup", "jfnk_residual", "jfnk_residual_noalloc", "jfnk_jv", "jfnk_precondition", "jfnk_solve", "jfnk_get_geometry",
     "jfnk_get_gradient", "jfnk_get_permutation", "jfnk_profile_enable", "jfnk_profile_get", "jfnk_profile_reset",
-    "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64",
+    "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64", "jfnk_batch_add", "jfnk_batch_size",
+    "jfnk_batch_problem_cells", "jfnk_batch_stats",
 ]
 
 
@@ -88,6 +89,10 @@ def load():
         "jfnk_launch_count": (C.c_int64, [vp]),
         "jfnk_device_bytes": (C.c_int64, [vp]),
         "jfnk_convert_f32_to_f64": (i, [vp, vp, C.c_int64, vp]),
+        "jfnk_batch_add": (i, [vp, vp, C.POINTER(C.c_int32)]),
+        "jfnk_batch_size": (i, [vp]),
+        "jfnk_batch_problem_cells": (i, [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "jfnk_batch_stats": (i, [vp, C.POINTER(Stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -290,8 +295,45 @@ class Solver:
         return int(self.L.jfnk_device_bytes(self.h))
 
 
+class Batch(Solver):
+    """Independent problems solved together in one concatenated index space.
+
+    Vectors are [sum of n_cells, 3] in the order the problems were added."""
+
+    def __init__(self, cases, options: Options | None = None, **opt_kw):
+        self.L = load()
+        if cases and "alpha_residual" not in opt_kw and options is None:
+            opt_kw["alpha_residual"] = cases[0].alpha
+        self.options = options if options is not None else default_options(**opt_kw)
+        h = C.c_void_p()
+        rc = self.L.jfnk_create(C.byref(h), C.byref(self.options))
+        if rc != OK:
+            raise JfnkError(rc, "jfnk_create failed (no usable CUDA device?)")
+        self.h = h
+        self.cases = list(cases)
+        self.sizes = [c.mesh.n_cells for c in self.cases]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(int)
+        self.nc = int(self.offsets[-1])
+        self.mesh = None
+        for case in self.cases:
+            prob = Solver(case.mesh, case.material, case.body_force, options=self.options)
+            idx = C.c_int32(0)
+            self._check(self.L.jfnk_batch_add(self.h, prob.h, C.byref(idx)))
+            prob.close()
+
+    def problem_stats(self):
+        n = self.L.jfnk_batch_size(self.h)
+        arr = (Stats * n)()
+        self._check(self.L.jfnk_batch_stats(self.h, arr))
+        return list(arr)
+
+    def split(self, u):
+        """Per-problem views of a concatenated vector."""
+        return [u[self.offsets[p]:self.offsets[p + 1]] for p in range(len(self.sizes))]
+
+
 def solver_for_case(case, **kw) -> Solver:
     return Solver.from_case(case, **kw)
 
 
-__all__ = ["Solver", "Options", "Stats", "default_options", "load", "EXPORTS", "JfnkError", "solver_for_case", "_inputs"]
+__all__ = ["Solver", "Batch", "Options", "Stats", "default_options", "load", "EXPORTS", "JfnkError", "solver_for_case", "_inputs"]

@@ -1,0 +1,85 @@
+"""Batches: independent problems concatenated into one index space (GPU).
+
+Every problem keeps its own material, Jv step, GMRES iteration, line search and convergence
+test, and a problem's internal numbering, face order and reduction chunks are the same alone
+and in a batch.  So with block-Jacobi the batched solve of each problem is bitwise the solve
+of that problem alone; with the multigrid preconditioner (whose coarse levels span the batch)
+they agree within the displacement tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_17217_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _mix():
+    sizes = I.batch_sizes(6, lo=200, hi=2000, seed=4)
+    cases = [I.case_batch_member(*sz, index=k) for k, sz in enumerate(sizes)]
+    cases.append(I.case_nh_beam(12, 4, 4, (1.0, 0.25, 0.25), end_uy=0.1, load_steps=1))  # mixed laws
+    return cases
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_batch_residual_and_jv_match_each_problem_alone():
+    from paper_2502_17217_gb300 import jfnk
+    cases = _mix()
+    B = jfnk.Batch(cases)
+    u = np.concatenate([I.random_field(k + 1, c.mesh.n_cells, 1e-4 if c.material.law == 0 else 0.002)
+                        for k, c in enumerate(cases)])
+    v = np.concatenate([I.random_field(k + 50, c.mesh.n_cells, 1.0) for k, c in enumerate(cases)])
+    R = B.residual(u)
+    J = B.jv(u, v)
+    for k, (c, Rk, Jk, uk, vk) in enumerate(zip(cases, B.split(R), B.split(J), B.split(u), B.split(v))):
+        s = jfnk.Solver.from_case(c)
+        assert np.array_equal(Rk, s.residual(uk)), k
+        assert np.array_equal(Jk, s.jv(uk, vk)), k  # eps from this problem's norms only
+        o = O.Oracle.from_case(c)
+        assert _rel(Rk, o.residual(uk)) <= 1e-12
+
+
+def test_batch_solve_bitwise_equals_alone_with_block_jacobi():
+    from paper_2502_17217_gb300 import jfnk
+    cases = _mix()
+    B = jfnk.Batch(cases, pc=jfnk.PC_BJACOBI, newton_rtol=1e-10)
+    u, st, rc = B.solve()
+    assert rc == 0
+    per = B.problem_stats()
+    for k, (c, uk) in enumerate(zip(cases, B.split(u))):
+        s = jfnk.Solver.from_case(c, pc=jfnk.PC_BJACOBI, newton_rtol=1e-10)
+        ua, sta, rca = s.solve()
+        assert rca == 0
+        assert np.array_equal(uk, ua), (k, _rel(uk, ua))
+        assert per[k].gmres_its == sta.gmres_its and per[k].newton_its == sta.newton_its
+
+
+def test_batch_solve_within_tolerance_with_multigrid_mixed_precision():
+    from paper_2502_17217_gb300 import jfnk
+    cases = _mix()
+    kw = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-11, mg_coarse_max=50)
+    B = jfnk.Batch(cases, **kw)
+    u, st, rc = B.solve()
+    assert rc == 0
+    for k, (c, uk) in enumerate(zip(cases, B.split(u))):
+        ua, _, rca = jfnk.Solver.from_case(c, **kw).solve()
+        assert rca == 0
+        assert _rel(uk, ua) <= 1e-8, (k, _rel(uk, ua))
+        # and the batched result is the discrete solution: the oracle's residual is small
+        o = O.Oracle.from_case(c)
+        R = o.residual(uk)
+        R0 = o.residual(np.zeros_like(uk))
+        assert np.linalg.norm(R) <= 1e-9 * np.linalg.norm(R0)
