@@ -44,15 +44,30 @@ def measured_peaks():
     return {"hbm_gbs": HBM_PEAK_FALLBACK}, "fallback"
 
 
-def workload_case():
+def workload_case(name="c2"):
     from paper_2502_17217_gb300 import inputs as I
+    if name == "c3":
+        return I.case_nh_beam()
+    if name == "c4":
+        return [I.case_batch_member(*x, index=k) for k, x in enumerate(I.batch_sizes())]
     return I.case_cantilever(200, 20, 20, (1.0, 0.1, 0.1), perturb=0.15, seed=2)
 
 
-WORKLOAD = {"workload": "cantilever_200x20x20_perturbed15", "cells": 80000, "dofs": 240000,
-            "law": "linear elastic (E=200 GPa, nu=0.3)", "pc": "multigrid V-cycle (FP32)",
-            "krylov": "GMRES(30), FP32 basis, FP64 Arnoldi arithmetic", "tolerance": "|R|/|R0| < 1e-8",
-            "eta": 1e-3, "jv_eps": "1e-7 (1+|u|)/|v|"}
+WORKLOADS = {
+    "c2": {"workload": "cantilever_200x20x20_perturbed15", "cells": 80000, "dofs": 240000,
+           "law": "linear elastic (E=200 GPa, nu=0.3)", "pc": "multigrid V-cycle (FP32)",
+           "krylov": "GMRES(30), FP32 basis, FP64 Arnoldi arithmetic", "tolerance": "|R|/|R0| < 1e-8",
+           "eta": 1e-3, "jv_eps": "1e-7 (1+|u|)/|v|", "load_steps": 1},
+    "c3": {"workload": "neo_hookean_beam_256x32x32", "cells": 262144, "dofs": 786432,
+           "law": "neo-Hookean total Lagrangian (mu=0.38 MPa, kappa=8.3 MPa)", "pc": "multigrid V-cycle (FP32)",
+           "krylov": "GMRES(30), FP32 basis, FP64 Arnoldi arithmetic", "tolerance": "|R|/|R0| < 1e-8 per load step",
+           "eta": 1e-3, "jv_eps": "1e-7 (1+|u|)/|v|", "load_steps": 10},
+    "c4": {"workload": "batch_512_boxes_logU_1k_64k", "cells": None, "dofs": None,
+           "law": "linear elastic, E~U(1,300) GPa, nu~U(0.2,0.45)", "pc": "multigrid V-cycle (FP32)",
+           "krylov": "GMRES(30) per problem, FP32 basis, FP64 Arnoldi arithmetic", "tolerance": "|R|/|R0| < 1e-8 per problem",
+           "eta": 1e-3, "jv_eps": "1e-7 (1+|u_p|)/|v_p| per problem", "load_steps": 1},
+}
+WORKLOAD = WORKLOADS["c2"]
 
 
 class ClockSampler:
@@ -137,10 +152,16 @@ def run_ours(args, rank, world):
     g.build()
     dev = torch.device("cuda", rank % max(1, torch.cuda.device_count()))
     torch.cuda.set_device(dev)
-    case = workload_case()
-    nc = case.mesh.n_cells
-    s = jfnk.Solver.from_case(case, device=dev.index, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED,
-                              newton_rtol=1e-8, gmres_restart=30, gmres_eta=1e-3)
+    case = workload_case(args.workload)
+    opts = dict(device=dev.index, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-8, gmres_restart=30,
+                gmres_eta=1e-3)
+    if args.workload == "c4":
+        s = jfnk.Batch(case, **opts)
+        case = case[0]
+    else:
+        s = jfnk.Solver.from_case(case, **opts)
+    nc = s.nc
+    load_steps = WORKLOADS[args.workload]["load_steps"]
     s.setup()
     # the library launches on the caller's stream: a dedicated stream, current for every call,
     # so the CUDA events below sit on the launching stream
@@ -150,7 +171,7 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step():
-        u, st, rc = s.solve(u0)
+        u, st, rc = s.solve(u0, load_steps=load_steps)
         if rc != 0:
             raise RuntimeError(f"solve failed: status {rc}, rel res {st.final_rel_res:.3e}")
         return st
@@ -172,7 +193,10 @@ def run_ours(args, rank, world):
             st = step()
             ev[k][1].record(stream)
             torch.cuda.synchronize()
-            jv_total += st.gmres_its
+            if args.workload == "c4":  # useful cell-updates: each problem's cells x its own iterations
+                jv_total += sum(ps.gmres_its * n for ps, n in zip(s.problem_stats(), s.sizes)) / nc
+            else:
+                jv_total += st.gmres_its
             stats.append(st)
     launches = s.launch_count() - launches0
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -202,16 +226,19 @@ def run_ours(args, rank, world):
         kt[name] = {"ms": ms, "launches": n}
     # end to end through the C ABI with host buffers (copies inside the timed region)
     u_host = np.zeros((nc, 3))
-    s.solve(u_host)
+    s.solve(u_host, load_steps=load_steps)
     t0 = time.perf_counter()
     jv_e2e = 0
     for _ in range(args.steps):
-        u, st, rc = s.solve(u_host)
-        jv_e2e += st.gmres_its
+        u, st, rc = s.solve(u_host, load_steps=load_steps)
+        if args.workload == "c4":
+            jv_e2e += sum(ps.gmres_its * n for ps, n in zip(s.problem_stats(), s.sizes)) / nc
+        else:
+            jv_e2e += st.gmres_its
     e2e_s = time.perf_counter() - t0
     e2e_value = nc * jv_e2e / e2e_s * world
     return {"value": value, "t_ms": t_ms, "stats": stats, "kernels": kt, "launches": launches, "clocks": clk.summary(),
-            "e2e": e2e_value, "case": case, "solver": s}
+            "e2e": e2e_value, "case": case, "solver": s, "nc": nc}
 
 
 def run_oracle_sample(case, seconds=10.0):
@@ -230,6 +257,48 @@ def run_oracle_sample(case, seconds=10.0):
     return nc * its_total / dt, its_total, dt
 
 
+def run_serving(args):
+    """Config 5: Poisson arrivals of solve requests (cells log-uniform 2k-1M, 70% Hooke / 30%
+    neo-Hookean with 2 load steps), served with continuous admission (mixed precision, MG),
+    against the same requests solved one after another in plain FP64."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_17217_gb300 import inputs as I, jfnk, serving
+    reqs_def = I.serving_requests(args.requests, seed=5)
+    cases = [c for c, _ in reqs_def]
+    steps = [st for _, st in reqs_def]
+    served_opts = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-8)
+    plain_opts = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_FP64, newton_rtol=1e-8)
+    # plain sequential FP64 solves (set-up included, as for a served request)
+    t0 = time.perf_counter()
+    plain_u = []
+    for c, st in reqs_def:
+        s = jfnk.Solver.from_case(c, **plain_opts)
+        u, stt, rc = s.solve(load_steps=st, raise_on_fail=False)
+        plain_u.append(u)
+        s.close()
+    t_seq = time.perf_counter() - t0
+    rates = {}
+    for rate in [float(x) for x in args.rates.split(",")]:
+        reqs, wall, srv = serving.serve_stream(cases, rate_per_s=rate, seed=int(rate), load_steps=steps, max_slots=8,
+                                               **served_opts)
+        summ = serving.summarize(reqs, wall)
+        err = max(float(np.linalg.norm(r.u - up) / max(np.linalg.norm(up), 1e-300)) for r, up in zip(reqs, plain_u))
+        summ.update(max_concurrent=srv.max_concurrent, max_rel_diff_vs_fp64=err)
+        rates[str(int(rate))] = summ
+    best = max(v["solves_per_s"] for v in rates.values())
+    line = {"metric": "served solves/s", "value": best, "unit": "solves/s", "n_gpus": 1, "steps": len(rates),
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "serving_poisson_logU_2k_1M_70lin_30nh", "requests": args.requests,
+                       "served": "continuous admission by HBM footprint, 8 slots, MG FP32 + FP32 basis",
+                       "baseline": "the same requests solved one after another, plain FP64"},
+            "rates": rates, "sequential_fp64_solves_per_s": len(reqs_def) / t_seq,
+            "speedup_vs_sequential_fp64": best / (len(reqs_def) / t_seq)}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -238,7 +307,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu", action="store_true", help="untimed solves only, for an ncu capture of the same kernels")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
+    ap.add_argument("--serve", action="store_true", help="config 5: Poisson request stream, served solves/s and p50/p99")
+    ap.add_argument("--rates", default="10,30,100,300,1000")
+    ap.add_argument("--requests", type=int, default=24)
     args = ap.parse_args()
+    if args.serve:
+        return run_serving(args)
     if args.ncu:
         import torch
         from paper_2502_17217_gb300 import jfnk
@@ -289,13 +364,18 @@ def main():
             torch.distributed.destroy_process_group()
         return
     case = r["case"]
-    nc = case.mesh.n_cells
+    nc = r["nc"]
     peaks, src = measured_peaks()
-    costs = kernel_costs(case)
+    costs = kernel_costs(case) if args.workload != "c4" else None
     # dominant kernel by total time
     top = max(("grad", "flux", "finish"), key=lambda k: r["kernels"][k]["ms"])
     kt = r["kernels"][top]
     avg_s = kt["ms"] / max(1, kt["launches"]) / 1e3
+    if costs is None:  # batch: costs of the whole union mesh
+        costs = {k: (0, 0) for k in ("grad", "flux", "finish")}
+        for cs in workload_case("c4"):
+            for k, (f_, b_) in kernel_costs(cs).items():
+                costs[k] = (costs[k][0] + f_, costs[k][1] + b_)
     flops, nbytes = costs[top]
     achieved = flops / avg_s / 1e12
     roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -308,7 +388,8 @@ def main():
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["t_ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, parallelism=f"replicas{world}", l2="flushed (256 MB write) before every step"),
+            "config": dict(WORKLOADS[args.workload], cells=nc, dofs=3 * nc, parallelism=f"replicas{world}",
+                           l2="flushed (256 MB write) before every step"),
             "solve_time_s": r["t_ms"] / args.steps / 1e3,
             "newton_its": st[-1].newton_its, "gmres_its": st[-1].gmres_its, "final_rel_res": st[-1].final_rel_res,
             "reorth_its": st[-1].reorth_its,

@@ -316,7 +316,7 @@ def batch_sizes(n_problems: int = 512, lo: int = 1000, hi: int = 64000, seed: in
     out = []
     for p in range(n_problems):
         n = math.exp(math.log(lo) + r[p, 0] * (math.log(hi) - math.log(lo)))
-        s = (n / 16.0) ** (1.0 / 3.0)
+        s = (n / 4.0) ** (1.0 / 3.0)  # nx:ny:nz = 4:1:1 gives 4 s^3 cells
         nx, ny, nz = max(4, round(4 * s)), max(4, round(s)), max(4, round(s))
         E = 1e9 + r[p, 1] * (300e9 - 1e9)
         nu = 0.2 + r[p, 2] * 0.25
@@ -335,3 +335,27 @@ def case_batch_member(nx, ny, nz, E, nu, u01, index: int, seed: int = 4, perturb
     h = 0.01
     return case_cantilever(nx, ny, nz, (nx * h, ny * h, nz * h), perturb=perturb, seed=seed * 100000 + index,
                            E=E, nu=nu, traction=t)
+
+
+def serving_requests(n: int, lo: int = 2000, hi: int = 1000000, seed: int = 5, frac_nh: float = 0.3):
+    """Solve requests of the serving workload: box meshes (4:1:1, +-15% interior-node
+    perturbation) with cell counts log-uniform in [lo, hi]; a fraction frac_nh are neo-Hookean
+    (mu = 0.38 MPa, kappa = 8.3 MPa, x-max moved transversally by 5% of the length over 2 load
+    steps), the others Hooke with a random material and end traction as in the batch workload.
+    Returns a list of (case, load_steps)."""
+    r = splitmix64_uniform(seed, 5 * n, key=21).reshape(n, 5)
+    out = []
+    for k in range(n):
+        cells = math.exp(math.log(lo) + r[k, 0] * (math.log(hi) - math.log(lo)))
+        s = (cells / 4.0) ** (1.0 / 3.0)
+        nx, ny, nz = max(4, round(4 * s)), max(4, round(s)), max(4, round(s))
+        h = 0.01
+        if r[k, 1] < frac_nh:
+            c = case_nh_beam(nx, ny, nz, (nx * h, ny * h, nz * h), end_uy=0.05 * nx * h, load_steps=2,
+                             perturb=0.15, seed=seed * 100000 + k)
+            out.append((c, 2))
+        else:
+            E = 1e9 + r[k, 2] * (300e9 - 1e9)
+            nu = 0.2 + r[k, 3] * 0.25
+            out.append((case_batch_member(nx, ny, nz, E, nu, float(r[k, 4]), index=k, seed=seed), 1))
+    return out

@@ -1,0 +1,189 @@
+"""Solve-request server on one GPU: continuous admission by HBM footprint, concurrent slots.
+
+Requests (a mesh + boundary conditions + material, and a number of load steps) arrive at any
+time.  The dispatcher admits queued requests in arrival order as soon as a slot is free and
+the request's device footprint fits the memory budget; each admitted request gets its own
+context (mesh, state, Krylov basis and preconditioner resident on the device for its whole
+life) and its own CUDA stream, and runs its Newton-Krylov solve in a slot worker.  Requests
+admitted while others are running overlap with them on the device.  A request's arithmetic
+never depends on the others (separate contexts), so its result is the same alone and in the
+mix.  Latency is completion time minus arrival time (queueing, set-up and solve).
+
+The footprint of a request is estimated as bytes-per-cell x cells; the server starts from a
+conservative figure per law and replaces it with the largest measured ratio
+(jfnk_device_bytes / cells) of the requests it has run.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import jfnk
+
+DEFAULT_BYTES_PER_CELL = {0: 2400.0, 1: 3200.0}  # Hooke, neo-Hookean; refined by measurement
+
+
+@dataclass
+class Request:
+    case: object
+    load_steps: int = 1
+    t_arrival: float = 0.0
+    tag: object = None
+    # filled by the server
+    t_admit: float = 0.0
+    t_done: float = 0.0
+    u: np.ndarray | None = None
+    status: int = 0
+    stats: object = None
+    bytes: int = 0
+    error: str | None = None
+    done: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+    @property
+    def cells(self) -> int:
+        return self.case.mesh.n_cells
+
+
+class Server:
+    """Continuous-batching JFNK solve server (one GPU)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: float | None = None, max_slots: int = 8, **options):
+        self.device = device
+        self.options = dict(options)
+        self.max_slots = max_slots
+        if hbm_budget_bytes is None:
+            import torch
+            free, _ = torch.cuda.mem_get_info(device)
+            hbm_budget_bytes = 0.8 * free
+        self.budget = float(hbm_budget_bytes)
+        self.bpc = dict(DEFAULT_BYTES_PER_CELL)
+        self._queue: collections.deque[Request] = collections.deque()
+        self._lock = threading.Condition()
+        self._in_use = 0.0
+        self._running = 0
+        self._stop = False
+        self._workers: list[threading.Thread] = []
+        self.completed: list[Request] = []
+        self.max_concurrent = 0
+        self.max_shared_footprint = 0.0  # largest admitted footprint total with > 1 request running
+        self._dispatcher = threading.Thread(target=self._dispatch, daemon=True)
+        self._dispatcher.start()
+
+    # ---------------------------------------------------------------- client side
+    def submit(self, case, load_steps: int = 1, tag=None) -> Request:
+        r = Request(case=case, load_steps=load_steps, t_arrival=time.perf_counter(), tag=tag)
+        with self._lock:
+            self._queue.append(r)
+            self._lock.notify_all()
+        return r
+
+    def drain(self):
+        """Waits until every submitted request has completed."""
+        with self._lock:
+            while self._queue or self._running:
+                self._lock.wait(0.05)
+
+    def close(self):
+        self.drain()
+        with self._lock:
+            self._stop = True
+            self._lock.notify_all()
+        self._dispatcher.join()
+        for w in self._workers:
+            w.join()
+
+    # ---------------------------------------------------------------- server side
+    def footprint(self, case) -> float:
+        return self.bpc[case.material.law] * case.mesh.n_cells
+
+    def _dispatch(self):
+        while True:
+            with self._lock:
+                while not self._stop and not self._admissible():
+                    self._lock.wait(0.01)
+                if self._stop and not self._queue:
+                    return
+                if not self._admissible():
+                    continue
+                r = self._queue.popleft()
+                need = self.footprint(r.case)
+                self._in_use += need
+                self._running += 1
+                self.max_concurrent = max(self.max_concurrent, self._running)
+                if self._running > 1:
+                    self.max_shared_footprint = max(self.max_shared_footprint, self._in_use)
+                r.t_admit = time.perf_counter()
+            t = threading.Thread(target=self._work, args=(r, need), daemon=True)
+            self._workers.append(t)
+            t.start()
+
+    def _admissible(self) -> bool:
+        if not self._queue or self._running >= self.max_slots:
+            return False
+        need = self.footprint(self._queue[0].case)
+        # an oversized request runs alone rather than never
+        return self._in_use + need <= self.budget or self._running == 0
+
+    def _work(self, r: Request, need: float):
+        try:
+            import torch
+            torch.cuda.set_device(self.device)
+            s = jfnk.Solver.from_case(r.case, device=self.device, **self.options)
+            s.setup()
+            u, st, rc = s.solve(load_steps=r.load_steps, raise_on_fail=False)
+            r.u, r.stats, r.status = u, st, rc
+            r.bytes = s.device_bytes()
+            s.close()
+        except Exception as e:  # reported on the request, the server keeps serving
+            r.error = f"{type(e).__name__}: {e}"
+            r.status = -99
+        r.t_done = time.perf_counter()
+        with self._lock:
+            if r.bytes:
+                law = r.case.material.law
+                self.bpc[law] = max(self.bpc[law] if law in self.bpc else 0.0, r.bytes / r.cells)
+            self._in_use -= need
+            self._running -= 1
+            self.completed.append(r)
+            self._lock.notify_all()
+        r.done.set()
+
+
+def serve_stream(cases, rate_per_s: float, seed: int = 0, load_steps=None, **server_kw):
+    """Submits `cases` with Poisson arrivals at `rate_per_s` (seeded exponential gaps) and
+    returns (requests, wall time from the first arrival to the last completion, server)."""
+    from .inputs import splitmix64_uniform
+    gaps = -np.log(1.0 - splitmix64_uniform(seed, len(cases), key=77)) / rate_per_s
+    srv = Server(**server_kw)
+    reqs = []
+    t0 = time.perf_counter()
+    t_next = t0
+    for k, case in enumerate(cases):
+        t_next += gaps[k]
+        while True:
+            now = time.perf_counter()
+            if now >= t_next:
+                break
+            time.sleep(min(0.002, t_next - now))
+        steps = load_steps[k] if load_steps is not None else 1
+        reqs.append(srv.submit(case, load_steps=steps, tag=k))
+    srv.drain()
+    wall = max(r.t_done for r in reqs) - reqs[0].t_arrival
+    srv.close()
+    return reqs, wall, srv
+
+
+def summarize(reqs, wall):
+    lat = np.array([r.latency for r in reqs])
+    ok = sum(1 for r in reqs if r.status == 0)
+    return {"requests": len(reqs), "converged": ok, "solves_per_s": len(reqs) / wall, "wall_s": wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "cells_total": int(sum(r.cells for r in reqs))}
