@@ -378,7 +378,10 @@ def main():
                 costs[k] = (costs[k][0] + f_, costs[k][1] + b_)
     flops, nbytes = costs[top]
     achieved = flops / avg_s / 1e12
+    from paper_2502_17217_gb300 import jfnk as _j
+    fp64_measured = _j.measure_fp64_rate(0)
     roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "fp64_measured_tflops": fp64_measured, "frac_of_measured_fp64": achieved / fp64_measured,
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
             "peak_source": "FP64 ALU: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (recipe nominal 1.25 TFLOP/s)",
             "hbm_achieved_gbs": nbytes / avg_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs"),

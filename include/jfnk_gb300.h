@@ -206,6 +206,10 @@ int jfnk_profile_reset(jfnk_ctx* ctx);
 int64_t jfnk_launch_count(const jfnk_ctx* ctx);
 /* Device bytes held by the context. */
 int64_t jfnk_device_bytes(const jfnk_ctx* ctx);
+/* Measured FP64 FMA throughput of `device` (TFLOP/s, an FMA counted as 2 flops): a full grid
+ * of independent FMA chains timed with CUDA events (allocates and frees a small buffer).  The
+ * residual and Arnoldi kernels are bound by this rate on GB300. */
+int jfnk_measure_fp64_rate(int device, double* tflops);
 /* The float -> double conversion the FP32 Krylov basis is read through (integer operations,
  * so it does not occupy the narrow FP64 pipe): out[i] = in[i] exactly for normal floats and
  * zeros; float subnormals give zero; Inf/NaN give NaN.  in/out are device arrays of n

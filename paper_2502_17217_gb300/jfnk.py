@@ -31,7 +31,7 @@ EXPORTS = [
     "jfnk_setup", "jfnk_residual", "jfnk_residual_noalloc", "jfnk_jv", "jfnk_precondition", "jfnk_solve", "jfnk_get_geometry",
     "jfnk_get_gradient", "jfnk_get_permutation", "jfnk_profile_enable", "jfnk_profile_get", "jfnk_profile_reset",
     "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64", "jfnk_batch_add", "jfnk_batch_size",
-    "jfnk_batch_problem_cells", "jfnk_batch_stats",
+    "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate",
 ]
 
 
@@ -93,6 +93,7 @@ def load():
         "jfnk_batch_size": (i, [vp]),
         "jfnk_batch_problem_cells": (i, [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "jfnk_batch_stats": (i, [vp, C.POINTER(Stats)]),
+        "jfnk_measure_fp64_rate": (i, [i, C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -330,6 +331,15 @@ class Batch(Solver):
     def split(self, u):
         """Per-problem views of a concatenated vector."""
         return [u[self.offsets[p]:self.offsets[p + 1]] for p in range(len(self.sizes))]
+
+
+def measure_fp64_rate(device: int = 0) -> float:
+    """Measured FP64 FMA throughput of the device in TFLOP/s."""
+    v = C.c_double(0.0)
+    rc = load().jfnk_measure_fp64_rate(device, C.byref(v))
+    if rc != OK:
+        raise JfnkError(rc, "jfnk_measure_fp64_rate failed")
+    return v.value
 
 
 def solver_for_case(case, **kw) -> Solver:
