@@ -145,6 +145,18 @@ def kernel_costs(case):
     return {"flux": (flux_flops, flux_bytes), "grad": (grad_flops, grad_bytes), "finish": (finish_flops, finish_bytes)}
 
 
+def aggregate_ranks(t_ms, units, device):
+    """Replicas: the job's time is the slowest rank's, its work the sum over ranks (every rank
+    gets both).  Works with any torch.distributed backend (gloo tensors on the CPU)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2502_17217_gb300 import jfnk
@@ -201,12 +213,7 @@ def run_ours(args, rank, world):
     launches = s.launch_count() - launches0
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-        j = torch.tensor([jv_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(j)
-        jv_total = float(j.item())
+        t_ms, jv_total = aggregate_ranks(t_ms, jv_total, dev)
     value = nc * jv_total / (t_ms / 1e3)
     # per-kernel times: the same solve with CUDA events on the launch stream around every
     # kernel (events cannot sit inside the captured iteration graph, so these steps launch
