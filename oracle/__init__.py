@@ -68,6 +68,8 @@ def lib():
             "orc_mg_vcycle": (None, [vp, vp, vp]),
             "orc_gmres": (i, [vp, vp, vp, vp, vp, i, d, i, i, vp, vp]),
             "orc_newton": (i, [vp, vp, i, d, d, i, i, d, i, vp]),
+            "orc_lgmres": (i, [vp, vp, vp, vp, vp, i, i, d, i, i, vp, vp]),
+            "orc_newton_ex": (i, [vp, vp, i, d, d, i, i, i, d, i, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -220,8 +222,20 @@ class Oracle:
         rc = lib().orc_gmres(self.h, _p(u), _p(Ru), _p(b), _p(x), m, eta, max_restarts, pc, C.byref(its), C.byref(rel))
         return x, rc, its.value, rel.value
 
-    def newton(self, u0=None, load_steps=1, rtol=1e-8, atol=1e-50, max_newton=50, m=30, eta=1e-3, pc=PC_BJACOBI):
+    def lgmres(self, u, b, m=30, aug=2, eta=1e-3, max_restarts=100, pc=PC_BJACOBI, R_u=None):
+        """Loose GMRES (Sec. 4.2): m columns per cycle, of which up to `aug` are corrections
+        kept from earlier cycles; aug = 0 is GMRES(m)."""
+        u, b = _f64(u, (self.nc, 3)), _f64(b, (self.nc, 3))
+        Ru = self.residual(u) if R_u is None else _f64(R_u, (self.nc, 3))
+        x = np.zeros((self.nc, 3))
+        its, rel = C.c_int(0), C.c_double(0)
+        rc = lib().orc_lgmres(self.h, _p(u), _p(Ru), _p(b), _p(x), m, aug, eta, max_restarts, pc, C.byref(its),
+                              C.byref(rel))
+        return x, rc, its.value, rel.value
+
+    def newton(self, u0=None, load_steps=1, rtol=1e-8, atol=1e-50, max_newton=50, m=30, eta=1e-3, pc=PC_BJACOBI,
+               aug=0):
         u = np.zeros((self.nc, 3)) if u0 is None else _f64(u0, (self.nc, 3)).copy()
         st = Stats()
-        rc = lib().orc_newton(self.h, _p(u), load_steps, rtol, atol, max_newton, m, eta, pc, C.byref(st))
+        rc = lib().orc_newton_ex(self.h, _p(u), load_steps, rtol, atol, max_newton, m, aug, eta, pc, C.byref(st))
         return u, rc, st

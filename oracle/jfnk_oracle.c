@@ -1091,6 +1091,134 @@ done:
     return status;
 }
 
+/* ------------------------------------------------------------------ Sec. 4.2, loose GMRES
+ * The paper runs restarted GMRES in its "loose" form: a restart keeps a few extra vectors,
+ * the corrections of earlier cycles (2 of them, restart 30), after Baker, Jessup and
+ * Manteuffel's LGMRES.  Written from that published method:
+ *   cycle i: the approximation space is K_{m-a}(J P^-1, r_i) (through P^-1 as in orc_gmres)
+ *            plus the a <= kaug stored corrections z_l, whose products J z_l are stored too;
+ *            the Arnoldi process runs over [P^-1 v_1 .. P^-1 v_{m-a}, z_1 .. z_a] (the images
+ *            of the last a columns are the stored J z_l, no new product), the least-squares
+ *            problem is the same as in GMRES, and the correction is
+ *            d = P^-1 (V_{m-a} y_{1..m-a}) + sum_l y_{m-a+l} z_l;
+ *   restart: r_{i+1} = b - J x_{i+1} (true residual); the newest correction is stored as
+ *            z = d / |d| with J z = (r_i - r_{i+1}) / |d|; the oldest is dropped beyond kaug.
+ * The total space per cycle stays m.  kaug = 0 is GMRES(m).  Newest correction first. */
+int orc_lgmres(const orc_problem* p, const double* u, const double* R_u, const double* b, double* x,
+               int m, int kaug, double eta, int max_restarts, int pc, int* its_out, double* relres_out)
+{
+    long n = 3L * p->nc;
+    if (kaug < 0) kaug = 0;
+    if (kaug > m - 1) kaug = m - 1;
+    double* V = (double*)xcalloc((size_t)(m + 1) * n, sizeof(double));
+    double* H = (double*)xcalloc((size_t)(m + 1) * m, sizeof(double));
+    double* cs = (double*)xcalloc((size_t)m, sizeof(double));
+    double* sn = (double*)xcalloc((size_t)m, sizeof(double));
+    double* g = (double*)xcalloc((size_t)m + 1, sizeof(double));
+    double* y = (double*)xcalloc((size_t)m, sizeof(double));
+    double* h = (double*)xcalloc((size_t)m + 1, sizeof(double));
+    double* w = (double*)xcalloc((size_t)n, sizeof(double));
+    double* z = (double*)xcalloc((size_t)n, sizeof(double));
+    double* d = (double*)xcalloc((size_t)n, sizeof(double));
+    double* rprev = (double*)xcalloc((size_t)n, sizeof(double));
+    double* Z = (double*)xcalloc((size_t)(kaug > 0 ? kaug : 1) * n, sizeof(double));
+    double* AZ = (double*)xcalloc((size_t)(kaug > 0 ? kaug : 1) * n, sizeof(double));
+    int na = 0;  /* stored corrections */
+    memset(x, 0, sizeof(double) * (size_t)n);
+    double beta0 = vnorm(b, n);
+    int its = 0, status = -1, have_d = 0;
+    double rel = 0.0;
+    if (beta0 == 0.0) { status = 0; goto done; }
+    double target = eta * beta0;
+    for (int rs = 0; rs < max_restarts; rs++) {
+        /* r = b - J x */
+        if (rs == 0) memcpy(w, b, sizeof(double) * (size_t)n);
+        else {
+            orc_jv(p, u, x, R_u, w);
+            for (long i = 0; i < n; i++) w[i] = b[i] - w[i];
+        }
+        if (kaug > 0 && have_d) {
+            double dn = vnorm(d, n);
+            if (dn > 0.0) {
+                for (int l = (na < kaug ? na : kaug - 1); l > 0; l--) {  /* shift older ones */
+                    memcpy(Z + (size_t)l * n, Z + (size_t)(l - 1) * n, sizeof(double) * (size_t)n);
+                    memcpy(AZ + (size_t)l * n, AZ + (size_t)(l - 1) * n, sizeof(double) * (size_t)n);
+                }
+                for (long i = 0; i < n; i++) {
+                    Z[i] = d[i] / dn;
+                    AZ[i] = (rprev[i] - w[i]) / dn;
+                }
+                if (na < kaug) na++;
+            }
+        }
+        double beta = vnorm(w, n);
+        rel = beta / beta0;
+        if (beta <= target) { status = 0; break; }
+        memcpy(rprev, w, sizeof(double) * (size_t)n);
+        int mk = m - na;  /* Krylov columns of this cycle */
+        for (long i = 0; i < n; i++) V[i] = w[i] / beta;
+        memset(g, 0, sizeof(double) * ((size_t)m + 1));
+        memset(H, 0, sizeof(double) * (size_t)(m + 1) * m);
+        g[0] = beta;
+        int k = 0, conv = 0;
+        for (int j = 0; j < m; j++) {
+            if (j < mk) {
+                apply_pc(p, pc, V + (size_t)j * n, z);
+                orc_jv(p, u, z, R_u, w);
+            } else {
+                memcpy(w, AZ + (size_t)(j - mk) * n, sizeof(double) * (size_t)n);
+            }
+            for (int pass = 0; pass < 2; pass++) {
+                for (int i = 0; i <= j; i++) h[i] = vdot(V + (size_t)i * n, w, n);
+                for (int i = 0; i <= j; i++) {
+                    for (long q = 0; q < n; q++) w[q] -= h[i] * V[(size_t)i * n + q];
+                    H[i * m + j] += h[i];
+                }
+            }
+            double hn = vnorm(w, n);
+            H[(j + 1) * m + j] = hn;
+            if (hn > 0.0)
+                for (long q = 0; q < n; q++) V[(size_t)(j + 1) * n + q] = w[q] / hn;
+            for (int i = 0; i < j; i++) {
+                double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+                H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+                H[i * m + j] = t;
+            }
+            double a = H[j * m + j], bb = H[(j + 1) * m + j];
+            double r = hypot(a, bb);
+            cs[j] = a / r; sn[j] = bb / r;
+            H[j * m + j] = r; H[(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            its++;
+            k = j + 1;
+            rel = fabs(g[j + 1]) / beta0;
+            if (fabs(g[j + 1]) <= target || hn == 0.0) { conv = 1; break; }
+        }
+        for (int i = k - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int q = i + 1; q < k; q++) s -= H[i * m + q] * y[q];
+            y[i] = s / H[i * m + i];
+        }
+        /* d = P^-1 (sum over the Krylov columns) + sum over the stored corrections */
+        memset(w, 0, sizeof(double) * (size_t)n);
+        for (int i = 0; i < k && i < mk; i++)
+            for (long q = 0; q < n; q++) w[q] += y[i] * V[(size_t)i * n + q];
+        apply_pc(p, pc, w, d);
+        for (int l = 0; mk + l < k; l++)
+            for (long q = 0; q < n; q++) d[q] += y[mk + l] * Z[(size_t)l * n + q];
+        have_d = 1;
+        for (long q = 0; q < n; q++) x[q] += d[q];
+        if (conv) { status = 0; break; }
+    }
+done:
+    if (its_out) *its_out = its;
+    if (relres_out) *relres_out = rel;
+    free(V); free(H); free(cs); free(sn); free(g); free(y); free(h); free(w); free(z); free(d); free(rprev);
+    free(Z); free(AZ);
+    return status;
+}
+
 /* ------------------------------------------------------------------ Eq. NewtonRaphson, Sec. 3.3
  * J du = -R; u += s du with a backtracking line search.  Reading (the line search is not
  * specified): s = 1, 1/2, 1/4, ... (at most 10 halvings), accepted when
@@ -1098,6 +1226,13 @@ done:
  * |R(u0)| taken at the start of each load step; stol = 0. */
 int orc_newton(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_newton,
                int m, double eta, int pc, orc_stats* st)
+{
+    return orc_newton_ex(p, u, n_load_steps, rtol, atol, max_newton, m, 0, eta, pc, st);
+}
+
+/* as orc_newton with loose GMRES keeping kaug corrections (kaug = 0: GMRES) */
+int orc_newton_ex(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_newton,
+                  int m, int kaug, double eta, int pc, orc_stats* st)
 {
     long n = 3L * p->nc;
     double* R = (double*)xcalloc((size_t)n, sizeof(double));
@@ -1122,7 +1257,8 @@ int orc_newton(orc_problem* p, double* u, int n_load_steps, double rtol, double 
             for (long i = 0; i < n; i++) b[i] = -R[i];
             int gits = 0;
             double grel = 0;
-            orc_gmres(p, u, R, b, du, m, eta, 100, pc, &gits, &grel);
+            if (kaug > 0) orc_lgmres(p, u, R, b, du, m, kaug, eta, 100, pc, &gits, &grel);
+            else orc_gmres(p, u, R, b, du, m, eta, 100, pc, &gits, &grel);
             st->gmres_its += gits;
             double s = 1.0;
             int accepted = 0;

@@ -80,9 +80,15 @@ void orc_mg_vcycle(const orc_problem* p, const double* v, double* z);
 /* right-preconditioned restarted GMRES(m) on J(u) x = b; x0 = 0 */
 int orc_gmres(const orc_problem* p, const double* u, const double* R_u, const double* b, double* x,
               int m, double eta, int max_restarts, int pc, int* its_out, double* relres_out);
+/* loose GMRES (LGMRES): restart m counts the Krylov columns plus up to kaug corrections of
+ * earlier cycles kept across restarts (Sec. 4.2: 30 and 2); kaug = 0 is GMRES(m) */
+int orc_lgmres(const orc_problem* p, const double* u, const double* R_u, const double* b, double* x,
+               int m, int kaug, double eta, int max_restarts, int pc, int* its_out, double* relres_out);
 /* Newton with backtracking line search over n_load_steps (lambda = k / n) */
 int orc_newton(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_newton,
                int m, double eta, int pc, orc_stats* stats);
+int orc_newton_ex(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_newton,
+                  int m, int kaug, double eta, int pc, orc_stats* stats);
 
 #ifdef __cplusplus
 }
