@@ -77,6 +77,11 @@ typedef struct jfnk_options {
     double mg_theta;        /* strength threshold of the aggregation                   (0.25)*/
     int mg_smooth_sweeps;   /* Jacobi sweeps before and after the coarse correction    (2)   */
     int mg_smoothed;        /* 1: smoothed-aggregation prolongation, 0: piecewise constant (1) */
+    int autotune;           /* 1: time the candidate launch shapes at set-up and keep the
+                               fastest (jfnk_get_tuning); 0: fixed defaults            (1)   */
+    int gmres_aug;          /* loose GMRES (Sec. 4.2): corrections of earlier cycles kept
+                               across restarts, 0..min(8, gmres_restart - 1); each cycle
+                               has gmres_restart columns in all; 0 = GMRES(m)          (2)   */
 } jfnk_options;
 
 typedef struct jfnk_stats {
@@ -91,6 +96,12 @@ typedef struct jfnk_stats {
     double hist[64];         /* |R| after each Newton iteration (first 64)                  */
     int n_hist;
     int reorth_its;          /* Arnoldi iterations that needed a second Gram-Schmidt pass   */
+    int jv_products;         /* Jacobian-vector products of the Krylov solves: Arnoldi
+                                iterations on new directions plus one per restart residual;
+                                the columns of kept corrections need none                  */
+    double arnoldi_cols;     /* sum over Arnoldi iterations of the basis vectors projected out
+                                (j + 1 at index j): the work of the Gram-Schmidt passes     */
+    double reorth_cols;      /* the same over the iterations that repeated the projection  */
 } jfnk_stats;
 
 typedef struct jfnk_ctx jfnk_ctx;
@@ -206,6 +217,18 @@ int jfnk_profile_reset(jfnk_ctx* ctx);
 int64_t jfnk_launch_count(const jfnk_ctx* ctx);
 /* Device bytes held by the context. */
 int64_t jfnk_device_bytes(const jfnk_ctx* ctx);
+/* Launch shapes of the hot-path kernels (no counterpart in the paper: a property of this
+ * implementation).  out[0..6): cells per block of the gradient pass {64,128,256}, faces per
+ * block of the face pass {128,256}, 1 if that pass stages its owner cells' gradients in
+ * shared memory, cells per block of the cell-sum pass {128,256,512}, rows per block of the
+ * fine-level multigrid kernels {128,256,512}, 1 if chosen by the autotuner at jfnk_setup
+ * (else the defaults 128, 256, 0, 256, 256).  n >= 6, else JFNK_EINVAL.  Results never depend
+ * on the shapes, only the timing. */
+int jfnk_get_tuning(jfnk_ctx* ctx, int32_t* out, int n);
+/* Sets the five shapes of jfnk_get_tuning (in[0..5), n >= 5), replacing the autotuner's
+ * choice until the next set-up; JFNK_EINVAL (nothing changed) for a value outside the
+ * candidate sets.  Both calls run a pending set-up first (its errors are returned). */
+int jfnk_set_tuning(jfnk_ctx* ctx, const int32_t* in, int n);
 /* Measured FP64 FMA throughput of `device` (TFLOP/s, an FMA counted as 2 flops): a full grid
  * of independent FMA chains timed with CUDA events (allocates and frees a small buffer).  The
  * residual and Arnoldi kernels are bound by this rate on GB300. */

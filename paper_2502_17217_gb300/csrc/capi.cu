@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -90,6 +91,7 @@ static void free_device(jfnk_ctx* c)
     c->dm = jfnk::DevMesh();
     c->u = c->Ru = c->w = c->R = c->z = c->x = c->bvec = c->wk = c->tmp = c->ext = nullptr;
     c->G = c->T = c->F = c->Fn = c->partials = c->V = nullptr;
+    c->Zaug = c->AZaug = c->rprev = c->dcorr = nullptr;
     c->pd = nullptr;
     c->gdev = nullptr;
     c->ch_beg = nullptr;
@@ -109,6 +111,11 @@ static bool valid_options(const jfnk_options* o, std::string& why)
     if (o->precision != JFNK_PREC_FP64 && o->precision != JFNK_PREC_MIXED) { why = "unknown precision"; return false; }
     if (!(o->jv_eps_scale > 0)) { why = "jv_eps_scale must be > 0"; return false; }
     if (o->mg_coarse_max < 1 || o->mg_coarse_max > 8192) { why = "mg_coarse_max must be in [1, 8192]"; return false; }
+    if (o->autotune != 0 && o->autotune != 1) { why = "autotune must be 0 or 1"; return false; }
+    if (o->gmres_aug < 0 || o->gmres_aug > 8 || o->gmres_aug >= o->gmres_restart) {
+        why = "gmres_aug must be in [0, min(8, gmres_restart - 1)]";
+        return false;
+    }
     return true;
 }
 
@@ -138,6 +145,8 @@ void jfnk_default_options(jfnk_options* o)
     o->mg_theta = 0.25;
     o->mg_smooth_sweeps = 2;
     o->mg_smoothed = 1;
+    o->autotune = 1;
+    o->gmres_aug = 2;
 }
 
 int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
@@ -164,13 +173,20 @@ int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
         delete c;
         return JFNK_ECUDA;
     }
-    if (cudaMallocHost(&c->gh, sizeof(jfnk::GlobalDev)) != cudaSuccess || cudaMallocHost(&c->scal_h, 16 * sizeof(double)) != cudaSuccess) {
+    if (cudaHostAlloc((void**)&c->gh, sizeof(jfnk::GlobalDev), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&c->gh_dev, c->gh, 0) != cudaSuccess ||
+        cudaMallocHost(&c->scal_h, 16 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         cudaStreamDestroy(c->stream);
         delete c;
         return JFNK_ENOMEM;
     }
     for (auto& e : c->it_ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    // programmatic dependent launch of the hot-path kernels (JFNK_PDL=1).  Off by default: with
+    // the iteration replayed as a CUDA graph it measured slower on GB300 (the kernels have no
+    // prologue to overlap, and the early-resident blocks only wait); same kernels and results
+    // either way
+    if (const char* v = getenv("JFNK_PDL")) c->pdl = atoi(v) != 0;
     c->cur = c->stream;
     *out = c;
     return JFNK_OK;
@@ -428,7 +444,7 @@ int jfnk_setup(jfnk_ctx* c)
     c->T = (double*)jfnk_dalloc(c, sizeof(double) * (c->law_mode != 0 ? 9 * (size_t)nc : 1));
     c->F = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)std::max(1, c->dm.nflux));
     c->Fn = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)std::max(1, c->dm.ni));
-    c->partials = (double*)jfnk_dalloc(c, sizeof(double) * ((size_t)c->n_chunks + 64) * (jfnk::kMaxRestart + 2));
+    c->partials = (double*)jfnk_dalloc(c, sizeof(double) * ((size_t)c->n_chunks * jfnk::kUpdSub + 64) * (jfnk::kMaxRestart + 2));
     c->V_is_float = c->opt.precision == JFNK_PREC_MIXED;
     c->V_ld = (v3 + 63) / 64 * 64;
     const size_t vbytes = (c->V_is_float ? sizeof(float) : sizeof(double)) * c->V_ld * (size_t)(c->opt.gmres_restart + 1);
@@ -436,6 +452,14 @@ int jfnk_setup(jfnk_ctx* c)
     c->pd = (jfnk::ProbDev*)jfnk_dalloc(c, sizeof(jfnk::ProbDev) * (size_t)P);
     c->gdev = (jfnk::GlobalDev*)jfnk_dalloc(c, sizeof(jfnk::GlobalDev));
     c->pmask = (int32_t*)jfnk_dalloc(c, sizeof(int32_t) * (size_t)P);
+    if (c->opt.gmres_aug > 0) {  // loose GMRES: kept corrections, their products, r and d of the last cycle
+        c->Zaug = (double*)jfnk_dalloc(c, sizeof(double) * v3 * (size_t)c->opt.gmres_aug);
+        c->AZaug = (double*)jfnk_dalloc(c, sizeof(double) * v3 * (size_t)c->opt.gmres_aug);
+        c->rprev = (double*)jfnk_dalloc(c, sizeof(double) * v3);
+        c->dcorr = (double*)jfnk_dalloc(c, sizeof(double) * v3);
+        if (!c->Zaug || !c->AZaug || !c->rprev || !c->dcorr)
+            return jfnk_fail(c, JFNK_ENOMEM, "device allocation of the loose-GMRES vectors failed");
+    }
     if (!c->G || !c->T || !c->F || !c->Fn || !c->partials || !c->V || !c->pd || !c->gdev || !c->pmask)
         return jfnk_fail(c, JFNK_ENOMEM, "device allocation of solver buffers failed");
     if (c->ph_count < (size_t)P) {
@@ -451,6 +475,11 @@ int jfnk_setup(jfnk_ctx* c)
     c->pmask_h_store.assign(P, 0);
     c->pmask_h = c->pmask_h_store.data();
     rc = jfnk::pc_setup(c);
+    if (rc) return rc;
+    // the uploads above are synchronous copies and memsets on the legacy stream: complete them
+    // before any kernel of the context's (non-blocking) stream reads the data
+    if (cudaDeviceSynchronize() != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "set-up");
+    rc = jfnk::autotune(c);
     if (rc) return rc;
     if (cudaDeviceSynchronize() != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "set-up");
     c->dirty = false;

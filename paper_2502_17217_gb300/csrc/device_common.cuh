@@ -9,6 +9,20 @@
 
 namespace jfnk {
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with the
+// programmatic-serialisation attribute may start while the kernel before it in the stream is
+// still draining; pdl_wait() blocks until that kernel has completed and its memory is
+// visible, so every kernel calls it before touching anything earlier work wrote.  Launched
+// without the attribute, the wait returns at once.  pdl_trigger() lets the next kernel's
+// blocks be scheduled as soon as every block of this grid has issued it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#define JF_PDL_ENTRY() \
+    do {                 \
+        jfnk::pdl_wait();    \
+        jfnk::pdl_trigger(); \
+    } while (0)
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll

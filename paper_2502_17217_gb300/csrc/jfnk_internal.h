@@ -97,7 +97,9 @@ struct DevMesh {
 // Chunks of the SoA vectors for per-problem (segmented) reductions: every chunk lies inside
 // one problem's range of one displacement component.
 constexpr int kChunk = 2048;
-constexpr int kChunkThreads = 128;   // kChunk / kChunkThreads = 16 elements per thread
+constexpr int kChunkThreads = 512;   // kChunk / kChunkThreads = 4 elements per thread
+constexpr int kUpdSub = 4;           // sub-blocks per chunk of the basis update / combination
+constexpr int kUpdE = kChunk / (kUpdSub * kChunkThreads);  // elements per thread there
 
 // Per-problem scalars of the GMRES cycle and the Newton step, resident on the device.
 struct ProbDev {
@@ -117,7 +119,9 @@ struct ProbDev {
     double res;       // |g_k| current residual estimate
     double step;      // line-search step s_p
     double nrm;       // output of plain per-problem norms
-    double pad2[7];
+    double n_cols;    // sum over Arnoldi iterations of the basis vectors projected out (j + 1)
+    double n_rcols;   // the same over the iterations that repeated the projection
+    double pad2[5];
     double h[kMaxRestart + 1];
     double H[(kMaxRestart + 1) * kMaxRestart];  // column-major: H[i + (m+1) j]
     double g[kMaxRestart + 1];
@@ -147,6 +151,17 @@ struct Profiler {
     int slot(const char* name);
 };
 
+}  // namespace jfnk
+
+namespace jfnk {
+// Launch shapes of the tunable kernels (chosen per mesh by the autotuner, autotune.cu):
+// cells per block of the gradient and cell-sum passes, faces per block of the face pass and
+// whether it stages its owner cells' gradients in shared memory, cells per block of the
+// fine-level multigrid kernels.  Results do not depend on them.
+struct Tuning {
+    int grad_bs = 128, flux_bs = 256, flux_stage = 0, finish_bs = 256, mg_bs = 256;
+    int tuned = 0;
+};
 }  // namespace jfnk
 
 // A problem copied into a batch: mesh, boundary data, material, body force.
@@ -195,6 +210,8 @@ struct jfnk_ctx {
     double* F = nullptr;                 // [3][nflux] face fluxes, owner-sorted
     double* Fn = nullptr;                // [3][ni] the same fluxes, neighbour-sorted
     double* partials = nullptr;          // reduction partials
+    double *Zaug = nullptr, *AZaug = nullptr;  // loose GMRES: kept corrections z_l and J z_l, [aug][3][nc]
+    double *rprev = nullptr, *dcorr = nullptr;  // residual at the start and correction of the last cycle
     double* V = nullptr;                 // Krylov basis (double or float storage)
     size_t V_ld = 0;                     // stride between basis vectors (elements)
     int V_is_float = 0;
@@ -209,7 +226,9 @@ struct jfnk_ctx {
     jfnk::ProbDev* pd = nullptr;         // device per-problem scalars [nprob]
     jfnk::ProbDev* ph = nullptr;         // pinned host mirror (header fields only are refreshed)
     jfnk::GlobalDev* gdev = nullptr;     // device global scalars
-    jfnk::GlobalDev* gh = nullptr;       // pinned host mirror
+    jfnk::GlobalDev* gh = nullptr;       // pinned, mapped host mirror
+    jfnk::GlobalDev* gh_dev = nullptr;   // device address of the mirror (kernels store to it)
+    int pdl = 0;                         // launch hot-path kernels with programmatic serialisation
     size_t ph_count = 0;                 // problems the pinned mirror can hold
     cudaGraphExec_t it_graph = nullptr;  // one captured Arnoldi iteration (replayed for every j)
     cudaEvent_t it_ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -224,6 +243,7 @@ struct jfnk_ctx {
     int64_t dev_bytes = 0;
     std::vector<void*> allocs;
     jfnk::Profiler prof;
+    jfnk::Tuning tune;
 };
 
 // ------------------------------------------------------------------ helpers (capi.cu)
@@ -236,6 +256,26 @@ void* jfnk_dalloc(jfnk_ctx* c, size_t bytes);   // tracked cudaMalloc, zeroed; n
         cudaError_t e_ = (call);                                   \
         if (e_ != cudaSuccess) return jfnk_cuda_fail(ctx, e_, #call); \
     } while (0)
+
+// Launches kernel k on the call's stream.  With ctx->pdl set, the launch carries the
+// programmatic-stream-serialisation attribute: its blocks may be scheduled while the previous
+// kernel drains, and the kernel itself (JF_PDL_ENTRY) waits for that kernel's results before
+// reading anything.  Inside a captured graph this becomes a programmatic edge.
+template <typename... KArgs, typename... Args>
+inline cudaError_t jfnk_launch(jfnk_ctx* c, void (*k)(KArgs...), dim3 grid, dim3 block, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c->cur;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = c->pdl ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
 
 #define JF_LAUNCHED(ctx)                                           \
     do {                                                           \
@@ -274,11 +314,17 @@ int pnorm(jfnk_ctx* c, const double* x, int mode, bool gated);
 int perturb(jfnk_ctx* c, const double* u, const double* z, double* w, bool gated);
 int cycle_init(jfnk_ctx* c, const double* r);
 int arnoldi_orthogonalise(jfnk_ctx* c, double* w);
-int cycle_solution(jfnk_ctx* c, double* out);
+int cycle_solution(jfnk_ctx* c, double* out, int ncols);  // out = sum_{i < min(k_p, ncols)} y_i V_i
+// loose GMRES (linalg.cu): kept correction l (0 = newest) of `na`, slots in a ring
+int aug_store(jfnk_ctx* c, int slot, const double* r);     // slot <- dcorr / |dcorr_p|, (rprev - r) / |dcorr_p|
+int aug_load(jfnk_ctx* c, int slot, double* w);            // w <- J z of slot (gated on `all done`)
+int aug_add(jfnk_ctx* c, const int* slots, int na, int ncols, const double* z, double* out);
 int line_trial(jfnk_ctx* c, const double* u, const double* x, double* w);       // w = u + s_p x (active)
 int accept_masked(jfnk_ctx* c, const int32_t* mask_dev, double* u, const double* w, double* Ru, const double* R);
 // precond.cu
 int pc_setup(jfnk_ctx* c);
+int autotune(jfnk_ctx* c);               // launch shapes for this mesh (autotune.cu)
+bool tuning_valid(const Tuning& t);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);
 int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate);

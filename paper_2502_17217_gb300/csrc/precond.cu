@@ -25,6 +25,7 @@ template <typename TV, typename TP>
 __global__ void k_bjacobi(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
                           const TP* __restrict__ dinv, double* __restrict__ z)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
@@ -38,6 +39,7 @@ template <typename TV>
 __global__ void k_copy_vec(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
                            double* __restrict__ z)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
@@ -49,6 +51,7 @@ __global__ void k_copy_vec(const int* gate, int nc, const TV* __restrict__ base,
 template <typename TV>
 __global__ void k_copy_to_double(const int* gate, size_t n, const TV* __restrict__ v, double* __restrict__ z)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
         z[e] = to_f64(v[e]);
@@ -111,6 +114,7 @@ template <typename TV, typename T>
 __global__ void k_mg_pre0(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
                           const T* __restrict__ dinv, T omega, T* __restrict__ b, T* __restrict__ x)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
@@ -124,10 +128,58 @@ __global__ void k_mg_pre0(const int* gate, int nc, const TV* __restrict__ base, 
     }
 }
 
+// a product rounded on its own (never fused into a following add), as when it is stored
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// level 0 entry fused with the first Jacobi sweep: b = -v, x0 = omega D^-1 b (formed where it
+// is needed, also at the neighbours), x1 = x0 + omega D^-1 (b - A x0).  Same arithmetic, in the
+// same order, as k_mg_pre0 followed by k_mg_jacobi.
+template <typename TV, typename T>
+__global__ void k_mg_pre0_jacobi(const int* gate, LevelOp<T> op, const TV* __restrict__ base, size_t ld,
+                                 const int* __restrict__ jidx, T omega, T* __restrict__ b, T* __restrict__ xo)
+{
+    JF_PDL_ENTRY();
+    if (gate && *gate) return;
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nc = op.n;
+    if (P >= nc) return;
+    const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
+    const T dP = omega * op.dinv[P];
+    T bb[3], x0[3], ax[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        bb[k] = -(T)v[(size_t)k * nc + P];
+        x0[k] = mul_rn(dP, bb[k]);
+    }
+    const T a = op.adiag[P];
+#pragma unroll
+    for (int k = 0; k < 3; k++) ax[k] = a * x0[k];
+    for (int f = op.p0[P]; f < op.p0[P + 1]; f++) {
+        const int N = op.nei[f];
+        const T cf = op.vals[f], dN = omega * op.dinv[N];
+#pragma unroll
+        for (int k = 0; k < 3; k++) ax[k] -= cf * mul_rn(dN, -(T)v[(size_t)k * nc + N]);
+    }
+    for (int q = op.p1[P]; q < op.p1[P + 1]; q++) {
+        const int f = op.p2[q];
+        const int N = op.own[f];
+        const T cf = op.vals[f], dN = omega * op.dinv[N];
+#pragma unroll
+        for (int k = 0; k < 3; k++) ax[k] -= cf * mul_rn(dN, -(T)v[(size_t)k * nc + N]);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        b[(size_t)k * nc + P] = bb[k];
+        xo[(size_t)k * nc + P] = x0[k] + dP * (bb[k] - ax[k]);
+    }
+}
+
 template <typename T>
 __global__ void k_mg_pre(const int* gate, int n, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
                          T* __restrict__ x)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -141,6 +193,7 @@ template <typename T>
 __global__ void k_mg_jacobi(const int* gate, LevelOp<T> op, T omega, const T* __restrict__ b, const T* __restrict__ x,
                             T* __restrict__ xo, double* __restrict__ zd)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = op.n;
@@ -161,6 +214,7 @@ template <typename T>
 __global__ void k_mg_resid(const int* gate, LevelOp<T> op, const T* __restrict__ b, const T* __restrict__ x,
                            T* __restrict__ r)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = op.n;
@@ -176,6 +230,7 @@ template <typename T>
 __global__ void k_mg_spmv(const int* gate, int nrow, int nx, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                           const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrow) return;
@@ -193,6 +248,7 @@ template <typename T>
 __global__ void k_mg_spmv_warp(const int* gate, int nrow, int nx, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= nrow) return;
@@ -215,20 +271,30 @@ __global__ void k_mg_spmv_warp(const int* gate, int nrow, int nx, const int32_t*
 }
 
 // Jacobi sweep or residual on a coarse (CSR) level, one warp per row:
-// mode 0: xo = x + omega D^-1 (b - A x);  mode 1: xo = b - A x
+// mode 0: xo = x + omega D^-1 (b - A x);  mode 1: xo = b - A x;
+// mode 2: the first sweep from x = omega D^-1 b, which is formed where it is needed (x unused)
 template <typename T>
 __global__ void k_mg_csr_warp(const int* gate, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                               const T* __restrict__ val, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
                               const T* __restrict__ x, T* __restrict__ xo, int mode)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (i >= n) return;
     T s0 = 0, s1 = 0, s2 = 0;
-    for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-        const int j = col[q];
-        const T a = val[q];
-        s0 += a * x[j]; s1 += a * x[n + j]; s2 += a * x[2 * (size_t)n + j];
+    if (mode == 2) {
+        for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            const int j = col[q];
+            const T a = val[q], dj = omega * dinv[j];
+            s0 += a * mul_rn(dj, b[j]); s1 += a * mul_rn(dj, b[n + j]); s2 += a * mul_rn(dj, b[2 * (size_t)n + j]);
+        }
+    } else {
+        for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            const int j = col[q];
+            const T a = val[q];
+            s0 += a * x[j]; s1 += a * x[n + j]; s2 += a * x[2 * (size_t)n + j];
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -239,7 +305,11 @@ __global__ void k_mg_csr_warp(const int* gate, int n, const int32_t* __restrict_
     if (lane == 0) {
         const T r0 = b[i] - s0, r1 = b[n + i] - s1, r2 = b[2 * (size_t)n + i] - s2;
         if (mode == 1) { xo[i] = r0; xo[n + i] = r1; xo[2 * (size_t)n + i] = r2; }
-        else {
+        else if (mode == 2) {
+            const T d = omega * dinv[i];
+            xo[i] = mul_rn(d, b[i]) + d * r0; xo[n + i] = mul_rn(d, b[n + i]) + d * r1;
+            xo[2 * (size_t)n + i] = mul_rn(d, b[2 * (size_t)n + i]) + d * r2;
+        } else {
             const T d = omega * dinv[i];
             xo[i] = x[i] + d * r0; xo[n + i] = x[n + i] + d * r1; xo[2 * (size_t)n + i] = x[2 * (size_t)n + i] + d * r2;
         }
@@ -250,6 +320,7 @@ __global__ void k_mg_csr_warp(const int* gate, int n, const int32_t* __restrict_
 template <typename T>
 __global__ void k_mg_coarse(const int* gate, int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= n) return;
@@ -494,13 +565,14 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     const T omega = (T)(2.0 / 3.0);
     const int nl = (int)M.L.size();
     const int sweeps = std::max(1, c->opt.mg_smooth_sweeps);
+    const int bs = c->tune.mg_bs;  // rows per block of the thread-per-row kernels
     if (nl == 1) {
         auto& D = M.L[0];
-        k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, vbase, ld, jidx, D.dinv, (T)0, D.b, D.x2);
+        jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, vbase, ld, jidx, D.dinv, (T)0, D.b, D.x2);
         JF_LAUNCHED(c);
-        k_mg_coarse<T><<<nb(32L * D.n, 256), 256, 0, s>>>(gate, D.n, M.Ainv, D.b, D.x);
+        jfnk_launch(c, k_mg_coarse<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, M.Ainv, D.b, D.x);
         JF_LAUNCHED(c);
-        k_copy_to_double<T><<<nb(3L * D.n, 256), 256, 0, s>>>(gate, 3 * (size_t)D.n, D.x, z);
+        jfnk_launch(c, k_copy_to_double<T>, dim3(nb(3L * D.n, 256)), dim3(256), gate, 3 * (size_t)D.n, D.x, z);
         JF_LAUNCHED(c);
         return JFNK_OK;
     }
@@ -509,31 +581,38 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         auto& D = M.L[l];
         const LevelOp<T> op = level_op<T>(c, M, l);
         jfnk_prof_begin(c, s_sm);
-        if (l == 0) k_mg_pre0<TV, T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, vbase, ld, jidx, D.dinv, omega, D.b, D.x);
-        else k_mg_pre<T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, D.dinv, omega, D.b, D.x);
+        // the entry and the first sweep are one kernel when there are two or more sweeps
+        if (sweeps >= 2) {
+            if (l == 0) jfnk_launch(c, k_mg_pre0_jacobi<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, vbase, ld, jidx, omega, D.b, D.x);
+            else jfnk_launch(c, k_mg_csr_warp<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col,
+                             (const T*)D.val, (const T*)D.dinv, omega, (const T*)D.b, (const T*)nullptr, D.x, 2);
+        } else {
+            if (l == 0) jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, vbase, ld, jidx, D.dinv, omega, D.b, D.x);
+            else jfnk_launch(c, k_mg_pre<T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, D.dinv, omega, D.b, D.x);
+        }
         JF_LAUNCHED(c);
-        for (int sw = 1; sw < sweeps; sw++) {
-            if (l == 0) k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, nullptr);
-            else k_mg_csr_warp<T><<<nb(32L * D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.x2, 0);
+        for (int sw = (sweeps >= 2 ? 2 : 1); sw < sweeps; sw++) {
+            if (l == 0) jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, D.b, D.x, D.x2, nullptr);
+            else jfnk_launch(c, k_mg_csr_warp<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.x2, 0);
             JF_LAUNCHED(c);
             std::swap(D.x, D.x2);
         }
         jfnk_prof_end(c, s_sm);
         jfnk_prof_begin(c, s_re);
-        if (l == 0) k_mg_resid<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, D.b, D.x, D.r);
-        else k_mg_csr_warp<T><<<nb(32L * D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.r, 1);
+        if (l == 0) jfnk_launch(c, k_mg_resid<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, D.b, D.x, D.r);
+        else jfnk_launch(c, k_mg_csr_warp<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.r, 1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_re);
         auto& Cn = M.L[l + 1];
         jfnk_prof_begin(c, s_rs);
-        k_mg_spmv_warp<T><<<nb(32L * D.nco, 256), 256, 0, s>>>(gate, D.nco, D.n, D.rrp, D.rcol, D.rval, D.r, Cn.b, 0);
+        jfnk_launch(c, k_mg_spmv_warp<T>, dim3(nb(32L * D.nco, 256)), dim3(256), gate, D.nco, D.n, D.rrp, D.rcol, D.rval, D.r, Cn.b, 0);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_rs);
     }
     {
         auto& Dc = M.L[nl - 1];
         jfnk_prof_begin(c, s_co);
-        k_mg_coarse<T><<<nb(32L * Dc.n, 256), 256, 0, s>>>(gate, Dc.n, M.Ainv, Dc.b, Dc.x);
+        jfnk_launch(c, k_mg_coarse<T>, dim3(nb(32L * Dc.n, 256)), dim3(256), gate, Dc.n, M.Ainv, Dc.b, Dc.x);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_co);
     }
@@ -543,14 +622,14 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         auto& Cn = M.L[l + 1];
         const LevelOp<T> op = level_op<T>(c, M, l);
         jfnk_prof_begin(c, s_pr);
-        k_mg_spmv<T><<<nb(D.n, 256), 256, 0, s>>>(gate, D.n, Cn.n, D.prp, D.pcol, D.pval, Cn.x, D.x, 1);
+        jfnk_launch(c, k_mg_spmv<T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, Cn.n, D.prp, D.pcol, D.pval, Cn.x, D.x, 1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_pr);
         jfnk_prof_begin(c, s_sm);
         for (int sw = 0; sw < sweeps; sw++) {
             const bool last = (l == 0 && sw == sweeps - 1);
-            if (l == 0) k_mg_jacobi<T><<<nb(D.n, 256), 256, 0, s>>>(gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
-            else k_mg_csr_warp<T><<<nb(32L * D.n, 256), 256, 0, s>>>(gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.x2, 0);
+            if (l == 0) jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
+            else jfnk_launch(c, k_mg_csr_warp<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.x2, 0);
             JF_LAUNCHED(c);
             if (!last) std::swap(D.x, D.x2);
         }
@@ -569,11 +648,11 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
     jfnk_prof_begin(c, sl);
     if (pc == JFNK_PC_BJACOBI) {
         if (v_is_float) {
-            if (fp32) k_bjacobi<float, float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)vbase, ld, jidx, c->dm.jt_dinv_f, z);
-            else k_bjacobi<float, double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)vbase, ld, jidx, c->dm.jt_dinv, z);
+            if (fp32) jfnk_launch(c, k_bjacobi<float, float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, c->dm.jt_dinv_f, z);
+            else jfnk_launch(c, k_bjacobi<float, double>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, c->dm.jt_dinv, z);
         } else {
-            if (fp32) k_bjacobi<double, float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)vbase, ld, jidx, c->dm.jt_dinv_f, z);
-            else k_bjacobi<double, double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)vbase, ld, jidx, c->dm.jt_dinv, z);
+            if (fp32) jfnk_launch(c, k_bjacobi<double, float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const double*)vbase, ld, jidx, c->dm.jt_dinv_f, z);
+            else jfnk_launch(c, k_bjacobi<double, double>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const double*)vbase, ld, jidx, c->dm.jt_dinv, z);
         }
         JF_LAUNCHED(c);
     } else if (pc == JFNK_PC_MG) {
@@ -586,8 +665,8 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
                              : vcycle<double, double>(c, S.d, (const double*)vbase, ld, jidx, z, gate);
         if (rc) return rc;
     } else {
-        if (v_is_float) k_copy_vec<float><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const float*)vbase, ld, jidx, z);
-        else k_copy_vec<double><<<nb(nc, 256), 256, 0, s>>>(gate, nc, (const double*)vbase, ld, jidx, z);
+        if (v_is_float) jfnk_launch(c, k_copy_vec<float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, z);
+        else jfnk_launch(c, k_copy_vec<double>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const double*)vbase, ld, jidx, z);
         JF_LAUNCHED(c);
     }
     jfnk_prof_end(c, sl);

@@ -17,13 +17,14 @@
 
 namespace jfnk {
 
-template <int LAW>
-__global__ void __launch_bounds__(128) k_grad(const int* __restrict__ gate, int nc, int dim, const int32_t* __restrict__ sell_off,
+template <int LAW, int BS>
+__global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int nc, int dim, const int32_t* __restrict__ sell_off,
                                               const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
                                               const double* __restrict__ sell_l, int n_slots,
                                               const double* __restrict__ u, double* __restrict__ G,
                                               double* __restrict__ T, MatDev mat, const int32_t* __restrict__ cell_prob)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
@@ -91,27 +92,51 @@ __global__ void __launch_bounds__(128) k_grad(const int* __restrict__ gate, int 
     (void)dim;
 }
 
-template <int LAW>
-__global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int ni, int nflux, int nc, const int32_t* __restrict__ own,
-                                              const int32_t* __restrict__ nei, const double* __restrict__ coef,
-                                              const double* __restrict__ u, const double* __restrict__ G,
-                                              const double* __restrict__ T, const double* __restrict__ bval,
-                                              const double* __restrict__ load_dev, const int32_t* __restrict__ fn_pos,
-                                              MatDev mat, const int32_t* __restrict__ cell_prob,
-                                              double* __restrict__ F, double* __restrict__ Fn)
+// STAGE = 1: the block first copies the gradients (and, neo-Hookean, the traction operators)
+// of the cell window [own[f0], own[f0] + BS) into shared memory, with coalesced loads;
+// faces are owner-sorted, so the owners of the block's faces lie in that window unless a
+// block spans the internal/boundary split or cells without faces, and those read global
+// memory.  Same arithmetic either way.
+template <int LAW, int BS, int STAGE>
+__global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int ni, int nflux, int nc, const int32_t* __restrict__ own,
+                                             const int32_t* __restrict__ nei, const double* __restrict__ coef,
+                                             const double* __restrict__ u, const double* __restrict__ G,
+                                             const double* __restrict__ T, const double* __restrict__ bval,
+                                             const double* __restrict__ load_dev, const int32_t* __restrict__ fn_pos,
+                                             MatDev mat, const int32_t* __restrict__ cell_prob,
+                                             double* __restrict__ F, double* __restrict__ Fn)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr bool kT = (LAW != JFNK_LAW_LINEAR);
+    __shared__ double sg[STAGE ? 9 : 1][STAGE ? BS : 1];
+    __shared__ double st[(STAGE && kT) ? 9 : 1][(STAGE && kT) ? BS : 1];
+    const int f0 = blockIdx.x * BS;
+    const int f = f0 + threadIdx.x;
+    int Pw = 0;
+    if (STAGE) {
+        Pw = own[min(f0, nflux - 1)];
+        const int cnt = min(BS, nc - Pw);
+#pragma unroll
+        for (int q = 0; q < 9; q++)
+            for (int k = threadIdx.x; k < cnt; k += BS) {
+                sg[q][k] = G[(size_t)q * nc + Pw + k];
+                if (kT) st[q][k] = T[(size_t)q * nc + Pw + k];
+            }
+        __syncthreads();
+    }
     if (f >= nflux) return;
     const double load = *load_dev;
     const int P = own[f];
     const bool internal = f < ni;
     const int N = internal ? nei[f] : P;
     const double w = coef[f], kc = coef[nflux + f];
+    const int kp = P - Pw;
+    const bool staged = STAGE && kp >= 0 && kp < BS;
     double gf[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        const double gp = G[(size_t)q * nc + P];
+        const double gp = staged ? sg[q][kp] : G[(size_t)q * nc + P];
         if (internal) {
             const double gn = G[(size_t)q * nc + N];
             gf[q] = fma(w, gp - gn, gn);
@@ -152,7 +177,7 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
         double tf[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) {
-            const double tp = T[(size_t)q * nc + P];
+            const double tp = (kT && staged) ? st[q][kp] : T[(size_t)q * nc + P];
             if (internal) {
                 const double tn = T[(size_t)q * nc + N];
                 tf[q] = fma(w, tp - tn, tn);
@@ -183,7 +208,7 @@ __global__ void __launch_bounds__(256) k_flux(const int* __restrict__ gate, int 
 
 // mode 0: out = R;  mode 1: out = (R - Ru) / eps_p with eps_p the Jv step of the cell's
 // problem (0 -> out = 0)
-__global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int ni, int dim, const int32_t* __restrict__ fo_ptr,
+__global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int dim, const int32_t* __restrict__ fo_ptr,
                                                 const int32_t* __restrict__ fn_ptr, const double* __restrict__ Fn,
                                                 const int32_t* __restrict__ fd_ptr, const double* __restrict__ F,
                                                 const double* __restrict__ b0, const double* __restrict__ load_dev, int mode,
@@ -191,6 +216,7 @@ __global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int ni, int d
                                                 const int32_t* __restrict__ cell_prob, const int* __restrict__ gate,
                                                 double* __restrict__ out)
 {
+    JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
@@ -222,12 +248,17 @@ __global__ void __launch_bounds__(256) k_finish(int nc, int nflux, int ni, int d
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
-// Makes the device copy of the load factor equal to c->load (rare: once per load step).
+// Makes the device copy of the load factor equal to c->load (rare: once per load step).  The
+// copy is ordered in the call's stream, from pinned memory, so the kernels enqueued after it
+// read the new factor.  (A plain cudaMemcpy from pageable memory may return before its DMA
+// lands, and kernels on a non-blocking stream do not wait for the legacy stream: under load
+// from other contexts they read the old factor.)
 int sync_load(jfnk_ctx* c)
 {
     if (c->load_on_device == c->load) return JFNK_OK;
-    JF_CUDA(c, cudaStreamSynchronize(c->cur));
-    JF_CUDA(c, cudaMemcpy(&c->gdev->load, &c->load, sizeof(double), cudaMemcpyHostToDevice));
+    JF_CUDA(c, cudaStreamSynchronize(c->cur));  // an earlier copy from the pinned slot is done
+    c->scal_h[0] = c->load;
+    JF_CUDA(c, cudaMemcpyAsync(&c->gdev->load, c->scal_h, sizeof(double), cudaMemcpyHostToDevice, c->cur));
     c->load_on_device = c->load;
     return JFNK_OK;
 }
@@ -246,29 +277,49 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     int sl[3];
     for (int q = 0; q < 3; q++) sl[q] = c->prof.enabled ? c->prof.slot(kNames[q]) : -1;
     jfnk_prof_begin(c, sl[0]);
-#define JF_GRAD(LAW_)                                                                                                  \
-    k_grad<LAW_><<<nblk(m.nc, 128), 128, 0, s>>>(gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr, m.sell_l,        \
-                                                 m.n_slots, u_int, G, T, c->mat, c->cell_prob)
+    const Tuning& tu = c->tune;
+#define JF_GRAD_BS(LAW_, BS_)                                                                                   \
+    jfnk_launch(c, k_grad<LAW_, BS_>, dim3(nblk(m.nc, BS_)), dim3(BS_), gate, m.nc, m.dim, m.sell_off, m.sell_w, \
+                m.sell_nbr, m.sell_l, m.n_slots, u_int, G, T, c->mat, (const int32_t*)c->cell_prob)
+#define JF_GRAD(LAW_)                                     \
+    do {                                                  \
+        if (tu.grad_bs == 64) JF_GRAD_BS(LAW_, 64);       \
+        else if (tu.grad_bs == 256) JF_GRAD_BS(LAW_, 256); \
+        else JF_GRAD_BS(LAW_, 128);                       \
+    } while (0)
     if (c->law_mode == 0) JF_GRAD(JFNK_LAW_LINEAR);
     else if (c->law_mode == 1) JF_GRAD(JFNK_LAW_NEOHOOKEAN);
     else JF_GRAD(2);
 #undef JF_GRAD
+#undef JF_GRAD_BS
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[0]);
     if (m.nflux > 0) {
         jfnk_prof_begin(c, sl[1]);
-#define JF_FLUX(LAW_)                                                                                                  \
-    k_flux<LAW_><<<nblk(m.nflux, 256), 256, 0, s>>>(gate, m.ni, m.nflux, m.nc, m.own, m.nei, m.coef, u_int, G, T,     \
-                                                    m.bval, &c->gdev->load, m.fn_pos, c->mat, c->cell_prob, F, Fn)
+#define JF_FLUX_BS(LAW_, BS_, ST_)                                                                                      \
+    jfnk_launch(c, k_flux<LAW_, BS_, ST_>, dim3(nblk(m.nflux, BS_)), dim3(BS_), gate, m.ni, m.nflux, m.nc, m.own, m.nei, \
+                m.coef, u_int, (const double*)G, (const double*)T, m.bval, (const double*)&c->gdev->load, m.fn_pos,   \
+                c->mat, (const int32_t*)c->cell_prob, F, Fn)
+#define JF_FLUX(LAW_)                                                        \
+    do {                                                                     \
+        if (tu.flux_bs == 128) {                                             \
+            if (tu.flux_stage) JF_FLUX_BS(LAW_, 128, 1);                     \
+            else JF_FLUX_BS(LAW_, 128, 0);                                   \
+        } else {                                                             \
+            if (tu.flux_stage) JF_FLUX_BS(LAW_, 256, 1);                     \
+            else JF_FLUX_BS(LAW_, 256, 0);                                   \
+        }                                                                    \
+    } while (0)
         if (c->law_mode == 0) JF_FLUX(JFNK_LAW_LINEAR);
         else if (c->law_mode == 1) JF_FLUX(JFNK_LAW_NEOHOOKEAN);
         else JF_FLUX(2);
 #undef JF_FLUX
+#undef JF_FLUX_BS
         JF_LAUNCHED(c);
         jfnk_prof_end(c, sl[1]);
     }
     jfnk_prof_begin(c, sl[2]);
-    k_finish<<<nblk(m.nc, 256), 256, 0, s>>>(m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr, F, m.b0,
+    jfnk_launch(c, k_finish, dim3(nblk(m.nc, tu.finish_bs)), dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr, F, m.b0,
                                             &c->gdev->load, mode, c->Ru, c->pd, c->cell_prob, gate, out);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);

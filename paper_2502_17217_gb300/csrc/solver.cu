@@ -93,12 +93,29 @@ static int capture_iteration(jfnk_ctx* c)
     return JFNK_OK;
 }
 
-// GMRES for every problem whose ph[p].active is set on entry (uploaded here).  its[p] gains
-// the Arnoldi iterations of problem p; conv[p] tells whether its tolerance was met.
-int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, std::vector<int>& conv)
+// One Arnoldi iteration on a kept correction (loose GMRES): its image J z_l is stored, so the
+// column needs no preconditioner and no product, only the orthogonalisation.
+static int enqueue_aug_iteration(jfnk_ctx* c, int slot)
+{
+    int rc;
+    if ((rc = aug_load(c, slot, c->wk))) return rc;
+    if ((rc = arnoldi_orthogonalise(c, c->wk))) return rc;
+    return JFNK_OK;
+}
+
+// Loose / restarted GMRES for every problem whose ph[p].active is set on entry (uploaded
+// here).  its[p] gains the Arnoldi iterations of problem p, jvs[p] its Jacobian products;
+// conv[p] tells whether its tolerance was met.
+//   cycle: m columns, of which the last na (0 <= na <= options.gmres_aug) are the kept
+//   corrections of earlier cycles (newest first), the first m - na Krylov directions;
+//   correction d = P^-1 (V y over the Krylov columns) + sum_l y_l z_l;  x += d;
+//   restart: r = b - J x, then d is kept as a correction with J d = r_prev - r.
+int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, std::vector<int>& jvs,
+                std::vector<int>& conv)
 {
     const size_t n = 3 * (size_t)c->dm.nc;
     const int m = c->opt.gmres_restart, P = c->nprob;
+    const int kaug = c->opt.gmres_aug;
     int rc;
     JF_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->cur));
     if ((rc = pnorm(c, b, 0, false))) return rc;
@@ -119,6 +136,8 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
     if ((rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
     const bool graphs = c->use_graphs && !c->prof.enabled;
     if (graphs && (rc = capture_iteration(c))) return rc;
+    int na = 0, head = 0;  // kept corrections; ring slot of the next one
+    bool have_d = false;
     for (int rs = 0; rs < c->opt.gmres_max_restarts; rs++) {
         int n_act = 0;
         for (int p = 0; p < P; p++) n_act += act[p];
@@ -129,7 +148,19 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
         } else {
             if ((rc = jv_direction(c, x, c->tmp))) return rc;
             if ((rc = axpby(c, n, 1.0, b, -1.0, c->tmp, c->wk))) return rc;
+            for (int p = 0; p < P; p++) jvs[p] += act[p];
         }
+        if (kaug > 0) {
+            if (have_d) {
+                if ((rc = aug_store(c, head, c->wk))) return rc;
+                head = (head + 1) % kaug;
+                na = std::min(na + 1, kaug);
+            }
+            JF_CUDA(c, cudaMemcpyAsync(c->rprev, c->wk, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cur));
+        }
+        int slots[8];
+        for (int l = 0; l < na; l++) slots[l] = ((head - 1 - l) % kaug + kaug) % kaug;  // newest first
+        const int mk = m - na;
         if ((rc = cycle_init(c, c->wk))) return rc;
         JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
         JF_CUDA(c, cudaStreamSynchronize(c->cur));
@@ -140,7 +171,9 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
                     JF_CUDA(c, cudaEventSynchronize(c->it_ev[(j - 2) & 3]));
                     if (((volatile GlobalDev*)c->gh)->all_done) break;
                 }
-                if (graphs) {
+                if (j >= mk) {
+                    if ((rc = enqueue_aug_iteration(c, slots[j - mk]))) return rc;
+                } else if (graphs) {
                     JF_CUDA(c, cudaGraphLaunch(c->it_graph, c->cur));
                     c->launches += c->graph_kernels;
                 } else if ((rc = enqueue_iteration(c))) {
@@ -148,9 +181,15 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
                 }
                 JF_CUDA(c, cudaEventRecord(c->it_ev[j & 3], c->cur));
             }
-            if ((rc = cycle_solution(c, c->tmp))) return rc;
+            if ((rc = cycle_solution(c, c->tmp, mk))) return rc;
             if ((rc = pc_apply_any(c, c->opt.pc, c->tmp, 0, c->z, nullptr))) return rc;
-            if ((rc = axpby(c, n, 1.0, x, 1.0, c->z, x))) return rc;
+            if (kaug > 0) {
+                if ((rc = aug_add(c, slots, na, mk, c->z, c->dcorr))) return rc;
+                if ((rc = axpby(c, n, 1.0, x, 1.0, c->dcorr, x))) return rc;
+                have_d = true;
+            } else if ((rc = axpby(c, n, 1.0, x, 1.0, c->z, x))) {
+                return rc;
+            }
         }
         if ((rc = read_problems(c))) return rc;
         bool any_change = false;
@@ -158,6 +197,7 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
             if (!act[p]) continue;
             const ProbDev& Q = c->ph[p];
             its[p] += Q.k;
+            jvs[p] += std::min(Q.k, mk);
             const bool nan = !(Q.beta == Q.beta) || !(Q.res == Q.res);
             if (Q.beta <= Q.target || (Q.k > 0 && Q.res <= Q.target) || nan) {
                 conv[p] = !nan;
@@ -180,11 +220,17 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
     std::vector<jfnk_stats>& S = c->pstats;
     S.assign(P, jfnk_stats());
     for (auto& s : S) std::memset(&s, 0, sizeof s);
-    std::vector<int> status(P, JFNK_OK), act(P), its(P), conv(P), newton_its(P);
+    std::vector<int> status(P, JFNK_OK), act(P), its(P), jvs(P), conv(P), newton_its(P);
     std::vector<double> rn(P), r0(P);
     if ((rc = read_problems(c))) return rc;
-    for (int p = 0; p < P; p++) { c->ph[p].n_reorth = 0; c->ph[p].active = 0; }
+    for (int p = 0; p < P; p++) {
+        c->ph[p].n_reorth = 0;
+        c->ph[p].active = 0;
+        c->ph[p].n_cols = c->ph[p].n_rcols = 0.0;
+    }
     if ((rc = write_problem_ints(c, offsetof(ProbDev, n_reorth)))) return rc;
+    if ((rc = write_problem_doubles(c, offsetof(ProbDev, n_cols)))) return rc;
+    if ((rc = write_problem_doubles(c, offsetof(ProbDev, n_rcols)))) return rc;
     if ((rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
     for (int step = 1; step <= n_load_steps; step++) {
         c->load = (double)step / n_load_steps;
@@ -210,12 +256,13 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
             if (!n_act) break;
             if ((rc = axpby(c, n, -1.0, c->Ru, 0.0, c->Ru, c->bvec))) return rc;
             if ((rc = pnorm(c, c->u, 2, false))) return rc;
-            for (int p = 0; p < P; p++) { c->ph[p].active = act[p]; its[p] = 0; }
-            if ((rc = gmres_batch(c, c->bvec, c->x, its, conv))) return rc;
+            for (int p = 0; p < P; p++) { c->ph[p].active = act[p]; its[p] = 0; jvs[p] = 0; }
+            if ((rc = gmres_batch(c, c->bvec, c->x, its, jvs, conv))) return rc;
             for (int p = 0; p < P; p++) {
                 if (!act[p]) continue;
                 S[p].gmres_its += its[p];
-                S[p].residual_evals += its[p];
+                S[p].jv_products += jvs[p];
+                S[p].residual_evals += jvs[p];
             }
             // backtracking line search, per problem
             std::vector<int> acc(P, 0), trial(act);
@@ -278,11 +325,16 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
     for (int p = 0; p < P; p++) {
         S[p].status = status[p];
         S[p].reorth_its = c->ph[p].n_reorth;
+        S[p].arnoldi_cols = c->ph[p].n_cols;
+        S[p].reorth_cols = c->ph[p].n_rcols;
         S[p].solve_ms = ms;
         st->newton_its = std::max(st->newton_its, S[p].newton_its);
         st->gmres_its += S[p].gmres_its;
         st->residual_evals += S[p].residual_evals;
         st->reorth_its += S[p].reorth_its;
+        st->jv_products += S[p].jv_products;
+        st->arnoldi_cols += S[p].arnoldi_cols;
+        st->reorth_cols += S[p].reorth_cols;
         st->load_steps_done = std::min(st->load_steps_done, S[p].load_steps_done);
         st->final_rel_res = std::max(st->final_rel_res, S[p].final_rel_res);
         st->final_abs_res = std::max(st->final_abs_res, S[p].final_abs_res);

@@ -31,7 +31,7 @@ EXPORTS = [
     "jfnk_setup", "jfnk_residual", "jfnk_residual_noalloc", "jfnk_jv", "jfnk_precondition", "jfnk_solve", "jfnk_get_geometry",
     "jfnk_get_gradient", "jfnk_get_permutation", "jfnk_profile_enable", "jfnk_profile_get", "jfnk_profile_reset",
     "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64", "jfnk_batch_add", "jfnk_batch_size",
-    "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate",
+    "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate", "jfnk_get_tuning", "jfnk_set_tuning",
 ]
 
 
@@ -41,14 +41,16 @@ class Options(C.Structure):
                 ("newton_max_its", C.c_int), ("line_search_max", C.c_int), ("alpha_residual", C.c_double),
                 ("alpha_pc", C.c_double), ("jv_eps_scale", C.c_double), ("pc", C.c_int), ("precision", C.c_int),
                 ("reorth", C.c_int), ("renumber", C.c_int), ("mg_max_levels", C.c_int), ("mg_coarse_max", C.c_int),
-                ("mg_theta", C.c_double), ("mg_smooth_sweeps", C.c_int), ("mg_smoothed", C.c_int)]
+                ("mg_theta", C.c_double), ("mg_smooth_sweeps", C.c_int), ("mg_smoothed", C.c_int),
+                ("autotune", C.c_int), ("gmres_aug", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("gmres_its", C.c_int), ("residual_evals", C.c_int),
                 ("load_steps_done", C.c_int), ("status", C.c_int), ("final_rel_res", C.c_double),
                 ("final_abs_res", C.c_double), ("solve_ms", C.c_double), ("hist", C.c_double * 64), ("n_hist", C.c_int),
-                ("reorth_its", C.c_int)]
+                ("reorth_its", C.c_int), ("jv_products", C.c_int), ("arnoldi_cols", C.c_double),
+                ("reorth_cols", C.c_double)]
 
 
 _lib = None
@@ -94,6 +96,8 @@ def load():
         "jfnk_batch_problem_cells": (i, [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "jfnk_batch_stats": (i, [vp, C.POINTER(Stats)]),
         "jfnk_measure_fp64_rate": (i, [i, C.POINTER(C.c_double)]),
+        "jfnk_get_tuning": (i, [vp, i32p, i]),
+        "jfnk_set_tuning": (i, [vp, i32p, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -294,6 +298,18 @@ class Solver:
 
     def device_bytes(self):
         return int(self.L.jfnk_device_bytes(self.h))
+
+    TUNING_KEYS = ("grad_bs", "flux_bs", "flux_stage", "finish_bs", "mg_bs", "tuned")
+
+    def tuning(self):
+        """Launch shapes of the hot-path kernels (dict; `tuned` = chosen by the autotuner)."""
+        out = np.zeros(6, np.int32)
+        self._check(self.L.jfnk_get_tuning(self.h, out.ctypes.data_as(C.POINTER(C.c_int32)), 6))
+        return dict(zip(self.TUNING_KEYS, (int(v) for v in out)))
+
+    def set_tuning(self, grad_bs, flux_bs, flux_stage, finish_bs, mg_bs):
+        v = np.array([grad_bs, flux_bs, flux_stage, finish_bs, mg_bs], np.int32)
+        self._check(self.L.jfnk_set_tuning(self.h, v.ctypes.data_as(C.POINTER(C.c_int32)), 5))
 
 
 class Batch(Solver):

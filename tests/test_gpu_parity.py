@@ -122,7 +122,8 @@ def _solve_both(case, pc=1, load_steps=1, **kw):
     if pc == jfnk.PC_MG:
         o.mg_setup(coarse_max=s.options.mg_coarse_max, smoothed=bool(s.options.mg_smoothed),
                    sweeps=s.options.mg_smooth_sweeps)
-    uo, rco, sto = o.newton(load_steps=load_steps, rtol=1e-11, pc=pc)
+    uo, rco, sto = o.newton(load_steps=load_steps, rtol=1e-11, pc=pc, m=s.options.gmres_restart,
+                            aug=s.options.gmres_aug)
     assert rco == 0
     return ug, uo, st, sto
 
@@ -148,6 +149,39 @@ def test_solve_parity_neo_hookean_load_steps():
     ug, uo, st, _ = _solve_both(case, load_steps=3)
     assert _rel(ug, uo) <= 1e-8
     assert st.load_steps_done == 3
+
+
+def test_solve_parity_restarted_gmres_without_corrections():
+    """gmres_aug = 0: plain restarted GMRES(30) on both sides."""
+    ug, uo, st, _ = _solve_both(I.case_mms2d(32), gmres_aug=0)
+    assert _rel(ug, uo) <= 1e-8
+    assert st.jv_products >= st.gmres_its  # one product per column plus one per restart
+
+
+@pytest.mark.parametrize("aug", [1, 2, 4])
+def test_solve_parity_loose_gmres(aug):
+    """Loose GMRES (Sec. 4.2) with a short restart, so that kept corrections take part: the
+    solution matches the oracle's loose GMRES."""
+    case = I.case_cantilever(24, 4, 4, (1.0, 0.17, 0.17), perturb=0.15, seed=2)
+    ug, uo, st, sto = _solve_both(case, gmres_restart=8, gmres_aug=aug)
+    assert _rel(ug, uo) <= 1e-8
+    assert st.jv_products > 0
+
+
+def test_loose_gmres_needs_fewer_iterations_than_restarted():
+    """As in the oracle: keeping corrections across restarts recovers what a short restart
+    discards.  On this slender box the oracle needs 31 Newton steps and 31000 Arnoldi
+    iterations with GMRES(10) (restart limit hit every step) against 3 and 1649 with loose
+    GMRES(10, 2)."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(12, 4, 4, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
+    res = {}
+    for aug in (0, 2):
+        s = _solver(case, pc=jfnk.PC_BJACOBI, gmres_restart=10, gmres_aug=aug)
+        u, st, rc = s.solve(raise_on_fail=False)
+        res[aug] = (rc, st.gmres_its, st.newton_its)
+    assert res[2][0] == 0 and res[2][2] <= 5
+    assert res[2][1] < 0.5 * res[0][1], res
 
 
 def test_device_pointer_path_matches_host_path():
@@ -177,6 +211,31 @@ def test_graph_and_direct_launch_agree():
     s.profile(False)
     assert rc1 == rc2 == 0 and st1.gmres_its == st2.gmres_its
     assert np.array_equal(u1, u2)
+
+
+@pytest.mark.parametrize("reorth", [0, 1, 2])
+def test_programmatic_and_plain_launch_agree(reorth, monkeypatch):
+    """Kernels launched with programmatic dependent launch (the default) and plainly
+    (JFNK_PDL=0, read when a context is created) give bitwise equal solves, for every
+    re-orthogonalisation mode (selective, always, never), graphs replayed or not."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(30, 6, 6, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
+    kw = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, mg_coarse_max=50, reorth=reorth)
+    monkeypatch.setenv("JFNK_PDL", "1")
+    s1 = _solver(case, **kw)
+    u1, st1, rc1 = s1.solve()
+    s1.profile(True)
+    u1d, st1d, rc1d = s1.solve()
+    monkeypatch.setenv("JFNK_PDL", "0")
+    s2 = _solver(case, **kw)
+    u2, st2, rc2 = s2.solve()
+    assert rc1 == rc1d == rc2 == 0
+    assert st1.gmres_its == st1d.gmres_its == st2.gmres_its
+    assert np.array_equal(u1, u2) and np.array_equal(u1, u1d)
+    if reorth == 1:
+        assert st1.reorth_its == st1.gmres_its
+    if reorth == 2:
+        assert st1.reorth_its == 0
 
 
 def test_f32_to_f64_conversion_matches_ieee():
@@ -260,3 +319,44 @@ def test_all_traction_problem_and_zero_load():
     s0 = _solver(case0)
     u0, st, rc = s0.solve()
     assert rc == 0 and st.newton_its == 0 and np.all(u0 == 0)
+
+
+@pytest.mark.parametrize("name", ["cantilever_48x12x12", "nh_beam_32x12x12"])
+def test_every_launch_shape_gives_the_same_results(name):
+    """The autotuner chooses among launch shapes that compute the same arithmetic: residual,
+    Jv and the multigrid application are bitwise equal under every candidate shape, including
+    the face pass with shared-memory staging of the owner cells' gradients."""
+    from paper_2502_17217_gb300 import jfnk
+    case = (I.case_cantilever(48, 12, 12, (1.0, 0.25, 0.25), perturb=0.15, seed=2) if name.startswith("cant")
+            else I.case_nh_beam(32, 12, 12, (1.0, 0.375, 0.375), end_uy=0.2, perturb=0.1, seed=3))
+    s = _solver(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED)
+    t = s.tuning()
+    assert t["tuned"] == 1 and case.mesh.n_cells >= 4096
+    scale = 0.004 if case.material.law == I.LAW_NEOHOOKEAN else 1e-4
+    u = I.random_field(5, case.mesh.n_cells, scale, dim=3)
+    v = I.random_field(6, case.mesh.n_cells, 1.0, dim=3)
+    ref = None
+    shapes = [(128, 256, 0, 256, 256), (64, 128, 1, 512, 128), (256, 256, 1, 128, 512), (128, 128, 0, 256, 256),
+              tuple(t[k] for k in jfnk.Solver.TUNING_KEYS[:5])]
+    for sh in shapes:
+        s.set_tuning(*sh)
+        got = (s.residual(u), s.jv(u, v), s.precondition(v, pc=jfnk.PC_MG))
+        if ref is None:
+            ref = got
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), sh
+    o = O.Oracle.from_case(case)
+    assert _rel(ref[0], o.residual(u)) <= 1e-12
+
+
+def test_set_tuning_rejects_values_outside_the_candidates():
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(20, 4, 4, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
+    s = _solver(case)
+    before = s.tuning()
+    assert before["tuned"] == 0  # below the tuning threshold: defaults
+    with pytest.raises(jfnk.JfnkError):
+        s.set_tuning(96, 256, 0, 256, 256)
+    with pytest.raises(jfnk.JfnkError):
+        s.set_tuning(128, 256, 2, 256, 256)
+    assert s.tuning() == before

@@ -47,3 +47,22 @@ def test_admission_respects_the_memory_budget():
     reqs, wall, srv = serving.serve_stream([c for c, _ in reqs_def[:3]], rate_per_s=1000.0, seed=5, max_slots=6,
                                            hbm_budget_bytes=1.0, pc=jfnk.PC_BJACOBI)
     assert all(r.status == 0 for r in reqs) and srv.max_concurrent == 1
+
+
+def test_served_results_under_contention_with_load_steps():
+    """Many large requests in a burst (copy engines and SMs shared by 8 contexts), half of
+    them neo-Hookean with two load steps: every result equals the request solved alone.  A
+    load factor uploaded outside the request's stream order showed up here as requests
+    converging to the wrong load step."""
+    from paper_2502_17217_gb300 import jfnk, serving
+    reqs_def = I.serving_requests(16, lo=20000, hi=200000, seed=11, frac_nh=0.5)
+    opts = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED)
+    cases = [c for c, _ in reqs_def]
+    steps = [s for _, s in reqs_def]
+    reqs, wall, srv = serving.serve_stream(cases, rate_per_s=5000.0, seed=6, load_steps=steps, max_slots=8, **opts)
+    assert srv.max_concurrent >= 4
+    assert all(r.status == 0 for r in reqs), [(r.status, r.error) for r in reqs]
+    for r, (c, st) in zip(reqs, reqs_def):
+        ua, sta, rc = jfnk.Solver.from_case(c, **opts).solve(load_steps=st)
+        assert rc == 0 and sta.load_steps_done == st
+        assert np.array_equal(r.u, ua)
