@@ -351,7 +351,9 @@ def main():
         import __graft_entry__ as g
         g.build()
         case = workload_case(args.workload)
-        s = jfnk.Solver.from_case(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-8)
+        # with --shapes the autotuner is off, so a capture's launch count starts at the solve
+        s = jfnk.Solver.from_case(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-8,
+                                  autotune=0 if args.shapes else 1)
         if args.shapes:
             s.set_tuning(*[int(v) for v in args.shapes.split(",")])
         for _ in range(args.warmup + args.steps):
