@@ -70,6 +70,7 @@ def lib():
             "orc_newton": (i, [vp, vp, i, d, d, i, i, d, i, vp]),
             "orc_lgmres": (i, [vp, vp, vp, vp, vp, i, i, d, i, i, vp, vp]),
             "orc_newton_ex": (i, [vp, vp, i, d, d, i, i, i, d, i, vp]),
+            "orc_segregated": (i, [vp, vp, i, d, d, i, d, i, i, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -232,6 +233,16 @@ class Oracle:
         rc = lib().orc_lgmres(self.h, _p(u), _p(Ru), _p(b), _p(x), m, aug, eta, max_restarts, pc, C.byref(its),
                               C.byref(rel))
         return x, rc, its.value, rel.value
+
+    def segregated(self, u0=None, load_steps=1, rtol=1e-8, atol=1e-50, max_outer=100000, inner_tol=0.9,
+                   max_inner=1000, pc=PC_BJACOBI):
+        """The segregated quasi-Newton method of Sec. 3.1 (J~ per component, PCG to inner_tol);
+        stats.newton_its = outer iterations, stats.gmres_its = CG iterations."""
+        u = np.zeros((self.nc, 3)) if u0 is None else _f64(u0, (self.nc, 3)).copy()
+        st = Stats()
+        rc = lib().orc_segregated(self.h, _p(u), load_steps, rtol, atol, max_outer, inner_tol, max_inner, pc,
+                                  C.byref(st))
+        return u, rc, st
 
     def newton(self, u0=None, load_steps=1, rtol=1e-8, atol=1e-50, max_newton=50, m=30, eta=1e-3, pc=PC_BJACOBI,
                aug=0):

@@ -1219,6 +1219,98 @@ done:
     return status;
 }
 
+/* ------------------------------------------------------------------ Sec. 3.1, segregated
+ * The segregated solution algorithm as the paper states it: a quasi-Newton method whose
+ * Jacobian is the compact-stencil J~, decoupled into one scalar system per displacement
+ * component with the same matrix (no symmetry faces here): each outer iteration solves
+ * J~ du = -R(u_k) component by component and sets u_{k+1} = u_k + du (the total-displacement
+ * form of the paper adds J~ u_k to both sides: the same iterate).  The inner systems are
+ * solved by preconditioned conjugate gradients on A = -J~ (symmetric positive definite once
+ * displacement faces exist), from du = 0, until the component's residual has fallen by the
+ * factor inner_tol (Sec. 3.2: 0.9 for the segregated approach).  Preconditioner: the
+ * block-Jacobi diagonal of J~ or the multigrid V-cycle on A (both in their A-form, the
+ * negatives of orc_bjacobi / orc_mg_vcycle).  Convergence as for Newton (Sec. 3.3).
+ * stats: newton_its counts outer iterations, gmres_its the inner CG iterations. */
+int orc_segregated(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_outer,
+                   double inner_tol, int max_inner, int pc, orc_stats* st)
+{
+    long n = 3L * p->nc;
+    int nc = p->nc;
+    double* R = (double*)xcalloc((size_t)n, sizeof(double));
+    double* v = (double*)xcalloc((size_t)n, sizeof(double));
+    double* z = (double*)xcalloc((size_t)n, sizeof(double));
+    double* r = (double*)xcalloc((size_t)nc, sizeof(double));
+    double* zc = (double*)xcalloc((size_t)nc, sizeof(double));
+    double* d = (double*)xcalloc((size_t)nc, sizeof(double));
+    double* q = (double*)xcalloc((size_t)nc, sizeof(double));
+    double* du = (double*)xcalloc((size_t)nc, sizeof(double));
+    orc_stats local;
+    if (!st) st = &local;
+    memset(st, 0, sizeof *st);
+    int status = 0;
+    int ncomp = (p->dim == 2) ? 2 : 3;
+    if (p->dim == 2)
+        for (int P = 0; P < nc; P++) u[3 * P + 2] = 0.0;
+    for (int step = 1; step <= n_load_steps && status == 0; step++) {
+        orc_set_load_factor(p, (double)step / n_load_steps);
+        orc_residual(p, u, R);
+        double r0 = vnorm(R, n), rn = r0;
+        int conv = 0;
+        for (int it = 0; it <= max_outer; it++) {
+            if (!(rn == rn)) { status = -4; break; }
+            if (rn <= fmax(atol, rtol * r0)) { conv = 1; break; }
+            if (it == max_outer) break;
+            for (int j = 0; j < ncomp; j++) {
+                /* A du = R_j with A = -J~; r = R_j - A 0 */
+                for (int P = 0; P < nc; P++) { r[P] = R[3 * P + j]; du[P] = 0.0; }
+                double rr0 = sqrt(vdot(r, r, nc));
+                if (rr0 == 0.0) continue;
+                double rz = 0.0;
+                for (int k = 0; k < max_inner; k++) {
+                    /* zc = M^-1 r (A-form of the preconditioner, through the 3-component
+                       routines with this component only) */
+                    memset(v, 0, sizeof(double) * (size_t)n);
+                    for (int P = 0; P < nc; P++) v[3 * P + j] = r[P];
+                    if (pc == ORC_PC_BJACOBI) orc_bjacobi(p, v, z);
+                    else if (pc == ORC_PC_MG) orc_mg_vcycle(p, v, z);
+                    else memcpy(z, v, sizeof(double) * (size_t)n);
+                    for (int P = 0; P < nc; P++) zc[P] = (pc == ORC_PC_NONE) ? z[3 * P + j] : -z[3 * P + j];
+                    double rz_new = vdot(r, zc, nc);
+                    if (k == 0) for (int P = 0; P < nc; P++) d[P] = zc[P];
+                    else {
+                        double beta = rz_new / rz;
+                        for (int P = 0; P < nc; P++) d[P] = zc[P] + beta * d[P];
+                    }
+                    rz = rz_new;
+                    /* q = A d = -J~ d */
+                    memset(v, 0, sizeof(double) * (size_t)n);
+                    for (int P = 0; P < nc; P++) v[3 * P + j] = d[P];
+                    orc_jtilde_apply(p, v, z);
+                    for (int P = 0; P < nc; P++) q[P] = -z[3 * P + j];
+                    double alpha = rz / vdot(d, q, nc);
+                    for (int P = 0; P < nc; P++) {
+                        du[P] += alpha * d[P];
+                        r[P] -= alpha * q[P];
+                    }
+                    st->gmres_its++;
+                    if (sqrt(vdot(r, r, nc)) <= inner_tol * rr0) break;
+                }
+                for (int P = 0; P < nc; P++) u[3 * P + j] += du[P];
+            }
+            orc_residual(p, u, R);
+            rn = vnorm(R, n);
+            st->newton_its++;
+            st->residual_evals++;
+            if (st->n_hist < 64) st->hist[st->n_hist++] = rn;
+        }
+        st->final_rel_res = (r0 > 0.0) ? rn / r0 : 0.0;
+        if (!conv && status == 0) status = -2;
+    }
+    st->status = status;
+    free(R); free(v); free(z); free(r); free(zc); free(d); free(q); free(du);
+    return status;
+}
+
 /* ------------------------------------------------------------------ Eq. NewtonRaphson, Sec. 3.3
  * J du = -R; u += s du with a backtracking line search.  Reading (the line search is not
  * specified): s = 1, 1/2, 1/4, ... (at most 10 halvings), accepted when

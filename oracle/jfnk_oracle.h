@@ -89,6 +89,11 @@ int orc_newton(orc_problem* p, double* u, int n_load_steps, double rtol, double 
                int m, double eta, int pc, orc_stats* stats);
 int orc_newton_ex(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_newton,
                   int m, int kaug, double eta, int pc, orc_stats* stats);
+/* the segregated quasi-Newton method of Sec. 3.1: J~ du = -R per component by preconditioned
+ * CG on -J~ to a residual reduction inner_tol (Sec. 3.2: 0.9); newton_its = outer iterations,
+ * gmres_its = CG iterations */
+int orc_segregated(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_outer,
+                   double inner_tol, int max_inner, int pc, orc_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -297,3 +297,39 @@ def test_smoothed_aggregation_prolongation_and_strength():
         _, rc, its[sm], _ = o.gmres(u, rhs, eta=1e-6, pc=O.PC_MG)
         assert rc == 0
     assert its[True] < its[False]
+
+
+@pytest.mark.parametrize("pc", [O.PC_BJACOBI, O.PC_MG])
+def test_segregated_reaches_the_newton_solution(pc):
+    """Sec. 3.1: the segregated quasi-Newton iteration (J~ per component, PCG reduced by 0.9,
+    Sec. 3.2) solves the same discrete equations, so it converges to the Newton solution."""
+    c = I.case_cantilever(6, 4, 4, (0.6, 0.4, 0.4), perturb=0.15, seed=2)
+    o = O.Oracle.from_case(c)
+    o.mg_setup(coarse_max=10)
+    un, rcn, _ = o.newton(rtol=1e-11, eta=1e-6, pc=O.PC_BJACOBI)
+    us, rcs, sts = o.segregated(rtol=1e-11, pc=pc)
+    assert rcn == 0 and rcs == 0
+    assert np.linalg.norm(us - un) < 1e-8 * np.linalg.norm(un)
+    assert sts.newton_its > 50 and sts.gmres_its >= sts.newton_its  # many small corrections
+
+
+def test_segregated_inner_solve_is_the_compact_stencil_system():
+    """One outer iteration with the inner systems solved tightly gives du = -J~^-1 R(0)
+    exactly, checked with the independent J~ product."""
+    c = I.case_cantilever(5, 3, 3, (0.5, 0.3, 0.3), perturb=0.15, seed=3)
+    o = O.Oracle.from_case(c)
+    nc = c.mesh.n_cells
+    R0 = o.residual(np.zeros((nc, 3)))
+    for pc in (O.PC_NONE, O.PC_BJACOBI):
+        u1, rc, st = o.segregated(rtol=0.0, max_outer=1, inner_tol=1e-13, pc=pc)
+        assert st.newton_its == 1
+        assert np.linalg.norm(o.jtilde_apply(u1) + R0) <= 1e-10 * np.linalg.norm(R0)
+
+
+def test_segregated_neo_hookean_load_steps():
+    c = I.case_nh_beam(8, 3, 3, (1.0, 0.375, 0.375), end_uy=0.1, load_steps=2)
+    o = O.Oracle.from_case(c)
+    un, rcn, _ = o.newton(load_steps=2, rtol=1e-10, eta=1e-6)
+    us, rcs, sts = o.segregated(load_steps=2, rtol=1e-10)
+    assert rcn == 0 and rcs == 0
+    assert np.linalg.norm(us - un) < 1e-7 * np.linalg.norm(un)
