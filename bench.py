@@ -245,8 +245,35 @@ def run_ours(args, rank, world):
         jv_e2e += jv_cell_updates(s, st, args.workload) / nc
     e2e_s = time.perf_counter() - t0
     e2e_value = nc * jv_e2e / e2e_s * world
+    seg = segregated_comparison(case, opts, stream) if args.workload == "c2" and not args.no_segregated else None
     return {"value": value, "t_ms": t_ms, "stats": stats, "kernels": kt, "launches": launches, "clocks": clk.summary(),
-            "e2e": e2e_value, "case": case, "solver": s, "nc": nc, "prof_work": prof_work, "tuning": s.tuning()}
+            "e2e": e2e_value, "case": case, "solver": s, "nc": nc, "prof_work": prof_work, "tuning": s.tuning(),
+            "segregated": seg}
+
+
+def segregated_comparison(case, opts, stream, rtol=1e-6, max_outer=60000):
+    """The paper's comparison (Sec. 4): the same problem solved by the Newton-Krylov path and
+    by the segregated quasi-Newton method of Sec. 3.1 (same residual, J~ and multigrid), both
+    to the paper's |R|/|R0| < 1e-6, timed with CUDA events on the launch stream."""
+    import torch
+    from paper_2502_17217_gb300 import jfnk
+    o = dict(opts, newton_rtol=rtol, seg_max_outer=max_outer)
+    s = jfnk.Solver.from_case(case, **o)
+    s.setup()
+    out = {"rtol": rtol}
+    s.solve(raise_on_fail=False)  # warm-up of the Newton-Krylov path (graph capture)
+    for name, fn in (("jfnk", s.solve), ("segregated", s.solve_segregated)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        u, st, rc = fn(raise_on_fail=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"solve_time_s": a.elapsed_time(b) / 1e3, "status": rc, "outer_its": st.newton_its,
+                     "krylov_or_cg_its": st.gmres_its, "final_rel_res": st.final_rel_res}
+    out["jfnk_speedup"] = out["segregated"]["solve_time_s"] / out["jfnk"]["solve_time_s"]
+    s.close()
+    return out
 
 
 def jv_cell_updates(s, st, workload):
@@ -335,6 +362,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-segregated", action="store_true", help="skip the segregated-solver comparison (C2)")
     ap.add_argument("--ncu", action="store_true", help="untimed solves only, for an ncu capture of the same kernels")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
     ap.add_argument("--serve", action="store_true", help="config 5: Poisson request stream, served solves/s and p50/p99")
@@ -446,6 +474,7 @@ def main():
             "roofline": roof,
             "kernels": r["kernels"],
             "gpu_launches": r["launches"],
+            "vs_segregated": r["segregated"],
             "clocks": r["clocks"],
             "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": 24 * nc, "d2h_bytes_per_step": 24 * nc}}
     if not args.no_cpu_baseline:

@@ -82,6 +82,10 @@ typedef struct jfnk_options {
     int gmres_aug;          /* loose GMRES (Sec. 4.2): corrections of earlier cycles kept
                                across restarts, 0..min(8, gmres_restart - 1); each cycle
                                has gmres_restart columns in all; 0 = GMRES(m)          (2)   */
+    double seg_inner_tol;   /* jfnk_solve_segregated: each component's CG stops when its
+                               residual has fallen by this factor (Sec. 3.2: 0.9)     (0.9) */
+    int seg_max_outer;      /* jfnk_solve_segregated: outer iterations per load step (100000) */
+    int seg_max_inner;      /* jfnk_solve_segregated: CG iterations per outer one    (1000)  */
 } jfnk_options;
 
 typedef struct jfnk_stats {
@@ -175,6 +179,13 @@ int jfnk_precondition(jfnk_ctx* ctx, const double* v, double* z, int pc, int mem
  * count, summed Krylov counts, worst status and relative residual) and jfnk_batch_stats
  * gives each one.  The call synchronises the stream before returning. */
 int jfnk_solve(jfnk_ctx* ctx, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream);
+/* The segregated quasi-Newton solve of Sec. 3.1, the method the paper compares with: per outer
+ * iteration J~ du = -R(u) is solved component by component by preconditioned conjugate
+ * gradients on -J~ (preconditioner opt.pc, the same block-Jacobi / multigrid) until each
+ * component's residual has fallen by opt.seg_inner_tol, then u += du; convergence, load
+ * steps, arguments, errors and batching as jfnk_solve.  stats.newton_its counts outer
+ * iterations, stats.gmres_its the conjugate-gradient iterations (all components). */
+int jfnk_solve_segregated(jfnk_ctx* ctx, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream);
 
 /* ---- batches of independent problems in one index space -------------------------------- */
 /* A context becomes a batch when problems are added to it instead of calling jfnk_set_mesh.

@@ -83,6 +83,10 @@ static void free_device(jfnk_ctx* c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->it_graph) cudaGraphExecDestroy(c->it_graph);
     c->it_graph = nullptr;
+    if (c->seg_graph) cudaGraphExecDestroy(c->seg_graph);
+    c->seg_graph = nullptr;
+    c->seg_slot = c->seg_sbeg = c->seg_scnt = nullptr;
+    c->seg_state = nullptr;
     c->load_on_device = -1.0;
     jfnk::mg_release(c);
     for (void* p : c->allocs) cudaFree(p);
@@ -112,6 +116,8 @@ static bool valid_options(const jfnk_options* o, std::string& why)
     if (!(o->jv_eps_scale > 0)) { why = "jv_eps_scale must be > 0"; return false; }
     if (o->mg_coarse_max < 1 || o->mg_coarse_max > 8192) { why = "mg_coarse_max must be in [1, 8192]"; return false; }
     if (o->autotune != 0 && o->autotune != 1) { why = "autotune must be 0 or 1"; return false; }
+    if (!(o->seg_inner_tol > 0 && o->seg_inner_tol < 1)) { why = "seg_inner_tol must be in (0, 1)"; return false; }
+    if (o->seg_max_outer < 1 || o->seg_max_inner < 1) { why = "seg_max_outer and seg_max_inner must be >= 1"; return false; }
     if (o->gmres_aug < 0 || o->gmres_aug > 8 || o->gmres_aug >= o->gmres_restart) {
         why = "gmres_aug must be in [0, min(8, gmres_restart - 1)]";
         return false;
@@ -147,6 +153,9 @@ void jfnk_default_options(jfnk_options* o)
     o->mg_smoothed = 1;
     o->autotune = 1;
     o->gmres_aug = 2;
+    o->seg_inner_tol = 0.9;
+    o->seg_max_outer = 100000;
+    o->seg_max_inner = 1000;
 }
 
 int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
@@ -611,6 +620,13 @@ int jfnk_precondition(jfnk_ctx* c, const double* v, double* z, int pc, int mem, 
 
 int jfnk_solve(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream)
 {
+    return jfnk_solve_method(c, u, mem, n_load_steps, stats, stream, 0);
+}
+
+}  // extern "C"
+
+int jfnk_solve_method(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream, int method)
+{
     int rc = begin_call(c, stream);
     if (rc) return rc;
     if (!u || n_load_steps < 1 || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE))
@@ -620,7 +636,7 @@ int jfnk_solve(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* st
     std::memset(st, 0, sizeof *st);
     if ((rc = load_vec(c, u, mem, c->u))) return rc;
     const double saved_load = c->load;
-    int status = jfnk::newton(c, n_load_steps, st);
+    int status = method == 1 ? jfnk::segregated(c, n_load_steps, st) : jfnk::newton(c, n_load_steps, st);
     c->load = saved_load;
     if (status == JFNK_ECUDA || status == JFNK_ENOMEM) return status;
     if ((rc = store_vec(c, c->u, mem, u))) return rc;
@@ -633,6 +649,8 @@ int jfnk_solve(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* st
     }
     return JFNK_OK;
 }
+
+extern "C" {
 
 int jfnk_get_geometry(jfnk_ctx* c, double* Sf, double* Cf, double* V, double* C)
 {

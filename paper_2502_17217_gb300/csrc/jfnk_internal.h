@@ -129,6 +129,17 @@ struct ProbDev {
     double y[kMaxRestart];
 };
 
+// Conjugate-gradient state of one component system of one problem (segregated solver).
+struct SegSlot {
+    double rr0, rr;   // |r| at the start and now
+    double rz;        // r . (preconditioned r)
+    double beta, alpha;
+    int its;          // CG iterations of this outer iteration
+    int done;         // residual reduced enough (or no work)
+    unsigned ticket;
+    int pad;
+};
+
 // Scalars shared by all problems of a context.
 struct GlobalDev {
     int jg;           // index of the lockstep Arnoldi iteration (all active problems share it)
@@ -244,9 +255,17 @@ struct jfnk_ctx {
     std::vector<void*> allocs;
     jfnk::Profiler prof;
     jfnk::Tuning tune;
+    // segregated solver (segregated.cu): chunk -> slot (3 p + component), per-slot chunk ranges
+    int32_t *seg_slot = nullptr, *seg_sbeg = nullptr, *seg_scnt = nullptr;
+    jfnk::SegSlot* seg_state = nullptr;
+    std::vector<jfnk::SegSlot> seg_state_h;
+    cudaGraphExec_t seg_graph = nullptr;
+    int64_t seg_graph_kernels = 0;
 };
 
 // ------------------------------------------------------------------ helpers (capi.cu)
+// jfnk_solve (method 0: Newton-Krylov) and jfnk_solve_segregated (method 1)
+int jfnk_solve_method(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream, int method);
 int jfnk_fail(jfnk_ctx* c, int code, const std::string& msg);
 int jfnk_cuda_fail(jfnk_ctx* c, cudaError_t e, const char* what);
 void* jfnk_dalloc(jfnk_ctx* c, size_t bytes);   // tracked cudaMalloc, zeroed; nullptr on failure
@@ -324,6 +343,7 @@ int accept_masked(jfnk_ctx* c, const int32_t* mask_dev, double* u, const double*
 // precond.cu
 int pc_setup(jfnk_ctx* c);
 int autotune(jfnk_ctx* c);               // launch shapes for this mesh (autotune.cu)
+int segregated(jfnk_ctx* c, int n_load_steps, jfnk_stats* st);  // Sec. 3.1 (segregated.cu)
 bool tuning_valid(const Tuning& t);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);

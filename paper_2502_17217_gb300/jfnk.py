@@ -32,6 +32,7 @@ EXPORTS = [
     "jfnk_get_gradient", "jfnk_get_permutation", "jfnk_profile_enable", "jfnk_profile_get", "jfnk_profile_reset",
     "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64", "jfnk_batch_add", "jfnk_batch_size",
     "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate", "jfnk_get_tuning", "jfnk_set_tuning",
+    "jfnk_solve_segregated",
 ]
 
 
@@ -42,7 +43,8 @@ class Options(C.Structure):
                 ("alpha_pc", C.c_double), ("jv_eps_scale", C.c_double), ("pc", C.c_int), ("precision", C.c_int),
                 ("reorth", C.c_int), ("renumber", C.c_int), ("mg_max_levels", C.c_int), ("mg_coarse_max", C.c_int),
                 ("mg_theta", C.c_double), ("mg_smooth_sweeps", C.c_int), ("mg_smoothed", C.c_int),
-                ("autotune", C.c_int), ("gmres_aug", C.c_int)]
+                ("autotune", C.c_int), ("gmres_aug", C.c_int), ("seg_inner_tol", C.c_double),
+                ("seg_max_outer", C.c_int), ("seg_max_inner", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -82,6 +84,7 @@ def load():
         "jfnk_jv": (i, [vp, dp, dp, dp, i, vp]),
         "jfnk_precondition": (i, [vp, dp, dp, i, i, vp]),
         "jfnk_solve": (i, [vp, dp, i, i, C.POINTER(Stats), vp]),
+        "jfnk_solve_segregated": (i, [vp, dp, i, i, C.POINTER(Stats), vp]),
         "jfnk_get_geometry": (i, [vp, dp, dp, dp, dp]),
         "jfnk_get_gradient": (i, [vp, dp]),
         "jfnk_get_permutation": (i, [vp, i32p]),
@@ -248,7 +251,13 @@ class Solver:
         self._check(self.L.jfnk_precondition(self.h, _ptr(v), _ptr(z), pc, mem, s))
         return z
 
-    def solve(self, u0=None, load_steps=1, raise_on_fail=True):
+    def solve_segregated(self, u0=None, load_steps=1, raise_on_fail=True):
+        """The segregated quasi-Newton solve of Sec. 3.1 (the paper's comparison method);
+        returns (u, stats, status) as solve(); stats.newton_its = outer iterations,
+        stats.gmres_its = conjugate-gradient iterations."""
+        return self.solve(u0, load_steps, raise_on_fail, _fn="jfnk_solve_segregated")
+
+    def solve(self, u0=None, load_steps=1, raise_on_fail=True, _fn="jfnk_solve"):
         """Newton solve; returns (u, stats, status).  u0: numpy or torch CUDA tensor (copied)."""
         if u0 is None:
             u = np.zeros((self.nc, 3))
@@ -258,7 +267,7 @@ class Solver:
             u = np.array(u0, dtype=np.float64).reshape(self.nc, 3)
         st = Stats()
         mem, s = self._io(u)
-        rc = self.L.jfnk_solve(self.h, _ptr(u), mem, int(load_steps), C.byref(st), s)
+        rc = getattr(self.L, _fn)(self.h, _ptr(u), mem, int(load_steps), C.byref(st), s)
         if rc != OK and raise_on_fail and rc not in (MAXIT, LS_FAILED, DIVERGED):
             self._check(rc)
         return u, st, rc

@@ -83,3 +83,18 @@ def test_batch_solve_within_tolerance_with_multigrid_mixed_precision():
         R = o.residual(uk)
         R0 = o.residual(np.zeros_like(uk))
         assert np.linalg.norm(R) <= 1e-9 * np.linalg.norm(R0)
+
+
+def test_batch_segregated_bitwise_equals_alone():
+    """The segregated solver's per-component CG scalars are per problem too: a batched
+    segregated solve gives each problem exactly its solve alone (block-Jacobi)."""
+    from paper_2502_17217_gb300 import jfnk
+    cases = _mix()
+    B = jfnk.Batch(cases, pc=jfnk.PC_BJACOBI, newton_rtol=1e-9)
+    u, st, rc = B.solve_segregated()
+    assert rc == 0
+    for k, (c, uk, ps) in enumerate(zip(cases, B.split(u), B.problem_stats())):
+        ua, sta, rca = jfnk.Solver.from_case(c, pc=jfnk.PC_BJACOBI, newton_rtol=1e-9).solve_segregated()
+        assert rca == 0
+        assert np.array_equal(uk, ua), k
+        assert ps.newton_its == sta.newton_its and ps.gmres_its == sta.gmres_its

@@ -360,3 +360,39 @@ def test_set_tuning_rejects_values_outside_the_candidates():
     with pytest.raises(jfnk.JfnkError):
         s.set_tuning(128, 256, 2, 256, 256)
     assert s.tuning() == before
+
+
+@pytest.mark.parametrize("pc,precision", [(1, 0), (2, 0), (2, 1)])
+def test_segregated_parity(pc, precision):
+    """The segregated quasi-Newton solve (Sec. 3.1: J~ per component, PCG reduced by 0.9)
+    against the oracle's, and against the Newton-Krylov solution of the same equations."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(10, 4, 4, (0.6, 0.25, 0.25), perturb=0.15, seed=2)
+    s = _solver(case, pc=pc, precision=precision, newton_rtol=1e-10, mg_coarse_max=20)
+    ug, st, rc = s.solve_segregated()
+    assert rc == 0, (rc, st.newton_its, st.final_rel_res)
+    o = O.Oracle.from_case(case)
+    if pc == jfnk.PC_MG:
+        o.mg_setup(coarse_max=20, smoothed=bool(s.options.mg_smoothed), sweeps=s.options.mg_smooth_sweeps)
+    uo, rco, sto = o.segregated(rtol=1e-10, pc=pc)
+    assert rco == 0
+    assert _rel(ug, uo) <= 1e-8
+    # the same outer iteration (same inner solves up to rounding): equal or nearly equal counts
+    assert abs(st.newton_its - sto.newton_its) <= max(2, sto.newton_its // 20), (st.newton_its, sto.newton_its)
+    un, stn, rcn = _solver(case, pc=pc, precision=precision, newton_rtol=1e-10, mg_coarse_max=20).solve()
+    assert rcn == 0 and _rel(ug, un) <= 1e-8
+    assert st.newton_its > 10 * stn.newton_its  # many small corrections against few large ones
+
+
+def test_segregated_neo_hookean_load_steps_and_graph_vs_direct():
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_nh_beam(12, 4, 4, (1.0, 0.33, 0.33), end_uy=0.1, load_steps=2)
+    s = _solver(case, pc=jfnk.PC_BJACOBI, newton_rtol=1e-10)
+    u1, st1, rc1 = s.solve_segregated(load_steps=2)
+    assert rc1 == 0 and st1.load_steps_done == 2
+    s.profile(True)  # direct launches instead of the captured CG iteration
+    u2, st2, rc2 = s.solve_segregated(load_steps=2)
+    s.profile(False)
+    assert rc2 == 0 and np.array_equal(u1, u2) and st1.gmres_its == st2.gmres_its
+    uo, rco, _ = O.Oracle.from_case(case).segregated(load_steps=2, rtol=1e-10)
+    assert rco == 0 and _rel(u1, uo) <= 1e-8
