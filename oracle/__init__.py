@@ -71,6 +71,8 @@ def lib():
             "orc_lgmres": (i, [vp, vp, vp, vp, vp, i, i, d, i, i, vp, vp]),
             "orc_newton_ex": (i, [vp, vp, i, d, d, i, i, i, d, i, vp]),
             "orc_segregated": (i, [vp, vp, i, d, d, i, d, i, i, vp]),
+            "orc_set_dynamics": (i, [vp, d, d]),
+            "orc_dynamic": (i, [vp, vp, i, d, d, i, i, i, d, i, vp, i, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -233,6 +235,21 @@ class Oracle:
         rc = lib().orc_lgmres(self.h, _p(u), _p(Ru), _p(b), _p(x), m, aug, eta, max_restarts, pc, C.byref(its),
                               C.byref(rel))
         return x, rc, its.value, rel.value
+
+    def set_dynamics(self, rho, dt):
+        """Inertia with density rho and time step dt (BDF2, from rest); before mg_setup."""
+        self._check(lib().orc_set_dynamics(self.h, float(rho), float(dt)))
+
+    def dynamic(self, n_steps, rtol=1e-8, atol=1e-50, max_newton=50, m=30, aug=0, eta=1e-3, pc=PC_BJACOBI,
+                probe_cell=-1):
+        """n_steps time steps from the stored state (predictor + Newton-Krylov per step);
+        returns (u, status, stats, probe [n_steps, 3] displacement of probe_cell)."""
+        u = np.zeros((self.nc, 3))
+        probe = np.zeros((max(1, n_steps), 3))
+        st = Stats()
+        rc = lib().orc_dynamic(self.h, _p(u), n_steps, rtol, atol, max_newton, m, aug, eta, pc, C.byref(st),
+                               int(probe_cell), _p(probe))
+        return u, rc, st, probe[:n_steps]
 
     def segregated(self, u0=None, load_steps=1, rtol=1e-8, atol=1e-50, max_outer=100000, inner_tol=0.9,
                    max_inner=1000, pc=PC_BJACOBI):

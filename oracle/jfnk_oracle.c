@@ -46,6 +46,11 @@ struct orc_problem {
     double** mg_pval;
     double* mg_chol;    /* dense Cholesky factor of the coarsest level */
     int mg_pre, mg_post; /* Jacobi sweeps before / after the coarse correction */
+    /* dynamics (Sec. 2.3 inertia term, BDF2 of Eq. inertia2): density, time step, the
+       state of the two previous time levels and the known part of the acceleration */
+    int dynamic;
+    double rho, dt;
+    double *dyn_ut, *dyn_utm1, *dyn_vt, *dyn_vtm1, *dyn_at, *dyn_c; /* [nc][3] */
     char err[256];
 };
 
@@ -143,6 +148,7 @@ void orc_destroy(orc_problem* p)
     mg_free(p);
     free(p->pts); free(p->fptr); free(p->fpts); free(p->own); free(p->nei); free(p->btype); free(p->bval);
     free(p->cfptr); free(p->cf); free(p->Sf); free(p->Cf); free(p->V); free(p->C); free(p->Ginv); free(p->fb);
+    free(p->dyn_ut); free(p->dyn_utm1); free(p->dyn_vt); free(p->dyn_vtm1); free(p->dyn_at); free(p->dyn_c);
     free(p);
 }
 
@@ -536,6 +542,12 @@ void orc_residual(const orc_problem* p, const double* u, double* R)
             }
         }
         for (int j = 0; j < 3; j++) r[j] += p->load * p->fb[3 * P + j] * p->V[P];
+        if (p->dynamic) {
+            /* inertia (Eq. inertia): -rho Omega_P a_P with the BDF2 acceleration of
+               Eq. inertia2, a_P = 9/(4 dt^2) u_P + c_P (c_P from the previous levels) */
+            double k2 = 9.0 / (4.0 * p->dt * p->dt);
+            for (int j = 0; j < 3; j++) r[j] -= p->rho * p->V[P] * (k2 * uP[j] + p->dyn_c[3 * P + j]);
+        }
         if (p->dim == 2) r[2] = 0.0;
         for (int j = 0; j < 3; j++) R[3 * P + j] = r[j];
     }
@@ -600,6 +612,7 @@ void orc_jtilde_diag(const orc_problem* p, double* diag)
             int f = p->cf[k];
             if (f < p->ni || p->btype[f - p->ni] == ORC_BC_DISP) a -= face_coef(p, f, P);
         }
+        if (p->dynamic) a -= 2.25 * p->rho * p->V[P] / (p->dt * p->dt);  /* Sec. 3.1: -(9/4) rho Omega / dt^2 */
         diag[P] = a;
     }
 }
@@ -621,6 +634,8 @@ void orc_jtilde_apply(const orc_problem* p, const double* v, double* out)
                 for (int j = 0; j < 3; j++) r[j] -= c * vP[j];
             }
         }
+        if (p->dynamic)
+            for (int j = 0; j < 3; j++) r[j] -= 2.25 * p->rho * p->V[P] / (p->dt * p->dt) * vP[j];
         if (p->dim == 2) r[2] = 0.0;
         for (int j = 0; j < 3; j++) out[3 * P + j] = r[j];
     }
@@ -1216,6 +1231,75 @@ done:
     if (relres_out) *relres_out = rel;
     free(V); free(H); free(cs); free(sn); free(g); free(y); free(h); free(w); free(z); free(d); free(rprev);
     free(Z); free(AZ);
+    return status;
+}
+
+/* ------------------------------------------------------------------ dynamics (Sec. 2.3, 3.2)
+ * Time integration of rho d2u/dt2 = div sigma + f with the BDF2 acceleration of Eq. inertia2
+ * (velocity and acceleration both by the second-order backward difference), constant dt,
+ * from rest (u = v = 0 at the two levels before the first step).  Each step solves the
+ * momentum equation at t + dt by the Newton-Krylov method at full load, starting from the
+ * transient-continuation predictor of Eq. predictor, u = u_t + dt v_t + dt^2/2 a_t; then
+ * v_{t+1} = (3 u_{t+1} - 4 u_t + u_{t-1}) / (2 dt), a_{t+1} = (3 v_{t+1} - 4 v_t + v_{t-1}) / (2 dt).
+ * The inertia term adds -(9/4) rho Omega / dt^2 to the diagonal of J~ (Sec. 3.1), so a
+ * multigrid hierarchy is set up after orc_set_dynamics. */
+int orc_set_dynamics(orc_problem* p, double rho, double dt)
+{
+    if (!(rho >= 0.0) || (rho > 0.0 && !(dt > 0.0))) {
+        snprintf(p->err, sizeof p->err, "density must be >= 0 and dt > 0");
+        return -1;
+    }
+    size_t n = 3 * (size_t)p->nc;
+    double** bufs[6] = {&p->dyn_ut, &p->dyn_utm1, &p->dyn_vt, &p->dyn_vtm1, &p->dyn_at, &p->dyn_c};
+    for (int k = 0; k < 6; k++) {
+        free(*bufs[k]);
+        *bufs[k] = (double*)xcalloc(n, sizeof(double));
+    }
+    p->rho = rho;
+    p->dt = dt;
+    p->dynamic = rho > 0.0;
+    return 0;
+}
+
+int orc_dynamic(orc_problem* p, double* u, int n_steps, double rtol, double atol, int max_newton, int m, int kaug,
+                double eta, int pc, orc_stats* st, int probe_cell, double* probe)
+{
+    if (!p->dynamic) {
+        snprintf(p->err, sizeof p->err, "orc_dynamic needs orc_set_dynamics with a density > 0");
+        return -1;
+    }
+    long n = 3L * p->nc;
+    double dt = p->dt;
+    double* vn = (double*)xcalloc((size_t)n, sizeof(double));
+    orc_stats local, one;
+    if (!st) st = &local;
+    memset(st, 0, sizeof *st);
+    int status = 0;
+    for (int step = 0; step < n_steps && status == 0; step++) {
+        for (long i = 0; i < n; i++) {
+            p->dyn_c[i] = (3.0 * (-4.0 * p->dyn_ut[i] + p->dyn_utm1[i]) / (2.0 * dt) - 4.0 * p->dyn_vt[i] + p->dyn_vtm1[i]) /
+                          (2.0 * dt);
+            u[i] = p->dyn_ut[i] + dt * p->dyn_vt[i] + 0.5 * dt * dt * p->dyn_at[i];
+        }
+        status = orc_newton_ex(p, u, 1, rtol, atol, max_newton, m, kaug, eta, pc, &one);
+        st->newton_its += one.newton_its;
+        st->gmres_its += one.gmres_its;
+        st->residual_evals += one.residual_evals;
+        st->final_rel_res = one.final_rel_res;
+        if (st->n_hist < 64) st->hist[st->n_hist++] = one.final_rel_res;
+        for (long i = 0; i < n; i++) {
+            vn[i] = (3.0 * u[i] - 4.0 * p->dyn_ut[i] + p->dyn_utm1[i]) / (2.0 * dt);
+            p->dyn_at[i] = (3.0 * vn[i] - 4.0 * p->dyn_vt[i] + p->dyn_vtm1[i]) / (2.0 * dt);
+            p->dyn_utm1[i] = p->dyn_ut[i];
+            p->dyn_ut[i] = u[i];
+            p->dyn_vtm1[i] = p->dyn_vt[i];
+            p->dyn_vt[i] = vn[i];
+        }
+        if (probe && probe_cell >= 0 && probe_cell < p->nc)
+            for (int j = 0; j < 3; j++) probe[3 * step + j] = u[3 * probe_cell + j];
+    }
+    st->status = status;
+    free(vn);
     return status;
 }
 

@@ -89,6 +89,12 @@ int orc_newton(orc_problem* p, double* u, int n_load_steps, double rtol, double 
                int m, double eta, int pc, orc_stats* stats);
 int orc_newton_ex(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_newton,
                   int m, int kaug, double eta, int pc, orc_stats* stats);
+/* dynamics: density > 0 enables the inertia term (BDF2, from rest); set before the multigrid */
+int orc_set_dynamics(orc_problem* p, double rho, double dt);
+/* n_steps time steps of dt from the stored state; u returns the last displacement; probe
+ * (if not NULL) receives the displacement of probe_cell after each step [n_steps][3] */
+int orc_dynamic(orc_problem* p, double* u, int n_steps, double rtol, double atol, int max_newton, int m, int kaug,
+                double eta, int pc, orc_stats* stats, int probe_cell, double* probe);
 /* the segregated quasi-Newton method of Sec. 3.1: J~ du = -R per component by preconditioned
  * CG on -J~ to a residual reduction inner_tol (Sec. 3.2: 0.9); newton_its = outer iterations,
  * gmres_its = CG iterations */

@@ -310,6 +310,33 @@ def case_nh_beam(nx: int = 256, ny: int = 32, nz: int = 32, lengths=(1.0, 0.125,
     return Case(f"nh_beam_{nx}x{ny}x{nz}", m, Material(LAW_NEOHOOKEAN, mu, kappa), None, load_steps=load_steps)
 
 
+def case_dynamic_beam(nx: int = 3, ny: int = 30, nz: int = 3, traction=(50e3, 50e3, 0.0), E: float = 15.293e6,
+                      nu: float = 0.3, law: int = LAW_NEOHOOKEAN):
+    """Case 6 of Sec. 4 (vibration of a cantilevered column): 0.2 x 2 x 0.2 m with y up, the
+    bottom face (y = 0) clamped, a sudden constant traction on the upper face (y = 2), the
+    other faces traction-free; neo-Hookean with E = 15.293 MPa, nu = 0.3 (density 1000 kg/m^3
+    and dt = 1 ms are run parameters), chosen by the paper for a 1 Hz first frequency.  The
+    paper's meshes are 3x30x3 .. 24x240x24 cells.  Returns (case, probe cell): the probe is the
+    cell at the centre of the upper face (one of the four central ones for even counts)."""
+    m = hex_box(nx, ny, nz, (0.2, 2.0, 0.2))
+    ny_ = m.shape[1]
+    for pt in m.patches:
+        if pt.name == "ymin":
+            pt.bc = BC_DISP
+            pt.values = np.zeros((pt.size, 3))
+        elif pt.name == "ymax":
+            pt.bc = BC_TRAC
+            pt.values = np.tile(np.asarray(traction, float), (pt.size, 1))
+    if law == LAW_NEOHOOKEAN:
+        mu, kappa = E / (2 * (1 + nu)), E / (3 * (1 - 2 * nu))
+        mat = Material(LAW_NEOHOOKEAN, mu, kappa)
+    else:
+        mat = Material(LAW_LINEAR, E, nu)
+    i, k = nx // 2, nz // 2
+    probe = i + nx * ((ny_ - 1) + ny_ * k)
+    return Case(f"dynamic_beam_{nx}x{ny}x{nz}", m, mat, None), probe
+
+
 def batch_sizes(n_problems: int = 512, lo: int = 1000, hi: int = 64000, seed: int = 4):
     """Cell-count targets drawn log-uniform in [lo, hi] and box shapes nx:ny:nz ~ 4:1:1 (each >= 4)."""
     r = splitmix64_uniform(seed, 4 * n_problems, key=11).reshape(n_problems, 4)
