@@ -50,6 +50,8 @@ def workload_case(name="c2"):
         return I.case_nh_beam()
     if name == "c4":
         return [I.case_batch_member(*x, index=k) for k, x in enumerate(I.batch_sizes())]
+    if name == "c6":
+        return I.case_dynamic_beam(24, 240, 24)[0]
     return I.case_cantilever(200, 20, 20, (1.0, 0.1, 0.1), perturb=0.15, seed=2)
 
 
@@ -64,6 +66,11 @@ WORKLOADS = {
            "law": "neo-Hookean total Lagrangian (mu=0.38 MPa, kappa=8.3 MPa)", "pc": "multigrid V-cycle (FP32)",
            "krylov": KRYLOV, "tolerance": "|R|/|R0| < 1e-8 per load step",
            "eta": 1e-3, "jv_eps": "1e-7 (1+|u|)/|v|", "load_steps": 10},
+    "c6": {"workload": "dynamic_column_24x240x24_case6", "cells": 138240, "dofs": 414720,
+           "law": "neo-Hookean (E=15.293 MPa, nu=0.3), rho=1000 kg/m^3, sudden traction (50,50,0) kPa on the upper face",
+           "pc": "multigrid V-cycle (FP32)", "krylov": KRYLOV,
+           "tolerance": "|R|/|R0| < 1e-8 per time step", "eta": 1e-3, "jv_eps": "1e-7 (1+|u|)/|v|", "load_steps": 1,
+           "time_steps_per_bench_step": 10, "dt_s": 1e-3, "integrator": "BDF2 with the Taylor predictor (Sec. 2.3, 3.2)"},
     "c4": {"workload": "batch_512_boxes_logU_1k_64k", "cells": None, "dofs": None,
            "law": "linear elastic, E~U(1,300) GPa, nu~U(0.2,0.45)", "pc": "multigrid V-cycle (FP32)",
            "krylov": KRYLOV + ", per problem", "tolerance": "|R|/|R0| < 1e-8 per problem",
@@ -172,6 +179,8 @@ def run_ours(args, rank, world):
     if args.workload == "c4":
         s = jfnk.Batch(case, **opts)
         case = case[0]
+    elif args.workload == "c6":
+        s = jfnk.Solver.from_case(case, density=1000.0, dt=1e-3, **opts)
     else:
         s = jfnk.Solver.from_case(case, **opts)
     nc = s.nc
@@ -187,7 +196,10 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step():
-        u, st, rc = s.solve(u0, load_steps=load_steps)
+        if args.workload == "c6":  # ten time steps, continuing the motion
+            u, st, rc, _ = s.solve_dynamic(WORKLOADS["c6"]["time_steps_per_bench_step"])
+        else:
+            u, st, rc = s.solve(u0, load_steps=load_steps)
         if rc != 0:
             raise RuntimeError(f"solve failed: status {rc}, rel res {st.final_rel_res:.3e}")
         return st
@@ -237,18 +249,48 @@ def run_ours(args, rank, world):
         kt[name] = {"ms": ms, "launches": n}
     # end to end through the C ABI with host buffers (copies inside the timed region)
     u_host = np.zeros((nc, 3))
-    s.solve(u_host, load_steps=load_steps)
+    if args.workload != "c6":
+        s.solve(u_host, load_steps=load_steps)
     t0 = time.perf_counter()
     jv_e2e = 0
     for _ in range(args.steps):
-        u, st, rc = s.solve(u_host, load_steps=load_steps)
+        if args.workload == "c6":  # the call returns the displacement to host memory
+            u, st, rc, _ = s.solve_dynamic(WORKLOADS["c6"]["time_steps_per_bench_step"])
+        else:
+            u, st, rc = s.solve(u_host, load_steps=load_steps)
         jv_e2e += jv_cell_updates(s, st, args.workload) / nc
     e2e_s = time.perf_counter() - t0
     e2e_value = nc * jv_e2e / e2e_s * world
-    seg = segregated_comparison(case, opts, stream) if args.workload == "c2" and not args.no_segregated else None
+    seg = None
+    if args.workload == "c2" and not args.no_segregated:
+        seg = segregated_comparison(case, opts, stream)
+    elif args.workload == "c6" and not args.no_segregated:
+        seg = segregated_comparison_dynamic(case, dict(opts, density=1000.0, dt=1e-3), stream)
     return {"value": value, "t_ms": t_ms, "stats": stats, "kernels": kt, "launches": launches, "clocks": clk.summary(),
             "e2e": e2e_value, "case": case, "solver": s, "nc": nc, "prof_work": prof_work, "tuning": s.tuning(),
             "segregated": seg}
+
+
+def segregated_comparison_dynamic(case, opts, stream, n_steps=5):
+    """Case 6 comparison: the first n_steps time steps from rest, each solved by the
+    Newton-Krylov method and by the segregated method (same residual, J~, multigrid)."""
+    import torch
+    from paper_2502_17217_gb300 import jfnk
+    out = {"time_steps": n_steps, "rtol": opts.get("newton_rtol")}
+    for name, seg in (("jfnk", False), ("segregated", True)):
+        s = jfnk.Solver.from_case(case, **opts)
+        s.setup()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        u, st, rc, _ = s.solve_dynamic(n_steps, raise_on_fail=False, segregated=seg)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"solve_time_s": a.elapsed_time(b) / 1e3, "status": rc, "outer_its": st.newton_its,
+                     "krylov_or_cg_its": st.gmres_its, "steps_done": st.load_steps_done}
+        s.close()
+    out["jfnk_speedup"] = out["segregated"]["solve_time_s"] / out["jfnk"]["solve_time_s"]
+    return out
 
 
 def segregated_comparison(case, opts, stream, rtol=1e-6, max_outer=60000):
@@ -364,7 +406,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-segregated", action="store_true", help="skip the segregated-solver comparison (C2)")
     ap.add_argument("--ncu", action="store_true", help="untimed solves only, for an ncu capture of the same kernels")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c6"])
     ap.add_argument("--serve", action="store_true", help="config 5: Poisson request stream, served solves/s and p50/p99")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--requests", type=int, default=24)
@@ -476,7 +518,8 @@ def main():
             "gpu_launches": r["launches"],
             "vs_segregated": r["segregated"],
             "clocks": r["clocks"],
-            "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": 24 * nc, "d2h_bytes_per_step": 24 * nc}}
+            "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": 0 if args.workload == "c6" else 24 * nc,
+                    "d2h_bytes_per_step": 24 * nc}}
     if not args.no_cpu_baseline:
         v, its, dt = run_oracle_sample(case, 12.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -86,6 +86,9 @@ typedef struct jfnk_options {
                                residual has fallen by this factor (Sec. 3.2: 0.9)     (0.9) */
     int seg_max_outer;      /* jfnk_solve_segregated: outer iterations per load step (100000) */
     int seg_max_inner;      /* jfnk_solve_segregated: CG iterations per outer one    (1000)  */
+    double density;         /* kg/m^3; > 0 adds the inertia term (Sec. 2.3, BDF2) for
+                               jfnk_solve_dynamic; 0 = static                          (0)   */
+    double dt;              /* time step of jfnk_solve_dynamic, s (> 0 when density > 0) (0) */
 } jfnk_options;
 
 typedef struct jfnk_stats {
@@ -186,6 +189,21 @@ int jfnk_solve(jfnk_ctx* ctx, double* u, int mem, int n_load_steps, jfnk_stats* 
  * steps, arguments, errors and batching as jfnk_solve.  stats.newton_its counts outer
  * iterations, stats.gmres_its the conjugate-gradient iterations (all components). */
 int jfnk_solve_segregated(jfnk_ctx* ctx, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream);
+/* Time integration (options.density > 0, options.dt): n_steps steps of dt from the context's
+ * state (at rest after jfnk_setup or jfnk_dynamic_reset; the state persists between calls, so
+ * calls continue the motion).  Each step predicts u = u_t + dt v_t + dt^2/2 a_t (Eq. predictor)
+ * and solves the momentum equation with the BDF2 inertia term of Eq. inertia2 at full load by
+ * the Newton-Krylov method (method 0, options as jfnk_solve) or the segregated method of
+ * Sec. 3.1 (method 1, as jfnk_solve_segregated), then updates velocity and acceleration by
+ * BDF2.  u (host or device per mem, [n_cells][3], caller order) receives the displacement
+ * after the last completed step; probe (host, [n_steps][3], or NULL) the displacement of cell
+ * probe_cell (caller numbering) after each completed step.  stats sums the steps (newton_its,
+ * gmres_its, ...), load_steps_done counts completed steps.  JFNK_ESTATE for a static context,
+ * JFNK_EINVAL for bad arguments; a failed step stops the run with its status. */
+int jfnk_solve_dynamic(jfnk_ctx* ctx, double* u, int mem, int n_steps, int32_t probe_cell, double* probe,
+                       int method, jfnk_stats* stats, void* stream);
+/* Puts the time-integration state back at rest (u = v = a = 0 at both previous levels). */
+int jfnk_dynamic_reset(jfnk_ctx* ctx);
 
 /* ---- batches of independent problems in one index space -------------------------------- */
 /* A context becomes a batch when problems are added to it instead of calling jfnk_set_mesh.

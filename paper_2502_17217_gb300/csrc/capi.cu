@@ -117,6 +117,7 @@ static bool valid_options(const jfnk_options* o, std::string& why)
     if (o->mg_coarse_max < 1 || o->mg_coarse_max > 8192) { why = "mg_coarse_max must be in [1, 8192]"; return false; }
     if (o->autotune != 0 && o->autotune != 1) { why = "autotune must be 0 or 1"; return false; }
     if (!(o->seg_inner_tol > 0 && o->seg_inner_tol < 1)) { why = "seg_inner_tol must be in (0, 1)"; return false; }
+    if (!(o->density >= 0) || (o->density > 0 && !(o->dt > 0))) { why = "density must be >= 0, and dt > 0 when density > 0"; return false; }
     if (o->seg_max_outer < 1 || o->seg_max_inner < 1) { why = "seg_max_outer and seg_max_inner must be >= 1"; return false; }
     if (o->gmres_aug < 0 || o->gmres_aug > 8 || o->gmres_aug >= o->gmres_restart) {
         why = "gmres_aug must be in [0, min(8, gmres_restart - 1)]";
@@ -156,6 +157,8 @@ void jfnk_default_options(jfnk_options* o)
     o->seg_inner_tol = 0.9;
     o->seg_max_outer = 100000;
     o->seg_max_inner = 1000;
+    o->density = 0.0;
+    o->dt = 0.0;
 }
 
 int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
@@ -483,6 +486,8 @@ int jfnk_setup(jfnk_ctx* c)
     std::memset(c->ph, 0, sizeof(jfnk::ProbDev) * (size_t)P);
     c->pmask_h_store.assign(P, 0);
     c->pmask_h = c->pmask_h_store.data();
+    rc = jfnk::dynamics_setup(c);
+    if (rc) return rc;
     rc = jfnk::pc_setup(c);
     if (rc) return rc;
     // the uploads above are synchronous copies and memsets on the legacy stream: complete them
@@ -624,6 +629,27 @@ int jfnk_solve(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* st
 }
 
 }  // extern "C"
+
+int jfnk_solve_dynamic_impl(jfnk_ctx* c, int n_steps, int32_t probe_cell, double* probe, jfnk_stats* st, int method);
+
+extern "C" int jfnk_solve_dynamic(jfnk_ctx* c, double* u, int mem, int n_steps, int32_t probe_cell, double* probe,
+                                  int method, jfnk_stats* stats, void* stream)
+{
+    int rc = begin_call(c, stream);
+    if (rc) return rc;
+    if (!u || n_steps < 1 || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE) || method < 0 || method > 1)
+        return jfnk_fail(c, JFNK_EINVAL, "jfnk_solve_dynamic: bad arguments");
+    jfnk_stats local;
+    jfnk_stats* st = stats ? stats : &local;
+    const double saved_load = c->load;
+    int status = jfnk_solve_dynamic_impl(c, n_steps, probe_cell, probe, st, method);
+    c->load = saved_load;
+    if (status == JFNK_ECUDA || status == JFNK_ENOMEM || status == JFNK_ESTATE || status == JFNK_EINVAL) return status;
+    if ((rc = store_vec(c, c->u, mem, u))) return rc;
+    JF_CUDA(c, cudaStreamSynchronize(c->cur));
+    if (status != JFNK_OK) return jfnk_fail(c, status, "a time step's Newton solve failed");
+    return JFNK_OK;
+}
 
 int jfnk_solve_method(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream, int method)
 {

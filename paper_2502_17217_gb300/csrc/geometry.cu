@@ -242,8 +242,8 @@ __global__ void k_cell_b0(int nc, int nf, int ni, int nd, const int32_t* __restr
 
 __global__ void k_jt_diag(int nc, const int32_t* __restrict__ fo_ptr, const int32_t* __restrict__ fn_ptr,
                           const int32_t* __restrict__ fn_face, const int32_t* __restrict__ fd_ptr,
-                          const double* __restrict__ jt_c, double* __restrict__ diag, double* __restrict__ dinv,
-                          float* __restrict__ dinv_f)
+                          const double* __restrict__ jt_c, const double* __restrict__ vol, double mass,
+                          double* __restrict__ diag, double* __restrict__ dinv, float* __restrict__ dinv_f)
 {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
@@ -251,6 +251,7 @@ __global__ void k_jt_diag(int nc, const int32_t* __restrict__ fo_ptr, const int3
     for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) s -= jt_c[f];
     for (int k = fn_ptr[P]; k < fn_ptr[P + 1]; k++) s -= jt_c[fn_face[k]];
     for (int f = fd_ptr[P]; f < fd_ptr[P + 1]; f++) s -= jt_c[f];
+    s -= mass * vol[P];  // dynamics (Sec. 3.1): -(9/4) rho Omega_P / dt^2, else 0
     diag[P] = s;
     dinv[P] = 1.0 / s;
     dinv_f[P] = (float)(1.0 / s);
@@ -350,8 +351,9 @@ int setup_material_coefficients(jfnk_ctx* c)
     }
     k_cell_b0<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.nf, m.ni, m.nd, m.ft_ptr, m.Sf, m.bval, m.V, m.fb, m.dim, m.b0);
     JF_LAUNCHED(c);
-    k_jt_diag<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.fo_ptr, m.fn_ptr, m.fn_face, m.fd_ptr, m.jt_c, m.jt_diag,
-                                                 m.jt_dinv, m.jt_dinv_f);
+    const double mass = c->opt.density > 0 ? 2.25 * c->opt.density / (c->opt.dt * c->opt.dt) : 0.0;
+    k_jt_diag<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.fo_ptr, m.fn_ptr, m.fn_face, m.fd_ptr, m.jt_c, m.V, mass,
+                                                 m.jt_diag, m.jt_dinv, m.jt_dinv_f);
     JF_LAUNCHED(c);
     JF_CUDA(c, cudaStreamSynchronize(s));
     return JFNK_OK;

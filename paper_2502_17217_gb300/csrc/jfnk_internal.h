@@ -261,6 +261,11 @@ struct jfnk_ctx {
     std::vector<jfnk::SegSlot> seg_state_h;
     cudaGraphExec_t seg_graph = nullptr;
     int64_t seg_graph_kernels = 0;
+    // dynamics (dynamics.cu): BDF2 history [3][nc] each, rho c of the current step, 9 rho/(4 dt^2)
+    bool dyn_on = false;
+    double dyn_mk = 0.0;
+    double *dyn_ut = nullptr, *dyn_utm1 = nullptr, *dyn_vt = nullptr, *dyn_vtm1 = nullptr, *dyn_at = nullptr;
+    double* dyn_rc = nullptr;
 };
 
 // ------------------------------------------------------------------ helpers (capi.cu)
@@ -344,6 +349,7 @@ int accept_masked(jfnk_ctx* c, const int32_t* mask_dev, double* u, const double*
 int pc_setup(jfnk_ctx* c);
 int autotune(jfnk_ctx* c);               // launch shapes for this mesh (autotune.cu)
 int segregated(jfnk_ctx* c, int n_load_steps, jfnk_stats* st);  // Sec. 3.1 (segregated.cu)
+int dynamics_setup(jfnk_ctx* c);       // history buffers at rest (dynamics.cu)
 bool tuning_valid(const Tuning& t);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);

@@ -207,14 +207,17 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
 }
 
 // mode 0: out = R;  mode 1: out = (R - Ru) / eps_p with eps_p the Jv step of the cell's
-// problem (0 -> out = 0)
+// problem (0 -> out = 0).  Dynamics (rc != null): the inertia term -rho Omega_P a_P of the
+// evaluated state u with the BDF2 acceleration a_P = 9/(4 dt^2) u_P + c_P (Eq. inertia2):
+// R_P -= Omega_P (mk u_P + rc_P), mk = 9 rho / (4 dt^2), rc = rho c from the previous levels.
 __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int dim, const int32_t* __restrict__ fo_ptr,
                                                 const int32_t* __restrict__ fn_ptr, const double* __restrict__ Fn,
                                                 const int32_t* __restrict__ fd_ptr, const double* __restrict__ F,
                                                 const double* __restrict__ b0, const double* __restrict__ load_dev, int mode,
                                                 const double* __restrict__ Ru, const ProbDev* __restrict__ pd,
                                                 const int32_t* __restrict__ cell_prob, const int* __restrict__ gate,
-                                                double* __restrict__ out)
+                                                const double* __restrict__ u, const double* __restrict__ vol,
+                                                const double* __restrict__ rc, double mk, double* __restrict__ out)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
@@ -230,6 +233,12 @@ __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int d
     }
     for (int f = fd_ptr[P]; f < fd_ptr[P + 1]; f++) {
         r0 += F[f]; r1 += F[nflux + f]; r2 += F[2 * (size_t)nflux + f];
+    }
+    if (rc) {
+        const double v = vol[P];
+        r0 -= v * fma(mk, u[P], rc[P]);
+        r1 -= v * fma(mk, u[nc + P], rc[nc + P]);
+        r2 -= v * fma(mk, u[2 * (size_t)nc + P], rc[2 * (size_t)nc + P]);
     }
     if (dim == 2) r2 = 0.0;
     if (mode == 1) {
@@ -320,7 +329,8 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     }
     jfnk_prof_begin(c, sl[2]);
     jfnk_launch(c, k_finish, dim3(nblk(m.nc, tu.finish_bs)), dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr, F, m.b0,
-                                            &c->gdev->load, mode, c->Ru, c->pd, c->cell_prob, gate, out);
+                                            &c->gdev->load, mode, c->Ru, c->pd, c->cell_prob, gate, u_int, (const double*)m.V,
+                (const double*)(c->dyn_on ? c->dyn_rc : nullptr), c->dyn_mk, out);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);
     return JFNK_OK;

@@ -32,7 +32,7 @@ EXPORTS = [
     "jfnk_get_gradient", "jfnk_get_permutation", "jfnk_profile_enable", "jfnk_profile_get", "jfnk_profile_reset",
     "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64", "jfnk_batch_add", "jfnk_batch_size",
     "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate", "jfnk_get_tuning", "jfnk_set_tuning",
-    "jfnk_solve_segregated",
+    "jfnk_solve_segregated", "jfnk_solve_dynamic", "jfnk_dynamic_reset",
 ]
 
 
@@ -44,7 +44,7 @@ class Options(C.Structure):
                 ("reorth", C.c_int), ("renumber", C.c_int), ("mg_max_levels", C.c_int), ("mg_coarse_max", C.c_int),
                 ("mg_theta", C.c_double), ("mg_smooth_sweeps", C.c_int), ("mg_smoothed", C.c_int),
                 ("autotune", C.c_int), ("gmres_aug", C.c_int), ("seg_inner_tol", C.c_double),
-                ("seg_max_outer", C.c_int), ("seg_max_inner", C.c_int)]
+                ("seg_max_outer", C.c_int), ("seg_max_inner", C.c_int), ("density", C.c_double), ("dt", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -85,6 +85,8 @@ def load():
         "jfnk_precondition": (i, [vp, dp, dp, i, i, vp]),
         "jfnk_solve": (i, [vp, dp, i, i, C.POINTER(Stats), vp]),
         "jfnk_solve_segregated": (i, [vp, dp, i, i, C.POINTER(Stats), vp]),
+        "jfnk_solve_dynamic": (i, [vp, dp, i, i, C.c_int32, dp, i, C.POINTER(Stats), vp]),
+        "jfnk_dynamic_reset": (i, [vp]),
         "jfnk_get_geometry": (i, [vp, dp, dp, dp, dp]),
         "jfnk_get_gradient": (i, [vp, dp]),
         "jfnk_get_permutation": (i, [vp, i32p]),
@@ -250,6 +252,23 @@ class Solver:
         mem, s = self._io(v)
         self._check(self.L.jfnk_precondition(self.h, _ptr(v), _ptr(z), pc, mem, s))
         return z
+
+    def solve_dynamic(self, n_steps, probe_cell=-1, raise_on_fail=True, segregated=False):
+        """n_steps time steps (options.density, options.dt) from the context's state, each
+        solved by the Newton-Krylov method (or the segregated one); returns
+        (u, stats, status, probe [steps, 3] displacement of probe_cell)."""
+        u = np.zeros((self.nc, 3))
+        probe = np.zeros((max(1, n_steps), 3))
+        st = Stats()
+        rc = self.L.jfnk_solve_dynamic(self.h, _ptr(u), MEM_HOST, int(n_steps), int(probe_cell),
+                                       probe.ctypes.data if probe_cell >= 0 else None, 1 if segregated else 0,
+                                       C.byref(st), None)
+        if rc != OK and raise_on_fail and rc not in (MAXIT, LS_FAILED, DIVERGED):
+            self._check(rc)
+        return u, st, rc, probe[:st.load_steps_done]
+
+    def dynamic_reset(self):
+        self._check(self.L.jfnk_dynamic_reset(self.h))
 
     def solve_segregated(self, u0=None, load_steps=1, raise_on_fail=True):
         """The segregated quasi-Newton solve of Sec. 3.1 (the paper's comparison method);
