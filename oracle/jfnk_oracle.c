@@ -181,6 +181,10 @@ int orc_set_material(orc_problem* p, int law, double p1, double p2)
         p->mu = p1;
         p->kappa = p2;
         p->lam = p->kappa - 2.0 * p->mu / 3.0;
+    } else if (law == ORC_LAW_STVK) {  /* App. B: Lame parameters from E, nu as for Hooke */
+        p->mu = p1 / (2.0 * (1.0 + p2));
+        p->lam = p1 * p2 / ((1.0 + p2) * (1.0 - 2.0 * p2));
+        p->kappa = p->lam + 2.0 * p->mu / 3.0;
     } else {
         snprintf(p->err, sizeof p->err, "unknown law %d", law);
         return -1;
@@ -412,6 +416,33 @@ void orc_cauchy_stress(const orc_problem* p, const double* g, double* s)
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) F[3 * i + j] = (i == j ? 1.0 : 0.0) + g[3 * j + i];
     double J = det33(F);
+    if (p->law == ORC_LAW_STVK) {
+        /* App. B St. Venant-Kirchhoff: E = (grad u + grad u^T + grad u . grad u^T) / 2,
+           S = 2 mu E + lambda tr(E) I, sigma = F S F^T / J (Eq. S2sigma) */
+        double E[9], S[9], FS[9];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double gg = 0.0;
+                for (int k = 0; k < 3; k++) gg += g[3 * i + k] * g[3 * j + k];
+                E[3 * i + j] = 0.5 * (g[3 * i + j] + g[3 * j + i] + gg);
+            }
+        double trE = E[0] + E[4] + E[8];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) S[3 * i + j] = 2.0 * p->mu * E[3 * i + j] + (i == j ? p->lam * trE : 0.0);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; k++) acc += F[3 * i + k] * S[3 * k + j];
+                FS[3 * i + j] = acc;
+            }
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; k++) acc += FS[3 * i + k] * F[3 * j + k];
+                s[3 * i + j] = acc / J;
+            }
+        return;
+    }
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) {
             double acc = 0.0;

@@ -25,7 +25,7 @@ extern "C" {
 #endif
 
 enum { ORC_BC_DISP = 0, ORC_BC_TRAC = 1, ORC_BC_SYMM = 2, ORC_BC_EMPTY = 3 };
-enum { ORC_LAW_LINEAR = 0, ORC_LAW_NEOHOOKEAN = 1 };
+enum { ORC_LAW_LINEAR = 0, ORC_LAW_NEOHOOKEAN = 1, ORC_LAW_STVK = 2 };
 enum { ORC_PC_NONE = 0, ORC_PC_BJACOBI = 1, ORC_PC_MG = 2 };
 
 typedef struct orc_problem orc_problem;

@@ -27,7 +27,7 @@ import numpy as np
 
 # Boundary-condition and material-law codes (same values as the C headers).
 BC_DISP, BC_TRAC, BC_SYMM, BC_EMPTY = 0, 1, 2, 3
-LAW_LINEAR, LAW_NEOHOOKEAN = 0, 1
+LAW_LINEAR, LAW_NEOHOOKEAN, LAW_STVK = 0, 1, 2
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 

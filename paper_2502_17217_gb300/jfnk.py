@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libjfnk_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, DIVERGED, MAXIT, LS_FAILED, GMRES_STAGNATED = 0, -1, -2, -3, -4, -5, -6, -7, -8
 BC_DISP, BC_TRAC, BC_SYMM, BC_EMPTY = 0, 1, 2, 3
-LAW_LINEAR, LAW_NEOHOOKEAN = 0, 1
+LAW_LINEAR, LAW_NEOHOOKEAN, LAW_STVK = 0, 1, 2
 PC_NONE, PC_BJACOBI, PC_MG = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1

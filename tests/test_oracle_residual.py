@@ -199,3 +199,19 @@ def test_linear_residual_is_affine():
     lhs = o.residual(a * u + (1 - a) * v)
     rhs = a * o.residual(u) + (1 - a) * o.residual(v)
     assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(rhs).max() * 10
+
+
+def test_uniform_stress_patch_test_st_venant_kirchhoff():
+    """App. B St. Venant-Kirchhoff in the total-Lagrangian form: a homogeneous deformation
+    gradient gives a uniform traction operator, so R = 0 with matching Dirichlet data."""
+    m = I.hex_box(5, 4, 4, (1.0, 0.8, 0.8), perturb=0.15, seed=27)
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((3, 3)) * 0.1
+    b = rng.standard_normal(3) * 0.01
+    mat = I.Material(I.LAW_STVK, 2.0e6, 0.3)
+    probe = O.Oracle(m, mat)
+    _all_disp(m, lambda p: _face_centres(probe, m, p) @ A.T + b)
+    o = O.Oracle(m, mat)
+    _, _, _, C = o.geometry()
+    R = o.residual(C @ A.T + b)
+    assert np.abs(R).max() < 1e-12 * 2.0e6 * 0.1 * 0.04

@@ -333,3 +333,29 @@ def test_segregated_neo_hookean_load_steps():
     us, rcs, sts = o.segregated(load_steps=2, rtol=1e-10)
     assert rcn == 0 and rcs == 0
     assert np.linalg.norm(us - un) < 1e-7 * np.linalg.norm(un)
+
+
+def test_st_venant_kirchhoff_law_from_its_definition():
+    """App. B: S = 2 mu E + lambda tr(E) I with the Green strain E, sigma = F S F^T / J; the
+    total-Lagrangian operator is then T = J F^-1 sigma = S F^T (the transpose of P = F S).
+    Written out here from the printed definitions; also objectivity and the small-strain
+    limit (Hooke)."""
+    E_, nu = 2.0e6, 0.3
+    mu, lam = E_ / (2 * (1 + nu)), E_ * nu / ((1 + nu) * (1 - 2 * nu))
+    o = _one_cell_oracle(I.LAW_STVK, E_, nu)
+    rng = np.random.default_rng(11)
+    G = 0.3 * rng.standard_normal((3, 3))
+    F = np.eye(3) + G.T
+    Eg = 0.5 * (G + G.T + G @ G.T)
+    S = 2 * mu * Eg + lam * np.trace(Eg) * np.eye(3)
+    sigma = F @ S @ F.T / np.linalg.det(F)
+    np.testing.assert_allclose(o.cauchy_stress(G), sigma, rtol=1e-12, atol=1e-9 * mu)
+    T = o.traction_operator(np.broadcast_to(G, (8, 3, 3)).copy())[0]
+    np.testing.assert_allclose(T, S @ F.T, rtol=1e-12, atol=1e-9 * mu)
+    Q = _rot(rng)
+    s_rot = o.cauchy_stress((Q @ F - np.eye(3)).T)
+    np.testing.assert_allclose(s_rot, Q @ sigma @ Q.T, atol=1e-9 * np.abs(sigma).max())
+    for t in (1e-5, 1e-6):
+        Gs = t * G
+        hooke = mu * (Gs + Gs.T) + lam * np.trace(Gs) * np.eye(3)
+        assert np.abs(o.cauchy_stress(Gs) - hooke).max() < 20 * t * np.abs(hooke).max()
