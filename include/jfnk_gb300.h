@@ -47,7 +47,7 @@ extern "C" {
 
 /* ---- enumerations ---------------------------------------------------------------------- */
 enum { JFNK_BC_DISP = 0, JFNK_BC_TRAC = 1, JFNK_BC_SYMM = 2, JFNK_BC_EMPTY = 3 };
-enum { JFNK_LAW_LINEAR = 0, JFNK_LAW_NEOHOOKEAN = 1 };
+enum { JFNK_LAW_LINEAR = 0, JFNK_LAW_NEOHOOKEAN = 1, JFNK_LAW_STVK = 2 };
 enum { JFNK_PC_NONE = 0, JFNK_PC_BJACOBI = 1, JFNK_PC_MG = 2 };
 enum { JFNK_MEM_HOST = 0, JFNK_MEM_DEVICE = 1 };
 /* FP64: everything in double.  MIXED: preconditioner (matrix, smoother, V-cycle) and the
@@ -142,7 +142,8 @@ int jfnk_set_mesh(jfnk_ctx* ctx, int dim, int32_t n_points, const double* points
  * supported). */
 int jfnk_set_patch(jfnk_ctx* ctx, int32_t first_face, int32_t n_faces, int bc_type, const double* values);
 /* App. B.  LINEAR (small strain, Eq. momentum_lingeom): p1 = E, p2 = nu.
- * NEOHOOKEAN (total Lagrangian, Eq. momentum_TL): p1 = mu, p2 = kappa.  Kbar = 4/3 mu + kappa. */
+ * NEOHOOKEAN (total Lagrangian, Eq. momentum_TL): p1 = mu, p2 = kappa.
+ * STVK (St. Venant-Kirchhoff, total Lagrangian): p1 = E, p2 = nu.  Kbar = 4/3 mu + kappa. */
 int jfnk_set_material(jfnk_ctx* ctx, int law, double p1, double p2);
 /* Body force per unit volume [n_cells][3] (host, copied), NULL = none (Eq. volume_integral). */
 int jfnk_set_body_force(jfnk_ctx* ctx, const double* fb);

@@ -291,8 +291,9 @@ int jfnk_set_patch(jfnk_ctx* c, int32_t first_face, int32_t n_faces, int bc_type
 int jfnk_set_material(jfnk_ctx* c, int law, double p1, double p2)
 {
     if (!c) return JFNK_EINVAL;
-    if (law == JFNK_LAW_LINEAR) {
-        if (!(p1 > 0) || !(p2 > -1.0 && p2 < 0.5)) return jfnk_fail(c, JFNK_EINVAL, "linear law needs E > 0 and -1 < nu < 1/2");
+    if (law == JFNK_LAW_LINEAR || law == JFNK_LAW_STVK) {
+        if (!(p1 > 0) || !(p2 > -1.0 && p2 < 0.5))
+            return jfnk_fail(c, JFNK_EINVAL, "linear and St. Venant-Kirchhoff laws need E > 0 and -1 < nu < 1/2");
         c->mu = p1 / (2.0 * (1.0 + p2));
         c->lam = p1 * p2 / ((1.0 + p2) * (1.0 - 2.0 * p2));
         c->kappa = c->lam + 2.0 * c->mu / 3.0;
@@ -395,16 +396,17 @@ int jfnk_setup(jfnk_ctx* c)
     // material table: law, mu, lambda, kappa, alpha Kbar, alpha_pc Kbar per problem
     const int P = c->nprob;
     c->mat_host.assign(6 * (size_t)P, 0.0);
-    int n_lin = 0;
+    int n_lin = 0, n_nh = 0;
     for (int p = 0; p < P; p++) {
         const int law = (int)mats[p][0];
         double mu, lam, kappa;
-        if (law == JFNK_LAW_LINEAR) {
+        if (law == JFNK_LAW_LINEAR || law == JFNK_LAW_STVK) {
             mu = mats[p][1] / (2.0 * (1.0 + mats[p][2]));
             lam = mats[p][1] * mats[p][2] / ((1.0 + mats[p][2]) * (1.0 - 2.0 * mats[p][2]));
             kappa = lam + 2.0 * mu / 3.0;
-            n_lin++;
+            n_lin += law == JFNK_LAW_LINEAR;
         } else {
+            n_nh++;
             mu = mats[p][1];
             kappa = mats[p][2];
             lam = kappa - 2.0 * mu / 3.0;
@@ -417,7 +419,9 @@ int jfnk_setup(jfnk_ctx* c)
         c->mat_host[4 * P + p] = c->opt.alpha_residual * Kbar;
         c->mat_host[5 * P + p] = c->opt.alpha_pc * Kbar;
     }
-    c->law_mode = (n_lin == P) ? 0 : (n_lin == 0 ? 1 : 2);
+    // kernels specialised for all-Hooke (0) and all-neo-Hookean (1); otherwise the law is read
+    // per cell (2: mixtures and St. Venant-Kirchhoff)
+    c->law_mode = (n_lin == P) ? 0 : (n_nh == P ? 1 : 2);
     std::string e = jfnk::build_topology(c->hm, c->opt.renumber != 0, c->topo, c->is_batch ? &group : nullptr);
     if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
     const int nc = c->hm.nc;

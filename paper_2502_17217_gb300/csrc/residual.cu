@@ -47,7 +47,36 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
 #pragma unroll
     for (int q = 0; q < 9; q++) G[(size_t)q * nc + P] = g[q];
     const int pr = (LAW == JFNK_LAW_LINEAR) ? 0 : cell_prob[P];
-    if (LAW == JFNK_LAW_NEOHOOKEAN || (LAW == 2 && mat.law[pr] == JFNK_LAW_NEOHOOKEAN)) {
+    if (LAW == 2 && mat.law[pr] == JFNK_LAW_STVK) {
+        // St. Venant-Kirchhoff (App. B): E = (G + G^T + G G^T) / 2, S = 2 mu E + lambda tr(E) I;
+        // the total-Lagrangian operator J F^-1 sigma with sigma = F S F^T / J is S F^T
+        // (F = I + G^T, so (S F^T)_ij = S_ij + sum_k S_ik G_kj)
+        const double mu = mat.mu[pr], lam = mat.lam[pr];
+        double E[9];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                double gg = g[3 * i] * g[3 * j];
+                gg = fma(g[3 * i + 1], g[3 * j + 1], gg);
+                gg = fma(g[3 * i + 2], g[3 * j + 2], gg);
+                E[3 * i + j] = 0.5 * (g[3 * i + j] + g[3 * j + i] + gg);
+            }
+        const double ltr = lam * (E[0] + E[4] + E[8]);
+        double S[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) S[q] = 2.0 * mu * E[q] + ((q % 4 == 0) ? ltr : 0.0);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                double t = S[3 * i + j];
+                t = fma(S[3 * i], g[j], t);
+                t = fma(S[3 * i + 1], g[3 + j], t);
+                t = fma(S[3 * i + 2], g[6 + j], t);
+                T[(size_t)(3 * i + j) * nc + P] = t;
+            }
+    } else if (LAW == JFNK_LAW_NEOHOOKEAN || (LAW == 2 && mat.law[pr] == JFNK_LAW_NEOHOOKEAN)) {
         const double mu = mat.mu[pr], kappa = mat.kappa[pr];
         // F = I + (grad u)^T: F_ij = delta_ij + g_ji
         const double F00 = 1.0 + g[0], F01 = g[3], F02 = g[6];

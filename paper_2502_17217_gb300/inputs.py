@@ -330,8 +330,8 @@ def case_dynamic_beam(nx: int = 3, ny: int = 30, nz: int = 3, traction=(50e3, 50
     if law == LAW_NEOHOOKEAN:
         mu, kappa = E / (2 * (1 + nu)), E / (3 * (1 - 2 * nu))
         mat = Material(LAW_NEOHOOKEAN, mu, kappa)
-    else:
-        mat = Material(LAW_LINEAR, E, nu)
+    else:  # Hooke or St. Venant-Kirchhoff: E, nu
+        mat = Material(law, E, nu)
     i, k = nx // 2, nz // 2
     probe = i + nx * ((ny_ - 1) + ny_ * k)
     return Case(f"dynamic_beam_{nx}x{ny}x{nz}", m, mat, None), probe

@@ -24,7 +24,7 @@ import numpy as np
 
 from . import jfnk
 
-DEFAULT_BYTES_PER_CELL = {0: 2400.0, 1: 3200.0}  # Hooke, neo-Hookean; refined by measurement
+DEFAULT_BYTES_PER_CELL = {0: 2400.0, 1: 3200.0, 2: 3200.0}  # Hooke, neo-Hookean, St. Venant-Kirchhoff; refined by measurement
 
 
 @dataclass

@@ -28,6 +28,9 @@ def _mix():
     sizes = I.batch_sizes(6, lo=200, hi=2000, seed=4)
     cases = [I.case_batch_member(*sz, index=k) for k, sz in enumerate(sizes)]
     cases.append(I.case_nh_beam(12, 4, 4, (1.0, 0.25, 0.25), end_uy=0.1, load_steps=1))  # mixed laws
+    stvk = I.case_nh_beam(10, 3, 3, (1.0, 0.3, 0.3), end_uy=0.08, load_steps=1)
+    stvk.material = I.Material(I.LAW_STVK, 3.0e6, 0.35)
+    cases.append(stvk)
     return cases
 
 
@@ -39,7 +42,7 @@ def test_batch_residual_and_jv_match_each_problem_alone():
     from paper_2502_17217_gb300 import jfnk
     cases = _mix()
     B = jfnk.Batch(cases)
-    u = np.concatenate([I.random_field(k + 1, c.mesh.n_cells, 1e-4 if c.material.law == 0 else 0.002)
+    u = np.concatenate([I.random_field(k + 1, c.mesh.n_cells, 1e-4 if c.material.law == I.LAW_LINEAR else 0.002)
                         for k, c in enumerate(cases)])
     v = np.concatenate([I.random_field(k + 50, c.mesh.n_cells, 1.0) for k, c in enumerate(cases)])
     R = B.residual(u)
