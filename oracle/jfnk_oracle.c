@@ -276,16 +276,28 @@ static int face_is_active(const orc_problem* p, int f)
     return f < p->ni || p->btype[f - p->ni] != ORC_BC_EMPTY;
 }
 
+static int is_symm(const orc_problem* p, int f) { return f >= p->ni && p->btype[f - p->ni] == ORC_BC_SYMM; }
+
+/* Symmetry face f of its owner P (Eq. symm, Eq. leastSquaresGrad, Eq. RhieChow).  Reading
+ * (the paper names d_s without defining it): the mirror neighbour of P is its reflection in
+ * the face plane, with value R u_P, R = I - 2 n n; so d_s = 2 delta n with delta = n . (x_f - x_P),
+ * Delta_s = n, |d_s| = 2 delta.  Outward unit normal n, |Gamma| and delta. */
+static void symm_geometry(const orc_problem* p, int f, double* n, double* mG, double* delta)
+{
+    *mG = norm3(p->Sf + 3 * f);
+    for (int c = 0; c < 3; c++) n[c] = p->Sf[3 * f + c] / *mG;
+    int P = p->own[f];
+    double xd[3];
+    for (int c = 0; c < 3; c++) xd[c] = p->Cf[3 * f + c] - p->C[3 * P + c];
+    *delta = dot3(n, xd);
+}
+
 int orc_prepare(orc_problem* p)
 {
     int nc = p->nc, nf = p->nf;
     for (int f = 0; f < nf; f++) {
         if (p->own[f] < 0 || p->own[f] >= nc || (f < p->ni && (p->nei[f] < 0 || p->nei[f] >= nc || p->nei[f] == p->own[f]))) {
             snprintf(p->err, sizeof p->err, "face %d has an out-of-range owner/neighbour", f);
-            return -1;
-        }
-        if (f >= p->ni && p->btype[f - p->ni] == ORC_BC_SYMM) {
-            snprintf(p->err, sizeof p->err, "symmetry faces are not supported");
             return -1;
         }
     }
@@ -328,10 +340,18 @@ int orc_prepare(orc_problem* p)
         double scale = 0.0;
         for (int k = p->cfptr[P]; k < p->cfptr[P + 1]; k++) {
             int f = p->cf[k];
-            if (f >= p->ni) continue; /* traction and displacement faces are excluded */
-            int N = (p->own[f] == P) ? p->nei[f] : p->own[f];
             double d[3];
-            for (int c = 0; c < 3; c++) d[c] = p->C[3 * N + c] - p->C[3 * P + c];
+            if (f >= p->ni) {
+                /* traction and displacement faces are excluded; a symmetry face counts with
+                   its mirror neighbour */
+                if (!is_symm(p, f)) continue;
+                double n[3], mGs, delta;
+                symm_geometry(p, f, n, &mGs, &delta);
+                for (int c = 0; c < 3; c++) d[c] = 2.0 * delta * n[c];
+            } else {
+                int N = (p->own[f] == P) ? p->nei[f] : p->own[f];
+                for (int c = 0; c < 3; c++) d[c] = p->C[3 * N + c] - p->C[3 * P + c];
+            }
             double w = norm3(p->Sf + 3 * f) / dot3(d, d);
             for (int i = 0; i < 3; i++)
                 for (int j = 0; j < 3; j++) G[3 * i + j] += w * d[i] * d[j];
@@ -385,11 +405,23 @@ void orc_gradient(const orc_problem* p, const double* u, double* grad)
         cell_u(p, u, P, uP);
         for (int k = p->cfptr[P]; k < p->cfptr[P + 1]; k++) {
             int f = p->cf[k];
-            if (f >= p->ni) continue;
-            int N = (p->own[f] == P) ? p->nei[f] : p->own[f];
             double d[3], uN[3], Gd[3], l[3];
-            cell_u(p, u, N, uN);
-            for (int c = 0; c < 3; c++) d[c] = p->C[3 * N + c] - p->C[3 * P + c];
+            if (f >= p->ni) {
+                if (!is_symm(p, f)) continue;
+                /* mirror neighbour: value R u_P at x_P + d_s */
+                double n[3], mGs, delta;
+                symm_geometry(p, f, n, &mGs, &delta);
+                double un = dot3(n, uP);
+                for (int c = 0; c < 3; c++) {
+                    d[c] = 2.0 * delta * n[c];
+                    uN[c] = uP[c] - 2.0 * un * n[c];
+                }
+                if (p->dim == 2) uN[2] = 0.0;
+            } else {
+                int N = (p->own[f] == P) ? p->nei[f] : p->own[f];
+                cell_u(p, u, N, uN);
+                for (int c = 0; c < 3; c++) d[c] = p->C[3 * N + c] - p->C[3 * P + c];
+            }
             const double* Gi = p->Ginv + 9 * P;
             for (int i = 0; i < 3; i++) Gd[i] = Gi[3 * i] * d[0] + Gi[3 * i + 1] * d[1] + Gi[3 * i + 2] * d[2];
             double coef = norm3(p->Sf + 3 * f) / dot3(d, d);
@@ -569,6 +601,23 @@ void orc_residual(const orc_problem* p, const double* u, double* R)
                     }
                 } else if (p->btype[b] == ORC_BC_TRAC) {
                     for (int j = 0; j < 3; j++) r[j] += mG * p->load * p->bval[3 * b + j];
+                } else if (p->btype[b] == ORC_BC_SYMM) {
+                    /* Reading of Eq. symm: the face stress is the mean of the cell's and its
+                       mirror image's, T_s = (T_P + R T_P R) / 2 (the printed one-sided form
+                       (I - n n) . sigma_P has no traction at all, while the text keeps the
+                       normal stress); so Gamma . T_s = |Gamma| (n . T_P . n) n, and likewise
+                       Delta . (grad u)_s = (n . (grad u)_P . n) n with Delta = n.  With the
+                       mirror value, (R u_P - u_P) / |d| = -(n . u_P) n / delta. */
+                    double ns[3], mGs, delta;
+                    symm_geometry(p, f, ns, &mGs, &delta);
+                    double Tnn = 0.0, Gnn = 0.0;
+                    for (int i = 0; i < 3; i++)
+                        for (int j = 0; j < 3; j++) {
+                            Tnn += ns[i] * TP[3 * i + j] * ns[j];
+                            Gnn += ns[i] * gP[3 * i + j] * ns[j];
+                        }
+                    double un = dot3(ns, uP);
+                    for (int j = 0; j < 3; j++) r[j] += mGs * (Tnn - aK * (un / delta + Gnn)) * ns[j];
                 }
             }
         }
@@ -663,6 +712,14 @@ void orc_jtilde_apply(const orc_problem* p, const double* v, double* out)
             } else if (p->btype[f - p->ni] == ORC_BC_DISP) {
                 double c = face_coef(p, f, P);
                 for (int j = 0; j < 3; j++) r[j] -= c * vP[j];
+            } else if (p->btype[f - p->ni] == ORC_BC_SYMM) {
+                /* Sec. 3.1 symmetry term: the compact part alpha Kbar |Delta| |Gamma| / |d|
+                   (R v_P - v_P) = -2 c (n . v_P) n with the mirror distance (reading above) */
+                double n[3], mGs, delta;
+                symm_geometry(p, f, n, &mGs, &delta);
+                double c = p->alpha_pc * p->Kbar * mGs / (2.0 * delta);
+                double vn = dot3(n, vP);
+                for (int j = 0; j < 3; j++) r[j] -= 2.0 * c * vn * n[j];
             }
         }
         if (p->dynamic)
@@ -672,13 +729,37 @@ void orc_jtilde_apply(const orc_problem* p, const double* v, double* out)
     }
 }
 
-/* Point-block Jacobi with the diagonal blocks of J~ (Sec. 3.1): z_P = [J~]_PP^-1 v_P. */
+/* Point-block Jacobi with the diagonal blocks of J~ (Sec. 3.1): z_P = [J~]_PP^-1 v_P.  The
+ * block is the scalar diagonal times I, plus -2 c n n for each symmetry face of P. */
 void orc_bjacobi(const orc_problem* p, const double* v, double* z)
 {
     double* diag = (double*)xcalloc((size_t)p->nc, sizeof(double));
     orc_jtilde_diag(p, diag);
-    for (int P = 0; P < p->nc; P++)
-        for (int j = 0; j < 3; j++) z[3 * P + j] = (p->dim == 2 && j == 2) ? 0.0 : v[3 * P + j] / diag[P];
+    for (int P = 0; P < p->nc; P++) {
+        double B[9] = {diag[P], 0, 0, 0, diag[P], 0, 0, 0, diag[P]}, Bi[9];
+        int has_symm = 0;
+        for (int k = p->cfptr[P]; k < p->cfptr[P + 1]; k++) {
+            int f = p->cf[k];
+            if (!is_symm(p, f)) continue;
+            double n[3], mGs, delta;
+            symm_geometry(p, f, n, &mGs, &delta);
+            double c = p->alpha_pc * p->Kbar * mGs / (2.0 * delta);
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) B[3 * i + j] -= 2.0 * c * n[i] * n[j];
+            has_symm = 1;
+        }
+        if (p->dim == 2) { B[2] = B[5] = B[6] = B[7] = 0.0; B[8] = 1.0; }
+        if (!has_symm) {
+            for (int j = 0; j < 3; j++) z[3 * P + j] = (p->dim == 2 && j == 2) ? 0.0 : v[3 * P + j] / diag[P];
+            continue;
+        }
+        inv33(B, Bi);
+        for (int i = 0; i < 3; i++) {
+            double acc = 0.0;
+            for (int j = 0; j < 3; j++) acc += Bi[3 * i + j] * v[3 * P + j];
+            z[3 * P + i] = (p->dim == 2 && i == 2) ? 0.0 : acc;
+        }
+    }
     free(diag);
 }
 
