@@ -138,8 +138,10 @@ int jfnk_set_mesh(jfnk_ctx* ctx, int dim, int32_t n_points, const double* points
                   int32_t n_internal, const int32_t* neighbour, int32_t n_cells);
 /* Boundary faces [first_face, first_face + n_faces) get bc_type.  values [n_faces][3]:
  * prescribed displacement (DISP) or traction per unit (reference) area (TRAC); NULL = zero.
- * EMPTY faces are the front/back planes of 2-D meshes.  SYMM returns JFNK_EINVAL (not yet
- * supported). */
+ * SYMM faces are symmetry planes (Eq. symm: shear-free, the face acting as a mirror; values
+ * ignored).  EMPTY faces are the front/back planes of 2-D meshes.  With symmetry faces the
+ * block-Jacobi preconditioner uses the 3x3 diagonal blocks of J~; the multigrid hierarchy is
+ * built on the scalar part of J~ (without the n n terms of those faces). */
 int jfnk_set_patch(jfnk_ctx* ctx, int32_t first_face, int32_t n_faces, int bc_type, const double* values);
 /* App. B.  LINEAR (small strain, Eq. momentum_lingeom): p1 = E, p2 = nu.
  * NEOHOOKEAN (total Lagrangian, Eq. momentum_TL): p1 = mu, p2 = kappa.

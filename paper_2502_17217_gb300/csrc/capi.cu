@@ -276,8 +276,7 @@ int jfnk_set_patch(jfnk_ctx* c, int32_t first_face, int32_t n_faces, int bc_type
     if (!c->have_mesh) return jfnk_fail(c, JFNK_ESTATE, "jfnk_set_patch before jfnk_set_mesh");
     if (first_face < c->hm.ni || n_faces < 0 || first_face + n_faces > c->hm.nf)
         return jfnk_fail(c, JFNK_EINVAL, "patch faces must be boundary faces");
-    if (bc_type == JFNK_BC_SYMM) return jfnk_fail(c, JFNK_EINVAL, "symmetry boundaries are not supported yet");
-    if (bc_type != JFNK_BC_DISP && bc_type != JFNK_BC_TRAC && bc_type != JFNK_BC_EMPTY)
+    if (bc_type != JFNK_BC_DISP && bc_type != JFNK_BC_TRAC && bc_type != JFNK_BC_SYMM && bc_type != JFNK_BC_EMPTY)
         return jfnk_fail(c, JFNK_EINVAL, "unknown boundary condition type");
     for (int32_t k = 0; k < n_faces; k++) {
         const int b = first_face - c->hm.ni + k;

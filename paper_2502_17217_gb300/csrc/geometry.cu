@@ -100,15 +100,32 @@ __global__ void k_cell_geom(int nc, int nf, const int32_t* __restrict__ ca_ptr, 
 // Least-squares tensor G_P = sum |Gamma| d d / (d.d) over internal faces (the weight w of
 // Eq. leastSquaresGrad read as 1/2 on both sums, so the gradient is exact for linear
 // fields) and the stored vectors l = |Gamma| G_P^-1 d / (d.d).
+// d of a sliced-ELL slot: to the neighbour's centroid, or for a symmetry face (N >= nc) to
+// the cell's mirror image, d = 2 delta n with delta = n . (x_f - x_P) (Eq. leastSquaresGrad,
+// reading: the mirror neighbour of Eq. symm sits at the reflection of x_P)
+__device__ __forceinline__ void slot_d(int P, int N, int f, int nc, int nf, const double* __restrict__ Sf,
+                                       const double* __restrict__ Cf, const double* __restrict__ C, double& dx,
+                                       double& dy, double& dz)
+{
+    if (N < nc) {
+        dx = C[N] - C[P]; dy = C[nc + N] - C[nc + P]; dz = C[2 * nc + N] - C[2 * nc + P];
+        return;
+    }
+    const double gx = Sf[f], gy = Sf[nf + f], gz = Sf[2 * nf + f];
+    const double mg = sqrt(gx * gx + gy * gy + gz * gz);
+    const double nx = gx / mg, ny = gy / mg, nz = gz / mg;
+    const double delta = nx * (Cf[f] - C[P]) + ny * (Cf[nf + f] - C[nc + P]) + nz * (Cf[2 * nf + f] - C[2 * nc + P]);
+    dx = 2.0 * delta * nx; dy = 2.0 * delta * ny; dz = 2.0 * delta * nz;
+}
+
 __global__ void k_cell_ls(int nc, int nf, int dim, const int32_t* __restrict__ sell_off, const int32_t* __restrict__ sell_w,
                           const int32_t* __restrict__ sell_nbr, const int32_t* __restrict__ sell_face,
-                          const double* __restrict__ Sf, const double* __restrict__ C, int n_slots,
-                          double* __restrict__ sell_l, int32_t* err)
+                          const double* __restrict__ Sf, const double* __restrict__ Cf, const double* __restrict__ C,
+                          int n_slots, double* __restrict__ sell_l, int32_t* err)
 {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= nc) return;
     const int s = P >> 5, lane = P & 31, base = sell_off[s], w = sell_w[s];
-    const double px = C[P], py = C[nc + P], pz = C[2 * nc + P];
     double g[6] = {0, 0, 0, 0, 0, 0};  // xx xy xz yy yz zz
     double scale = 0;
     for (int k = 0; k < w; k++) {
@@ -116,7 +133,8 @@ __global__ void k_cell_ls(int nc, int nf, int dim, const int32_t* __restrict__ s
         const int N = sell_nbr[slot];
         if (N < 0) break;
         const int f = sell_face[slot];
-        const double dx = C[N] - px, dy = C[nc + N] - py, dz = C[2 * nc + N] - pz;
+        double dx, dy, dz;
+        slot_d(P, N, f, nc, nf, Sf, Cf, C, dx, dy, dz);
         const double mS = sqrt(Sf[f] * Sf[f] + Sf[nf + f] * Sf[nf + f] + Sf[2 * nf + f] * Sf[2 * nf + f]);
         const double c = mS / (dx * dx + dy * dy + dz * dz);
         g[0] += c * dx * dx; g[1] += c * dx * dy; g[2] += c * dx * dz;
@@ -147,7 +165,8 @@ __global__ void k_cell_ls(int nc, int nf, int dim, const int32_t* __restrict__ s
         const int N = sell_nbr[slot];
         if (N < 0) break;
         const int f = sell_face[slot];
-        const double dx = C[N] - px, dy = C[nc + N] - py, dz = C[2 * nc + N] - pz;
+        double dx, dy, dz;
+        slot_d(P, N, f, nc, nf, Sf, Cf, C, dx, dy, dz);
         const double mS = sqrt(Sf[f] * Sf[f] + Sf[nf + f] * Sf[nf + f] + Sf[2 * nf + f] * Sf[2 * nf + f]);
         const double c = mS / (dx * dx + dy * dy + dz * dz);
         sell_l[slot] = c * (iv[0] * dx + iv[1] * dy + iv[2] * dz);
@@ -166,7 +185,10 @@ __global__ void k_cell_ls(int nc, int nf, int dim, const int32_t* __restrict__ s
 //   t_j = sum_i p_i G_ij + sum_i q_i G_ji + r_j tr(G),  p = mu Gamma - a, q = mu Gamma, r = lambda Gamma.
 // Neo-Hookean (total Lagrangian) keeps Gamma and a:  t = Gamma . T_f - a . G_f.
 // slots: 0 w | 1 kc | 2-4 p (or Gamma) | 5-7 q (or a) | 8-10 r.  J~ gets alpha_pc Kbar |Delta||Gamma|/|d|.
-__global__ void k_flux_coef(int ni, int nflux, int nf, int nc, MatDev mat, const int32_t* __restrict__ cell_prob,
+// Symmetry faces [ni + nd, nflux) (Eq. symm; mirror neighbour at d = 2 delta n, Delta = n):
+//   slots 0 alpha Kbar | 1 1/delta | 2-4 Gamma | 5-7 n;  J~ gets alpha_pc Kbar |Gamma| / (2 delta)
+//   on the n n part of the diagonal block.
+__global__ void k_flux_coef(int ni, int nd, int nflux, int nf, int nc, MatDev mat, const int32_t* __restrict__ cell_prob,
                             const int32_t* __restrict__ own, const int32_t* __restrict__ nei,
                             const double* __restrict__ Sf, const double* __restrict__ Cf, const double* __restrict__ C,
                             double* __restrict__ coef, double* __restrict__ jt_c)
@@ -181,6 +203,17 @@ __global__ void k_flux_coef(int ni, int nflux, int nf, int nc, MatDev mat, const
     const double Gx = Sf[f], Gy = Sf[nf + f], Gz = Sf[2 * nf + f];
     const double mG = sqrt(Gx * Gx + Gy * Gy + Gz * Gz);
     const double nx = Gx / mG, ny = Gy / mG, nz = Gz / mG;
+    if (f >= ni + nd) {
+        const double delta = nx * (Cf[f] - C[P]) + ny * (Cf[nf + f] - C[nc + P]) + nz * (Cf[2 * nf + f] - C[2 * nc + P]);
+        coef[f] = aK;
+        coef[nflux + f] = 1.0 / delta;
+        coef[2 * nflux + f] = Gx; coef[3 * nflux + f] = Gy; coef[4 * nflux + f] = Gz;
+        coef[5 * nflux + f] = nx; coef[6 * nflux + f] = ny; coef[7 * nflux + f] = nz;
+        coef[8 * nflux + f] = 0.0; coef[9 * nflux + f] = 0.0; coef[10 * nflux + f] = 0.0;
+        jt_c[f] = aKpc * mG / (2.0 * delta);
+        (void)mu; (void)lam; (void)law;
+        return;
+    }
     double dx, dy, dz, w = 1.0;
     if (f < ni) {
         const int N = nei[f];
@@ -257,6 +290,49 @@ __global__ void k_jt_diag(int nc, const int32_t* __restrict__ fo_ptr, const int3
     dinv_f[P] = (float)(1.0 / s);
 }
 
+// Cells with symmetry faces have the 3x3 diagonal block B = diag I - 2 sum_s c_s n_s n_s of J~
+// (Sec. 3.1): its inverse for block-Jacobi ([6][nc]: xx xy xz yy yz zz; 2-D keeps the plane
+// block and 1/diag in z), the unit normals of the symmetry faces, and for the segregated
+// solver the A = -J~ diagonal additions 2 sum_s c_s n_k^2 per component.
+__global__ void k_jt_block(int nc, int nf, int ni, int nd, int dim, const int32_t* __restrict__ fs_ptr,
+                           const double* __restrict__ Sf, const double* __restrict__ jt_c, const double* __restrict__ diag,
+                           double* __restrict__ binv, float* __restrict__ binv_f, double* __restrict__ symd,
+                           double* __restrict__ sym_n, int nsy)
+{
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= nc) return;
+    const double d = diag[P];
+    double b[6] = {d, 0.0, 0.0, d, 0.0, d};  // xx xy xz yy yz zz
+    double sd[3] = {0.0, 0.0, 0.0};
+    for (int f = fs_ptr[P]; f < fs_ptr[P + 1]; f++) {
+        const double gx = Sf[f], gy = Sf[nf + f], gz = Sf[2 * nf + f];
+        const double mg = sqrt(gx * gx + gy * gy + gz * gz);
+        const double n[3] = {gx / mg, gy / mg, gz / mg};
+        const int s = f - ni - nd;
+        for (int k = 0; k < 3; k++) sym_n[(size_t)k * nsy + s] = n[k];
+        const double c2 = 2.0 * jt_c[f];
+        b[0] -= c2 * n[0] * n[0]; b[1] -= c2 * n[0] * n[1]; b[2] -= c2 * n[0] * n[2];
+        b[3] -= c2 * n[1] * n[1]; b[4] -= c2 * n[1] * n[2]; b[5] -= c2 * n[2] * n[2];
+        for (int k = 0; k < 3; k++) sd[k] += c2 * n[k] * n[k];
+    }
+    double iv[6];
+    if (dim == 2) {
+        const double det = b[0] * b[3] - b[1] * b[1];
+        iv[0] = b[3] / det; iv[1] = -b[1] / det; iv[2] = 0.0; iv[3] = b[0] / det; iv[4] = 0.0; iv[5] = 1.0 / d;
+    } else {
+        const double c00 = b[3] * b[5] - b[4] * b[4], c01 = b[2] * b[4] - b[1] * b[5], c02 = b[1] * b[4] - b[2] * b[3];
+        const double det = b[0] * c00 + b[1] * c01 + b[2] * c02;
+        const double r = 1.0 / det;
+        iv[0] = c00 * r; iv[1] = c01 * r; iv[2] = c02 * r;
+        iv[3] = (b[0] * b[5] - b[2] * b[2]) * r; iv[4] = (b[1] * b[2] - b[0] * b[4]) * r; iv[5] = (b[0] * b[3] - b[1] * b[1]) * r;
+    }
+    for (int q = 0; q < 6; q++) {
+        binv[(size_t)q * nc + P] = iv[q];
+        binv_f[(size_t)q * nc + P] = (float)iv[q];
+    }
+    for (int k = 0; k < 3; k++) symd[(size_t)k * nc + P] = sd[k];
+}
+
 template <typename T>
 static T* upload(jfnk_ctx* c, const std::vector<T>& h)
 {
@@ -272,8 +348,8 @@ int setup_device_mesh(jfnk_ctx* c)
     const Topology& t = c->topo;
     DevMesh& m = c->dm;
     m.dim = c->hm.dim;
-    m.nc = t.nc; m.ni = t.ni; m.nd = t.nd; m.nt = t.nt; m.nf = t.nf;
-    m.nflux = t.ni + t.nd;
+    m.nc = t.nc; m.ni = t.ni; m.nd = t.nd; m.nsy = t.nsy; m.nt = t.nt; m.nf = t.nf;
+    m.nflux = t.ni + t.nd + t.nsy;
     m.n_slots = t.n_slots;
     m.n_slices = (t.nc + 31) / 32;
     m.pts = upload(c, c->hm.pts);
@@ -290,6 +366,7 @@ int setup_device_mesh(jfnk_ctx* c)
         m.fn_pos = upload(c, pos);
     }
     m.fd_ptr = upload(c, t.fd_ptr);
+    m.fs_ptr = upload(c, t.fs_ptr);
     m.ft_ptr = upload(c, t.ft_ptr);
     m.ca_ptr = upload(c, t.ca_ptr);
     m.ca_face = upload(c, t.ca_face);
@@ -313,7 +390,15 @@ int setup_device_mesh(jfnk_ctx* c)
     m.jt_dinv = (double*)jfnk_dalloc(c, sizeof(double) * (size_t)nc);
     m.jt_dinv_f = (float*)jfnk_dalloc(c, sizeof(float) * (size_t)nc);
     m.err = (int32_t*)jfnk_dalloc(c, sizeof(int32_t));
-    if (!m.pts || !m.fptr || !m.fpts || !m.own || !m.nei || !m.fo_ptr || !m.fn_ptr || !m.fn_face || !m.fn_pos || !m.fd_ptr ||
+    if (t.nsy > 0) {
+        m.jt_binv = (double*)jfnk_dalloc(c, sizeof(double) * 6 * (size_t)nc);
+        m.jt_binv_f = (float*)jfnk_dalloc(c, sizeof(float) * 6 * (size_t)nc);
+        m.seg_symd = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)nc);
+        m.sym_n = (double*)jfnk_dalloc(c, sizeof(double) * 3 * (size_t)t.nsy);
+        if (!m.jt_binv || !m.jt_binv_f || !m.seg_symd || !m.sym_n)
+            return jfnk_fail(c, JFNK_ENOMEM, "device allocation failed during mesh set-up");
+    }
+    if (!m.fs_ptr || !m.pts || !m.fptr || !m.fpts || !m.own || !m.nei || !m.fo_ptr || !m.fn_ptr || !m.fn_face || !m.fn_pos || !m.fd_ptr ||
         !m.ft_ptr || !m.ca_ptr || !m.ca_face || !m.sell_off || !m.sell_w || !m.sell_nbr || !m.sell_face || !m.n2o ||
         !m.bval || !m.sell_l || !m.Sf || !m.Cf || !m.V || !m.C || !m.coef || !m.b0 || !m.fb || !m.jt_c ||
         !m.jt_diag || !m.jt_dinv || !m.jt_dinv_f || !m.err)
@@ -323,8 +408,8 @@ int setup_device_mesh(jfnk_ctx* c)
     JF_LAUNCHED(c);
     k_cell_geom<<<blocks(nc, 256), 256, 0, s>>>(nc, nf, m.ca_ptr, m.ca_face, m.fptr, m.fpts, m.pts, m.Cf, m.V, m.C, m.err);
     JF_LAUNCHED(c);
-    k_cell_ls<<<blocks(nc, 128), 128, 0, s>>>(nc, nf, m.dim, m.sell_off, m.sell_w, m.sell_nbr, m.sell_face, m.Sf, m.C,
-                                              m.n_slots, m.sell_l, m.err);
+    k_cell_ls<<<blocks(nc, 128), 128, 0, s>>>(nc, nf, m.dim, m.sell_off, m.sell_w, m.sell_nbr, m.sell_face, m.Sf, m.Cf,
+                                              m.C, m.n_slots, m.sell_l, m.err);
     JF_LAUNCHED(c);
     int err = 0;
     JF_CUDA(c, cudaMemcpyAsync(&err, m.err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -345,8 +430,8 @@ int setup_material_coefficients(jfnk_ctx* c)
             for (int k = 0; k < 3; k++) fbs[(size_t)k * m.nc + P] = c->fb_host[(size_t)c->topo.n2o[P] * 3 + k];
     JF_CUDA(c, cudaMemcpyAsync(m.fb, fbs.data(), sizeof(double) * fbs.size(), cudaMemcpyHostToDevice, s));
     if (m.nflux > 0) {
-        k_flux_coef<<<blocks(m.nflux, 256), 256, 0, s>>>(m.ni, m.nflux, m.nf, m.nc, c->mat, c->cell_prob, m.own, m.nei,
-                                                         m.Sf, m.Cf, m.C, m.coef, m.jt_c);
+        k_flux_coef<<<blocks(m.nflux, 256), 256, 0, s>>>(m.ni, m.nd, m.nflux, m.nf, m.nc, c->mat, c->cell_prob, m.own,
+                                                         m.nei, m.Sf, m.Cf, m.C, m.coef, m.jt_c);
         JF_LAUNCHED(c);
     }
     k_cell_b0<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.nf, m.ni, m.nd, m.ft_ptr, m.Sf, m.bval, m.V, m.fb, m.dim, m.b0);
@@ -355,6 +440,11 @@ int setup_material_coefficients(jfnk_ctx* c)
     k_jt_diag<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.fo_ptr, m.fn_ptr, m.fn_face, m.fd_ptr, m.jt_c, m.V, mass,
                                                  m.jt_diag, m.jt_dinv, m.jt_dinv_f);
     JF_LAUNCHED(c);
+    if (m.nsy > 0) {
+        k_jt_block<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.nf, m.ni, m.nd, m.dim, m.fs_ptr, m.Sf, m.jt_c, m.jt_diag,
+                                                     m.jt_binv, m.jt_binv_f, m.seg_symd, m.sym_n, m.nsy);
+        JF_LAUNCHED(c);
+    }
     JF_CUDA(c, cudaStreamSynchronize(s));
     return JFNK_OK;
 }

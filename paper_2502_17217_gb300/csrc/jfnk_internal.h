@@ -29,10 +29,11 @@ struct HostMesh {
 // Internal (device) numbering: cells renumbered, faces reordered into
 //   [0, ni)                internal faces, sorted by (owner, neighbour), owner < neighbour
 //   [ni, ni + nd)          displacement faces, sorted by owner
-//   [ni + nd, ni + nd + nt) traction faces, sorted by owner
+//   [ni + nd, .. + nsy)    symmetry faces, sorted by owner
+//   [.., .. + nt)          traction faces, sorted by owner
 //   [.., nf)               empty faces
 struct Topology {
-    int nc = 0, ni = 0, nd = 0, nt = 0, ne = 0, nf = 0;
+    int nc = 0, ni = 0, nd = 0, nsy = 0, nt = 0, ne = 0, nf = 0;
     std::vector<int32_t> n2o, o2n;           // cell permutation
     std::vector<int32_t> face_src;           // new face -> input face
     std::vector<uint8_t> face_flip;          // 1 if the point loop was reversed
@@ -41,13 +42,15 @@ struct Topology {
     std::vector<int32_t> fo_ptr;             // [nc+1] internal faces owned by each cell
     std::vector<int32_t> fn_ptr, fn_face;    // [nc+1], [ni] internal faces whose neighbour is the cell
     std::vector<int32_t> fd_ptr;             // [nc+1] displacement faces (absolute indices)
+    std::vector<int32_t> fs_ptr;             // [nc+1] symmetry faces (absolute indices)
     std::vector<int32_t> ft_ptr;             // [nc+1] traction faces (absolute indices)
     std::vector<int32_t> ca_ptr, ca_face;    // all faces of each cell; ~f marks the neighbour side
-    // sliced-ELL (32 cells per slice) list of the internal neighbours of each cell
+    // sliced-ELL (32 cells per slice) list of the internal neighbours of each cell, then its
+    // symmetry faces (the mirror neighbour, coded nc + symmetry-face index)
     std::vector<int32_t> sell_off, sell_w;   // per slice: first slot, width (slots per lane)
     std::vector<int32_t> sell_nbr, sell_face;// per slot: neighbour cell (-1 = padding), face
     int n_slots = 0;
-    std::vector<double> bval;                // [nd + nt][3] boundary values in new face order
+    std::vector<double> bval;                // [nd + nsy + nt][3] boundary values in new face order
     int bandwidth = 0;
 };
 
@@ -71,11 +74,13 @@ std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels,
 
 // ------------------------------------------------------------------ device state
 struct DevMesh {
-    int dim = 3, nc = 0, ni = 0, nd = 0, nt = 0, nf = 0, nflux = 0, n_slots = 0, n_slices = 0;
+    int dim = 3, nc = 0, ni = 0, nd = 0, nsy = 0, nt = 0, nf = 0, nflux = 0, n_slots = 0, n_slices = 0;
     double* pts = nullptr;
     int32_t *fptr = nullptr, *fpts = nullptr;
     int32_t *own = nullptr, *nei = nullptr;
     int32_t *fo_ptr = nullptr, *fn_ptr = nullptr, *fn_face = nullptr, *fd_ptr = nullptr, *ft_ptr = nullptr;
+    int32_t* fs_ptr = nullptr;       // [nc+1] symmetry faces of each cell
+    double* sym_n = nullptr;         // [3][nsy] unit outward normals of the symmetry faces
     int32_t* fn_pos = nullptr;       // [ni] position of each internal face in the neighbour-sorted list
     int32_t *ca_ptr = nullptr, *ca_face = nullptr;
     int32_t *sell_off = nullptr, *sell_w = nullptr, *sell_nbr = nullptr, *sell_face = nullptr;
@@ -83,13 +88,18 @@ struct DevMesh {
     double *Sf = nullptr, *Cf = nullptr;   // [3][nf]
     double *V = nullptr, *C = nullptr;     // [nc], [3][nc]
     double* coef = nullptr;          // [11][nflux] face coefficients of the residual
-    double* bval = nullptr;          // [3][nd + nt] boundary values (unscaled)
+    double* bval = nullptr;          // [nd + nsy + nt][3] boundary values (unscaled)
     double* b0 = nullptr;            // [3][nc] body force + traction (unscaled)
     double* fb = nullptr;            // [3][nc] body force density
-    double* jt_c = nullptr;          // [nflux] J~ face coefficients (internal and displacement)
-    double* jt_diag = nullptr;       // [nc]
+    double* jt_c = nullptr;          // [nflux] J~ face coefficients (internal, displacement, symmetry)
+    double* jt_diag = nullptr;       // [nc] scalar part of the diagonal blocks
     double* jt_dinv = nullptr;       // [nc] 1 / diag
     float* jt_dinv_f = nullptr;      // [nc]
+    // with symmetry faces: inverses of the 3x3 diagonal blocks diag I - 2 sum c n n, [6][nc]
+    // (xx xy xz yy yz zz), and the blocks' diagonals in A = -J~ form for the segregated solver
+    double* jt_binv = nullptr;
+    float* jt_binv_f = nullptr;
+    double* seg_symd = nullptr;      // [3][nc] sum 2 c n_k^2
     int32_t* n2o = nullptr;
     int32_t* err = nullptr;          // set-up error word
 };

@@ -35,6 +35,25 @@ __global__ void k_bjacobi(const int* gate, int nc, const TV* __restrict__ base, 
     for (int k = 0; k < 3; k++) z[(size_t)k * nc + P] = to_f64((TP)v[(size_t)k * nc + P] * d);
 }
 
+// block-Jacobi with the 3x3 diagonal blocks of cells on symmetry faces (symmetric inverse
+// [6][nc]: xx xy xz yy yz zz; the other cells' blocks are diag I)
+template <typename TV, typename TP>
+__global__ void k_bjacobi_block(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
+                                const TP* __restrict__ binv, double* __restrict__ z)
+{
+    JF_PDL_ENTRY();
+    if (gate && *gate) return;
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= nc) return;
+    const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
+    const TP v0 = (TP)v[P], v1 = (TP)v[nc + P], v2 = (TP)v[2 * (size_t)nc + P];
+    const TP b0 = binv[P], b1 = binv[nc + P], b2 = binv[2 * (size_t)nc + P];
+    const TP b3 = binv[3 * (size_t)nc + P], b4 = binv[4 * (size_t)nc + P], b5 = binv[5 * (size_t)nc + P];
+    z[P] = to_f64(b0 * v0 + b1 * v1 + b2 * v2);
+    z[nc + P] = to_f64(b1 * v0 + b3 * v1 + b4 * v2);
+    z[2 * (size_t)nc + P] = to_f64(b2 * v0 + b4 * v1 + b5 * v2);
+}
+
 template <typename TV>
 __global__ void k_copy_vec(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
                            double* __restrict__ z)
@@ -646,7 +665,18 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
     cudaStream_t s = c->cur;
     int sl = c->prof.enabled ? c->prof.slot(pc == JFNK_PC_MG ? "pc_mg" : "pc_bjacobi") : -1;
     jfnk_prof_begin(c, sl);
-    if (pc == JFNK_PC_BJACOBI) {
+    if (pc == JFNK_PC_BJACOBI && c->dm.jt_binv) {
+        const double* bd = c->dm.jt_binv;
+        const float* bf = c->dm.jt_binv_f;
+        if (v_is_float) {
+            if (fp32) jfnk_launch(c, k_bjacobi_block<float, float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, bf, z);
+            else jfnk_launch(c, k_bjacobi_block<float, double>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, bd, z);
+        } else {
+            if (fp32) jfnk_launch(c, k_bjacobi_block<double, float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const double*)vbase, ld, jidx, bf, z);
+            else jfnk_launch(c, k_bjacobi_block<double, double>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const double*)vbase, ld, jidx, bd, z);
+        }
+        JF_LAUNCHED(c);
+    } else if (pc == JFNK_PC_BJACOBI) {
         if (v_is_float) {
             if (fp32) jfnk_launch(c, k_bjacobi<float, float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, c->dm.jt_dinv_f, z);
             else jfnk_launch(c, k_bjacobi<float, double>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, c->dm.jt_dinv, z);

@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
                                               const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
                                               const double* __restrict__ sell_l, int n_slots,
                                               const double* __restrict__ u, double* __restrict__ G,
-                                              double* __restrict__ T, MatDev mat, const int32_t* __restrict__ cell_prob)
+                                              double* __restrict__ T, MatDev mat, const int32_t* __restrict__ cell_prob,
+                                              const double* __restrict__ sym_n, int nsy)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
@@ -39,7 +40,15 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
         const int N = sell_nbr[slot];
         if (N < 0) break;
         const double l0 = sell_l[slot], l1 = sell_l[n_slots + slot], l2 = sell_l[2 * n_slots + slot];
-        const double d0 = u[N] - u0, d1 = u[nc + N] - u1, d2 = u[2 * nc + N] - u2;
+        double d0, d1, d2;
+        if (N < nc) {
+            d0 = u[N] - u0; d1 = u[nc + N] - u1; d2 = u[2 * nc + N] - u2;
+        } else {  // symmetry face: the mirror value R u_P - u_P = -2 (n . u_P) n
+            const int q = N - nc;
+            const double n0 = sym_n[q], n1 = sym_n[nsy + q], n2 = sym_n[2 * nsy + q];
+            const double m2 = -2.0 * (n0 * u0 + n1 * u1 + n2 * u2);
+            d0 = m2 * n0; d1 = m2 * n1; d2 = m2 * n2;
+        }
         g[0] = fma(l0, d0, g[0]); g[1] = fma(l0, d1, g[1]); g[2] = fma(l0, d2, g[2]);
         g[3] = fma(l1, d0, g[3]); g[4] = fma(l1, d1, g[4]); g[5] = fma(l1, d2, g[5]);
         g[6] = fma(l2, d0, g[6]); g[7] = fma(l2, d1, g[7]); g[8] = fma(l2, d2, g[8]);
@@ -127,7 +136,7 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
 // block spans the internal/boundary split or cells without faces, and those read global
 // memory.  Same arithmetic either way.
 template <int LAW, int BS, int STAGE>
-__global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int ni, int nflux, int nc, const int32_t* __restrict__ own,
+__global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int ni, int nd, int nflux, int nc, const int32_t* __restrict__ own,
                                              const int32_t* __restrict__ nei, const double* __restrict__ coef,
                                              const double* __restrict__ u, const double* __restrict__ G,
                                              const double* __restrict__ T, const double* __restrict__ bval,
@@ -155,6 +164,41 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
         __syncthreads();
     }
     if (f >= nflux) return;
+    if (f >= ni + nd) {
+        // symmetry face (Eq. symm read as the mirror mean (T_P + R T_P R) / 2; Rhie-Chow with the
+        // mirror neighbour at 2 delta n): t = Gamma [n.T_P.n - alpha Kbar ((n.u_P) / delta + n.G_P.n)]
+        const int P = own[f];
+        const double aK = coef[f], idelta = coef[nflux + f];
+        const double n0 = coef[5 * (size_t)nflux + f], n1 = coef[6 * (size_t)nflux + f], n2 = coef[7 * (size_t)nflux + f];
+        const double nv[3] = {n0, n1, n2};
+        double Gnn = 0.0, Tnn = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            double gi = 0.0;
+#pragma unroll
+            for (int j = 0; j < 3; j++) gi = fma(G[(size_t)(3 * i + j) * nc + P], nv[j], gi);
+            Gnn = fma(nv[i], gi, Gnn);
+        }
+        const int pr = cell_prob[P];
+        const bool hooke_s = (LAW == JFNK_LAW_LINEAR) || (LAW == 2 && mat.law[pr] == JFNK_LAW_LINEAR);
+        if (hooke_s) {
+            const double tr = G[P] + G[4 * (size_t)nc + P] + G[8 * (size_t)nc + P];
+            Tnn = 2.0 * mat.mu[pr] * Gnn + mat.lam[pr] * tr;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                double ti = 0.0;
+#pragma unroll
+                for (int j = 0; j < 3; j++) ti = fma(T[(size_t)(3 * i + j) * nc + P], nv[j], ti);
+                Tnn = fma(nv[i], ti, Tnn);
+            }
+        }
+        const double un = n0 * u[P] + n1 * u[nc + P] + n2 * u[2 * (size_t)nc + P];
+        const double sc = Tnn - aK * fma(un, idelta, Gnn);
+#pragma unroll
+        for (int c = 0; c < 3; c++) F[(size_t)c * nflux + f] = coef[(size_t)(2 + c) * nflux + f] * sc;
+        return;
+    }
     const double load = *load_dev;
     const int P = own[f];
     const bool internal = f < ni;
@@ -241,7 +285,8 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
 // R_P -= Omega_P (mk u_P + rc_P), mk = 9 rho / (4 dt^2), rc = rho c from the previous levels.
 __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int dim, const int32_t* __restrict__ fo_ptr,
                                                 const int32_t* __restrict__ fn_ptr, const double* __restrict__ Fn,
-                                                const int32_t* __restrict__ fd_ptr, const double* __restrict__ F,
+                                                const int32_t* __restrict__ fd_ptr, const int32_t* __restrict__ fs_ptr,
+                                                const double* __restrict__ F,
                                                 const double* __restrict__ b0, const double* __restrict__ load_dev, int mode,
                                                 const double* __restrict__ Ru, const ProbDev* __restrict__ pd,
                                                 const int32_t* __restrict__ cell_prob, const int* __restrict__ gate,
@@ -261,6 +306,9 @@ __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int d
         r0 -= Fn[k]; r1 -= Fn[ni + k]; r2 -= Fn[2 * (size_t)ni + k];
     }
     for (int f = fd_ptr[P]; f < fd_ptr[P + 1]; f++) {
+        r0 += F[f]; r1 += F[nflux + f]; r2 += F[2 * (size_t)nflux + f];
+    }
+    for (int f = fs_ptr[P]; f < fs_ptr[P + 1]; f++) {
         r0 += F[f]; r1 += F[nflux + f]; r2 += F[2 * (size_t)nflux + f];
     }
     if (rc) {
@@ -318,7 +366,8 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     const Tuning& tu = c->tune;
 #define JF_GRAD_BS(LAW_, BS_)                                                                                   \
     jfnk_launch(c, k_grad<LAW_, BS_>, dim3(nblk(m.nc, BS_)), dim3(BS_), gate, m.nc, m.dim, m.sell_off, m.sell_w, \
-                m.sell_nbr, m.sell_l, m.n_slots, u_int, G, T, c->mat, (const int32_t*)c->cell_prob)
+                m.sell_nbr, m.sell_l, m.n_slots, u_int, G, T, c->mat, (const int32_t*)c->cell_prob,   \
+                (const double*)m.sym_n, m.nsy)
 #define JF_GRAD(LAW_)                                     \
     do {                                                  \
         if (tu.grad_bs == 64) JF_GRAD_BS(LAW_, 64);       \
@@ -335,7 +384,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     if (m.nflux > 0) {
         jfnk_prof_begin(c, sl[1]);
 #define JF_FLUX_BS(LAW_, BS_, ST_)                                                                                      \
-    jfnk_launch(c, k_flux<LAW_, BS_, ST_>, dim3(nblk(m.nflux, BS_)), dim3(BS_), gate, m.ni, m.nflux, m.nc, m.own, m.nei, \
+    jfnk_launch(c, k_flux<LAW_, BS_, ST_>, dim3(nblk(m.nflux, BS_)), dim3(BS_), gate, m.ni, m.nd, m.nflux, m.nc, m.own, m.nei, \
                 m.coef, u_int, (const double*)G, (const double*)T, m.bval, (const double*)&c->gdev->load, m.fn_pos,   \
                 c->mat, (const int32_t*)c->cell_prob, F, Fn)
 #define JF_FLUX(LAW_)                                                        \
@@ -357,7 +406,8 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
         jfnk_prof_end(c, sl[1]);
     }
     jfnk_prof_begin(c, sl[2]);
-    jfnk_launch(c, k_finish, dim3(nblk(m.nc, tu.finish_bs)), dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr, F, m.b0,
+    jfnk_launch(c, k_finish, dim3(nblk(m.nc, tu.finish_bs)), dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr,
+                (const int32_t*)m.fs_ptr, (const double*)F, m.b0,
                                             &c->gdev->load, mode, c->Ru, c->pd, c->cell_prob, gate, u_int, (const double*)m.V,
                 (const double*)(c->dyn_on ? c->dyn_rc : nullptr), c->dyn_mk, out);
     JF_LAUNCHED(c);

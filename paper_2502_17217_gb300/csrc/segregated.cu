@@ -192,8 +192,8 @@ __global__ void k_seg_count(const SegSlot* sl, int nslots, GlobalDev* gdev)
 __global__ void k_seg_apply(int nc, const int32_t* __restrict__ fo_ptr, const int32_t* __restrict__ fn_ptr,
                             const int32_t* __restrict__ fn_face, const int32_t* __restrict__ own,
                             const int32_t* __restrict__ nei, const double* __restrict__ jc,
-                            const double* __restrict__ jdiag, const double* __restrict__ d,
-                            const GlobalDev* gdev, double* __restrict__ q)
+                            const double* __restrict__ jdiag, const double* __restrict__ symd,
+                            const double* __restrict__ d, const GlobalDev* gdev, double* __restrict__ q)
 {
     JF_PDL_ENTRY();
     if (gdev->all_done) return;
@@ -201,6 +201,11 @@ __global__ void k_seg_apply(int nc, const int32_t* __restrict__ fo_ptr, const in
     if (P >= nc) return;
     const double a = -jdiag[P];
     double o0 = a * d[P], o1 = a * d[nc + P], o2 = a * d[2 * (size_t)nc + P];
+    if (symd) {  // symmetry faces: the component's own part of the n n block (Sec. 3.1)
+        o0 = fma(symd[P], d[P], o0);
+        o1 = fma(symd[nc + P], d[nc + P], o1);
+        o2 = fma(symd[2 * (size_t)nc + P], d[2 * (size_t)nc + P], o2);
+    }
     for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) {
         const int N = nei[f];
         const double cf = jc[f];
@@ -279,7 +284,8 @@ static int seg_enqueue_iteration(jfnk_ctx* c)
     JF_LAUNCHED(c);
     const DevMesh& m = c->dm;
     jfnk_launch(c, k_seg_apply, dim3(nblk(m.nc, 256)), dim3(256), m.nc, m.fo_ptr, m.fn_ptr, m.fn_face, m.own, m.nei,
-                (const double*)m.jt_c, (const double*)m.jt_diag, (const double*)c->x, (const GlobalDev*)c->gdev, c->tmp);
+                (const double*)m.jt_c, (const double*)m.jt_diag, (const double*)m.seg_symd, (const double*)c->x,
+                (const GlobalDev*)c->gdev, c->tmp);
     JF_LAUNCHED(c);
     jfnk_launch(c, k_seg_dot<2>, dim3(c->n_chunks), dim3(kChunkThreads), ch, (const double*)c->x, (const double*)c->tmp,
                 (double*)nullptr, (double*)nullptr, (const ProbDev*)c->pd, c->seg_state, c->partials, c->gdev, zsign);

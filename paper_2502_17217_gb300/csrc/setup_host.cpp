@@ -80,18 +80,19 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     std::sort(in.begin(), in.end(), [](const FK& x, const FK& y) {
         return x.a != y.a ? x.a < y.a : (x.b != y.b ? x.b < y.b : x.src < y.src);
     });
-    std::vector<FK> bd[3];  // disp, trac, empty
+    std::vector<FK> bd[4];  // disp, symm, trac, empty
     for (int f = ni; f < nf; f++) {
         int bt = hm.btype[f - ni];
-        int cls = bt == JFNK_BC_DISP ? 0 : (bt == JFNK_BC_TRAC ? 1 : 2);
+        int cls = bt == JFNK_BC_DISP ? 0 : (bt == JFNK_BC_SYMM ? 1 : (bt == JFNK_BC_TRAC ? 2 : 3));
         bd[cls].push_back({t.o2n[hm.own[f]], -1, f, 0});
     }
     for (auto& v : bd)
         std::sort(v.begin(), v.end(), [](const FK& x, const FK& y) { return x.a != y.a ? x.a < y.a : x.src < y.src; });
     t.ni = ni;
     t.nd = (int)bd[0].size();
-    t.nt = (int)bd[1].size();
-    t.ne = (int)bd[2].size();
+    t.nsy = (int)bd[1].size();
+    t.nt = (int)bd[2].size();
+    t.ne = (int)bd[3].size();
     t.nf = nf;
     std::vector<FK> all;
     all.reserve(nf);
@@ -129,7 +130,8 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     };
     ranges(0, ni, t.fo_ptr);
     ranges(ni, ni + t.nd, t.fd_ptr);
-    ranges(ni + t.nd, ni + t.nd + t.nt, t.ft_ptr);
+    ranges(ni + t.nd, ni + t.nd + t.nsy, t.fs_ptr);
+    ranges(ni + t.nd + t.nsy, ni + t.nd + t.nsy + t.nt, t.ft_ptr);
     // neighbour-sorted internal faces
     t.fn_ptr.assign(nc + 1, 0);
     for (int f = 0; f < ni; f++) t.fn_ptr[t.nei[f] + 1]++;
@@ -157,6 +159,7 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     // sliced ELL of internal neighbours (32 cells per slice), faces in increasing index
     std::vector<int32_t> cnt(nc, 0);
     for (int f = 0; f < ni; f++) { cnt[t.own[f]]++; cnt[t.nei[f]]++; }
+    for (int f = ni + t.nd; f < ni + t.nd + t.nsy; f++) cnt[t.own[f]]++;
     const int ns = (nc + 31) / 32;
     t.sell_off.resize(ns + 1);
     t.sell_w.resize(ns);
@@ -187,10 +190,16 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
             t.sell_face[slot] = f;
             k[P]++;
         }
+        for (int f = t.fs_ptr[P]; f < t.fs_ptr[P + 1]; f++) {  // mirror neighbours
+            int slot = t.sell_off[s] + 32 * k[P] + lane;
+            t.sell_nbr[slot] = nc + (f - ni - t.nd);
+            t.sell_face[slot] = f;
+            k[P]++;
+        }
     }
     // boundary values in the new face order
-    t.bval.assign((size_t)(t.nd + t.nt) * 3, 0.0);
-    for (int f = ni; f < ni + t.nd + t.nt; f++)
+    t.bval.assign((size_t)(t.nd + t.nsy + t.nt) * 3, 0.0);
+    for (int f = ni; f < ni + t.nd + t.nsy + t.nt; f++)
         for (int c = 0; c < 3; c++) t.bval[(size_t)(f - ni) * 3 + c] = hm.bval[(size_t)(t.face_src[f] - ni) * 3 + c];
     return "";
 }

@@ -297,7 +297,7 @@ def test_invalid_inputs_fail_cleanly():
         jfnk.Solver(bad, I.Material(I.LAW_LINEAR, 1.0, 0.3))
     s = jfnk.Solver(m, I.Material(I.LAW_LINEAR, 1.0, 0.3))
     with pytest.raises(jfnk.JfnkError):
-        s._check(s.L.jfnk_set_patch(s.h, m.patch("xmin").start, 3, jfnk.BC_SYMM, None))
+        s._check(s.L.jfnk_set_patch(s.h, m.patch("xmin").start, 3, 7, None))  # unknown type
     with pytest.raises(jfnk.JfnkError):
         s._check(s.L.jfnk_set_material(s.h, jfnk.LAW_LINEAR, -1.0, 0.3))
     # a one-cell-wide direction gives a singular least-squares tensor
