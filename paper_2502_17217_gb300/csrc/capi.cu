@@ -633,8 +633,6 @@ int jfnk_solve(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* st
 
 }  // extern "C"
 
-int jfnk_solve_dynamic_impl(jfnk_ctx* c, int n_steps, int32_t probe_cell, double* probe, jfnk_stats* st, int method);
-
 extern "C" int jfnk_solve_dynamic(jfnk_ctx* c, double* u, int mem, int n_steps, int32_t probe_cell, double* probe,
                                   int method, jfnk_stats* stats, void* stream)
 {
@@ -645,7 +643,7 @@ extern "C" int jfnk_solve_dynamic(jfnk_ctx* c, double* u, int mem, int n_steps, 
     jfnk_stats local;
     jfnk_stats* st = stats ? stats : &local;
     const double saved_load = c->load;
-    int status = jfnk_solve_dynamic_impl(c, n_steps, probe_cell, probe, st, method);
+    int status = jfnk::solve_dynamic(c, n_steps, probe_cell, probe, st, method);
     c->load = saved_load;
     if (status == JFNK_ECUDA || status == JFNK_ENOMEM || status == JFNK_ESTATE || status == JFNK_EINVAL) return status;
     if ((rc = store_vec(c, c->u, mem, u))) return rc;

@@ -69,6 +69,37 @@ __device__ __forceinline__ double reduce_partials(const double* partials, int n,
     return block_sum(s, sh);
 }
 
+// Of the `expected` blocks that arrive at `ticket` (each after storing its partials), the
+// last returns true; it then reads the partials with __ldcg and resets the ticket.
+__device__ __forceinline__ bool ticket_last(unsigned* ticket, unsigned expected)
+{
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == expected - 1);
+    __syncthreads();
+    return is_last;
+}
+
+// Sum of p[0..count) over one warp in a fixed order, four loads in flight per lane (the
+// final sums of a reduction sit on the critical path of every Krylov iteration, so they are
+// issued together rather than one dependent L2 round trip at a time); valid in lane 0.
+__device__ __forceinline__ double warp_sum_strided(const double* p, int count)
+{
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b0 = 0; b0 < count; b0 += 128) {
+        double t[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int b = b0 + 32 * k + lane;
+            t[k] = b < count ? __ldcg(p + b) : 0.0;
+        }
+        s += (t[0] + t[1]) + (t[2] + t[3]);
+    }
+    return warp_sum(s);
+}
+
 // float -> double without the FP64 pipe (on GB300 a conversion costs as much as a DFMA):
 // the exponent is re-biased and the mantissa shifted with integer operations.  Exact for
 // normal floats and zero; float subnormals (|x| < 1.2e-38) become zero; Inf/NaN become NaN.

@@ -92,9 +92,10 @@ extern "C" int jfnk_dynamic_reset(jfnk_ctx* c)
     return JFNK_OK;
 }
 
-int jfnk_solve_dynamic_impl(jfnk_ctx* c, int n_steps, int32_t probe_cell, double* probe, jfnk_stats* st, int method)
+namespace jfnk {
+
+int solve_dynamic(jfnk_ctx* c, int n_steps, int32_t probe_cell, double* probe, jfnk_stats* st, int method)
 {
-    using namespace jfnk;
     if (!c->dyn_on) return jfnk_fail(c, JFNK_ESTATE, "jfnk_solve_dynamic: options.density is 0 (static context)");
     const size_t n = 3 * (size_t)c->dm.nc;
     const int nc = c->dm.nc;
@@ -142,3 +143,5 @@ int jfnk_solve_dynamic_impl(jfnk_ctx* c, int n_steps, int32_t probe_cell, double
     }
     return status;
 }
+
+}  // namespace jfnk

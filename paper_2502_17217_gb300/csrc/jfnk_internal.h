@@ -360,6 +360,7 @@ int pc_setup(jfnk_ctx* c);
 int autotune(jfnk_ctx* c);               // launch shapes for this mesh (autotune.cu)
 int segregated(jfnk_ctx* c, int n_load_steps, jfnk_stats* st);  // Sec. 3.1 (segregated.cu)
 int dynamics_setup(jfnk_ctx* c);       // history buffers at rest (dynamics.cu)
+int solve_dynamic(jfnk_ctx* c, int n_steps, int32_t probe_cell, double* probe, jfnk_stats* st, int method);
 bool tuning_valid(const Tuning& t);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);

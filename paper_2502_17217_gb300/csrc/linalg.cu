@@ -63,31 +63,7 @@ __device__ __forceinline__ bool skip_problem(const ProbDev& P) { return !P.activ
 // partials); it must reset the ticket.
 __device__ __forceinline__ bool last_of_problem(unsigned* ticket, unsigned expected)
 {
-    __shared__ bool is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == expected - 1);
-    __syncthreads();
-    return is_last;
-}
-
-// Sum of p[0..count) over one warp in a fixed order, four loads in flight per lane (the
-// final sums of a reduction sit on the critical path of every Krylov iteration, so they are
-// issued together rather than one dependent L2 round trip at a time); valid in lane 0.
-__device__ __forceinline__ double warp_sum_strided(const double* p, int count)
-{
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int b0 = 0; b0 < count; b0 += 128) {
-        double t[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int b = b0 + 32 * k + lane;
-            t[k] = b < count ? __ldcg(p + b) : 0.0;
-        }
-        s += (t[0] + t[1]) + (t[2] + t[3]);
-    }
-    return warp_sum(s);
+    return ticket_last(ticket, expected);
 }
 
 // Sum of one problem's chunk partials (fixed order), by one warp; valid in lane 0.

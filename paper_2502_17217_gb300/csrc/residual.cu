@@ -34,24 +34,36 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
     double g[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) g[q] = 0.0;
+    // internal neighbours first; a cell's symmetry faces (mirror neighbours, coded N >= nc)
+    // follow them in its slot list and are taken in a second loop, so meshes without
+    // symmetry faces run the first loop alone
+    int k = 0;
 #pragma unroll 2
-    for (int k = 0; k < w; k++) {
+    for (; k < w; k++) {
         const int slot = base + 32 * k + lane;
         const int N = sell_nbr[slot];
-        if (N < 0) break;
+        if ((unsigned)N >= (unsigned)nc) break;  // padding (-1) or a mirror neighbour
         const double l0 = sell_l[slot], l1 = sell_l[n_slots + slot], l2 = sell_l[2 * n_slots + slot];
-        double d0, d1, d2;
-        if (N < nc) {
-            d0 = u[N] - u0; d1 = u[nc + N] - u1; d2 = u[2 * nc + N] - u2;
-        } else {  // symmetry face: the mirror value R u_P - u_P = -2 (n . u_P) n
-            const int q = N - nc;
-            const double n0 = sym_n[q], n1 = sym_n[nsy + q], n2 = sym_n[2 * nsy + q];
-            const double m2 = -2.0 * (n0 * u0 + n1 * u1 + n2 * u2);
-            d0 = m2 * n0; d1 = m2 * n1; d2 = m2 * n2;
-        }
+        const double d0 = u[N] - u0, d1 = u[nc + N] - u1, d2 = u[2 * nc + N] - u2;
         g[0] = fma(l0, d0, g[0]); g[1] = fma(l0, d1, g[1]); g[2] = fma(l0, d2, g[2]);
         g[3] = fma(l1, d0, g[3]); g[4] = fma(l1, d1, g[4]); g[5] = fma(l1, d2, g[5]);
         g[6] = fma(l2, d0, g[6]); g[7] = fma(l2, d1, g[7]); g[8] = fma(l2, d2, g[8]);
+    }
+    if (nsy > 0) {
+        for (; k < w; k++) {
+            const int slot = base + 32 * k + lane;
+            const int N = sell_nbr[slot];
+            if (N < 0) break;
+            // symmetry face: the mirror value R u_P - u_P = -2 (n . u_P) n
+            const double l0 = sell_l[slot], l1 = sell_l[n_slots + slot], l2 = sell_l[2 * n_slots + slot];
+            const int q = N - nc;
+            const double n0 = sym_n[q], n1 = sym_n[nsy + q], n2 = sym_n[2 * nsy + q];
+            const double m2 = -2.0 * (n0 * u0 + n1 * u1 + n2 * u2);
+            const double d0 = m2 * n0, d1 = m2 * n1, d2 = m2 * n2;
+            g[0] = fma(l0, d0, g[0]); g[1] = fma(l0, d1, g[1]); g[2] = fma(l0, d2, g[2]);
+            g[3] = fma(l1, d0, g[3]); g[4] = fma(l1, d1, g[4]); g[5] = fma(l1, d2, g[5]);
+            g[6] = fma(l2, d0, g[6]); g[7] = fma(l2, d1, g[7]); g[8] = fma(l2, d2, g[8]);
+        }
     }
 #pragma unroll
     for (int q = 0; q < 9; q++) G[(size_t)q * nc + P] = g[q];

@@ -36,32 +36,6 @@ struct SlotChunks {
     const int32_t* scnt;   // chunks of each slot
 };
 
-__device__ __forceinline__ bool slot_last(unsigned* ticket, unsigned expected)
-{
-    __shared__ bool is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == expected - 1);
-    __syncthreads();
-    return is_last;
-}
-
-__device__ __forceinline__ double slot_sum(const double* p, int count)
-{
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int b0 = 0; b0 < count; b0 += 128) {
-        double t[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int b = b0 + 32 * k + lane;
-            t[k] = b < count ? __ldcg(p + b) : 0.0;
-        }
-        s += (t[0] + t[1]) + (t[2] + t[3]);
-    }
-    return warp_sum(s);
-}
-
 __device__ void slot_finish(SegSlot& S, GlobalDev* gdev)
 {
     S.done = 1;
@@ -100,9 +74,9 @@ __global__ void __launch_bounds__(kChunkThreads) k_seg_dot(SlotChunks ch, const 
     }
     a = block_sum(a, sh);
     if (threadIdx.x == 0) partials[c] = a;
-    if (!slot_last(&S.ticket, (unsigned)ch.scnt[s])) return;
+    if (!ticket_last(&S.ticket, (unsigned)ch.scnt[s])) return;
     if (threadIdx.x < 32) {
-        const double tot = slot_sum(partials + ch.sbeg[s], ch.scnt[s]);
+        const double tot = warp_sum_strided(partials + ch.sbeg[s], ch.scnt[s]);
         if (threadIdx.x == 0) {
             if (MODE == 0) {
                 S.rr0 = sqrt(tot);
@@ -165,9 +139,9 @@ __global__ void __launch_bounds__(kChunkThreads) k_seg_update(SlotChunks ch, con
     }
     a = block_sum(a, sh);
     if (threadIdx.x == 0) partials[c] = a;
-    if (!slot_last(&S.ticket, (unsigned)ch.scnt[s])) return;
+    if (!ticket_last(&S.ticket, (unsigned)ch.scnt[s])) return;
     if (threadIdx.x < 32) {
-        const double tot = slot_sum(partials + ch.sbeg[s], ch.scnt[s]);
+        const double tot = warp_sum_strided(partials + ch.sbeg[s], ch.scnt[s]);
         if (threadIdx.x == 0) {
             S.rr = sqrt(tot);
             S.its++;

@@ -274,10 +274,13 @@ class Solver:
         """The segregated quasi-Newton solve of Sec. 3.1 (the paper's comparison method);
         returns (u, stats, status) as solve(); stats.newton_its = outer iterations,
         stats.gmres_its = conjugate-gradient iterations."""
-        return self.solve(u0, load_steps, raise_on_fail, _fn="jfnk_solve_segregated")
+        return self._solve_with(self.L.jfnk_solve_segregated, u0, load_steps, raise_on_fail)
 
-    def solve(self, u0=None, load_steps=1, raise_on_fail=True, _fn="jfnk_solve"):
+    def solve(self, u0=None, load_steps=1, raise_on_fail=True):
         """Newton solve; returns (u, stats, status).  u0: numpy or torch CUDA tensor (copied)."""
+        return self._solve_with(self.L.jfnk_solve, u0, load_steps, raise_on_fail)
+
+    def _solve_with(self, fn, u0, load_steps, raise_on_fail):
         if u0 is None:
             u = np.zeros((self.nc, 3))
         elif _is_device(u0):
@@ -286,7 +289,7 @@ class Solver:
             u = np.array(u0, dtype=np.float64).reshape(self.nc, 3)
         st = Stats()
         mem, s = self._io(u)
-        rc = getattr(self.L, _fn)(self.h, _ptr(u), mem, int(load_steps), C.byref(st), s)
+        rc = fn(self.h, _ptr(u), mem, int(load_steps), C.byref(st), s)
         if rc != OK and raise_on_fail and rc not in (MAXIT, LS_FAILED, DIVERGED):
             self._check(rc)
         return u, st, rc
