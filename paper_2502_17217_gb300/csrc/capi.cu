@@ -30,10 +30,46 @@ void* jfnk_dalloc(jfnk_ctx* c, size_t bytes)
         cudaGetLastError();
         return nullptr;
     }
-    cudaMemset(p, 0, bytes);
+    if (cudaMemsetAsync(p, 0, bytes, c->cur ? c->cur : c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        return nullptr;
+    }
     c->allocs.push_back(p);
     c->dev_bytes += (int64_t)bytes;
     return p;
+}
+
+int jfnk_upload(jfnk_ctx* c, void* dst, const void* src, size_t bytes)
+{
+    if (!bytes) return JFNK_OK;
+    JF_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->cur ? c->cur : c->stream));
+    return JFNK_OK;
+}
+
+int jfnk_download(jfnk_ctx* c, void* dst, const void* src, size_t bytes)
+{
+    cudaStream_t s = c->cur ? c->cur : c->stream;
+    if (bytes) JF_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+    JF_CUDA(c, cudaStreamSynchronize(s));
+    return JFNK_OK;
+}
+
+int jfnk_use_stream(jfnk_ctx* c, cudaStream_t s)
+{
+    if (!s) s = c->stream;
+    if (c->cur && c->cur != s) {
+        // the previous call's work (on its stream) comes before this call's on the device; a
+        // stream being captured is left to the caller's ordering
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        JF_CUDA(c, cudaStreamIsCapturing(s, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            JF_CUDA(c, cudaEventRecord(c->sw_ev, c->cur));
+            JF_CUDA(c, cudaStreamWaitEvent(s, c->sw_ev, 0));
+        }
+    }
+    c->cur = s;
+    return JFNK_OK;
 }
 
 int jfnk::Profiler::slot(const char* name)
@@ -80,6 +116,7 @@ void jfnk_prof_end(jfnk_ctx* c, int slot)
 
 static void free_device(jfnk_ctx* c)
 {
+    if (c->cur && c->cur != c->stream) cudaStreamSynchronize(c->cur);  // the last call's stream
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->it_graph) cudaGraphExecDestroy(c->it_graph);
     c->it_graph = nullptr;
@@ -194,6 +231,7 @@ int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
         return JFNK_ENOMEM;
     }
     for (auto& e : c->it_ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&c->sw_ev, cudaEventDisableTiming);
     // programmatic dependent launch of the hot-path kernels (JFNK_PDL=1).  Off by default: with
     // the iteration replayed as a CUDA graph it measured slower on GB300 (the kernels have no
     // prologue to overlap, and the early-resident blocks only wait); same kernels and results
@@ -213,6 +251,7 @@ int jfnk_destroy(jfnk_ctx* c)
         for (auto e : s.ev) cudaEventDestroy(e);
     for (auto e : c->it_ev)
         if (e) cudaEventDestroy(e);
+    if (c->sw_ev) cudaEventDestroy(c->sw_ev);
     if (c->gh) cudaFreeHost(c->gh);
     if (c->ph) cudaFreeHost(c->ph);
     if (c->scal_h) cudaFreeHost(c->scal_h);
@@ -438,9 +477,11 @@ int jfnk_setup(jfnk_ctx* c)
         double* dm = (double*)jfnk_dalloc(c, sizeof(double) * 5 * (size_t)P);
         c->cell_prob = (int32_t*)jfnk_dalloc(c, sizeof(int32_t) * (size_t)nc);
         if (!dl || !dm || !c->cell_prob) return jfnk_fail(c, JFNK_ENOMEM, "device allocation of the material table failed");
-        JF_CUDA(c, cudaMemcpy(dl, lawv.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice));
-        JF_CUDA(c, cudaMemcpy(dm, c->mat_host.data() + P, sizeof(double) * 5 * (size_t)P, cudaMemcpyHostToDevice));
-        JF_CUDA(c, cudaMemcpy(c->cell_prob, cell_prob.data(), sizeof(int32_t) * (size_t)nc, cudaMemcpyHostToDevice));
+        int e;
+        if ((e = jfnk_upload(c, dl, lawv.data(), sizeof(int32_t) * P)) ||
+            (e = jfnk_upload(c, dm, c->mat_host.data() + P, sizeof(double) * 5 * (size_t)P)) ||
+            (e = jfnk_upload(c, c->cell_prob, cell_prob.data(), sizeof(int32_t) * (size_t)nc)))
+            return e;
         c->mat = MatDev{dl, dm, dm + P, dm + 2 * (size_t)P, dm + 3 * (size_t)P, dm + 4 * (size_t)P};
     }
     int rc = jfnk::setup_device_mesh(c);
@@ -493,12 +534,11 @@ int jfnk_setup(jfnk_ctx* c)
     if (rc) return rc;
     rc = jfnk::pc_setup(c);
     if (rc) return rc;
-    // the uploads above are synchronous copies and memsets on the legacy stream: complete them
-    // before any kernel of the context's (non-blocking) stream reads the data
-    if (cudaDeviceSynchronize() != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "set-up");
+    // every upload and zero-fill above is ordered on the context's stream
+    JF_CUDA(c, cudaStreamSynchronize(c->stream));
     rc = jfnk::autotune(c);
     if (rc) return rc;
-    if (cudaDeviceSynchronize() != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "set-up");
+    JF_CUDA(c, cudaStreamSynchronize(c->stream));
     c->dirty = false;
     return JFNK_OK;
 }
@@ -561,8 +601,7 @@ static int begin_call(jfnk_ctx* c, void* stream)
         if (rc) return rc;
     }
     if (cudaSetDevice(c->opt.device) != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
-    c->cur = stream ? (cudaStream_t)stream : c->stream;
-    return JFNK_OK;
+    return jfnk_use_stream(c, (cudaStream_t)stream);
 }
 
 static int load_vec(jfnk_ctx* c, const double* src, int mem, double* dst_int)
@@ -686,10 +725,11 @@ int jfnk_get_geometry(jfnk_ctx* c, double* Sf, double* Cf, double* V, double* C)
     const auto& t = c->topo;
     const int nf = t.nf, nc = t.nc;
     std::vector<double> a((size_t)3 * nf), b((size_t)3 * nf), v(nc), cc((size_t)3 * nc);
-    JF_CUDA(c, cudaMemcpy(a.data(), c->dm.Sf, sizeof(double) * a.size(), cudaMemcpyDeviceToHost));
-    JF_CUDA(c, cudaMemcpy(b.data(), c->dm.Cf, sizeof(double) * b.size(), cudaMemcpyDeviceToHost));
-    JF_CUDA(c, cudaMemcpy(v.data(), c->dm.V, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
-    JF_CUDA(c, cudaMemcpy(cc.data(), c->dm.C, sizeof(double) * cc.size(), cudaMemcpyDeviceToHost));
+    if ((rc = jfnk_download(c, a.data(), c->dm.Sf, sizeof(double) * a.size())) ||
+        (rc = jfnk_download(c, b.data(), c->dm.Cf, sizeof(double) * b.size())) ||
+        (rc = jfnk_download(c, v.data(), c->dm.V, sizeof(double) * v.size())) ||
+        (rc = jfnk_download(c, cc.data(), c->dm.C, sizeof(double) * cc.size())))
+        return rc;
     for (int f = 0; f < nf; f++) {
         const int o = t.face_src[f];
         const double sg = t.face_flip[f] ? -1.0 : 1.0;
@@ -714,8 +754,7 @@ int jfnk_get_gradient(jfnk_ctx* c, double* grad)
     if (!grad) return jfnk_fail(c, JFNK_EINVAL, "null gradient buffer");
     const int nc = c->dm.nc;
     std::vector<double> g((size_t)9 * nc);
-    JF_CUDA(c, cudaDeviceSynchronize());
-    JF_CUDA(c, cudaMemcpy(g.data(), c->G, sizeof(double) * g.size(), cudaMemcpyDeviceToHost));
+    if ((rc = jfnk_download(c, g.data(), c->G, sizeof(double) * g.size()))) return rc;
     for (int P = 0; P < nc; P++)
         for (int q = 0; q < 9; q++) grad[(size_t)c->topo.n2o[P] * 9 + q] = g[(size_t)q * nc + P];
     return JFNK_OK;

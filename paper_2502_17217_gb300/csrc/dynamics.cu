@@ -85,6 +85,8 @@ extern "C" int jfnk_dynamic_reset(jfnk_ctx* c)
     if (!c) return JFNK_EINVAL;
     if (c->dirty) return jfnk_fail(c, JFNK_ESTATE, "jfnk_dynamic_reset: set the context up first");
     if (!c->dyn_on) return jfnk_fail(c, JFNK_ESTATE, "jfnk_dynamic_reset: options.density is 0 (static context)");
+    const int rc = jfnk_use_stream(c, nullptr);
+    if (rc) return rc;
     const size_t bytes = sizeof(double) * 3 * (size_t)c->dm.nc;
     double* bufs[6] = {c->dyn_ut, c->dyn_utm1, c->dyn_vt, c->dyn_vtm1, c->dyn_at, c->dyn_rc};
     for (auto b : bufs) JF_CUDA(c, cudaMemsetAsync(b, 0, bytes, c->stream));

@@ -337,7 +337,7 @@ template <typename T>
 static T* upload(jfnk_ctx* c, const std::vector<T>& h)
 {
     T* d = (T*)jfnk_dalloc(c, sizeof(T) * (h.empty() ? 1 : h.size()));
-    if (d && !h.empty()) cudaMemcpy(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+    if (d && jfnk_upload(c, d, h.data(), sizeof(T) * h.size())) return nullptr;
     return d;
 }
 

@@ -203,7 +203,8 @@ struct jfnk_ctx {
     jfnk_options opt;
     std::string err;
     cudaStream_t stream = nullptr;      // context's own stream
-    cudaStream_t cur = nullptr;         // stream of the call in progress
+    cudaStream_t cur = nullptr;         // stream of the call in progress (or of the last call)
+    cudaEvent_t sw_ev = nullptr;        // orders a call after the previous one on another stream
     jfnk::HostMesh hm;
     bool have_mesh = false, have_material = false;
     bool is_batch = false;
@@ -283,7 +284,16 @@ struct jfnk_ctx {
 int jfnk_solve_method(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_stats* stats, void* stream, int method);
 int jfnk_fail(jfnk_ctx* c, int code, const std::string& msg);
 int jfnk_cuda_fail(jfnk_ctx* c, cudaError_t e, const char* what);
-void* jfnk_dalloc(jfnk_ctx* c, size_t bytes);   // tracked cudaMalloc, zeroed; nullptr on failure
+// Device memory and host transfers of set-up and inspection calls.  Every one is ordered on
+// the stream of the call in progress (the context's own during set-up): the synchronous
+// cudaMemcpy / cudaMemset run on the legacy stream, which the context's non-blocking streams
+// do not wait for, and a pageable host-to-device cudaMemcpy may return before its data lands.
+void* jfnk_dalloc(jfnk_ctx* c, size_t bytes);   // tracked cudaMalloc, zeroed in stream order; nullptr on failure
+int jfnk_upload(jfnk_ctx* c, void* dst, const void* src, size_t bytes);    // host (pageable) -> device
+int jfnk_download(jfnk_ctx* c, void* dst, const void* src, size_t bytes);  // device -> host; returns when landed
+// Makes s (NULL: the context's own stream) the stream of the call in progress; when it differs
+// from the previous call's, the previous call's work is ordered before it on the device.
+int jfnk_use_stream(jfnk_ctx* c, cudaStream_t s);
 
 #define JF_CUDA(ctx, call)                                         \
     do {                                                           \

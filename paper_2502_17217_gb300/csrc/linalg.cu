@@ -571,7 +571,7 @@ int build_chunks(jfnk_ctx* c)
     c->n_chunks = (int)beg.size();
     auto up = [&](const void* h, size_t bytes) -> void* {
         void* d = jfnk_dalloc(c, std::max<size_t>(bytes, 8));
-        if (d && bytes) cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice);
+        if (d && jfnk_upload(c, d, h, bytes)) return (void*)nullptr;
         return d;
     };
     c->ch_beg = (int64_t*)up(beg.data(), beg.size() * sizeof(int64_t));

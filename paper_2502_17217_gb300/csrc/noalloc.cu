@@ -72,14 +72,15 @@ extern "C" int jfnk_residual_noalloc(jfnk_ctx* c, const double* u, double* R, vo
     cudaError_t e;
     double* base = scratch_address(c->opt.device, &e);
     if (!base) return jfnk_cuda_fail(c, e, "cudaGetSymbolAddress");
-    c->cur = stream ? (cudaStream_t)stream : c->stream;
+    int rc = jfnk_use_stream(c, (cudaStream_t)stream);
+    if (rc) return rc;
     double* u_int = base;
     double* G = u_int + 3 * nc;
     double* T = G + 9 * nc;
     double* F = T + (c->law_mode != 0 ? 9 * nc : 0);
     double* Fn = F + 3 * (size_t)m.nflux;
     double* R_int = Fn + 3 * (size_t)m.ni;
-    int rc = jfnk::sync_load(c);
+    rc = jfnk::sync_load(c);
     if (!rc) rc = jfnk::perm_in(c, u, u_int);
     if (!rc) rc = jfnk::residual_bufs(c, u_int, R_int, jfnk::OUT_R, nullptr, nullptr, G, T, F, Fn);
     if (!rc) rc = jfnk::perm_out(c, R_int, R);

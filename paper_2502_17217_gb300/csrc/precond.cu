@@ -387,13 +387,13 @@ static T* upload_as(jfnk_ctx* c, const std::vector<double>& h)
 {
     std::vector<T> t(h.begin(), h.end());
     T* d = (T*)jfnk_dalloc(c, sizeof(T) * std::max<size_t>(1, t.size()));
-    if (d && !t.empty()) cudaMemcpy(d, t.data(), sizeof(T) * t.size(), cudaMemcpyHostToDevice);
+    if (d && jfnk_upload(c, d, t.data(), sizeof(T) * t.size())) return nullptr;
     return d;
 }
 static int32_t* upload_i(jfnk_ctx* c, const std::vector<int32_t>& h)
 {
     int32_t* d = (int32_t*)jfnk_dalloc(c, sizeof(int32_t) * std::max<size_t>(1, h.size()));
-    if (d && !h.empty()) cudaMemcpy(d, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice);
+    if (d && jfnk_upload(c, d, h.data(), sizeof(int32_t) * h.size())) return nullptr;
     return d;
 }
 
@@ -497,9 +497,10 @@ int pc_setup(jfnk_ctx* c)
     const Topology& t = c->topo;
     const int nc = m.nc;
     std::vector<double> jc(std::max(1, m.nflux)), diag(nc);
-    JF_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (m.nflux) JF_CUDA(c, cudaMemcpy(jc.data(), m.jt_c, sizeof(double) * m.nflux, cudaMemcpyDeviceToHost));
-    JF_CUDA(c, cudaMemcpy(diag.data(), m.jt_diag, sizeof(double) * nc, cudaMemcpyDeviceToHost));
+    int rc;
+    if ((rc = jfnk_download(c, jc.data(), m.jt_c, sizeof(double) * m.nflux)) ||
+        (rc = jfnk_download(c, diag.data(), m.jt_diag, sizeof(double) * nc)))
+        return rc;
     // level 0 in the caller's cell order (so the aggregation does not depend on the internal
     // renumbering): rows by input index, columns ascending
     MgLevelHost L0;
@@ -528,7 +529,7 @@ int pc_setup(jfnk_ctx* c)
         make_transfer(lv[l].prp, lv[l].pcol, lv[l].pval, lv[l].n, lv[l + 1].n, l == 0 ? &t.n2o : nullptr, tr[l]);
     std::vector<double> adiag0(nc);
     for (int P = 0; P < nc; P++) adiag0[P] = -diag[P];
-    int rc = mg_upload<float>(c, S.f, lv, inv, jc, adiag0, tr);
+    rc = mg_upload<float>(c, S.f, lv, inv, jc, adiag0, tr);
     if (rc) return rc;
     rc = mg_upload<double>(c, S.d, lv, inv, jc, adiag0, tr);
     if (rc) return rc;

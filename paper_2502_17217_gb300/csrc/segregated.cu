@@ -206,10 +206,12 @@ int seg_setup(jfnk_ctx* c)
     const int P = c->nprob, nch = c->n_chunks;
     std::vector<int32_t> pbeg(P), pcnt(P), len(nch);
     std::vector<int64_t> beg(nch);
-    JF_CUDA(c, cudaMemcpy(pbeg.data(), c->pch_beg, sizeof(int32_t) * P, cudaMemcpyDeviceToHost));
-    JF_CUDA(c, cudaMemcpy(pcnt.data(), c->pch_cnt, sizeof(int32_t) * P, cudaMemcpyDeviceToHost));
-    JF_CUDA(c, cudaMemcpy(beg.data(), c->ch_beg, sizeof(int64_t) * nch, cudaMemcpyDeviceToHost));
-    JF_CUDA(c, cudaMemcpy(len.data(), c->ch_len, sizeof(int32_t) * nch, cudaMemcpyDeviceToHost));
+    int rc;
+    if ((rc = jfnk_download(c, pbeg.data(), c->pch_beg, sizeof(int32_t) * P)) ||
+        (rc = jfnk_download(c, pcnt.data(), c->pch_cnt, sizeof(int32_t) * P)) ||
+        (rc = jfnk_download(c, beg.data(), c->ch_beg, sizeof(int64_t) * nch)) ||
+        (rc = jfnk_download(c, len.data(), c->ch_len, sizeof(int32_t) * nch)))
+        return rc;
     const int64_t nc = c->dm.nc;
     std::vector<int32_t> slot(nch), sbeg(3 * P, 0), scnt(3 * P, 0);
     for (int p = 0; p < P; p++)
@@ -222,7 +224,7 @@ int seg_setup(jfnk_ctx* c)
         }
     auto up = [&](const std::vector<int32_t>& h) -> int32_t* {
         int32_t* d = (int32_t*)jfnk_dalloc(c, sizeof(int32_t) * std::max<size_t>(1, h.size()));
-        if (d) cudaMemcpy(d, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice);
+        if (d && jfnk_upload(c, d, h.data(), sizeof(int32_t) * h.size())) return (int32_t*)nullptr;
         return d;
     };
     c->seg_slot = up(slot);
@@ -231,7 +233,6 @@ int seg_setup(jfnk_ctx* c)
     c->seg_state = (SegSlot*)jfnk_dalloc(c, sizeof(SegSlot) * 3 * (size_t)P);
     if (!c->seg_slot || !c->seg_sbeg || !c->seg_scnt || !c->seg_state)
         return jfnk_fail(c, JFNK_ENOMEM, "device allocation of the segregated solver's tables failed");
-    JF_CUDA(c, cudaDeviceSynchronize());  // the uploads above run on the legacy stream
     c->seg_state_h.assign(3 * (size_t)P, SegSlot());
     return JFNK_OK;
 }

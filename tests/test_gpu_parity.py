@@ -410,3 +410,20 @@ def test_segregated_neo_hookean_load_steps_and_graph_vs_direct():
     assert rc2 == 0 and np.array_equal(u1, u2) and st1.gmres_its == st2.gmres_its
     uo, rco, _ = O.Oracle.from_case(case).segregated(load_steps=2, rtol=1e-10)
     assert rco == 0 and _rel(u1, uo) <= 1e-8
+
+
+def test_inspection_calls():
+    """The permutation is a permutation; launch counts grow with work; the FP64 probe gives a
+    rate within the unit count's bound (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz) and above
+    a tenth of it; device bytes are counted."""
+    from paper_2502_17217_gb300 import jfnk
+    case = CASES["cantilever_ragged_37x5x3"]()
+    s = _solver(case)
+    perm = s.permutation()
+    assert np.array_equal(np.sort(perm), np.arange(case.mesh.n_cells))
+    n0 = s.launch_count()
+    s.residual(np.zeros((case.mesh.n_cells, 3)))
+    assert s.launch_count() >= n0 + 3  # gradient, face and cell passes at least
+    assert s.device_bytes() > 0
+    rate = jfnk.measure_fp64_rate(0)
+    assert 0.126 < rate < 1.26 * 1.05

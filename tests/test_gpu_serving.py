@@ -23,7 +23,8 @@ def test_served_results_equal_alone_results_and_requests_overlap():
     cases = [c for c, _ in reqs_def]
     steps = [s for _, s in reqs_def]
     reqs, wall, srv = serving.serve_stream(cases, rate_per_s=500.0, seed=3, load_steps=steps, max_slots=4, **opts)
-    assert all(r.status == 0 for r in reqs), [(r.status, r.error) for r in reqs]
+    bad = [(k, r.status, r.error, r.cells) for k, r in enumerate(reqs) if r.status != 0]
+    assert not bad, bad
     assert srv.max_concurrent > 1  # requests ran concurrently
     for r, (c, st) in zip(reqs, reqs_def):
         ua, _, rc = jfnk.Solver.from_case(c, **opts).solve(load_steps=st)
@@ -61,7 +62,8 @@ def test_served_results_under_contention_with_load_steps():
     steps = [s for _, s in reqs_def]
     reqs, wall, srv = serving.serve_stream(cases, rate_per_s=5000.0, seed=6, load_steps=steps, max_slots=8, **opts)
     assert srv.max_concurrent >= 4
-    assert all(r.status == 0 for r in reqs), [(r.status, r.error) for r in reqs]
+    bad = [(k, r.status, r.error, r.cells) for k, r in enumerate(reqs) if r.status != 0]
+    assert not bad, bad
     for r, (c, st) in zip(reqs, reqs_def):
         ua, sta, rc = jfnk.Solver.from_case(c, **opts).solve(load_steps=st)
         assert rc == 0 and sta.load_steps_done == st
