@@ -69,8 +69,9 @@ typedef struct jfnk_options {
     double jv_eps_scale;    /* eps = jv_eps_scale (1 + |u|) / |v| (Eq. JF)             (1e-7)*/
     int pc;                 /* JFNK_PC_*                                         (BJACOBI)   */
     int precision;          /* JFNK_PREC_*                                          (FP64)   */
-    int reorth;             /* 0: classical Gram-Schmidt twice when the norm drops by more
-                               than 1/sqrt(2) (selective); 1: always twice; 2: once   (0)   */
+    int reorth;             /* classical Gram-Schmidt: 2 once; 0 twice when the first pass
+                               lowers the norm below 1/sqrt(2) of it (selective);
+                               1 always twice                                          (2)   */
     int renumber;           /* 1: reverse Cuthill-McKee cell renumbering               (1)   */
     int mg_max_levels;      /* multigrid levels (Sec. 4.2: up to 25)                   (25)  */
     int mg_coarse_max;      /* rows of the coarsest (dense Cholesky) level             (2000)*/

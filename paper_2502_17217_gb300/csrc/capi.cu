@@ -182,7 +182,7 @@ void jfnk_default_options(jfnk_options* o)
     o->jv_eps_scale = 1e-7;
     o->pc = JFNK_PC_BJACOBI;
     o->precision = JFNK_PREC_FP64;
-    o->reorth = 0;
+    o->reorth = 2;
     o->renumber = 1;
     o->mg_max_levels = 25;
     o->mg_coarse_max = 1000;
