@@ -17,9 +17,12 @@
  *    is ignored on input and returned as zero.
  *  - mem = JFNK_MEM_HOST: host pointers, copied in and out; the call returns when the result
  *    is in the caller's buffer.  mem = JFNK_MEM_DEVICE: device pointers of the context's
- *    device, borrowed for the duration of the work enqueued on `stream` (a cudaStream_t;
- *    NULL means the context's own stream); the call returns once the work is enqueued and
- *    the caller synchronises the stream before reading the result.
+ *    device, borrowed for the duration of the work enqueued on `stream` (a cudaStream_t,
+ *    cudaStreamLegacy or cudaStreamPerThread included; NULL means the context's own stream);
+ *    the call returns once the work is enqueued and the caller synchronises the stream (or
+ *    calls jfnk_synchronize) before reading the result.  A call on another stream than the
+ *    previous call's is ordered after that call's work on the device, so the previous call's
+ *    stream must still exist when the next call is made.
  *  - One context is not thread-safe: calls on a context must not overlap in time (they
  *    share device scratch buffers).  Distinct contexts are independent.
  *  - Host arrays passed to set-up calls are caller-owned and copied; they may be freed on
@@ -246,6 +249,9 @@ int jfnk_profile_enable(jfnk_ctx* ctx, int enable);
  * JFNK_EINVAL for unknown names.  Synchronises the context's last stream. */
 int jfnk_profile_get(jfnk_ctx* ctx, const char* name, double* total_ms, int64_t* launches);
 int jfnk_profile_reset(jfnk_ctx* ctx);
+/* Waits until the work of the context's last call has finished (that call's stream; the
+ * context's own stream after calls made with stream = NULL).  JFNK_ECUDA if that work failed. */
+int jfnk_synchronize(jfnk_ctx* ctx);
 /* Number of kernel launches made by the context since creation (every stream). */
 int64_t jfnk_launch_count(const jfnk_ctx* ctx);
 /* Device bytes held by the context. */

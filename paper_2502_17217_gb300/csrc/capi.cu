@@ -809,6 +809,14 @@ int jfnk_profile_reset(jfnk_ctx* c)
     return JFNK_OK;
 }
 
+int jfnk_synchronize(jfnk_ctx* c)
+{
+    if (!c) return JFNK_EINVAL;
+    if (cudaSetDevice(c->opt.device) != cudaSuccess) return jfnk_cuda_fail(c, cudaGetLastError(), "cudaSetDevice");
+    JF_CUDA(c, cudaStreamSynchronize(c->cur ? c->cur : c->stream));
+    return JFNK_OK;
+}
+
 int64_t jfnk_launch_count(const jfnk_ctx* c) { return c ? c->launches : 0; }
 
 int64_t jfnk_device_bytes(const jfnk_ctx* c) { return c ? c->dev_bytes : 0; }

@@ -78,51 +78,93 @@ __global__ void k_copy_to_double(const int* gate, size_t n, const TV* __restrict
 
 // ------------------------------------------------------------------ multigrid kernels
 // Fine level (A = -J~, matrix-free):
-//   (A x)_P = -diag_P x_P - sum_{faces f of P} c_f x_other(f)
+//   (A x)_P = -diag_P x_P - sum_{internal faces f of P} c_f x_other(f)
+// over the cell's sliced-ELL neighbour slots (32 cells per slice, slot-major, so a warp's
+// loads coalesce), with the face coefficient copied per slot: one round of index and
+// coefficient loads and one of neighbour values, instead of walking the owner and neighbour
+// face lists (three to four dependent loads a face).  Padding (-1) and mirror neighbours of
+// symmetry faces (>= nc, not part of the scalar multigrid operator) are skipped.
+constexpr int kSellUnroll = 8;  // slots taken in one unrolled round (hexahedra have 6)
+
+template <typename T, typename F>
+__device__ __forceinline__ void for_sell_slots(int P, int nc, const int32_t* __restrict__ sell_off,
+                                               const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
+                                               const T* __restrict__ sc, F&& f)
+{
+    const int sl = P >> 5, lane = P & 31, base = sell_off[sl], w = sell_w[sl];
+    // all index and coefficient loads of the first kSellUnroll slots first, so that they are
+    // in flight together, then the neighbour terms in slot order
+    int Ns[kSellUnroll];
+    T cs[kSellUnroll];
+#pragma unroll
+    for (int k = 0; k < kSellUnroll; k++) {
+        const int slot = base + 32 * k + lane;
+        Ns[k] = k < w ? sell_nbr[slot] : -1;
+        cs[k] = k < w ? sc[slot] : (T)0;
+    }
+#pragma unroll
+    for (int k = 0; k < kSellUnroll; k++)
+        if ((unsigned)Ns[k] < (unsigned)nc) f(Ns[k], cs[k]);
+    for (int k = kSellUnroll; k < w; k++) {
+        const int slot = base + 32 * k + lane;
+        const int N = sell_nbr[slot];
+        const T cf = sc[slot];
+        if ((unsigned)N < (unsigned)nc) f(N, cf);
+    }
+}
+
 template <typename T>
-__device__ __forceinline__ void a0_row(int P, int nc, const int32_t* __restrict__ fo_ptr, const int32_t* __restrict__ fn_ptr,
-                                       const int32_t* __restrict__ fn_face, const int32_t* __restrict__ own,
-                                       const int32_t* __restrict__ nei, const T* __restrict__ jc, const T* __restrict__ adiag,
-                                       const T* __restrict__ x, T out[3])
+__device__ __forceinline__ void a0_row(int P, int nc, const int32_t* __restrict__ sell_off, const int32_t* __restrict__ sell_w,
+                                       const int32_t* __restrict__ sell_nbr, const T* __restrict__ sc,
+                                       const T* __restrict__ adiag, const T* __restrict__ x, T out[3])
 {
     const T d = adiag[P];
     out[0] = d * x[P]; out[1] = d * x[nc + P]; out[2] = d * x[2 * (size_t)nc + P];
-    for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) {
-        const int N = nei[f];
-        const T cf = jc[f];
+    for_sell_slots<T>(P, nc, sell_off, sell_w, sell_nbr, sc, [&](int N, T cf) {
         out[0] -= cf * x[N]; out[1] -= cf * x[nc + N]; out[2] -= cf * x[2 * (size_t)nc + N];
-    }
-    for (int k = fn_ptr[P]; k < fn_ptr[P + 1]; k++) {
-        const int f = fn_face[k];
-        const int N = own[f];
-        const T cf = jc[f];
-        out[0] -= cf * x[N]; out[1] -= cf * x[nc + N]; out[2] -= cf * x[2 * (size_t)nc + N];
-    }
+    });
 }
+
+// one CSR row, the first kCsrUnroll entries' column indices and values loaded together
+constexpr int kCsrUnroll = 8;
 
 template <typename T>
 __device__ __forceinline__ void csr_row(int i, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                         const T* __restrict__ val, const T* __restrict__ x, int nx, T out[3])
 {
     out[0] = out[1] = out[2] = (T)0;
-    for (int q = rp[i]; q < rp[i + 1]; q++) {
+    const int a = rp[i], b = rp[i + 1];
+    int js[kCsrUnroll];
+    T as[kCsrUnroll];
+#pragma unroll
+    for (int q = 0; q < kCsrUnroll; q++) {
+        js[q] = a + q < b ? col[a + q] : 0;
+        as[q] = a + q < b ? val[a + q] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < kCsrUnroll; q++)
+        if (a + q < b) {
+            const int j = js[q];
+            out[0] += as[q] * x[j]; out[1] += as[q] * x[nx + j]; out[2] += as[q] * x[2 * (size_t)nx + j];
+        }
+    for (int q = a + kCsrUnroll; q < b; q++) {
         const int j = col[q];
-        const T a = val[q];
-        out[0] += a * x[j]; out[1] += a * x[nx + j]; out[2] += a * x[2 * (size_t)nx + j];
+        const T v = val[q];
+        out[0] += v * x[j]; out[1] += v * x[nx + j]; out[2] += v * x[2 * (size_t)nx + j];
     }
     (void)n;
 }
 
-// Operator of one level: the fine level from face coefficients, coarse levels from CSR.
+// Operator of one level: the fine level from per-slot face coefficients, coarse levels from CSR.
 template <typename T>
 struct LevelOp {
     int n;
     bool fine;
-    const int32_t *p0, *p1, *p2, *own, *nei;  // fine: fo_ptr, fn_ptr, fn_face, own, nei; coarse: rp, col
-    const T *vals, *adiag, *dinv;
+    const int32_t *p0, *p1, *p2;  // fine: sell_off, sell_w, sell_nbr; coarse: rp, col
+    const T *vals, *adiag, *dinv;  // vals: fine per-slot coefficients, coarse CSR values
     __device__ __forceinline__ void row(int i, const T* x, T out[3]) const
     {
-        if (fine) a0_row<T>(i, n, p0, p1, p2, own, nei, vals, adiag, x, out);
+        if (fine) a0_row<T>(i, n, p0, p1, p2, vals, adiag, x, out);
         else csr_row<T>(i, n, p0, p1, vals, x, n, out);
     }
 };
@@ -174,19 +216,11 @@ __global__ void k_mg_pre0_jacobi(const int* gate, LevelOp<T> op, const TV* __res
     const T a = op.adiag[P];
 #pragma unroll
     for (int k = 0; k < 3; k++) ax[k] = a * x0[k];
-    for (int f = op.p0[P]; f < op.p0[P + 1]; f++) {
-        const int N = op.nei[f];
-        const T cf = op.vals[f], dN = omega * op.dinv[N];
+    for_sell_slots<T>(P, nc, op.p0, op.p1, op.p2, op.vals, [&](int N, T cf) {
+        const T dN = omega * op.dinv[N];
 #pragma unroll
         for (int k = 0; k < 3; k++) ax[k] -= cf * mul_rn(dN, -(T)v[(size_t)k * nc + N]);
-    }
-    for (int q = op.p1[P]; q < op.p1[P + 1]; q++) {
-        const int f = op.p2[q];
-        const int N = op.own[f];
-        const T cf = op.vals[f], dN = omega * op.dinv[N];
-#pragma unroll
-        for (int k = 0; k < 3; k++) ax[k] -= cf * mul_rn(dN, -(T)v[(size_t)k * nc + N]);
-    }
+    });
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         b[(size_t)k * nc + P] = bb[k];
@@ -374,6 +408,7 @@ struct MgDev {
     std::vector<Level> L;
     T* Ainv = nullptr;
     T* jc = nullptr;   // fine-level face coefficients in T
+    T* sc = nullptr;   // the same per sliced-ELL neighbour slot (0 on padding and mirror slots)
 };
 
 struct MgState {
@@ -432,11 +467,13 @@ static void make_transfer(const std::vector<int32_t>& prp, const std::vector<int
 
 template <typename T>
 static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& lv, const std::vector<double>& inv,
-                     const std::vector<double>& jc_h, const std::vector<double>& adiag0, const std::vector<HostTransfer>& tr)
+                     const std::vector<double>& jc_h, const std::vector<double>& sc_h, const std::vector<double>& adiag0,
+                     const std::vector<HostTransfer>& tr)
 {
     const int nl = (int)lv.size();
     M.L.assign(nl, typename MgDev<T>::Level());
     M.jc = upload_as<T>(c, jc_h);
+    M.sc = upload_as<T>(c, sc_h);
     for (int l = 0; l < nl; l++) {
         auto& D = M.L[l];
         const MgLevelHost& H = lv[l];
@@ -471,7 +508,7 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
         if (!D.adiag || !D.dinv || !D.b || !D.x || !D.x2 || !D.r) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
     }
     M.Ainv = upload_as<T>(c, inv);
-    if (!M.Ainv || !M.jc) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
+    if (!M.Ainv || !M.jc || !M.sc) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
     return JFNK_OK;
 }
 
@@ -529,9 +566,13 @@ int pc_setup(jfnk_ctx* c)
         make_transfer(lv[l].prp, lv[l].pcol, lv[l].pval, lv[l].n, lv[l + 1].n, l == 0 ? &t.n2o : nullptr, tr[l]);
     std::vector<double> adiag0(nc);
     for (int P = 0; P < nc; P++) adiag0[P] = -diag[P];
-    rc = mg_upload<float>(c, S.f, lv, inv, jc, adiag0, tr);
+    // fine-level coefficient of every sliced-ELL neighbour slot
+    std::vector<double> sc(std::max<size_t>(1, t.sell_nbr.size()), 0.0);
+    for (size_t q = 0; q < t.sell_nbr.size(); q++)
+        if (t.sell_nbr[q] >= 0 && t.sell_nbr[q] < nc) sc[q] = jc[t.sell_face[q]];
+    rc = mg_upload<float>(c, S.f, lv, inv, jc, sc, adiag0, tr);
     if (rc) return rc;
-    rc = mg_upload<double>(c, S.d, lv, inv, jc, adiag0, tr);
+    rc = mg_upload<double>(c, S.d, lv, inv, jc, sc, adiag0, tr);
     if (rc) return rc;
     c->mg_coarse_n = lv.back().n;
     if (getenv("JFNK_VERBOSE")) {
@@ -563,10 +604,10 @@ static LevelOp<T> level_op(const jfnk_ctx* c, const MgDev<T>& M, int l)
     op.n = D.n;
     op.fine = (l == 0);
     if (l == 0) {
-        op.p0 = c->dm.fo_ptr; op.p1 = c->dm.fn_ptr; op.p2 = c->dm.fn_face; op.own = c->dm.own; op.nei = c->dm.nei;
-        op.vals = M.jc;
+        op.p0 = c->dm.sell_off; op.p1 = c->dm.sell_w; op.p2 = c->dm.sell_nbr;
+        op.vals = M.sc;
     } else {
-        op.p0 = D.rp; op.p1 = D.col; op.p2 = nullptr; op.own = nullptr; op.nei = nullptr;
+        op.p0 = D.rp; op.p1 = D.col; op.p2 = nullptr;
         op.vals = D.val;
     }
     op.adiag = D.adiag;

@@ -17,6 +17,8 @@
 
 namespace jfnk {
 
+constexpr int kGradUnroll = 6;  // hexahedra have up to 6 internal neighbours
+
 template <int LAW, int BS>
 __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int nc, int dim, const int32_t* __restrict__ sell_off,
                                               const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
@@ -37,18 +39,41 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
     // internal neighbours first; a cell's symmetry faces (mirror neighbours, coded N >= nc)
     // follow them in its slot list and are taken in a second loop, so meshes without
     // symmetry faces run the first loop alone
-    int k = 0;
-#pragma unroll 2
-    for (; k < w; k++) {
-        const int slot = base + 32 * k + lane;
-        const int N = sell_nbr[slot];
-        if ((unsigned)N >= (unsigned)nc) break;  // padding (-1) or a mirror neighbour
-        const double l0 = sell_l[slot], l1 = sell_l[n_slots + slot], l2 = sell_l[2 * n_slots + slot];
+    // the first kGradUnroll slots' indices and weights are loaded together (one round of
+    // loads in flight instead of one per neighbour), then summed in slot order
+    auto add = [&](int N, double l0, double l1, double l2) {
         const double d0 = u[N] - u0, d1 = u[nc + N] - u1, d2 = u[2 * nc + N] - u2;
         g[0] = fma(l0, d0, g[0]); g[1] = fma(l0, d1, g[1]); g[2] = fma(l0, d2, g[2]);
         g[3] = fma(l1, d0, g[3]); g[4] = fma(l1, d1, g[4]); g[5] = fma(l1, d2, g[5]);
         g[6] = fma(l2, d0, g[6]); g[7] = fma(l2, d1, g[7]); g[8] = fma(l2, d2, g[8]);
+    };
+    int Ns[kGradUnroll];
+    double ls[kGradUnroll][3];
+#pragma unroll
+    for (int q = 0; q < kGradUnroll; q++) {
+        const int slot = base + 32 * q + lane;
+        Ns[q] = q < w ? sell_nbr[slot] : -1;
+        ls[q][0] = q < w ? sell_l[slot] : 0.0;
+        ls[q][1] = q < w ? sell_l[n_slots + slot] : 0.0;
+        ls[q][2] = q < w ? sell_l[2 * n_slots + slot] : 0.0;
     }
+    int k = 0;
+    bool internal = true;  // internal neighbours come first in a cell's slot list
+#pragma unroll
+    for (int q = 0; q < kGradUnroll; q++) {
+        internal = internal && (unsigned)Ns[q] < (unsigned)nc;  // padding (-1) or a mirror neighbour ends them
+        if (internal) {
+            add(Ns[q], ls[q][0], ls[q][1], ls[q][2]);
+            k = q + 1;
+        }
+    }
+    if (internal)
+        for (; k < w; k++) {
+            const int slot = base + 32 * k + lane;
+            const int N = sell_nbr[slot];
+            if ((unsigned)N >= (unsigned)nc) break;
+            add(N, sell_l[slot], sell_l[n_slots + slot], sell_l[2 * n_slots + slot]);
+        }
     if (nsy > 0) {
         for (; k < w; k++) {
             const int slot = base + 32 * k + lane;

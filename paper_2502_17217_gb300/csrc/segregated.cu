@@ -277,9 +277,18 @@ static int seg_capture(jfnk_ctx* c)
     if (c->seg_graph) return JFNK_OK;
     cudaGraph_t g = nullptr;
     const int64_t before = c->launches;
-    JF_CUDA(c, cudaStreamBeginCapture(c->cur, cudaStreamCaptureModeThreadLocal));
+    // captured on the context's own stream (the caller's may be the legacy stream, which
+    // cannot be captured); the graph is launched on the caller's
+    cudaStream_t caller = c->cur;
+    c->cur = c->stream;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        c->cur = caller;
+        return jfnk_cuda_fail(c, e, "cudaStreamBeginCapture");
+    }
     int rc = seg_enqueue_iteration(c);
-    cudaError_t e = cudaStreamEndCapture(c->cur, &g);
+    e = cudaStreamEndCapture(c->stream, &g);
+    c->cur = caller;
     c->seg_graph_kernels = c->launches - before;
     c->launches = before;
     if (rc) {

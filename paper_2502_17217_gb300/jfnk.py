@@ -32,7 +32,7 @@ EXPORTS = [
     "jfnk_get_gradient", "jfnk_get_permutation", "jfnk_profile_enable", "jfnk_profile_get", "jfnk_profile_reset",
     "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64", "jfnk_batch_add", "jfnk_batch_size",
     "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate", "jfnk_get_tuning", "jfnk_set_tuning",
-    "jfnk_solve_segregated", "jfnk_solve_dynamic", "jfnk_dynamic_reset",
+    "jfnk_solve_segregated", "jfnk_solve_dynamic", "jfnk_dynamic_reset", "jfnk_synchronize",
 ]
 
 
@@ -87,6 +87,7 @@ def load():
         "jfnk_solve_segregated": (i, [vp, dp, i, i, C.POINTER(Stats), vp]),
         "jfnk_solve_dynamic": (i, [vp, dp, i, i, C.c_int32, dp, i, C.POINTER(Stats), vp]),
         "jfnk_dynamic_reset": (i, [vp]),
+        "jfnk_synchronize": (i, [vp]),
         "jfnk_get_geometry": (i, [vp, dp, dp, dp, dp]),
         "jfnk_get_gradient": (i, [vp, dp]),
         "jfnk_get_permutation": (i, [vp, i32p]),
@@ -141,9 +142,13 @@ def _is_device(a):
 
 
 def _stream(a):
+    """The caller's current torch stream for device arrays; torch's default stream (handle 0)
+    is passed as cudaStreamLegacy, so that the library's work is ordered with the torch work
+    around it (a NULL stream would select the context's own, unordered, stream)."""
     if _is_device(a):
         import torch
-        return C.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+        h = torch.cuda.current_stream(a.device).cuda_stream
+        return C.c_void_p(h if h else 1)  # 1 = cudaStreamLegacy
     return None
 
 
@@ -323,6 +328,10 @@ class Solver:
 
     def profile_reset(self):
         self._check(self.L.jfnk_profile_reset(self.h))
+
+    def synchronize(self):
+        """Waits for the work of the last call (its stream, or the context's own)."""
+        self._check(self.L.jfnk_synchronize(self.h))
 
     def launch_count(self):
         return int(self.L.jfnk_launch_count(self.h))

@@ -427,3 +427,34 @@ def test_inspection_calls():
     assert s.device_bytes() > 0
     rate = jfnk.measure_fp64_rate(0)
     assert 0.126 < rate < 1.26 * 1.05
+
+
+def test_device_calls_on_torch_default_stream_are_ordered():
+    """Device-array calls made on torch's default stream run on it (cudaStreamLegacy), so a
+    torch read right after sees the result without a device-wide synchronise; a call on the
+    context's own stream (NULL) is waited for by jfnk_synchronize; and a solve from the
+    default stream (whose iteration graph is captured on the context's own stream) gives the
+    solve made on a side stream."""
+    import torch
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(60, 12, 12, (1.0, 0.2, 0.2), perturb=0.15, seed=3)
+    s = _solver(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED)
+    uh = I.random_field(1, case.mesh.n_cells, 1e-4)
+    Rh = s.residual(uh)
+    u = torch.from_numpy(uh).cuda()
+    assert torch.cuda.current_stream().cuda_stream == 0
+    for _ in range(3):
+        R = s.residual(u)
+        assert np.array_equal(R.cpu().numpy(), Rh)  # no synchronise in between
+    R2 = torch.empty_like(u)
+    rc = s.L.jfnk_residual(s.h, jfnk._ptr(u), jfnk._ptr(R2), jfnk.MEM_DEVICE, None)
+    assert rc == 0
+    s.synchronize()
+    assert np.array_equal(R2.cpu().numpy(), Rh)
+    ud, std, rcd = s.solve(torch.zeros_like(u))
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        us, sts, rcs = s.solve(torch.zeros_like(u))
+    side.synchronize()
+    assert rcd == 0 and rcs == 0
+    assert np.array_equal(ud.cpu().numpy(), us.cpu().numpy())
