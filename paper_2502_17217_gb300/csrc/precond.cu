@@ -296,76 +296,129 @@ __global__ void k_mg_spmv(const int* gate, int nrow, int nx, const int32_t* __re
     }
 }
 
-// y = M x (add = 0) or y += M x (add = 1), one warp per row (long rows: P^T and coarse A)
-template <typename T>
-__global__ void k_mg_spmv_warp(const int* gate, int nrow, int nx, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                               const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add)
+// Long CSR rows (P^T, coarse A) are taken by a group of G lanes (G a power of two <= 32,
+// about half the row's mean length, so a warp holds 32/G rows and each lane two entries of a
+// row per step, both loaded before they are used), then summed by a shuffle tree of the group.
+template <int G, typename T>
+__device__ __forceinline__ void group_sum(T& s0, T& s1, T& s2)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o, G);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o, G);
+    }
+}
+
+// sum_q a_q xin(j_q) over the group's share of row entries [qa, qb); xin(j, k) gives component k
+template <int G, typename T, typename X>
+__device__ __forceinline__ void group_row(int qa, int qb, int sub, const int32_t* __restrict__ col,
+                                          const T* __restrict__ val, X&& xin, T& s0, T& s1, T& s2)
+{
+    for (int q = qa + sub; q < qb; q += 2 * G) {
+        const int q1 = q + G;
+        const bool h1 = q1 < qb;
+        const int j0 = col[q], j1 = h1 ? col[q1] : j0;
+        const T a0 = val[q], a1 = h1 ? val[q1] : (T)0;
+        const T x00 = xin(j0, 0), x01 = xin(j0, 1), x02 = xin(j0, 2);
+        T x10 = 0, x11 = 0, x12 = 0;
+        if (h1) { x10 = xin(j1, 0); x11 = xin(j1, 1); x12 = xin(j1, 2); }
+        s0 += a0 * x00; s1 += a0 * x01; s2 += a0 * x02;
+        if (h1) { s0 += a1 * x10; s1 += a1 * x11; s2 += a1 * x12; }
+    }
+}
+
+// y = M x (add = 0) or y += M x (add = 1)
+template <typename T, int G>
+__global__ void k_mg_spmv_grp(const int* gate, int nrow, int nx, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (i >= nrow) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / G, sub = t & (G - 1);
     T s0 = 0, s1 = 0, s2 = 0;
-    for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-        const int j = col[q];
-        const T a = val[q];
-        s0 += a * x[j]; s1 += a * x[nx + j]; s2 += a * x[2 * (size_t)nx + j];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, o);
-        s1 += __shfl_down_sync(0xffffffffu, s1, o);
-        s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    }
-    if (lane == 0) {
+    if (i < nrow)  // lanes past the last row still take part in the shuffles
+        group_row<G, T>(rp[i], rp[i + 1], sub, col, val, [&](int j, int k) { return x[(size_t)k * nx + j]; }, s0, s1, s2);
+    group_sum<G>(s0, s1, s2);
+    if (i < nrow && sub == 0) {
         if (add) { y[i] += s0; y[nrow + i] += s1; y[2 * (size_t)nrow + i] += s2; }
         else { y[i] = s0; y[nrow + i] = s1; y[2 * (size_t)nrow + i] = s2; }
     }
 }
 
-// Jacobi sweep or residual on a coarse (CSR) level, one warp per row:
+// Jacobi sweep or residual on a coarse (CSR) level:
 // mode 0: xo = x + omega D^-1 (b - A x);  mode 1: xo = b - A x;
 // mode 2: the first sweep from x = omega D^-1 b, which is formed where it is needed (x unused)
-template <typename T>
-__global__ void k_mg_csr_warp(const int* gate, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                              const T* __restrict__ val, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
-                              const T* __restrict__ x, T* __restrict__ xo, int mode)
+template <typename T, int G>
+__global__ void k_mg_csr_grp(const int* gate, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const T* __restrict__ val, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
+                             const T* __restrict__ x, T* __restrict__ xo, int mode)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (i >= n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / G, sub = t & (G - 1);
     T s0 = 0, s1 = 0, s2 = 0;
-    if (mode == 2) {
-        for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-            const int j = col[q];
-            const T a = val[q], dj = omega * dinv[j];
-            s0 += a * mul_rn(dj, b[j]); s1 += a * mul_rn(dj, b[n + j]); s2 += a * mul_rn(dj, b[2 * (size_t)n + j]);
+    // the row's own values, loaded ahead of the sums
+    T bi0 = 0, bi1 = 0, bi2 = 0, xi0 = 0, xi1 = 0, xi2 = 0, di = 0;
+    if (i < n) {
+        if (sub == 0) {
+            bi0 = b[i]; bi1 = b[n + i]; bi2 = b[2 * (size_t)n + i];
+            di = dinv[i];
+            if (mode == 0) { xi0 = x[i]; xi1 = x[n + i]; xi2 = x[2 * (size_t)n + i]; }
         }
-    } else {
-        for (int q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-            const int j = col[q];
-            const T a = val[q];
-            s0 += a * x[j]; s1 += a * x[n + j]; s2 += a * x[2 * (size_t)n + j];
-        }
+        const int qa = rp[i], qb = rp[i + 1];
+        if (mode == 2)
+            group_row<G, T>(qa, qb, sub, col, val,
+                            [&](int j, int k) { return mul_rn(omega * dinv[j], b[(size_t)k * n + j]); }, s0, s1, s2);
+        else
+            group_row<G, T>(qa, qb, sub, col, val, [&](int j, int k) { return x[(size_t)k * n + j]; }, s0, s1, s2);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_down_sync(0xffffffffu, s0, o);
-        s1 += __shfl_down_sync(0xffffffffu, s1, o);
-        s2 += __shfl_down_sync(0xffffffffu, s2, o);
-    }
-    if (lane == 0) {
-        const T r0 = b[i] - s0, r1 = b[n + i] - s1, r2 = b[2 * (size_t)n + i] - s2;
+    group_sum<G>(s0, s1, s2);
+    if (i < n && sub == 0) {
+        const T r0 = bi0 - s0, r1 = bi1 - s1, r2 = bi2 - s2;
         if (mode == 1) { xo[i] = r0; xo[n + i] = r1; xo[2 * (size_t)n + i] = r2; }
         else if (mode == 2) {
-            const T d = omega * dinv[i];
-            xo[i] = mul_rn(d, b[i]) + d * r0; xo[n + i] = mul_rn(d, b[n + i]) + d * r1;
-            xo[2 * (size_t)n + i] = mul_rn(d, b[2 * (size_t)n + i]) + d * r2;
+            const T d = omega * di;
+            xo[i] = mul_rn(d, bi0) + d * r0; xo[n + i] = mul_rn(d, bi1) + d * r1;
+            xo[2 * (size_t)n + i] = mul_rn(d, bi2) + d * r2;
         } else {
-            const T d = omega * dinv[i];
-            xo[i] = x[i] + d * r0; xo[n + i] = x[n + i] + d * r1; xo[2 * (size_t)n + i] = x[2 * (size_t)n + i] + d * r2;
+            const T d = omega * di;
+            xo[i] = xi0 + d * r0; xo[n + i] = xi1 + d * r1; xo[2 * (size_t)n + i] = xi2 + d * r2;
         }
+    }
+}
+
+// lanes per row for CSR rows of mean length `mean`: the power of two near half of it, 4..32
+inline int group_lanes(double mean)
+{
+    int g = 4;
+    while (g < 32 && 2.0 * g < mean) g *= 2;
+    return g;
+}
+
+template <typename T, typename... A>
+static void launch_csr_grp(jfnk_ctx* c, int g, long rows, A... args)
+{
+    const dim3 grid((unsigned)std::max<long>(1, (rows * g + 255) / 256)), block(256);
+    switch (g) {
+        case 4: jfnk_launch(c, k_mg_csr_grp<T, 4>, grid, block, args...); break;
+        case 8: jfnk_launch(c, k_mg_csr_grp<T, 8>, grid, block, args...); break;
+        case 16: jfnk_launch(c, k_mg_csr_grp<T, 16>, grid, block, args...); break;
+        default: jfnk_launch(c, k_mg_csr_grp<T, 32>, grid, block, args...); break;
+    }
+}
+
+template <typename T, typename... A>
+static void launch_spmv_grp(jfnk_ctx* c, int g, long rows, A... args)
+{
+    const dim3 grid((unsigned)std::max<long>(1, (rows * g + 255) / 256)), block(256);
+    switch (g) {
+        case 4: jfnk_launch(c, k_mg_spmv_grp<T, 4>, grid, block, args...); break;
+        case 8: jfnk_launch(c, k_mg_spmv_grp<T, 8>, grid, block, args...); break;
+        case 16: jfnk_launch(c, k_mg_spmv_grp<T, 16>, grid, block, args...); break;
+        default: jfnk_launch(c, k_mg_spmv_grp<T, 32>, grid, block, args...); break;
     }
 }
 
@@ -403,6 +456,7 @@ struct MgDev {
         T* pval = nullptr;
         int32_t *rrp = nullptr, *rcol = nullptr;  // R = P^T: nco x n
         T* rval = nullptr;
+        int ga = 32, gr = 32;                      // lanes per row of A (coarse levels) and of R
         T *b = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr;
     };
     std::vector<Level> L;
@@ -488,6 +542,7 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
             D.rp = upload_i(c, H.rp);
             D.col = upload_i(c, H.col);
             D.val = upload_as<T>(c, H.val);
+            D.ga = group_lanes((double)H.col.size() / std::max(1, H.n));
         }
         for (int i = 0; i < H.n; i++) di[i] = 1.0 / ad[i];
         D.adiag = upload_as<T>(c, ad);
@@ -504,6 +559,7 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
             D.rrp = upload_i(c, tr[l].rrp);
             D.rcol = upload_i(c, tr[l].rcol);
             D.rval = upload_as<T>(c, tr[l].rval);
+            D.gr = group_lanes((double)tr[l].rcol.size() / std::max(1, D.nco));
         }
         if (!D.adiag || !D.dinv || !D.b || !D.x || !D.x2 || !D.r) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
     }
@@ -645,8 +701,8 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         // the entry and the first sweep are one kernel when there are two or more sweeps
         if (sweeps >= 2) {
             if (l == 0) jfnk_launch(c, k_mg_pre0_jacobi<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, vbase, ld, jidx, omega, D.b, D.x);
-            else jfnk_launch(c, k_mg_csr_warp<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col,
-                             (const T*)D.val, (const T*)D.dinv, omega, (const T*)D.b, (const T*)nullptr, D.x, 2);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+                                   (const T*)D.dinv, omega, (const T*)D.b, (const T*)nullptr, D.x, 2);
         } else {
             if (l == 0) jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, vbase, ld, jidx, D.dinv, omega, D.b, D.x);
             else jfnk_launch(c, k_mg_pre<T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, D.dinv, omega, D.b, D.x);
@@ -654,19 +710,22 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         JF_LAUNCHED(c);
         for (int sw = (sweeps >= 2 ? 2 : 1); sw < sweeps; sw++) {
             if (l == 0) jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, D.b, D.x, D.x2, nullptr);
-            else jfnk_launch(c, k_mg_csr_warp<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.x2, 0);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+                                   (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
             JF_LAUNCHED(c);
             std::swap(D.x, D.x2);
         }
         jfnk_prof_end(c, s_sm);
         jfnk_prof_begin(c, s_re);
         if (l == 0) jfnk_launch(c, k_mg_resid<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, D.b, D.x, D.r);
-        else jfnk_launch(c, k_mg_csr_warp<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.r, 1);
+        else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+                               (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.r, 1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_re);
         auto& Cn = M.L[l + 1];
         jfnk_prof_begin(c, s_rs);
-        jfnk_launch(c, k_mg_spmv_warp<T>, dim3(nb(32L * D.nco, 256)), dim3(256), gate, D.nco, D.n, D.rrp, D.rcol, D.rval, D.r, Cn.b, 0);
+        launch_spmv_grp<T>(c, D.gr, D.nco, gate, D.nco, D.n, (const int32_t*)D.rrp, (const int32_t*)D.rcol, (const T*)D.rval,
+                           (const T*)D.r, Cn.b, 0);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_rs);
     }
@@ -690,7 +749,8 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         for (int sw = 0; sw < sweeps; sw++) {
             const bool last = (l == 0 && sw == sweeps - 1);
             if (l == 0) jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
-            else jfnk_launch(c, k_mg_csr_warp<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, D.rp, D.col, D.val, D.dinv, omega, D.b, D.x, D.x2, 0);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+                                   (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
             JF_LAUNCHED(c);
             if (!last) std::swap(D.x, D.x2);
         }
