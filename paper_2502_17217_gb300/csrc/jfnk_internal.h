@@ -131,7 +131,8 @@ struct ProbDev {
     double nrm;       // output of plain per-problem norms
     double n_cols;    // sum over Arnoldi iterations of the basis vectors projected out (j + 1)
     double n_rcols;   // the same over the iterations that repeated the projection
-    double pad2[5];
+    double ieps;      // 1 / eps (0 when eps = 0), formed once where eps is set
+    double pad2[4];
     double h[kMaxRestart + 1];
     double H[(kMaxRestart + 1) * kMaxRestart];  // column-major: H[i + (m+1) j]
     double g[kMaxRestart + 1];

@@ -99,7 +99,10 @@ __global__ void __launch_bounds__(kChunkThreads) k_pnorm(Chunks ch, const double
         if (threadIdx.x == 0) {
             const double nrm = sqrt(tot);
             if (mode == 0) P.nrm = nrm;
-            else if (mode == 1) P.eps = (nrm > 0.0) ? s * (1.0 + P.unorm) / nrm : 0.0;
+            else if (mode == 1) {
+                P.eps = (nrm > 0.0) ? s * (1.0 + P.unorm) / nrm : 0.0;
+                P.ieps = P.eps != 0.0 ? 1.0 / P.eps : 0.0;
+            }
             else if (mode == 2) P.unorm = nrm;
             else { P.beta = nrm; P.inv = nrm > 0.0 ? 1.0 / nrm : 0.0; }
             P.ticket[2] = 0u;

@@ -133,34 +133,24 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
         const double A10 = F12 * F20 - F10 * F22, A11 = F00 * F22 - F02 * F20, A12 = F02 * F10 - F00 * F12;
         const double A20 = F10 * F21 - F11 * F20, A21 = F01 * F20 - F00 * F21, A22 = F00 * F11 - F01 * F10;
         const double J = F00 * A00 + F01 * A10 + F02 * A20;
-        // b = F F^T (symmetric)
-        const double b00 = F00 * F00 + F01 * F01 + F02 * F02;
-        const double b01 = F00 * F10 + F01 * F11 + F02 * F12;
-        const double b02 = F00 * F20 + F01 * F21 + F02 * F22;
-        const double b11 = F10 * F10 + F11 * F11 + F12 * F12;
-        const double b12 = F10 * F20 + F11 * F21 + F12 * F22;
-        const double b22 = F20 * F20 + F21 * F21 + F22 * F22;
+        // sigma = mu J^-5/3 (b - tr(b)/3 I) + kappa/2 (J - 1/J) I with b = F F^T, and
+        // T = adj(F) sigma.  Since adj(F) b = J F^T:
+        //   T = mu J^-2/3 F^T + (kappa/2 (J - 1/J) - mu J^-5/3 tr(b)/3) adj(F),
+        // which needs tr(b) only, not b or the product adj(F) sigma.
+        const double trb = F00 * F00 + F01 * F01 + F02 * F02 + F10 * F10 + F11 * F11 + F12 * F12 + F20 * F20 +
+                           F21 * F21 + F22 * F22;
         // an inverted cell (J <= 0) has no stress: NaN makes the residual non-finite so the
-        // line search rejects the state
-        const double cj = cbrt(J);
-        const double Jm23 = (J > 0.0) ? 1.0 / (cj * cj) : __longlong_as_double(0x7ff8000000000000LL);
-        const double rJ = 1.0 / J;
-        const double cm = mu * rJ * Jm23;                       // mu/J J^-2/3
-        const double tr3 = (b00 + b11 + b22) * (1.0 / 3.0);
-        const double p = 0.5 * kappa * (J * J - 1.0) * rJ;      // kappa/2 (J^2 - 1)/J
-        const double s00 = cm * (b00 - tr3) + p, s11 = cm * (b11 - tr3) + p, s22 = cm * (b22 - tr3) + p;
-        const double s01 = cm * b01, s02 = cm * b02, s12 = cm * b12;
-        // T = adj(F) sigma
+        // line search rejects the state.  One reciprocal cube root r3 gives J^-2/3 = r3^2 and
+        // 1/J = r3^3 (no divisions, no cube root: the FP64 pipe is the bound).
+        const double r3 = (J > 0.0) ? rcbrt(J) : __longlong_as_double(0x7ff8000000000000LL);
+        const double Jm23 = r3 * r3;
+        const double rJ = Jm23 * r3;
+        const double cF = mu * Jm23;                                             // mu J^-2/3
+        const double cA = 0.5 * kappa * (J - rJ) - cF * rJ * trb * (1.0 / 3.0);  // coefficient of adj(F)
         double t[9];
-        t[0] = A00 * s00 + A01 * s01 + A02 * s02;
-        t[1] = A00 * s01 + A01 * s11 + A02 * s12;
-        t[2] = A00 * s02 + A01 * s12 + A02 * s22;
-        t[3] = A10 * s00 + A11 * s01 + A12 * s02;
-        t[4] = A10 * s01 + A11 * s11 + A12 * s12;
-        t[5] = A10 * s02 + A11 * s12 + A12 * s22;
-        t[6] = A20 * s00 + A21 * s01 + A22 * s02;
-        t[7] = A20 * s01 + A21 * s11 + A22 * s12;
-        t[8] = A20 * s02 + A21 * s12 + A22 * s22;
+        t[0] = cF * F00 + cA * A00; t[1] = cF * F10 + cA * A01; t[2] = cF * F20 + cA * A02;
+        t[3] = cF * F01 + cA * A10; t[4] = cF * F11 + cA * A11; t[5] = cF * F21 + cA * A12;
+        t[6] = cF * F02 + cA * A20; t[7] = cF * F12 + cA * A21; t[8] = cF * F22 + cA * A22;
 #pragma unroll
         for (int q = 0; q < 9; q++) T[(size_t)q * nc + P] = t[q];
     }
@@ -356,11 +346,11 @@ __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int d
     }
     if (dim == 2) r2 = 0.0;
     if (mode == 1) {
-        const double eps = pd[cell_prob[P]].eps;
-        if (eps == 0.0) {
+        const ProbDev& Q = pd[cell_prob[P]];
+        if (Q.eps == 0.0) {
             r0 = r1 = r2 = 0.0;
         } else {
-            const double ie = 1.0 / eps;
+            const double ie = Q.ieps;  // 1 / eps, formed once per problem
             r0 = (r0 - Ru[P]) * ie;
             r1 = (r1 - Ru[nc + P]) * ie;
             r2 = (r2 - Ru[2 * nc + P]) * ie;
