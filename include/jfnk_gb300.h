@@ -78,7 +78,7 @@ typedef struct jfnk_options {
     int renumber;           /* 1: reverse Cuthill-McKee cell renumbering               (1)   */
     int mg_max_levels;      /* multigrid levels (Sec. 4.2: up to 25)                   (25)  */
     int mg_coarse_max;      /* rows of the coarsest (dense Cholesky) level             (2000)*/
-    double mg_theta;        /* strength threshold of the aggregation                   (0.25)*/
+    double mg_theta;        /* strength threshold of the aggregation                   (0.4) */
     int mg_smooth_sweeps;   /* Jacobi sweeps before and after the coarse correction    (2)   */
     int mg_smoothed;        /* 1: smoothed-aggregation prolongation, 0: piecewise constant (1) */
     int autotune;           /* 1: time the candidate launch shapes at set-up and keep the

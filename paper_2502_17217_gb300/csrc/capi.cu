@@ -186,7 +186,7 @@ void jfnk_default_options(jfnk_options* o)
     o->renumber = 1;
     o->mg_max_levels = 25;
     o->mg_coarse_max = 1000;
-    o->mg_theta = 0.25;
+    o->mg_theta = 0.4;
     o->mg_smooth_sweeps = 2;
     o->mg_smoothed = 1;
     o->autotune = 1;

@@ -113,7 +113,7 @@ def test_multigrid_vcycle_parity(precision, tol, smoothed, sweeps):
     s = _solver(case, pc=jfnk.PC_MG, precision=precision, mg_coarse_max=200, mg_smoothed=smoothed,
                 mg_smooth_sweeps=sweeps)
     o = O.Oracle.from_case(case)
-    o.mg_setup(theta=0.25, max_levels=25, coarse_max=200, smoothed=bool(smoothed), sweeps=sweeps)
+    o.mg_setup(theta=s.options.mg_theta, max_levels=25, coarse_max=200, smoothed=bool(smoothed), sweeps=sweeps)
     v = I.random_field(9, case.mesh.n_cells, 1.0)
     z = s.precondition(v, jfnk.PC_MG)
     zo = o.mg_vcycle(v)
@@ -127,7 +127,7 @@ def _solve_both(case, pc=1, load_steps=1, **kw):
     assert rc == 0, (rc, st.final_rel_res, st.newton_its, st.gmres_its)
     o = O.Oracle.from_case(case)
     if pc == jfnk.PC_MG:
-        o.mg_setup(coarse_max=s.options.mg_coarse_max, smoothed=bool(s.options.mg_smoothed),
+        o.mg_setup(theta=s.options.mg_theta, coarse_max=s.options.mg_coarse_max, smoothed=bool(s.options.mg_smoothed),
                    sweeps=s.options.mg_smooth_sweeps)
     uo, rco, sto = o.newton(load_steps=load_steps, rtol=1e-11, pc=pc, m=s.options.gmres_restart,
                             aug=s.options.gmres_aug)
