@@ -93,6 +93,11 @@ typedef struct jfnk_options {
     double density;         /* kg/m^3; > 0 adds the inertia term (Sec. 2.3, BDF2) for
                                jfnk_solve_dynamic; 0 = static                          (0)   */
     double dt;              /* time step of jfnk_solve_dynamic, s (> 0 when density > 0) (0) */
+    int pc_side;            /* 0: right preconditioning, GMRES on J P^-1 (P^-1 x) = b, true
+                               residual norms; 1: left, GMRES on P^-1 J x = P^-1 b with
+                               preconditioned norms (the paper's choice, Sec. 3.2): each
+                               Arnoldi column is P^-1 (R(u + eps v) - R(u)) / eps with
+                               eps = jv_eps_scale (1 + |u|) for the unit vector v   (0)   */
 } jfnk_options;
 
 typedef struct jfnk_stats {

@@ -153,6 +153,7 @@ static bool valid_options(const jfnk_options* o, std::string& why)
     if (!(o->jv_eps_scale > 0)) { why = "jv_eps_scale must be > 0"; return false; }
     if (o->mg_coarse_max < 1 || o->mg_coarse_max > 8192) { why = "mg_coarse_max must be in [1, 8192]"; return false; }
     if (o->autotune != 0 && o->autotune != 1) { why = "autotune must be 0 or 1"; return false; }
+    if (o->pc_side != 0 && o->pc_side != 1) { why = "pc_side must be 0 (right) or 1 (left)"; return false; }
     if (!(o->seg_inner_tol > 0 && o->seg_inner_tol < 1)) { why = "seg_inner_tol must be in (0, 1)"; return false; }
     if (!(o->density >= 0) || (o->density > 0 && !(o->dt > 0))) { why = "density must be >= 0, and dt > 0 when density > 0"; return false; }
     if (o->seg_max_outer < 1 || o->seg_max_inner < 1) { why = "seg_max_outer and seg_max_inner must be >= 1"; return false; }
@@ -196,6 +197,7 @@ void jfnk_default_options(jfnk_options* o)
     o->seg_max_inner = 1000;
     o->density = 0.0;
     o->dt = 0.0;
+    o->pc_side = 0;
 }
 
 int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)

@@ -357,6 +357,7 @@ int axpy_dev_scalar(jfnk_ctx* c, size_t n, const double* x, const double* a_dev,
 // 3 -> pd[p].beta and inv; gated = skip problems that are inactive or whose cycle is done
 int pnorm(jfnk_ctx* c, const double* x, int mode, bool gated);
 int perturb(jfnk_ctx* c, const double* u, const double* z, double* w, bool gated);
+int perturb_basis(jfnk_ctx* c, const double* u, double* w);  // w = u + eps V_jg (gated)
 int cycle_init(jfnk_ctx* c, const double* r);
 int arnoldi_orthogonalise(jfnk_ctx* c, double* w);
 int cycle_solution(jfnk_ctx* c, double* out, int ncols);  // out = sum_{i < min(k_p, ncols)} y_i V_i

@@ -74,7 +74,8 @@ __device__ __forceinline__ double sum_problem_partials(const double* partials, i
 
 // ------------------------------------------------------------------ per-problem norms
 // mode 0: nrm = |x_p|;  1: eps = s (1 + unorm) / |x_p| (0 for x_p = 0);  2: unorm = |x_p|;
-// 3: beta = |x_p|, inv = 1/beta (0 for beta = 0)
+// 3: beta = |x_p|, inv = 1/beta (0 for beta = 0);  4: unorm = |x_p| and eps = s (1 + unorm),
+// the step for a unit direction (the Arnoldi vectors of left-preconditioned GMRES)
 __global__ void __launch_bounds__(kChunkThreads) k_pnorm(Chunks ch, const double* __restrict__ x,
                                                         double* __restrict__ partials, ProbDev* pd, int mode,
                                                         double s, int gated, const GlobalDev* gdev)
@@ -104,6 +105,11 @@ __global__ void __launch_bounds__(kChunkThreads) k_pnorm(Chunks ch, const double
                 P.ieps = P.eps != 0.0 ? 1.0 / P.eps : 0.0;
             }
             else if (mode == 2) P.unorm = nrm;
+            else if (mode == 4) {
+                P.unorm = nrm;
+                P.eps = s * (1.0 + nrm);
+                P.ieps = 1.0 / P.eps;
+            }
             else { P.beta = nrm; P.inv = nrm > 0.0 ? 1.0 / nrm : 0.0; }
             P.ticket[2] = 0u;
         }
@@ -157,6 +163,26 @@ __global__ void __launch_bounds__(kChunkThreads) k_accept(Chunks ch, const int32
 }
 
 // ------------------------------------------------------------------ Arnoldi
+// w = u + eps_p V_j with j = *jidx (the current Arnoldi vector, unit norm), active problems
+// whose cycle runs: the perturbed state of a left-preconditioned Arnoldi column
+template <typename TV>
+__global__ void __launch_bounds__(kChunkThreads) k_perturb_basis(Chunks ch, const double* __restrict__ u,
+                                                                const TV* __restrict__ V, size_t ld,
+                                                                const int* __restrict__ jidx,
+                                                                const ProbDev* __restrict__ pd,
+                                                                const GlobalDev* __restrict__ gdev, double* __restrict__ w)
+{
+    JF_PDL_ENTRY();
+    const int c = blockIdx.x;
+    const ProbDev& P = pd[ch.prob[c]];
+    if (gdev->all_done || skip_problem(P)) return;
+    const double eps = P.eps;
+    const int64_t b0 = ch.beg[c];
+    const int len = ch.len[c];
+    const TV* v = V + (size_t)(*jidx) * ld + b0;
+    for (int q = threadIdx.x; q < len; q += kChunkThreads) w[b0 + q] = fma(eps, to_f64(v[q]), u[b0 + q]);
+}
+
 // One block per problem: start a cycle (beta and inv already computed).
 __global__ void k_cycle_init(ProbDev* pd, int m)
 {
@@ -619,6 +645,18 @@ int axpby(jfnk_ctx* c, size_t n, double a, const double* x, double b, const doub
 int perturb(jfnk_ctx* c, const double* u, const double* z, double* w, bool gated)
 {
     jfnk_launch(c, k_perturb, dim3(c->n_chunks), dim3(kChunkThreads), chunks(c), u, z, c->pd, c->gdev, gated ? 1 : 0, w);
+    JF_LAUNCHED(c);
+    return JFNK_OK;
+}
+
+int perturb_basis(jfnk_ctx* c, const double* u, double* w)
+{
+    if (c->V_is_float)
+        jfnk_launch(c, k_perturb_basis<float>, dim3(c->n_chunks), dim3(kChunkThreads), chunks(c), u, (const float*)c->V,
+                    c->V_ld, (const int*)&c->gdev->jg, (const ProbDev*)c->pd, (const GlobalDev*)c->gdev, w);
+    else
+        jfnk_launch(c, k_perturb_basis<double>, dim3(c->n_chunks), dim3(kChunkThreads), chunks(c), u, (const double*)c->V,
+                    c->V_ld, (const int*)&c->gdev->jg, (const ProbDev*)c->pd, (const GlobalDev*)c->gdev, w);
     JF_LAUNCHED(c);
     return JFNK_OK;
 }

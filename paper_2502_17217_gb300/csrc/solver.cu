@@ -1,13 +1,17 @@
 // Host orchestration of the device-resident Jacobian-free Newton-Krylov loop (Sec. 3.2-3.3)
 // for P >= 1 independent problems advancing together.
-//   gmres():  restarted right-preconditioned GMRES(m) on J_p(u_p) x_p = b_p for every active
-//             problem, x0 = 0.  One Arnoldi iteration enqueues: z = P^-1 V_j; eps_p =
-//             s (1 + |u_p|) / |z_p|; w = u + eps z; the three residual passes ending in
-//             Jv = (R(w) - R(u)) / eps_p; Gram-Schmidt (twice when needed) with each problem's
-//             Givens step; V_{j+1} = w / |w|.  The iteration is captured once as a CUDA graph
-//             and replayed; every scalar lives on the device and the host keeps two iterations
-//             in flight ahead of its view of the `all done` flag.  At the end of a cycle
-//             x += P^-1 (V y) per problem.
+//   gmres():  restarted preconditioned GMRES(m) on J_p(u_p) x_p = b_p for every active
+//             problem, x0 = 0.  Right preconditioning (Eq. JF with P^-1): one Arnoldi
+//             iteration enqueues z = P^-1 V_j; eps_p = s (1 + |u_p|) / |z_p|; w = u + eps z;
+//             the three residual passes ending in Jv = (R(w) - R(u)) / eps_p; Gram-Schmidt
+//             with each problem's Givens step; V_{j+1} = w / |w|; at the end of a cycle
+//             x += P^-1 (V y).  Left preconditioning (the form of Sec. 3.2 the paper used):
+//             w = u + eps V_j with eps_p = s (1 + |u_p|) (V_j has unit norm), the residual
+//             passes, z = P^-1 Jv, Gram-Schmidt on z; the cycle starts from P^-1 (b - J x),
+//             norms and the tolerance are the preconditioned ones, and x += V y.  The
+//             iteration is captured once as a CUDA graph and replayed; every scalar lives on
+//             the device and the host keeps two iterations in flight ahead of its view of the
+//             `all done` flag.
 //   newton(): per problem, J du = -R with inner tolerance eta (Sec. 3.2: three orders), a
 //             backtracking line search on |R_p| (s = 1, 1/2, ...; accepted when
 //             |R(u + s du)| <= (1 - 1e-4 s) |R(u)|), convergence |R_p| <= max(atol, rtol |R_p(u0)|)
@@ -56,10 +60,20 @@ static int jv_direction(jfnk_ctx* c, const double* x, double* out)
 
 // One lockstep Arnoldi iteration; kernels read the iteration index and the per-problem flags
 // from the device and return at once when every cycle is done.
+static bool left_pc(const jfnk_ctx* c) { return c->opt.pc_side == 1 && c->opt.pc != JFNK_PC_NONE; }
+
 static int enqueue_iteration(jfnk_ctx* c)
 {
     const int* gate = &c->gdev->all_done;
     int rc;
+    if (left_pc(c)) {
+        if ((rc = perturb_basis(c, c->u, c->w))) return rc;
+        if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, nullptr, gate))) return rc;
+        if ((rc = pc_apply_any(c, c->opt.pc, c->wk, 0, c->z, gate))) return rc;
+        if ((rc = arnoldi_orthogonalise(c, c->z))) return rc;
+        JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
+        return JFNK_OK;
+    }
     if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate))) return rc;
     if ((rc = pnorm(c, c->z, 1, true))) return rc;
     if ((rc = perturb(c, c->u, c->z, c->w, true))) return rc;
@@ -125,9 +139,12 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
     const size_t n = 3 * (size_t)c->dm.nc;
     const int m = c->opt.gmres_restart, P = c->nprob;
     const int kaug = c->opt.gmres_aug;
+    const bool left = left_pc(c);
     int rc;
     JF_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->cur));
-    if ((rc = pnorm(c, b, 0, false))) return rc;
+    // the norm the tolerance refers to: |b_p|, or |P^-1 b_p| (kept in wk for the first cycle)
+    if (left && (rc = pc_apply_any(c, c->opt.pc, b, 0, c->wk, nullptr))) return rc;
+    if ((rc = pnorm(c, left ? c->wk : b, 0, false))) return rc;
     std::vector<int> act(P);
     for (int p = 0; p < P; p++) act[p] = c->ph[p].active;
     if ((rc = read_problems(c))) return rc;
@@ -151,14 +168,18 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
         int n_act = 0;
         for (int p = 0; p < P; p++) n_act += act[p];
         if (!n_act) break;
-        // r = b - J x
+        // r = b - J x (left: r = P^-1 (b - J x); P^-1 b is in wk already for the first cycle)
         if (rs == 0) {
-            JF_CUDA(c, cudaMemcpyAsync(c->wk, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cur));
+            if (!left) JF_CUDA(c, cudaMemcpyAsync(c->wk, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->cur));
         } else {
             if ((rc = jv_direction(c, x, c->tmp))) return rc;
-            if ((rc = axpby(c, n, 1.0, b, -1.0, c->tmp, c->wk))) return rc;
+            if ((rc = axpby(c, n, 1.0, b, -1.0, c->tmp, left ? c->z : c->wk))) return rc;
+            if (left && (rc = pc_apply_any(c, c->opt.pc, c->z, 0, c->wk, nullptr))) return rc;
             for (int p = 0; p < P; p++) jvs[p] += act[p];
         }
+        // left: the Arnoldi vectors have unit norm, so eps_p = s (1 + |u_p|) for the whole cycle
+        // (the restart's product above set eps for x)
+        if (left && (rc = pnorm(c, c->u, 4, false))) return rc;
         if (kaug > 0) {
             if (have_d) {
                 if ((rc = aug_store(c, head, c->wk))) return rc;
@@ -191,12 +212,17 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
                 JF_CUDA(c, cudaEventRecord(c->it_ev[j & 3], c->cur));
             }
             if ((rc = cycle_solution(c, c->tmp, mk))) return rc;
-            if ((rc = pc_apply_any(c, c->opt.pc, c->tmp, 0, c->z, nullptr))) return rc;
+            // the Krylov part of the correction: P^-1 (V y) (right) or V y (left)
+            const double* dk = c->tmp;
+            if (!left) {
+                if ((rc = pc_apply_any(c, c->opt.pc, c->tmp, 0, c->z, nullptr))) return rc;
+                dk = c->z;
+            }
             if (kaug > 0) {
-                if ((rc = aug_add(c, slots, na, mk, c->z, c->dcorr))) return rc;
+                if ((rc = aug_add(c, slots, na, mk, dk, c->dcorr))) return rc;
                 if ((rc = axpby(c, n, 1.0, x, 1.0, c->dcorr, x))) return rc;
                 have_d = true;
-            } else if ((rc = axpby(c, n, 1.0, x, 1.0, c->z, x))) {
+            } else if ((rc = axpby(c, n, 1.0, x, 1.0, dk, x))) {
                 return rc;
             }
         }

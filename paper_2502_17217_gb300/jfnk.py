@@ -23,6 +23,7 @@ LAW_LINEAR, LAW_NEOHOOKEAN, LAW_STVK = 0, 1, 2
 PC_NONE, PC_BJACOBI, PC_MG = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+PC_RIGHT, PC_LEFT = 0, 1
 
 # every function declared in include/jfnk_gb300.h
 EXPORTS = [
@@ -44,7 +45,8 @@ class Options(C.Structure):
                 ("reorth", C.c_int), ("renumber", C.c_int), ("mg_max_levels", C.c_int), ("mg_coarse_max", C.c_int),
                 ("mg_theta", C.c_double), ("mg_smooth_sweeps", C.c_int), ("mg_smoothed", C.c_int),
                 ("autotune", C.c_int), ("gmres_aug", C.c_int), ("seg_inner_tol", C.c_double),
-                ("seg_max_outer", C.c_int), ("seg_max_inner", C.c_int), ("density", C.c_double), ("dt", C.c_double)]
+                ("seg_max_outer", C.c_int), ("seg_max_inner", C.c_int), ("density", C.c_double), ("dt", C.c_double),
+                ("pc_side", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -55,15 +55,16 @@ def test_batch_residual_and_jv_match_each_problem_alone():
         assert _rel(Rk, o.residual(uk)) <= 1e-12
 
 
-def test_batch_solve_bitwise_equals_alone_with_block_jacobi():
+@pytest.mark.parametrize("pc_side", [0, 1])
+def test_batch_solve_bitwise_equals_alone_with_block_jacobi(pc_side):
     from paper_2502_17217_gb300 import jfnk
     cases = _mix()
-    B = jfnk.Batch(cases, pc=jfnk.PC_BJACOBI, newton_rtol=1e-10)
+    B = jfnk.Batch(cases, pc=jfnk.PC_BJACOBI, newton_rtol=1e-10, pc_side=pc_side)
     u, st, rc = B.solve()
     assert rc == 0
     per = B.problem_stats()
     for k, (c, uk) in enumerate(zip(cases, B.split(u))):
-        s = jfnk.Solver.from_case(c, pc=jfnk.PC_BJACOBI, newton_rtol=1e-10)
+        s = jfnk.Solver.from_case(c, pc=jfnk.PC_BJACOBI, newton_rtol=1e-10, pc_side=pc_side)
         ua, sta, rca = s.solve()
         assert rca == 0
         assert np.array_equal(uk, ua), (k, _rel(uk, ua))

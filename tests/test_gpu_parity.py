@@ -214,11 +214,13 @@ def test_device_pointer_path_matches_host_path():
     assert np.array_equal(Jh, Jd.cpu().numpy())
 
 
-def test_graph_and_direct_launch_agree():
-    """The captured Arnoldi-iteration graph and direct launches give bitwise equal solves."""
+@pytest.mark.parametrize("pc_side", [0, 1])
+def test_graph_and_direct_launch_agree(pc_side):
+    """The captured Arnoldi-iteration graph and direct launches give bitwise equal solves
+    (right and left preconditioning)."""
     from paper_2502_17217_gb300 import jfnk
     case = I.case_cantilever(30, 6, 6, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
-    s = _solver(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, mg_coarse_max=50)
+    s = _solver(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, mg_coarse_max=50, pc_side=pc_side)
     u1, st1, rc1 = s.solve()
     s.profile(True)  # per-kernel events force direct launches
     u2, st2, rc2 = s.solve()
@@ -458,3 +460,53 @@ def test_device_calls_on_torch_default_stream_are_ordered():
     side.synchronize()
     assert rcd == 0 and rcs == 0
     assert np.array_equal(ud.cpu().numpy(), us.cpu().numpy())
+
+
+@pytest.mark.parametrize("name", ["mms2d_bjacobi", "cantilever_mg_mixed", "nh_beam_load_steps", "loose_gmres8", "gmres_no_corrections"])
+def test_solve_parity_left_preconditioning(name):
+    """Left preconditioning (Sec. 3.2, the paper's choice): GMRES on P^-1 J x = P^-1 b with
+    preconditioned norms reaches the oracle's Newton solution (right-preconditioned there; the
+    converged displacements do not depend on the side) to the same tolerance."""
+    from paper_2502_17217_gb300 import jfnk
+    if name == "mms2d_bjacobi":
+        ug, uo, st, _ = _solve_both(I.case_mms2d(32), pc_side=1)
+    elif name == "cantilever_mg_mixed":
+        case = I.case_cantilever(20, 4, 4, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
+        ug, uo, st, _ = _solve_both(case, pc=jfnk.PC_MG, mg_coarse_max=50, precision=jfnk.PREC_MIXED, pc_side=1)
+    elif name == "nh_beam_load_steps":
+        case = I.case_nh_beam(16, 4, 4, (1.0, 0.25, 0.25), end_uy=0.25, load_steps=3)
+        ug, uo, st, _ = _solve_both(case, load_steps=3, pc_side=1)
+        assert st.load_steps_done == 3
+    elif name == "loose_gmres8":
+        case = I.case_cantilever(12, 4, 4, (1.0, 0.3, 0.3), perturb=0.1, seed=5)
+        ug, uo, st, _ = _solve_both(case, gmres_restart=8, gmres_aug=2, pc_side=1)
+    else:
+        ug, uo, st, _ = _solve_both(I.case_mms2d(32), gmres_aug=0, pc_side=1)
+    assert _rel(ug, uo) <= 1e-8, _rel(ug, uo)
+
+
+def test_left_preconditioning_first_column():
+    """The first Arnoldi column of a left-preconditioned cycle is P^-1 J V_0: with GMRES(1) and
+    no kept corrections, each Newton step's correction is y V_0 with V_0 = P^-1 b / |P^-1 b|
+    and y minimising |P^-1 (b - J y V_0)|.  Checked against products taken through the C ABI
+    (block-Jacobi, a linear problem, one Newton step with GMRES capped at one restart)."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(8, 3, 3, (1.0, 0.3, 0.3), perturb=0.1, seed=5)
+    s = _solver(case, pc=jfnk.PC_BJACOBI, pc_side=1, gmres_restart=2, gmres_aug=0, gmres_max_restarts=1,
+                newton_max_its=1)
+    u, st, rc = s.solve(raise_on_fail=False)
+    assert st.gmres_its == 2 and st.newton_its == 1
+    u0 = np.zeros_like(u)
+    b = -s.residual(u0)
+    Pb = s.precondition(b, jfnk.PC_BJACOBI)
+    v0 = Pb / np.linalg.norm(Pb)
+    a0 = s.precondition(s.jv(u0, v0), jfnk.PC_BJACOBI)
+    # second basis vector and its image
+    w = a0 - (a0.ravel() @ v0.ravel()) * v0
+    v1 = w / np.linalg.norm(w)
+    a1 = s.precondition(s.jv(u0, v1), jfnk.PC_BJACOBI)
+    A = np.stack([a0.ravel(), a1.ravel()], axis=1)
+    y, *_ = np.linalg.lstsq(A, Pb.ravel(), rcond=None)
+    x = y[0] * v0 + y[1] * v1
+    # the solve's line search takes the full step on a linear problem
+    assert _rel(u, x) <= 1e-6, _rel(u, x)
