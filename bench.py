@@ -56,6 +56,10 @@ def workload_case(name="c2"):
 
 
 DRAM_BYTES_PER_LAUNCH = {"c2": {"update": 16.04e6, "mdot": 16.57e6, "flux": 30.90e6}}
+# FP64 thread instructions (DFMA + DADD + DMUL) per launch, from ncu's per-cycle instruction
+# rates x elapsed cycles of the same capture (k_flux: 47 per internal face, 231,600 of them)
+FP64_INSTR_PER_LAUNCH = {"c2": {"flux": 10.90e6}}
+FP64_ISSUE_PEAK_GINSTR = 152 * 2 * 2.07  # thread instructions per ns: 152 SM x 2 per clock x 2.07 GHz
 KRYLOV = ("loose GMRES(30) keeping 2 corrections across restarts (Sec. 4.2), right-preconditioned, "
           "FP32 basis, FP64 Arnoldi arithmetic")
 WORKLOADS = {
@@ -357,6 +361,20 @@ def run_oracle_sample(case, seconds=10.0):
     return nc * its_total / dt, its_total, dt
 
 
+def fp64_issue(workload, kernel, launch_s, fp64_measured_tflops):
+    """The dominant kernel against the FP64 issue rate rather than the flop rate: a DADD or
+    DMUL takes an issue slot for one flop, so a kernel whose mix has them cannot reach the flop
+    roof even with the pipe always busy.  None where no instruction count was captured."""
+    n = FP64_INSTR_PER_LAUNCH.get(workload, {}).get(kernel)
+    if n is None:
+        return None
+    ach = n / launch_s / 1e9
+    measured = fp64_measured_tflops * 1e3 / 2  # the measuring kernel issues FMAs only
+    return {"instr_per_launch": n, "achieved_ginstr_s": ach, "peak_ginstr_s": FP64_ISSUE_PEAK_GINSTR,
+            "frac": ach / FP64_ISSUE_PEAK_GINSTR, "frac_of_measured": ach / measured,
+            "source": "ncu sm__sass_thread_inst_executed_op_{dfma,dadd,dmul} rates x cycles, one capture"}
+
+
 def run_serving(args):
     """Config 5: Poisson arrivals of solve requests (cells log-uniform 2k-1M, 70% Hooke / 30%
     neo-Hookean with 2 load steps), served with continuous admission (mixed precision, MG),
@@ -506,6 +524,7 @@ def main():
             "hbm_achieved_gbs": nbytes / t_s / 1e9, "hbm_peak_gbs": peaks.get("hbm_gbs"),
             "hbm_frac": nbytes / t_s / 1e9 / peaks.get("hbm_gbs", HBM_PEAK_FALLBACK), "hbm_peak_source": src,
             "avg_launch_us": t_s / max(1, kt["launches"]) * 1e6,
+            "fp64_issue": fp64_issue(args.workload, top, t_s / max(1, kt["launches"]), fp64_measured),
             "others": {k: {"tflops": tot[k][0] / (r["kernels"][k]["ms"] / 1e3) / 1e12,
                            "gbs": tot[k][1] / (r["kernels"][k]["ms"] / 1e3) / 1e9,
                            "share_of_profiled": r["kernels"][k]["ms"] / sum(r["kernels"][q]["ms"] for q in
