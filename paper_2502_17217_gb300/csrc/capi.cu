@@ -5,6 +5,7 @@
 #include <array>
 #include <cmath>
 #include <cstdlib>
+#include <chrono>
 #include <cstring>
 #include <new>
 
@@ -372,8 +373,22 @@ int jfnk_set_load_factor(jfnk_ctx* c, double lambda)
     return JFNK_OK;
 }
 
+// set-up phase times, printed to stderr when JFNK_VERBOSE is set
+struct SetupClock {
+    bool on = getenv("JFNK_VERBOSE") != nullptr;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void lap(const char* what)
+    {
+        if (!on) return;
+        const auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[jfnk] set-up %-22s %8.1f ms\n", what, std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
+
 int jfnk_setup(jfnk_ctx* c)
 {
+    SetupClock clk;
     if (!c) return JFNK_EINVAL;
     if (c->is_batch ? c->batch.empty() : (!c->have_mesh || !c->have_material))
         return jfnk_fail(c, JFNK_ESTATE, "mesh and material (or batch problems) must be set before set-up");
@@ -462,8 +477,10 @@ int jfnk_setup(jfnk_ctx* c)
     // kernels specialised for all-Hooke (0) and all-neo-Hookean (1); otherwise the law is read
     // per cell (2: mixtures and St. Venant-Kirchhoff)
     c->law_mode = (n_lin == P) ? 0 : (n_nh == P ? 1 : 2);
+    clk.lap("problems and materials");
     std::string e = jfnk::build_topology(c->hm, c->opt.renumber != 0, c->topo, c->is_batch ? &group : nullptr);
     if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
+    clk.lap("topology (host)");
     const int nc = c->hm.nc;
     // problems' internal cell ranges and the internal cell -> problem map
     std::vector<int32_t> cell_prob(nc, 0);
@@ -488,10 +505,12 @@ int jfnk_setup(jfnk_ctx* c)
     }
     int rc = jfnk::setup_device_mesh(c);
     if (rc) return rc;
+    clk.lap("mesh upload, geometry");
     rc = jfnk::setup_material_coefficients(c);
     if (rc) return rc;
     rc = jfnk::build_chunks(c);
     if (rc) return rc;
+    clk.lap("coefficients, chunks");
     const size_t v3 = 3 * (size_t)nc;
     double** vecs[] = {&c->u, &c->Ru, &c->w, &c->R, &c->z, &c->x, &c->bvec, &c->wk, &c->tmp, &c->ext};
     for (double** p : vecs) {
@@ -534,13 +553,16 @@ int jfnk_setup(jfnk_ctx* c)
     c->pmask_h = c->pmask_h_store.data();
     rc = jfnk::dynamics_setup(c);
     if (rc) return rc;
+    clk.lap("work vectors");
     rc = jfnk::pc_setup(c);
     if (rc) return rc;
+    clk.lap("preconditioner");
     // every upload and zero-fill above is ordered on the context's stream
     JF_CUDA(c, cudaStreamSynchronize(c->stream));
     rc = jfnk::autotune(c);
     if (rc) return rc;
     JF_CUDA(c, cudaStreamSynchronize(c->stream));
+    clk.lap("autotune");
     c->dirty = false;
     return JFNK_OK;
 }

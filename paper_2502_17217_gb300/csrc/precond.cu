@@ -9,6 +9,7 @@
 // Arithmetic: FP64 (precision FP64) or FP32 (precision MIXED: matrix, smoother, V-cycle).
 // FP32 runs on the wide FP32 pipe of GB300, FP64 on a pipe ~64x narrower.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -598,24 +599,44 @@ int pc_setup(jfnk_ctx* c)
     // renumbering): rows by input index, columns ascending
     MgLevelHost L0;
     L0.n = nc;
-    std::vector<std::vector<std::pair<int32_t, double>>> rows(nc);
-    for (int P = 0; P < nc; P++) rows[t.n2o[P]].push_back({t.n2o[P], -diag[P]});
-    for (int f = 0; f < m.ni; f++) {
-        const int a = t.n2o[t.own[f]], b = t.n2o[t.nei[f]];
-        rows[a].push_back({b, -jc[f]});
-        rows[b].push_back({a, -jc[f]});
-    }
+    // CSR by counting: the diagonal and one entry per internal face on each side, then each
+    // (short) row sorted by column
     L0.rp.assign(nc + 1, 0);
-    for (int i = 0; i < nc; i++) {
-        std::sort(rows[i].begin(), rows[i].end(),
-                  [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
-        for (auto& e : rows[i]) { L0.col.push_back(e.first); L0.val.push_back(e.second); }
-        L0.rp[i + 1] = (int32_t)L0.col.size();
+    for (int i = 0; i < nc; i++) L0.rp[i + 1] = 1;
+    for (int f = 0; f < m.ni; f++) { L0.rp[t.n2o[t.own[f]] + 1]++; L0.rp[t.n2o[t.nei[f]] + 1]++; }
+    for (int i = 0; i < nc; i++) L0.rp[i + 1] += L0.rp[i];
+    L0.col.assign(L0.rp[nc], 0);
+    L0.val.assign(L0.rp[nc], 0.0);
+    {
+        std::vector<int32_t> fill(L0.rp.begin(), L0.rp.end() - 1);
+        for (int P = 0; P < nc; P++) {
+            const int i = t.n2o[P];
+            L0.col[fill[i]] = i;
+            L0.val[fill[i]++] = -diag[P];
+        }
+        for (int f = 0; f < m.ni; f++) {
+            const int a = t.n2o[t.own[f]], b = t.n2o[t.nei[f]];
+            L0.col[fill[a]] = b; L0.val[fill[a]++] = -jc[f];
+            L0.col[fill[b]] = a; L0.val[fill[b]++] = -jc[f];
+        }
     }
+    for (int i = 0; i < nc; i++)  // insertion sort: a handful of entries per row
+        for (int q = L0.rp[i] + 1; q < L0.rp[i + 1]; q++) {
+            const int32_t cq = L0.col[q];
+            const double vq = L0.val[q];
+            int r = q - 1;
+            for (; r >= L0.rp[i] && L0.col[r] > cq; r--) { L0.col[r + 1] = L0.col[r]; L0.val[r + 1] = L0.val[r]; }
+            L0.col[r + 1] = cq;
+            L0.val[r + 1] = vq;
+        }
     std::vector<MgLevelHost> lv;
     std::vector<double> inv;
+    const auto t0 = std::chrono::steady_clock::now();
     std::string e = mg_build_hierarchy(std::move(L0), c->opt.mg_theta, c->opt.mg_max_levels, c->opt.mg_coarse_max,
                                        c->opt.mg_smoothed != 0, lv, inv);
+    if (getenv("JFNK_VERBOSE"))
+        fprintf(stderr, "[jfnk] multigrid hierarchy (host) %8.1f ms\n",
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
     if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
     std::vector<HostTransfer> tr(lv.size());
     for (size_t l = 0; l + 1 < lv.size(); l++)

@@ -4,21 +4,45 @@
 // kernel; plus the aggregation multigrid hierarchy on -J~.  Runs once per mesh (off the hot
 // path); everything it builds is uploaded and used by the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <numeric>
+#include <thread>
 
 #include "jfnk_internal.h"
 
 namespace jfnk {
 
-static std::vector<int32_t> rcm_order(int nc, const std::vector<std::vector<int32_t>>& adj)
+// Runs f(lo, hi) over [0, n) in blocks of `grain` taken by up to 8 host threads (blocks are
+// handed out in order through an atomic counter, so uneven blocks balance).  Each block's
+// results depend on the block alone: the outcome is the same for any thread count.
+template <typename F>
+static void parallel_blocks(int n, int grain, F&& f)
+{
+    const int nblocks = (n + grain - 1) / grain;
+    const int nt = std::max(1, std::min({nblocks, 8, (int)std::thread::hardware_concurrency()}));
+    if (nt <= 1) {
+        for (int b = 0; b < nblocks; b++) f(b * grain, std::min(n, (b + 1) * grain));
+        return;
+    }
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        for (int b = next++; b < nblocks; b = next++) f(b * grain, std::min(n, (b + 1) * grain));
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; t++) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+}
+
+static std::vector<int32_t> rcm_order(int nc, const std::vector<int32_t>& aptr, const std::vector<int32_t>& adj)
 {
     // Reverse Cuthill-McKee (Cuthill & McKee 1969; George 1971): breadth-first search from a
     // minimum-degree cell of each component, visiting neighbours by increasing degree (then
-    // index), and the final order reversed.
+    // index), and the final order reversed.  Adjacency in CSR form (aptr, adj).
     std::vector<int32_t> deg(nc);
-    for (int i = 0; i < nc; i++) deg[i] = (int32_t)adj[i].size();
+    for (int i = 0; i < nc; i++) deg[i] = aptr[i + 1] - aptr[i];
     std::vector<int32_t> cand(nc);
     std::iota(cand.begin(), cand.end(), 0);
     std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return deg[a] < deg[b]; });
@@ -34,8 +58,8 @@ static std::vector<int32_t> rcm_order(int nc, const std::vector<std::vector<int3
         while (head < order.size()) {
             int v = order[head++];
             nb.clear();
-            for (int w : adj[v])
-                if (!seen[w]) nb.push_back(w);
+            for (int q = aptr[v]; q < aptr[v + 1]; q++)
+                if (!seen[adj[q]]) nb.push_back(adj[q]);
             std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
             for (int w : nb) {
                 seen[w] = 1;
@@ -54,12 +78,16 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     t.nc = nc;
     // --- cell numbering
     if (rcm) {
-        std::vector<std::vector<int32_t>> adj(nc);
+        // cell adjacency in CSR form, each cell's neighbours in face order
+        std::vector<int32_t> aptr(nc + 1, 0), adj(2 * (size_t)ni);
+        for (int f = 0; f < ni; f++) { aptr[hm.own[f] + 1]++; aptr[hm.nei[f] + 1]++; }
+        for (int i = 0; i < nc; i++) aptr[i + 1] += aptr[i];
+        std::vector<int32_t> fill(aptr.begin(), aptr.end() - 1);
         for (int f = 0; f < ni; f++) {
-            adj[hm.own[f]].push_back(hm.nei[f]);
-            adj[hm.nei[f]].push_back(hm.own[f]);
+            adj[fill[hm.own[f]]++] = hm.nei[f];
+            adj[fill[hm.nei[f]]++] = hm.own[f];
         }
-        t.n2o = rcm_order(nc, adj);
+        t.n2o = rcm_order(nc, aptr, adj);
     } else {
         t.n2o.resize(nc);
         std::iota(t.n2o.begin(), t.n2o.end(), 0);
@@ -77,9 +105,19 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
         if (a > b) { std::swap(a, b); flip = 1; }
         in[f] = {a, b, f, flip};
     }
-    std::sort(in.begin(), in.end(), [](const FK& x, const FK& y) {
-        return x.a != y.a ? x.a < y.a : (x.b != y.b ? x.b < y.b : x.src < y.src);
-    });
+    {
+        // order by (a, b, src): bucket by a (counting), then each short bucket by (b, src)
+        std::vector<int32_t> cnt(nc + 1, 0);
+        for (const FK& k : in) cnt[k.a + 1]++;
+        for (int i = 0; i < nc; i++) cnt[i + 1] += cnt[i];
+        std::vector<FK> out(ni);
+        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
+        for (const FK& k : in) out[fill[k.a]++] = k;  // stable: src ascending within a bucket
+        for (int i = 0; i < nc; i++)
+            std::sort(out.begin() + cnt[i], out.begin() + cnt[i + 1],
+                      [](const FK& x, const FK& y) { return x.b != y.b ? x.b < y.b : x.src < y.src; });
+        in.swap(out);
+    }
     std::vector<FK> bd[4];  // disp, symm, trac, empty
     for (int f = ni; f < nf; f++) {
         int bt = hm.btype[f - ni];
@@ -279,19 +317,35 @@ static void smoothed_prolongation(const MgLevelHost& F, const std::vector<int32_
         rho = std::max(rho, s / diag[i]);
     }
     const double omega = 4.0 / (3.0 * rho);
-    std::vector<double> acc(nco, 0.0);
-    std::vector<int32_t> mark(nco, -1), list;
-    for (int i = 0; i < n; i++) {
-        list.clear();
-        mark[agg[i]] = i; acc[agg[i]] = 1.0; list.push_back(agg[i]);
-        for (int q = F.rp[i]; q < F.rp[i + 1]; q++) {
-            const int J = agg[F.col[q]];
-            if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list.push_back(J); }
-            acc[J] -= omega * F.val[q] / diag[i];
+    // rows in blocks, each block into its own arrays, then concatenated in row order
+    const int grain = 4096, nb = (n + grain - 1) / grain;
+    std::vector<std::vector<int32_t>> bcol(nb);
+    std::vector<std::vector<double>> bval(nb);
+    std::vector<int32_t> len(n, 0);
+    parallel_blocks(n, grain, [&](int lo, int hi) {
+        std::vector<double> acc(nco, 0.0);
+        std::vector<int32_t> mark(nco, -1), list;
+        auto& oc = bcol[lo / grain];
+        auto& ov = bval[lo / grain];
+        for (int i = lo; i < hi; i++) {
+            list.clear();
+            mark[agg[i]] = i; acc[agg[i]] = 1.0; list.push_back(agg[i]);
+            for (int q = F.rp[i]; q < F.rp[i + 1]; q++) {
+                const int J = agg[F.col[q]];
+                if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list.push_back(J); }
+                acc[J] -= omega * F.val[q] / diag[i];
+            }
+            std::sort(list.begin(), list.end());
+            for (int J : list) { oc.push_back(J); ov.push_back(acc[J]); }
+            len[i] = (int32_t)list.size();
         }
-        std::sort(list.begin(), list.end());
-        for (int J : list) { pcol.push_back(J); pval.push_back(acc[J]); }
-        prp[i + 1] = (int32_t)pcol.size();
+    });
+    for (int i = 0; i < n; i++) prp[i + 1] = prp[i] + len[i];
+    pcol.reserve(prp[n]);
+    pval.reserve(prp[n]);
+    for (int b = 0; b < nb; b++) {
+        pcol.insert(pcol.end(), bcol[b].begin(), bcol[b].end());
+        pval.insert(pval.end(), bval[b].begin(), bval[b].end());
     }
 }
 
@@ -319,26 +373,41 @@ static void galerkin(const MgLevelHost& F, int nco, MgLevelHost& Cl)
     Cl.rp.assign(nco + 1, 0);
     Cl.col.clear();
     Cl.val.clear();
-    std::vector<double> acc(nco, 0.0);
-    std::vector<int32_t> mark(nco, -1), list;
-    for (int I = 0; I < nco; I++) {
-        list.clear();
-        for (int t = tp[I]; t < tp[I + 1]; t++) {
-            const int i = tr[t];
-            const double pI = tv[t];
-            for (int k = F.rp[i]; k < F.rp[i + 1]; k++) {
-                const int j = F.col[k];
-                const double a = pI * F.val[k];
-                for (int q = F.prp[j]; q < F.prp[j + 1]; q++) {
-                    const int J = F.pcol[q];
-                    if (mark[J] != I) { mark[J] = I; acc[J] = 0.0; list.push_back(J); }
-                    acc[J] += a * F.pval[q];
+    const int grain = 1024, nb = (nco + grain - 1) / grain;
+    std::vector<std::vector<int32_t>> bcol(nb);
+    std::vector<std::vector<double>> bval(nb);
+    std::vector<int32_t> len(nco, 0);
+    parallel_blocks(nco, grain, [&](int lo, int hi) {
+        std::vector<double> acc(nco, 0.0);
+        std::vector<int32_t> mark(nco, -1), list;
+        auto& oc = bcol[lo / grain];
+        auto& ov = bval[lo / grain];
+        for (int I = lo; I < hi; I++) {
+            list.clear();
+            for (int t = tp[I]; t < tp[I + 1]; t++) {
+                const int i = tr[t];
+                const double pI = tv[t];
+                for (int k = F.rp[i]; k < F.rp[i + 1]; k++) {
+                    const int j = F.col[k];
+                    const double a = pI * F.val[k];
+                    for (int q = F.prp[j]; q < F.prp[j + 1]; q++) {
+                        const int J = F.pcol[q];
+                        if (mark[J] != I) { mark[J] = I; acc[J] = 0.0; list.push_back(J); }
+                        acc[J] += a * F.pval[q];
+                    }
                 }
             }
+            std::sort(list.begin(), list.end());
+            for (int J : list) { oc.push_back(J); ov.push_back(acc[J]); }
+            len[I] = (int32_t)list.size();
         }
-        std::sort(list.begin(), list.end());
-        for (int J : list) { Cl.col.push_back(J); Cl.val.push_back(acc[J]); }
-        Cl.rp[I + 1] = (int32_t)Cl.col.size();
+    });
+    for (int I = 0; I < nco; I++) Cl.rp[I + 1] = Cl.rp[I] + len[I];
+    Cl.col.reserve(Cl.rp[nco]);
+    Cl.val.reserve(Cl.rp[nco]);
+    for (int b = 0; b < nb; b++) {
+        Cl.col.insert(Cl.col.end(), bcol[b].begin(), bcol[b].end());
+        Cl.val.insert(Cl.val.end(), bval[b].begin(), bval[b].end());
     }
 }
 
@@ -359,44 +428,63 @@ std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels,
         galerkin(F, nco, Cl);
         levels.push_back(std::move(Cl));
     }
-    // explicit inverse of the coarsest matrix via its Cholesky factor
+    // explicit inverse of the coarsest matrix via its Cholesky factor.  The inner products run
+    // with four partial sums (independent chains for the host's FP pipes)
     const MgLevelHost& Lc = levels.back();
     const int n = Lc.n;
+    auto dot = [](const double* a, const double* b, int len) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int q = 0;
+        for (; q + 3 < len; q += 4) {
+            s0 += a[q] * b[q]; s1 += a[q + 1] * b[q + 1]; s2 += a[q + 2] * b[q + 2]; s3 += a[q + 3] * b[q + 3];
+        }
+        for (; q < len; q++) s0 += a[q] * b[q];
+        return (s0 + s1) + (s2 + s3);
+    };
     std::vector<double> A((size_t)n * n, 0.0);
     for (int i = 0; i < n; i++)
         for (int q = Lc.rp[i]; q < Lc.rp[i + 1]; q++) A[(size_t)i * n + Lc.col[q]] = Lc.val[q];
     for (int j = 0; j < n; j++) {
-        double s = A[(size_t)j * n + j];
-        for (int q = 0; q < j; q++) s -= A[(size_t)j * n + q] * A[(size_t)j * n + q];
+        const double* Lj = A.data() + (size_t)j * n;
+        const double s = Lj[j] - dot(Lj, Lj, j);
         if (!(s > 0)) {
             char buf[96];
             snprintf(buf, sizeof buf, "coarse multigrid matrix not positive definite at row %d", j);
             return buf;
         }
-        double d = std::sqrt(s);
+        const double d = std::sqrt(s);
         A[(size_t)j * n + j] = d;
         for (int i = j + 1; i < n; i++) {
-            double t = A[(size_t)i * n + j];
-            for (int q = 0; q < j; q++) t -= A[(size_t)i * n + q] * A[(size_t)j * n + q];
-            A[(size_t)i * n + j] = t / d;
+            double* Li = A.data() + (size_t)i * n;
+            Li[j] = (Li[j] - dot(Li, Lj, j)) / d;
         }
     }
-    // inverse: solve L L^T X = I column by column
+    // X = (L L^T)^-1 = W^T W with W = L^-1: the columns of W by forward substitution (column c
+    // is zero above row c; W is kept transposed, row c of Wt = column c of W, so that the
+    // substitution reads rows of L and of Wt contiguously), then the symmetric product, each
+    // entry a contiguous dot product over the rows both columns share
+    std::vector<double> Wt((size_t)n * n, 0.0);
+    parallel_blocks(n, 8, [&](int lo, int hi) {
+        for (int c = lo; c < hi; c++) {
+            double* w = Wt.data() + (size_t)c * n;
+            w[c] = 1.0 / A[(size_t)c * n + c];
+            for (int i = c + 1; i < n; i++) {
+                const double* Li = A.data() + (size_t)i * n;
+                w[i] = -dot(Li + c, w + c, i - c) / Li[i];
+            }
+        }
+    });
     chol.assign((size_t)n * n, 0.0);
-    std::vector<double> y(n);
-    for (int c = 0; c < n; c++) {
-        for (int i = 0; i < n; i++) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int q = 0; q < i; q++) s -= A[(size_t)i * n + q] * y[q];
-            y[i] = s / A[(size_t)i * n + i];
+    parallel_blocks(n, 8, [&](int lo, int hi) {
+        for (int i = lo; i < hi; i++) {
+            const double* wi = Wt.data() + (size_t)i * n;
+            for (int j = 0; j <= i; j++) {
+                const double t = dot(wi + i, Wt.data() + (size_t)j * n + i, n - i);
+                chol[(size_t)i * n + j] = t;
+                chol[(size_t)j * n + i] = t;
+            }
         }
-        for (int i = n - 1; i >= 0; i--) {
-            double s = y[i];
-            for (int q = i + 1; q < n; q++) s -= A[(size_t)q * n + i] * y[q];
-            y[i] = s / A[(size_t)i * n + i];
-        }
-        for (int i = 0; i < n; i++) chol[(size_t)i * n + c] = y[i];
-    }
+    });
     return "";
 }
 
