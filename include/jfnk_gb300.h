@@ -145,6 +145,17 @@ int jfnk_set_options(jfnk_ctx* ctx, const jfnk_options* opt);
 int jfnk_set_mesh(jfnk_ctx* ctx, int dim, int32_t n_points, const double* points, int32_t n_faces,
                   const int32_t* face_ptr, const int32_t* face_pts, const int32_t* owner,
                   int32_t n_internal, const int32_t* neighbour, int32_t n_cells);
+/* Convenience builder: the structured nx x ny x nz hexahedral block whose lattice points are
+ * points [(nx+1)(ny+1)(nz+1)][3], point (i, j, k) at i + (nx+1)(j + (ny+1) k), cell (i, j, k)
+ * numbered i + nx (j + ny k), as a face-addressed mesh (same semantics as jfnk_set_mesh):
+ * internal faces ordered by (owner, neighbour), then six boundary patches x-min, x-max,
+ * y-min, y-max, z-min, z-max (jfnk_hex_patch gives their face ranges).  dim = 2 needs nz = 1
+ * and makes the z patches EMPTY.  Errors: JFNK_EINVAL for sizes below 1, a null array, or
+ * more faces than int32 indexing holds; then those of jfnk_set_mesh. */
+int jfnk_set_mesh_hex(jfnk_ctx* ctx, int nx, int ny, int nz, const double* points, int dim);
+/* First face and face count of side 0..5 (x-min, x-max, y-min, y-max, z-min, z-max) of the
+ * block built by jfnk_set_mesh_hex; pure arithmetic, no context.  JFNK_EINVAL otherwise. */
+int jfnk_hex_patch(int nx, int ny, int nz, int side, int32_t* first_face, int32_t* n_faces);
 /* Boundary faces [first_face, first_face + n_faces) get bc_type.  values [n_faces][3]:
  * prescribed displacement (DISP) or traction per unit (reference) area (TRAC); NULL = zero.
  * SYMM faces are symmetry planes (Eq. symm: shear-free, the face acting as a mirror; values

@@ -34,6 +34,7 @@ EXPORTS = [
     "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64", "jfnk_batch_add", "jfnk_batch_size",
     "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate", "jfnk_get_tuning", "jfnk_set_tuning",
     "jfnk_solve_segregated", "jfnk_solve_dynamic", "jfnk_dynamic_reset", "jfnk_synchronize",
+    "jfnk_set_mesh_hex", "jfnk_hex_patch",
 ]
 
 
@@ -90,6 +91,8 @@ def load():
         "jfnk_solve_dynamic": (i, [vp, dp, i, i, C.c_int32, dp, i, C.POINTER(Stats), vp]),
         "jfnk_dynamic_reset": (i, [vp]),
         "jfnk_synchronize": (i, [vp]),
+        "jfnk_set_mesh_hex": (i, [vp, i, i, i, dp, i]),
+        "jfnk_hex_patch": (i, [i, i, i, i, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
         "jfnk_get_geometry": (i, [vp, dp, dp, dp, dp]),
         "jfnk_get_gradient": (i, [vp, dp]),
         "jfnk_get_permutation": (i, [vp, i32p]),

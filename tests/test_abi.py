@@ -61,3 +61,18 @@ def test_no_cpu_fallback_in_the_binding():
     assert "oracle" not in src
     for name in os.listdir(os.path.join(ROOT, "paper_2502_17217_gb300", "csrc")):
         assert "oracle" not in open(os.path.join(ROOT, "paper_2502_17217_gb300", "csrc", name)).read().lower()
+
+
+def test_hex_patch_ranges_match_the_python_block_builder(lib):
+    """jfnk_hex_patch (pure arithmetic, no device) gives the face ranges of the six sides of the
+    structured block, in the order and sizes of the face-addressed builder in inputs.py."""
+    from paper_2502_17217_gb300 import inputs as I
+    for nx, ny, nz in [(3, 4, 5), (1, 1, 1), (7, 2, 1), (200, 20, 20)]:
+        m = I.hex_box(nx, ny, nz)
+        for side, name in enumerate(["xmin", "xmax", "ymin", "ymax", "zmin", "zmax"]):
+            f0, nf = C.c_int32(-1), C.c_int32(-1)
+            assert lib.jfnk_hex_patch(nx, ny, nz, side, C.byref(f0), C.byref(nf)) == 0
+            p = m.patch(name)
+            assert (f0.value, nf.value) == (p.start, p.size), (nx, ny, nz, name)
+    assert lib.jfnk_hex_patch(0, 1, 1, 0, None, None) == -1
+    assert lib.jfnk_hex_patch(2, 2, 2, 6, None, None) == -1
