@@ -3,9 +3,11 @@
 //   block-Jacobi  z_P = [J~]_PP^-1 v_P  (a scalar per cell without symmetry faces);
 //   multigrid     one V-cycle of an aggregation AMG on A = -J~ (the paper uses BoomerAMG,
 //                 one V-cycle per Krylov iteration with one pre- and one post-sweep;
-//                 Sec. 4.2).  The fine level is applied matrix-free from the per-face J~
-//                 coefficients; coarse levels are CSR; the coarsest is a dense inverse.
-//                 All three components go through each level in one pass.
+//                 Sec. 4.2).  The fine level is applied matrix-free over the cells'
+//                 sliced-ELL neighbour slots with a per-slot copy of the J~ face
+//                 coefficient; coarse levels are CSR rows taken by lane groups; the
+//                 coarsest is a dense inverse.  All three components go through each level
+//                 in one pass.
 // Arithmetic: FP64 (precision FP64) or FP32 (precision MIXED: matrix, smoother, V-cycle).
 // FP32 runs on the wide FP32 pipe of GB300, FP64 on a pipe ~64x narrower.
 #include <algorithm>
