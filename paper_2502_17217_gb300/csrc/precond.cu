@@ -299,6 +299,8 @@ __global__ void k_mg_spmv(const int* gate, int nrow, int nx, const int32_t* __re
     }
 }
 
+constexpr int kCoarseWarps = 4;  // warps per row of the block-per-row kernels
+
 // Long CSR rows (P^T, coarse A) are taken by a group of G lanes (G a power of two <= 32,
 // about half the row's mean length, so a warp holds 32/G rows and each lane two entries of a
 // row per step, both loaded before they are used), then summed by a shuffle tree of the group.
@@ -393,9 +395,46 @@ __global__ void k_mg_csr_grp(const int* gate, int n, const int32_t* __restrict__
     }
 }
 
-// lanes per row for CSR rows of mean length `mean`: the power of two near half of it, 4..32
+// y = M x (add = 0) or y += M x (add = 1) for rows longer than a warp's two-entry step: one
+// block of kCoarseWarps warps per row, the warps' sums combined in shared memory
+template <typename T>
+__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_spmv_blk(const int* gate, int nrow, int nx,
+                                                                   const int32_t* __restrict__ rp,
+                                                                   const int32_t* __restrict__ col,
+                                                                   const T* __restrict__ val, const T* __restrict__ x,
+                                                                   T* __restrict__ y, int add)
+{
+    JF_PDL_ENTRY();
+    if (gate && *gate) return;
+    const int i = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ T part[3][kCoarseWarps];
+    T s0 = 0, s1 = 0, s2 = 0;
+    group_row<32 * kCoarseWarps, T>(rp[i], rp[i + 1], threadIdx.x, col, val,
+                                    [&](int j, int k) { return x[(size_t)k * nx + j]; }, s0, s1, s2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) { part[0][wid] = s0; part[1][wid] = s1; part[2][wid] = s2; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        T t = 0;
+#pragma unroll
+        for (int w = 0; w < kCoarseWarps; w++) t += part[threadIdx.x][w];
+        T* yk = y + (size_t)threadIdx.x * nrow + i;
+        if (add) *yk += t;
+        else *yk = t;
+    }
+}
+
+// lanes per row for CSR rows of mean length `mean`: the power of two near half of it, 4..32,
+// and 32 * kCoarseWarps (a block per row, restrictions only) for rows of more than two warp
+// steps of two entries per lane
 inline int group_lanes(double mean)
 {
+    if (mean > 4.0 * 32) return 32 * kCoarseWarps;
     int g = 4;
     while (g < 32 && 2.0 * g < mean) g *= 2;
     return g;
@@ -404,6 +443,7 @@ inline int group_lanes(double mean)
 template <typename T, typename... A>
 static void launch_csr_grp(jfnk_ctx* c, int g, long rows, A... args)
 {
+    g = std::min(g, 32);
     const dim3 grid((unsigned)std::max<long>(1, (rows * g + 255) / 256)), block(256);
     switch (g) {
         case 4: jfnk_launch(c, k_mg_csr_grp<T, 4>, grid, block, args...); break;
@@ -416,6 +456,10 @@ static void launch_csr_grp(jfnk_ctx* c, int g, long rows, A... args)
 template <typename T, typename... A>
 static void launch_spmv_grp(jfnk_ctx* c, int g, long rows, A... args)
 {
+    if (g > 32) {
+        jfnk_launch(c, k_mg_spmv_blk<T>, dim3((unsigned)std::max<long>(1, rows)), dim3(32 * kCoarseWarps), args...);
+        return;
+    }
     const dim3 grid((unsigned)std::max<long>(1, (rows * g + 255) / 256)), block(256);
     switch (g) {
         case 4: jfnk_launch(c, k_mg_spmv_grp<T, 4>, grid, block, args...); break;
@@ -425,19 +469,30 @@ static void launch_spmv_grp(jfnk_ctx* c, int g, long rows, A... args)
     }
 }
 
-// coarsest level: x = A_c^-1 b with the dense (symmetric) inverse, one warp per row
+// coarsest level: x = A_c^-1 b with the dense (symmetric) inverse, one block of kCoarseWarps
+// warps per row, each warp a strided quarter of the row with two entries per lane and step
+// loaded before use, the warps' sums combined in shared memory
+
 template <typename T>
-__global__ void k_mg_coarse(const int* gate, int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x)
+__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_coarse(const int* gate, int n, const T* __restrict__ Ainv,
+                                                                 const T* __restrict__ b, T* __restrict__ x)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= n) return;
+    const int r = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ T part[3][kCoarseWarps];
     T s0 = 0, s1 = 0, s2 = 0;
-    const T* row = Ainv + (size_t)w * n;
-    for (int k = lane; k < n; k += 32) {
-        const T a = row[k];
-        s0 += a * b[k]; s1 += a * b[n + k]; s2 += a * b[2 * (size_t)n + k];
+    const T* row = Ainv + (size_t)r * n;
+    constexpr int step = 32 * kCoarseWarps;
+    for (int k = threadIdx.x; k < n; k += 2 * step) {
+        const int k1 = k + step;
+        const bool h1 = k1 < n;
+        const T a0 = row[k], a1 = h1 ? row[k1] : (T)0;
+        const T b00 = b[k], b01 = b[n + k], b02 = b[2 * (size_t)n + k];
+        T b10 = 0, b11 = 0, b12 = 0;
+        if (h1) { b10 = b[k1]; b11 = b[n + k1]; b12 = b[2 * (size_t)n + k1]; }
+        s0 += a0 * b00; s1 += a0 * b01; s2 += a0 * b02;
+        if (h1) { s0 += a1 * b10; s1 += a1 * b11; s2 += a1 * b12; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -445,7 +500,14 @@ __global__ void k_mg_coarse(const int* gate, int n, const T* __restrict__ Ainv, 
         s1 += __shfl_down_sync(0xffffffffu, s1, o);
         s2 += __shfl_down_sync(0xffffffffu, s2, o);
     }
-    if (lane == 0) { x[w] = s0; x[n + w] = s1; x[2 * (size_t)n + w] = s2; }
+    if (lane == 0) { part[0][wid] = s0; part[1][wid] = s1; part[2][wid] = s2; }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        T t = 0;
+#pragma unroll
+        for (int w = 0; w < kCoarseWarps; w++) t += part[threadIdx.x][w];
+        x[(size_t)threadIdx.x * n + r] = t;
+    }
 }
 
 // ------------------------------------------------------------------ device hierarchy
@@ -710,7 +772,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         auto& D = M.L[0];
         jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, vbase, ld, jidx, D.dinv, (T)0, D.b, D.x2);
         JF_LAUNCHED(c);
-        jfnk_launch(c, k_mg_coarse<T>, dim3(nb(32L * D.n, 256)), dim3(256), gate, D.n, M.Ainv, D.b, D.x);
+        jfnk_launch(c, k_mg_coarse<T>, dim3(D.n), dim3(32 * kCoarseWarps), gate, D.n, M.Ainv, D.b, D.x);
         JF_LAUNCHED(c);
         jfnk_launch(c, k_copy_to_double<T>, dim3(nb(3L * D.n, 256)), dim3(256), gate, 3 * (size_t)D.n, D.x, z);
         JF_LAUNCHED(c);
@@ -755,7 +817,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     {
         auto& Dc = M.L[nl - 1];
         jfnk_prof_begin(c, s_co);
-        jfnk_launch(c, k_mg_coarse<T>, dim3(nb(32L * Dc.n, 256)), dim3(256), gate, Dc.n, M.Ainv, Dc.b, Dc.x);
+        jfnk_launch(c, k_mg_coarse<T>, dim3(Dc.n), dim3(32 * kCoarseWarps), gate, Dc.n, M.Ainv, Dc.b, Dc.x);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_co);
     }
