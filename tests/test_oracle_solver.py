@@ -359,3 +359,35 @@ def test_st_venant_kirchhoff_law_from_its_definition():
         Gs = t * G
         hooke = mu * (Gs + Gs.T) + lam * np.trace(Gs) * np.eye(3)
         assert np.abs(o.cauchy_stress(Gs) - hooke).max() < 20 * t * np.abs(hooke).max()
+
+
+def _beam_tip(nx, ny, nz, u, mesh):
+    """Mean y-displacement of the last cell layer and the cantilever-beam value at its centre
+    plane (Euler-Bernoulli F x^2 (3L - x) / (6 E I) plus the Timoshenko shear term F x / (k G A),
+    k = 5/6) for the 1 x 0.1 x 0.1 m, E = 200 GPa, nu = 0.3 beam under F = 1 MPa x 0.01 m^2."""
+    x = mesh.nominal_cell_centres()
+    tip = x[:, 0] > 1.0 - 1.0 / nx
+    L, E, nu, A = 1.0, 200e9, 0.3, 0.01
+    I_ = 0.1 * 0.1 ** 3 / 12.0
+    F = 1e6 * A
+    xc = x[tip, 0].mean()
+    beam = F * xc ** 2 * (3 * L - xc) / (6 * E * I_) + F * xc / (5.0 / 6.0 * E / (2 * (1 + nu)) * A)
+    return u[tip, 1].mean(), beam
+
+
+def test_cantilever_tip_deflection_approaches_beam_theory():
+    """Config 2 sanity (the 1 m cantilever with the 1 MPa end shear): the tip deflection tends to
+    the beam value F L^3 / (3 E I) = 2.0 mm (+ shear) from below as the cross-section is refined
+    (4 and 8 cells through the thickness: ratio 0.65 and 0.85; 20, the 80k-cell case, 0.96 in
+    the GPU tests), the error falling by more than half per halving of h."""
+    ratios = []
+    for n in (4, 8):
+        c = I.case_cantilever(10 * n, n, n, (1.0, 0.1, 0.1))
+        o = O.Oracle.from_case(c)
+        o.mg_setup(coarse_max=50, smoothed=True, sweeps=2)
+        u, rc, st = o.newton(load_steps=1, rtol=1e-8, pc=O.PC_MG, m=30, aug=2)
+        assert rc == 0
+        tip, beam = _beam_tip(10 * n, n, n, u, c.mesh)
+        ratios.append(tip / beam)
+    assert 0.6 < ratios[0] < ratios[1] < 1.0, ratios
+    assert (1.0 - ratios[1]) < 0.5 * (1.0 - ratios[0]), ratios
