@@ -377,8 +377,10 @@ bool tuning_valid(const Tuning& t);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);
 int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate);
+// eps_formed (optional): asks the multigrid's last sweep to form the following Jv's eps for a
+// single problem; set to whether it did (else the caller runs the norm pass)
 int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z,
-                 const int* gate);
+                 const int* gate, bool* eps_formed = nullptr);
 void mg_release(jfnk_ctx* c);
 int mg_levels_info(jfnk_ctx* c, std::vector<int>& sizes);
 // solver.cu

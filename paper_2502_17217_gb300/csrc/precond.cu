@@ -265,6 +265,54 @@ __global__ void k_mg_jacobi(const int* gate, LevelOp<T> op, T omega, const T* __
     }
 }
 
+// The last sweep of a V-cycle that feeds a Jacobian product (one problem): as k_mg_jacobi with
+// z written as double, and |z|^2 summed per block; the last block forms the product's step
+// eps = s (1 + |u|) / |z| (Eq. JF) and 1 / eps, as the norm pass would have (no launch of it)
+struct EpsOut {
+    ProbDev* pd;
+    double* partials;  // one per block
+    double s;          // jv_eps_scale
+};
+
+template <typename T>
+__global__ void k_mg_jacobi_eps(const int* gate, LevelOp<T> op, T omega, const T* __restrict__ b, const T* __restrict__ x,
+                                double* __restrict__ zd, EpsOut E)
+{
+    JF_PDL_ENTRY();
+    if (gate && *gate) return;
+    ProbDev& P = E.pd[0];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = op.n;
+    double a = 0.0;
+    if (i < n) {  // threads past the end still take part in the block sum
+        T ax[3];
+        op.row(i, x, ax);
+        const T d = omega * op.dinv[i];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const T xn = x[(size_t)k * n + i] + d * (b[(size_t)k * n + i] - ax[k]);
+            const double zv = to_f64(xn);
+            zd[(size_t)k * n + i] = zv;
+            a = fma(zv, zv, a);
+        }
+    }
+    __shared__ double sh[32];
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) E.partials[blockIdx.x] = a;
+    if (!ticket_last(&P.ticket[2], gridDim.x)) return;
+    if (threadIdx.x < 32) {
+        const double tot = warp_sum_strided(E.partials, gridDim.x);
+        if (threadIdx.x == 0) {
+            const double nrm = sqrt(tot);
+            if (P.active && !P.done) {
+                P.eps = (nrm > 0.0) ? E.s * (1.0 + P.unorm) / nrm : 0.0;
+                P.ieps = P.eps != 0.0 ? 1.0 / P.eps : 0.0;
+            }
+            P.ticket[2] = 0u;
+        }
+    }
+}
+
 // r = b - A x
 template <typename T>
 __global__ void k_mg_resid(const int* gate, LevelOp<T> op, const T* __restrict__ b, const T* __restrict__ x,
@@ -757,7 +805,8 @@ static LevelOp<T> level_op(const jfnk_ctx* c, const MgDev<T>& M, int l)
 }
 
 template <typename T, typename TV>
-static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const int* jidx, double* z, const int* gate)
+static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const int* jidx, double* z, const int* gate,
+                  bool* eps_formed)
 {
     cudaStream_t s = c->cur;
     const bool pf = c->prof.enabled;
@@ -833,7 +882,12 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         jfnk_prof_begin(c, s_sm);
         for (int sw = 0; sw < sweeps; sw++) {
             const bool last = (l == 0 && sw == sweeps - 1);
-            if (l == 0) jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
+            if (last && eps_formed) {
+                const EpsOut E{c->pd, c->partials, c->opt.jv_eps_scale};
+                jfnk_launch(c, k_mg_jacobi_eps<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, (const T*)D.b, (const T*)D.x, z, E);
+                *eps_formed = true;
+            } else if (l == 0)
+                jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
             else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                    (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
             JF_LAUNCHED(c);
@@ -845,8 +899,12 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
 }
 
 // z = P^-1 v with v = vbase + (*jidx) * ld (jidx given) or vbase; v double or float; gate may be null
-int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z, const int* gate)
+int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z, const int* gate,
+                 bool* eps_formed)
 {
+    if (eps_formed) *eps_formed = false;
+    // the multigrid's last sweep forms the Jv step of a single problem (batches keep the norm pass)
+    bool* want_eps = (eps_formed && c->nprob == 1) ? eps_formed : nullptr;
     const int nc = c->dm.nc;
     const bool fp32 = c->opt.precision == JFNK_PREC_MIXED;
     cudaStream_t s = c->cur;
@@ -876,10 +934,10 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
         MgState& S = mg_state(c);
         if (!S.ready) return jfnk_fail(c, JFNK_ESTATE, "multigrid preconditioner not set up (options.pc must be JFNK_PC_MG at set-up)");
         int rc;
-        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)vbase, ld, jidx, z, gate)
-                                  : vcycle<float, double>(c, S.f, (const double*)vbase, ld, jidx, z, gate);
-        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)vbase, ld, jidx, z, gate)
-                             : vcycle<double, double>(c, S.d, (const double*)vbase, ld, jidx, z, gate);
+        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)vbase, ld, jidx, z, gate, want_eps)
+                                  : vcycle<float, double>(c, S.f, (const double*)vbase, ld, jidx, z, gate, want_eps);
+        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)vbase, ld, jidx, z, gate, want_eps)
+                             : vcycle<double, double>(c, S.d, (const double*)vbase, ld, jidx, z, gate, want_eps);
         if (rc) return rc;
     } else {
         if (v_is_float) jfnk_launch(c, k_copy_vec<float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, z);

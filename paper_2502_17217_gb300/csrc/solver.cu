@@ -74,8 +74,9 @@ static int enqueue_iteration(jfnk_ctx* c)
         JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
         return JFNK_OK;
     }
-    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate))) return rc;
-    if ((rc = pnorm(c, c->z, 1, true))) return rc;
+    bool eps_formed = false;
+    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate, &eps_formed))) return rc;
+    if (!eps_formed && (rc = pnorm(c, c->z, 1, true))) return rc;
     if ((rc = perturb(c, c->u, c->z, c->w, true))) return rc;
     if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, nullptr, gate))) return rc;
     if ((rc = arnoldi_orthogonalise(c, c->wk))) return rc;
