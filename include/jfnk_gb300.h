@@ -259,7 +259,12 @@ int jfnk_get_geometry(jfnk_ctx* ctx, double* Sf, double* Cf, double* V, double* 
 int jfnk_get_gradient(jfnk_ctx* ctx, double* grad);
 /* Internal cell order: new_to_old[n_cells] (host array). */
 int jfnk_get_permutation(jfnk_ctx* ctx, int32_t* new_to_old);
-/* Kernel timing: when enabled, CUDA events bracket every launch of the named kernels. */
+/* Kernel timing: enable = 1 brackets every launch of the residual passes ("grad", "flux",
+ * "finish"), the Gram-Schmidt kernels ("mdot", "update") and each preconditioner application
+ * ("pc_mg", "pc_bjacobi") with CUDA events (the solver then launches kernels directly instead
+ * of replaying its iteration graph); 2 also brackets the steps inside each V-cycle
+ * ("mg_smooth", "mg_resid", "mg_restrict", "mg_prolong", "mg_coarse"), whose own events add to
+ * "pc_mg"; 0 turns timing off. */
 int jfnk_profile_enable(jfnk_ctx* ctx, int enable);
 /* Accumulated time (ms) and launch count of kernel `name` since the last reset; returns
  * JFNK_EINVAL for unknown names.  Synchronises the context's last stream. */

@@ -797,6 +797,7 @@ int jfnk_profile_enable(jfnk_ctx* c, int enable)
 {
     if (!c) return JFNK_EINVAL;
     c->prof.enabled = enable != 0;
+    c->prof.detail = enable >= 2;
     return JFNK_OK;
 }
 

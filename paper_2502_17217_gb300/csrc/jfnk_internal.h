@@ -162,6 +162,7 @@ struct GlobalDev {
 
 struct Profiler {
     bool enabled = false;
+    bool detail = false;  // also the multigrid's steps inside each V-cycle
     struct Slot {
         std::string name;
         std::vector<cudaEvent_t> ev;   // pairs

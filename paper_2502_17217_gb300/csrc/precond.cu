@@ -809,7 +809,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
                   bool* eps_formed)
 {
     cudaStream_t s = c->cur;
-    const bool pf = c->prof.enabled;
+    const bool pf = c->prof.enabled && c->prof.detail;
     const int s_sm = pf ? c->prof.slot("mg_smooth") : -1, s_re = pf ? c->prof.slot("mg_resid") : -1;
     const int s_rs = pf ? c->prof.slot("mg_restrict") : -1, s_pr = pf ? c->prof.slot("mg_prolong") : -1;
     const int s_co = pf ? c->prof.slot("mg_coarse") : -1;

@@ -321,8 +321,9 @@ class Solver:
         self._check(self.L.jfnk_get_permutation(self.h, _ptr(p)))
         return p
 
-    def profile(self, enable=True):
-        self._check(self.L.jfnk_profile_enable(self.h, int(enable)))
+    def profile(self, enable=True, detail=False):
+        """Per-kernel CUDA-event timing; detail=True also times the steps inside each V-cycle."""
+        self._check(self.L.jfnk_profile_enable(self.h, (2 if detail else 1) if enable else 0))
 
     def profile_get(self, name):
         ms, n = C.c_double(0), C.c_int64(0)
