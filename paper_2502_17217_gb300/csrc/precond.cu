@@ -296,12 +296,20 @@ __global__ void k_mg_jacobi_eps(const int* gate, LevelOp<T> op, T omega, const T
             a = fma(zv, zv, a);
         }
     }
+    // partial sums per group of 128 cells (four warps), whatever the block size (a multiple of
+    // 128 chosen by the autotuner), so that eps does not depend on the launch shape
     __shared__ double sh[32];
-    a = block_sum(a, sh);
-    if (threadIdx.x == 0) E.partials[blockIdx.x] = a;
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    const int gpb = blockDim.x / 128;  // groups per block
+    if ((int)threadIdx.x < gpb) {
+        const double* w = sh + 4 * threadIdx.x;
+        E.partials[blockIdx.x * gpb + threadIdx.x] = (w[0] + w[1]) + (w[2] + w[3]);
+    }
     if (!ticket_last(&P.ticket[2], gridDim.x)) return;
     if (threadIdx.x < 32) {
-        const double tot = warp_sum_strided(E.partials, gridDim.x);
+        const double tot = warp_sum_strided(E.partials, (n + 127) / 128);
         if (threadIdx.x == 0) {
             const double nrm = sqrt(tot);
             if (P.active && !P.done) {

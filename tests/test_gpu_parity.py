@@ -573,3 +573,20 @@ def test_cantilever_80k_tip_deflection_within_a_few_percent_of_beam_theory():
     beam = F * xc ** 2 * (3 * L - xc) / (6 * E * I_) + F * xc / (5.0 / 6.0 * E / (2 * (1 + nu)) * A)
     ratio = u[tip, 1].mean() / beam
     assert 0.95 < ratio < 1.0, ratio
+
+
+def test_solve_does_not_depend_on_the_launch_shapes():
+    """Whole solves (the V-cycle's last sweep also forms the Jv step) are bitwise equal for
+    every launch shape the autotuner may pick, so a served request's result does not depend
+    on the shapes its set-up timed under contention."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(40, 12, 12, (1.0, 0.3, 0.3), perturb=0.15, seed=2)
+    s = _solver(case, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED)
+    ref = None
+    for sh in [(128, 256, 0, 256, 128), (64, 128, 1, 512, 512), (256, 256, 0, 128, 256)]:
+        s.set_tuning(*sh)
+        u, st, rc = s.solve()
+        assert rc == 0
+        if ref is None:
+            ref = u
+        assert np.array_equal(u, ref), sh
