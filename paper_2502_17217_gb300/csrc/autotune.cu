@@ -98,7 +98,7 @@ int autotune(jfnk_ctx* c)
     c->prof.enabled = false;
     c->cur = c->stream;
     const int64_t launches = c->launches;
-    auto res = [&]() { return residual_bufs(c, c->u, c->R, OUT_R, nullptr, nullptr, c->G, c->T, c->F, c->Fn); };
+    auto res = [&]() { return residual_bufs(c, c->u, c->R, OUT_R, nullptr, c->G, c->T, c->F, c->Fn); };
     Tuning& t = c->tune;
     int rc = sync_load(c);
     // coordinate descent: each parameter over its candidates, the others held

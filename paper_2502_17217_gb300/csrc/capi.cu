@@ -659,7 +659,7 @@ int jfnk_residual(jfnk_ctx* c, const double* u, double* R, int mem, void* stream
     if (rc) return rc;
     if (!u || !R || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE)) return jfnk_fail(c, JFNK_EINVAL, "jfnk_residual: bad arguments");
     if ((rc = load_vec(c, u, mem, c->u))) return rc;
-    if ((rc = jfnk::residual(c, c->u, c->R, jfnk::OUT_R, nullptr))) return rc;
+    if ((rc = jfnk::residual(c, c->u, c->R, jfnk::OUT_R))) return rc;
     return store_vec(c, c->R, mem, R);
 }
 
@@ -670,11 +670,11 @@ int jfnk_jv(jfnk_ctx* c, const double* u, const double* v, double* Jv, int mem, 
     if (!u || !v || !Jv || (mem != JFNK_MEM_HOST && mem != JFNK_MEM_DEVICE)) return jfnk_fail(c, JFNK_EINVAL, "jfnk_jv: bad arguments");
     if ((rc = load_vec(c, u, mem, c->u))) return rc;
     if ((rc = load_vec(c, v, mem, c->z))) return rc;
-    if ((rc = jfnk::residual(c, c->u, c->Ru, jfnk::OUT_R, nullptr))) return rc;
+    if ((rc = jfnk::residual(c, c->u, c->Ru, jfnk::OUT_R))) return rc;
     if ((rc = jfnk::pnorm(c, c->u, 2, false))) return rc;
     if ((rc = jfnk::pnorm(c, c->z, 1, false))) return rc;
     if ((rc = jfnk::perturb(c, c->u, c->z, c->w, false))) return rc;
-    if ((rc = jfnk::residual(c, c->w, c->tmp, jfnk::OUT_JV, nullptr))) return rc;
+    if ((rc = jfnk::residual(c, c->w, c->tmp, jfnk::OUT_JV))) return rc;
     return store_vec(c, c->tmp, mem, Jv);
 }
 

@@ -341,13 +341,13 @@ int setup_device_mesh(jfnk_ctx* c);
 int setup_material_coefficients(jfnk_ctx* c);
 // residual.cu
 enum ResidualOut { OUT_R = 0, OUT_JV = 1 };
-// R(u_int) into `out` (internal order); mode OUT_JV writes (R - Ru) * (1/eps) with eps read
-// from the device scalar `eps_dev`.
-int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev);
-int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate);
+// R(u_int) into `out` (internal order); mode OUT_JV writes (R - Ru) / eps_p with each
+// problem's eps_p (and 1 / eps_p) from its ProbDev.
+int residual(jfnk_ctx* c, const double* u_int, double* out, int mode);
+int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate);
 int sync_load(jfnk_ctx* c);
-int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate,
-                  double* G, double* T, double* F, double* Fn);
+int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
+                  double* F, double* Fn);
 // linalg.cu
 int perm_in(jfnk_ctx* c, const double* ext_aos, double* int_soa);
 int build_chunks(jfnk_ctx* c);

@@ -82,7 +82,7 @@ extern "C" int jfnk_residual_noalloc(jfnk_ctx* c, const double* u, double* R, vo
     double* R_int = Fn + 3 * (size_t)m.ni;
     rc = jfnk::sync_load(c);
     if (!rc) rc = jfnk::perm_in(c, u, u_int);
-    if (!rc) rc = jfnk::residual_bufs(c, u_int, R_int, jfnk::OUT_R, nullptr, nullptr, G, T, F, Fn);
+    if (!rc) rc = jfnk::residual_bufs(c, u_int, R_int, jfnk::OUT_R, nullptr, G, T, F, Fn);
     if (!rc) rc = jfnk::perm_out(c, R_int, R);
     return rc;
 }

@@ -816,7 +816,6 @@ template <typename T, typename TV>
 static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const int* jidx, double* z, const int* gate,
                   bool* eps_formed)
 {
-    cudaStream_t s = c->cur;
     const bool pf = c->prof.enabled && c->prof.detail;
     const int s_sm = pf ? c->prof.slot("mg_smooth") : -1, s_re = pf ? c->prof.slot("mg_resid") : -1;
     const int s_rs = pf ? c->prof.slot("mg_restrict") : -1, s_pr = pf ? c->prof.slot("mg_prolong") : -1;
@@ -915,7 +914,6 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
     bool* want_eps = (eps_formed && c->nprob == 1) ? eps_formed : nullptr;
     const int nc = c->dm.nc;
     const bool fp32 = c->opt.precision == JFNK_PREC_MIXED;
-    cudaStream_t s = c->cur;
     int sl = c->prof.enabled ? c->prof.slot(pc == JFNK_PC_MG ? "pc_mg" : "pc_bjacobi") : -1;
     jfnk_prof_begin(c, sl);
     if (pc == JFNK_PC_BJACOBI && c->dm.jt_binv) {

@@ -366,16 +366,15 @@ int sync_load(jfnk_ctx* c)
     return JFNK_OK;
 }
 
-int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate)
+int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate)
 {
-    return residual_bufs(c, u_int, out, mode, eps_dev, gate, c->G, c->T, c->F, c->Fn);
+    return residual_bufs(c, u_int, out, mode, gate, c->G, c->T, c->F, c->Fn);
 }
 
-int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev, const int* gate,
-                  double* G, double* T, double* F, double* Fn)
+int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
+                  double* F, double* Fn)
 {
     const DevMesh& m = c->dm;
-    cudaStream_t s = c->cur;
     static const char* const kNames[3] = {"grad", "flux", "finish"};
     int sl[3];
     for (int q = 0; q < 3; q++) sl[q] = c->prof.enabled ? c->prof.slot(kNames[q]) : -1;
@@ -432,11 +431,11 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     return JFNK_OK;
 }
 
-int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, const double* eps_dev)
+int residual(jfnk_ctx* c, const double* u_int, double* out, int mode)
 {
     int rc = sync_load(c);
     if (rc) return rc;
-    return residual_gated(c, u_int, out, mode, eps_dev, nullptr);
+    return residual_gated(c, u_int, out, mode, nullptr);
 }
 
 }  // namespace jfnk

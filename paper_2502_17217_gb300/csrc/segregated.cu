@@ -328,7 +328,7 @@ int segregated(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
     for (int step = 1; step <= n_load_steps; step++) {
         c->load = (double)step / n_load_steps;
         if ((rc = sync_load(c))) return rc;
-        if ((rc = residual(c, c->u, c->Ru, OUT_R, nullptr))) return rc;
+        if ((rc = residual(c, c->u, c->Ru, OUT_R))) return rc;
         if ((rc = pnorm(c, c->Ru, 0, false))) return rc;
         JF_CUDA(c, cudaMemcpy2DAsync(c->ph, sizeof(ProbDev), c->pd, sizeof(ProbDev), offsetof(ProbDev, h), P,
                                      cudaMemcpyDeviceToHost, c->cur));
@@ -379,7 +379,7 @@ int segregated(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
             }
             // u += du for the problems that iterated (converged ones have du = 0)
             if ((rc = axpby(c, n, 1.0, c->u, 1.0, c->bvec, c->u))) return rc;
-            if ((rc = residual(c, c->u, c->Ru, OUT_R, nullptr))) return rc;
+            if ((rc = residual(c, c->u, c->Ru, OUT_R))) return rc;
             if ((rc = pnorm(c, c->Ru, 0, false))) return rc;
             if ((rc = read_slots())) return rc;
             JF_CUDA(c, cudaMemcpy2DAsync(c->ph, sizeof(ProbDev), c->pd, sizeof(ProbDev), offsetof(ProbDev, h), P,

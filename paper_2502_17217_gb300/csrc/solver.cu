@@ -54,7 +54,7 @@ static int jv_direction(jfnk_ctx* c, const double* x, double* out)
 {
     int rc = pnorm(c, x, 1, false);
     if (!rc) rc = perturb(c, c->u, x, c->w, false);
-    if (!rc) rc = residual(c, c->w, out, OUT_JV, nullptr);
+    if (!rc) rc = residual(c, c->w, out, OUT_JV);
     return rc;
 }
 
@@ -68,7 +68,7 @@ static int enqueue_iteration(jfnk_ctx* c)
     int rc;
     if (left_pc(c)) {
         if ((rc = perturb_basis(c, c->u, c->w))) return rc;
-        if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, nullptr, gate))) return rc;
+        if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate))) return rc;
         if ((rc = pc_apply_any(c, c->opt.pc, c->wk, 0, c->z, gate))) return rc;
         if ((rc = arnoldi_orthogonalise(c, c->z))) return rc;
         JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
@@ -78,7 +78,7 @@ static int enqueue_iteration(jfnk_ctx* c)
     if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate, &eps_formed))) return rc;
     if (!eps_formed && (rc = pnorm(c, c->z, 1, true))) return rc;
     if ((rc = perturb(c, c->u, c->z, c->w, true))) return rc;
-    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, nullptr, gate))) return rc;
+    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate))) return rc;
     if ((rc = arnoldi_orthogonalise(c, c->wk))) return rc;
     JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
     return JFNK_OK;
@@ -271,7 +271,7 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
     for (int step = 1; step <= n_load_steps; step++) {
         c->load = (double)step / n_load_steps;
         if ((rc = sync_load(c))) return rc;
-        if ((rc = residual(c, c->u, c->Ru, OUT_R, nullptr))) return rc;
+        if ((rc = residual(c, c->u, c->Ru, OUT_R))) return rc;
         if ((rc = pnorm(c, c->Ru, 0, false))) return rc;
         if ((rc = read_problems(c))) return rc;
         for (int p = 0; p < P; p++) {
@@ -314,7 +314,7 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
                 if ((rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
                 if ((rc = write_problem_doubles(c, offsetof(ProbDev, step)))) return rc;
                 if ((rc = line_trial(c, c->u, c->x, c->w))) return rc;
-                if ((rc = residual(c, c->w, c->R, OUT_R, nullptr))) return rc;
+                if ((rc = residual(c, c->w, c->R, OUT_R))) return rc;
                 if ((rc = pnorm(c, c->R, 0, false))) return rc;
                 if ((rc = read_problems(c))) return rc;
                 bool any = false;
