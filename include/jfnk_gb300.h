@@ -227,6 +227,14 @@ int jfnk_solve_dynamic(jfnk_ctx* ctx, double* u, int mem, int n_steps, int32_t p
                        int method, jfnk_stats* stats, void* stream);
 /* Puts the time-integration state back at rest (u = v = a = 0 at both previous levels). */
 int jfnk_dynamic_reset(jfnk_ctx* ctx);
+/* Checkpoint and restart of the time integration: the state that jfnk_solve_dynamic carries
+ * between calls, five fields u_t, u_{t-1}, v_t, v_{t-1}, a_t, each [n_cells][3] in the caller's
+ * cell order, as one host array state[5][n_cells][3].  get copies the context's state out, set
+ * replaces it (same mesh and options: a context restarted from a checkpoint continues the
+ * motion exactly as the one that wrote it).  Both wait for the copies.  JFNK_ESTATE before
+ * set-up or for a static context (options.density = 0), JFNK_EINVAL for a null array. */
+int jfnk_dynamic_get_state(jfnk_ctx* ctx, double* state);
+int jfnk_dynamic_set_state(jfnk_ctx* ctx, const double* state);
 
 /* ---- batches of independent problems in one index space -------------------------------- */
 /* A context becomes a batch when problems are added to it instead of calling jfnk_set_mesh.

@@ -94,6 +94,41 @@ extern "C" int jfnk_dynamic_reset(jfnk_ctx* c)
     return JFNK_OK;
 }
 
+// Checkpoint and restart of the time integration: the five state fields in the caller's
+// cell order, [5][n_cells][3] (u_t, u_{t-1}, v_t, v_{t-1}, a_t).
+extern "C" int jfnk_dynamic_get_state(jfnk_ctx* c, double* state)
+{
+    if (!c || !state) return JFNK_EINVAL;
+    if (c->dirty) return jfnk_fail(c, JFNK_ESTATE, "jfnk_dynamic_get_state: set the context up first");
+    if (!c->dyn_on) return jfnk_fail(c, JFNK_ESTATE, "jfnk_dynamic_get_state: options.density is 0 (static context)");
+    int rc = jfnk_use_stream(c, nullptr);
+    if (rc) return rc;
+    const size_t n = 3 * (size_t)c->dm.nc;
+    const double* f[5] = {c->dyn_ut, c->dyn_utm1, c->dyn_vt, c->dyn_vtm1, c->dyn_at};
+    for (int k = 0; k < 5; k++) {
+        if ((rc = jfnk::perm_out(c, f[k], c->ext))) return rc;
+        if ((rc = jfnk_download(c, state + k * n, c->ext, sizeof(double) * n))) return rc;
+    }
+    return JFNK_OK;
+}
+
+extern "C" int jfnk_dynamic_set_state(jfnk_ctx* c, const double* state)
+{
+    if (!c || !state) return JFNK_EINVAL;
+    if (c->dirty) return jfnk_fail(c, JFNK_ESTATE, "jfnk_dynamic_set_state: set the context up first");
+    if (!c->dyn_on) return jfnk_fail(c, JFNK_ESTATE, "jfnk_dynamic_set_state: options.density is 0 (static context)");
+    int rc = jfnk_use_stream(c, nullptr);
+    if (rc) return rc;
+    const size_t n = 3 * (size_t)c->dm.nc;
+    double* f[5] = {c->dyn_ut, c->dyn_utm1, c->dyn_vt, c->dyn_vtm1, c->dyn_at};
+    for (int k = 0; k < 5; k++) {
+        if ((rc = jfnk_upload(c, c->ext, state + k * n, sizeof(double) * n))) return rc;
+        if ((rc = jfnk::perm_in(c, c->ext, f[k]))) return rc;
+    }
+    JF_CUDA(c, cudaStreamSynchronize(c->stream));
+    return JFNK_OK;
+}
+
 namespace jfnk {
 
 int solve_dynamic(jfnk_ctx* c, int n_steps, int32_t probe_cell, double* probe, jfnk_stats* st, int method)

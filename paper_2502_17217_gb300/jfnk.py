@@ -34,7 +34,7 @@ EXPORTS = [
     "jfnk_launch_count", "jfnk_device_bytes", "jfnk_convert_f32_to_f64", "jfnk_batch_add", "jfnk_batch_size",
     "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate", "jfnk_get_tuning", "jfnk_set_tuning",
     "jfnk_solve_segregated", "jfnk_solve_dynamic", "jfnk_dynamic_reset", "jfnk_synchronize",
-    "jfnk_set_mesh_hex", "jfnk_hex_patch",
+    "jfnk_set_mesh_hex", "jfnk_hex_patch", "jfnk_dynamic_get_state", "jfnk_dynamic_set_state",
 ]
 
 
@@ -90,6 +90,8 @@ def load():
         "jfnk_solve_segregated": (i, [vp, dp, i, i, C.POINTER(Stats), vp]),
         "jfnk_solve_dynamic": (i, [vp, dp, i, i, C.c_int32, dp, i, C.POINTER(Stats), vp]),
         "jfnk_dynamic_reset": (i, [vp]),
+        "jfnk_dynamic_get_state": (i, [vp, dp]),
+        "jfnk_dynamic_set_state": (i, [vp, dp]),
         "jfnk_synchronize": (i, [vp]),
         "jfnk_set_mesh_hex": (i, [vp, i, i, i, dp, i]),
         "jfnk_hex_patch": (i, [i, i, i, i, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -279,6 +281,17 @@ class Solver:
 
     def dynamic_reset(self):
         self._check(self.L.jfnk_dynamic_reset(self.h))
+
+    def dynamic_state(self):
+        """Checkpoint of the time integration: [5, n_cells, 3] (u_t, u_t-1, v_t, v_t-1, a_t)."""
+        st = np.zeros((5, self.nc, 3))
+        self._check(self.L.jfnk_dynamic_get_state(self.h, _ptr(st)))
+        return st
+
+    def set_dynamic_state(self, state):
+        """Restart the time integration from a checkpoint of dynamic_state()."""
+        st = np.ascontiguousarray(state, np.float64).reshape(5, self.nc, 3)
+        self._check(self.L.jfnk_dynamic_set_state(self.h, _ptr(st)))
 
     def solve_segregated(self, u0=None, load_steps=1, raise_on_fail=True):
         """The segregated quasi-Newton solve of Sec. 3.1 (the paper's comparison method);

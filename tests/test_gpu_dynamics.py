@@ -107,3 +107,32 @@ def test_dynamic_steps_by_the_segregated_method_reach_the_same_motion():
     assert rc1 == 0 and rc2 == 0
     assert _rel(u2, u1) <= 1e-7 and _rel(p2, p1) <= 1e-7
     assert st2.newton_its > st1.newton_its  # outer iterations against Newton iterations
+
+
+def test_checkpoint_restart_continues_the_motion_bitwise():
+    """A checkpoint of the time-integration state (jfnk_dynamic_get_state) restarted in a fresh
+    context (jfnk_dynamic_set_state) continues the motion exactly: 10 + 10 steps across two
+    contexts equal 20 steps in one, and the state reads back as written."""
+    from paper_2502_17217_gb300 import jfnk
+    case, probe = I.case_dynamic_beam(3, 12, 3)
+    kw = dict(density=RHO, dt=DT, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, mg_coarse_max=20)
+    a = jfnk.Solver.from_case(case, **kw)
+    u20, _, rc, p20 = a.solve_dynamic(20, probe_cell=probe)
+    assert rc == 0
+    b = jfnk.Solver.from_case(case, **kw)
+    _, _, rc, pb = b.solve_dynamic(10, probe_cell=probe)
+    assert rc == 0
+    state = b.dynamic_state()
+    assert state.shape == (5, case.mesh.n_cells, 3) and np.any(state != 0)
+    c = jfnk.Solver.from_case(case, **kw)
+    c.setup()
+    c.set_dynamic_state(state)
+    assert np.array_equal(c.dynamic_state(), state)
+    u, _, rc, pc_ = c.solve_dynamic(10, probe_cell=probe)
+    assert rc == 0
+    assert np.array_equal(u, u20)
+    assert np.array_equal(np.concatenate([pb, pc_]), p20)
+    static = jfnk.Solver.from_case(case)
+    static.setup()
+    with pytest.raises(jfnk.JfnkError):
+        static.dynamic_state()
