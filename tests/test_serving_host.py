@@ -1,0 +1,142 @@
+"""Host-side logic of the solve server (no GPU): admission in arrival order by estimated HBM
+footprint, the slot limit, an oversized request running alone, refinement of the
+bytes-per-cell estimate from measured footprints, a failing request reported on the request
+while the others are served, and the Poisson-arrival driver with its latency summary.  The
+per-request solver is replaced by a fake that sleeps and records how many requests were
+live at once and in which order they were set up."""
+import threading
+import time
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+from paper_2502_17217_gb300 import serving
+
+
+class _Live:
+    def __init__(self):
+        self.lock = threading.Lock()
+        self.n = 0
+        self.max_n = 0
+        self.order = []
+
+
+def _case(cells, law=0, hold=0.05, fail=False, true_bpc=None):
+    return SimpleNamespace(mesh=SimpleNamespace(n_cells=cells), material=SimpleNamespace(law=law),
+                           hold=hold, fail=fail, true_bpc=true_bpc)
+
+
+@pytest.fixture
+def live(monkeypatch):
+    rec = _Live()
+
+    class FakeSolver:
+        def __init__(self, case):
+            self.case = case
+
+        @classmethod
+        def from_case(cls, case, **kw):
+            return cls(case)
+
+        def setup(self):
+            with rec.lock:
+                rec.n += 1
+                rec.max_n = max(rec.max_n, rec.n)
+                rec.order.append(id(self.case))
+
+        def solve(self, load_steps=1, raise_on_fail=True):
+            try:
+                time.sleep(self.case.hold)
+                if self.case.fail:
+                    raise RuntimeError("planted solve failure")
+                st = SimpleNamespace(load_steps=load_steps)
+                return np.zeros((self.case.mesh.n_cells, 3)), st, 0
+            finally:
+                with rec.lock:
+                    rec.n -= 1
+
+        def device_bytes(self):
+            bpc = self.case.true_bpc
+            return int(bpc * self.case.mesh.n_cells) if bpc else 0
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(serving.jfnk, "Solver", FakeSolver)
+    import torch
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    return rec
+
+
+def _run(cases, **kw):
+    srv = serving.Server(**kw)
+    reqs = [srv.submit(c, tag=k) for k, c in enumerate(cases)]
+    srv.drain()
+    srv.close()
+    return srv, reqs
+
+
+def test_admission_keeps_the_footprint_within_the_budget(live):
+    one = serving.DEFAULT_BYTES_PER_CELL[0] * 1000
+    srv, reqs = _run([_case(1000) for _ in range(8)], hbm_budget_bytes=2.5 * one, max_slots=8)
+    assert all(r.status == 0 and r.error is None for r in reqs)
+    assert srv.max_concurrent == 2 and live.max_n == 2
+    assert srv.max_shared_footprint <= 2.5 * one
+    assert srv._in_use == 0 and srv._running == 0
+
+
+def test_slot_limit_caps_concurrency(live):
+    srv, reqs = _run([_case(100, hold=0.1) for _ in range(10)], hbm_budget_bytes=1e15, max_slots=3)
+    assert len(srv.completed) == 10
+    assert srv.max_concurrent == 3 and live.max_n == 3
+
+
+def test_oversized_request_runs_alone(live):
+    srv, reqs = _run([_case(5000), _case(5000), _case(5000)], hbm_budget_bytes=1000.0, max_slots=8)
+    assert all(r.status == 0 for r in reqs)
+    assert srv.max_concurrent == 1 and live.max_n == 1
+
+
+def test_admission_is_in_arrival_order(live):
+    # A (small, long) runs; B needs the whole budget, so it waits for A; C (small) would fit
+    # beside A but must not overtake B.
+    bpc = serving.DEFAULT_BYTES_PER_CELL[0]
+    a, b, c = _case(100, hold=0.3), _case(950, hold=0.05), _case(100, hold=0.05)
+    srv, (ra, rb, rc) = _run([a, b, c], hbm_budget_bytes=1000 * bpc, max_slots=8)
+    assert ra.t_admit <= rb.t_admit <= rc.t_admit
+    assert rb.t_admit >= ra.t_done  # B started only once A released its footprint
+    assert live.order == [id(a), id(b), id(c)]
+
+
+def test_bytes_per_cell_estimate_grows_to_the_measured_footprint(live):
+    srv, reqs = _run([_case(1000, law=1, true_bpc=5000.0), _case(1000, law=0, true_bpc=100.0)],
+                     hbm_budget_bytes=1e12)
+    assert srv.bpc[1] == pytest.approx(5000.0)
+    # a measured figure below the conservative start does not lower it
+    assert srv.bpc[0] == serving.DEFAULT_BYTES_PER_CELL[0]
+    assert reqs[0].bytes == 5_000_000
+
+
+def test_failing_request_is_reported_and_the_rest_are_served(live):
+    cases = [_case(100), _case(100, fail=True), _case(100)]
+    srv, reqs = _run(cases, hbm_budget_bytes=1e12, max_slots=2)
+    assert reqs[1].status == -99 and "planted solve failure" in reqs[1].error
+    assert reqs[0].status == 0 and reqs[2].status == 0
+    assert srv._in_use == 0 and srv._running == 0
+    assert all(r.done.is_set() for r in reqs)
+
+
+def test_poisson_stream_and_latency_summary(live):
+    cases = [_case(200, hold=0.02) for _ in range(12)]
+    reqs, wall, srv = serving.serve_stream(cases, rate_per_s=200.0, seed=3, hbm_budget_bytes=1e12, max_slots=4)
+    s = serving.summarize(reqs, wall)
+    assert s["requests"] == 12 and s["converged"] == 12
+    assert s["cells_total"] == 12 * 200
+    lat = sorted(r.latency for r in reqs)
+    assert min(lat) >= 0.02
+    assert s["p50_latency_s"] <= s["p99_latency_s"] <= max(lat) + 1e-12
+    assert s["solves_per_s"] == pytest.approx(12 / wall)
+    # arrivals follow the seeded gaps: submission times are increasing
+    t = [r.t_arrival for r in reqs]
+    assert all(x < y for x, y in zip(t, t[1:]))
