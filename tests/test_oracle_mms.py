@@ -4,7 +4,11 @@
   needs f_b = -div(sigma(u*)).  The golden file transcribes App. E term by term; the test
   shows it equals +div(sigma(u*)) (derived symbolically), and that the generator's f_b is
   its negative.
-* Displacement converges at second order (Sec. 4.1: 'approximately second-order').
+* Displacement converges at second order (Sec. 4.1: 'approximately second-order', average
+  and maximum error alike), the cell stresses at least at the rates Sec. 4.1 reports for the
+  3-D cube: average error order about 1.5 on regular hexahedra and 1 on distorted ones,
+  maximum error order approaching 1.  (On this 2-D case the measured stress orders are
+  1.8-2.0, above those lower bounds; a wrong gradient weight or stress term drops them to 0.)
 """
 import os
 
@@ -81,7 +85,25 @@ def test_app_e_is_plus_div_sigma_and_generator_is_minus():
     np.testing.assert_allclose(I.mms_body_force(x, E, nu, dim=2), -ref2, rtol=1e-10, atol=1e-10 * np.abs(ref2).max())
 
 
+def _exact_stress_2d(C, E, nu):
+    """Hooke stress of the manufactured field u* = (a_x, a_y) sin(4 pi x) sin(2 pi y), plane
+    strain, from its analytic gradient, (grad u)_ij = d u_j / d x_i."""
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    ax, ay = I.MMS_AMPLITUDES[0], I.MMS_AMPLITUDES[1]
+    x, y = C[:, 0], C[:, 1]
+    dx = 4 * np.pi * np.cos(4 * np.pi * x) * np.sin(2 * np.pi * y)
+    dy = 2 * np.pi * np.sin(4 * np.pi * x) * np.cos(2 * np.pi * y)
+    g = np.zeros((len(C), 3, 3))
+    g[:, 0, 0], g[:, 0, 1] = ax * dx, ay * dx
+    g[:, 1, 0], g[:, 1, 1] = ax * dy, ay * dy
+    tr = np.trace(g, axis1=1, axis2=2)
+    return mu * (g + np.transpose(g, (0, 2, 1))) + lam * tr[:, None, None] * np.eye(3)
+
+
 def _mms_error(n, perturb):
+    """(L2, Linf) of the displacement error and (L2, Linf) of the cell stress error (Frobenius
+    norm per cell) after a converged Newton solve of the n x n case."""
     c = I.case_mms2d(n, perturb=perturb, seed=n)
     o = O.Oracle.from_case(c)
     _, Cf, _, C = o.geometry()
@@ -91,13 +113,20 @@ def _mms_error(n, perturb):
     assert rc == 0, (rc, st.final_rel_res)
     ex = I.mms_displacement(C, dim=2)
     e = np.linalg.norm(u[:, :2] - ex[:, :2], axis=1)
-    return np.sqrt(np.mean(e ** 2)), e.max()
+    g = o.gradient(u)
+    s_num = np.array([o.cauchy_stress(g[i]) for i in range(len(g))])
+    es = np.linalg.norm((s_num - _exact_stress_2d(C, 200e9, 0.3)).reshape(len(g), 9), axis=1)
+    return np.array([np.sqrt(np.mean(e ** 2)), e.max(), np.sqrt(np.mean(es ** 2)), es.max()])
 
 
 @pytest.mark.parametrize("perturb", [0.0, 0.15])
-def test_mms_second_order_displacement(perturb):
-    errs = [_mms_error(n, perturb) for n in (16, 32, 64)]
-    l2 = [e[0] for e in errs]
-    order = np.log2(l2[1] / l2[2])
-    assert order > 1.85, (l2, order)  # measured 1.95 on both mesh types
-    assert l2[2] < 0.05 * I.MMS_AMPLITUDES[1]
+def test_mms_second_order_displacement_and_stress_order(perturb):
+    errs = np.array([_mms_error(n, perturb) for n in (16, 32, 64)])
+    order = np.log2(errs[1] / errs[2])  # finest pair: displacement L2, Linf; stress L2, Linf
+    assert order[0] > 1.85, (errs, order)  # measured 1.95 on both mesh types
+    assert order[1] > 1.8, (errs, order)  # measured 1.99 / 1.96
+    assert errs[2, 0] < 0.05 * I.MMS_AMPLITUDES[1]
+    # stresses: at least the 3-D rates of Sec. 4.1 (measured 2.01 / 1.81 average, 1.88 / 1.85 max)
+    assert order[2] > (1.5 if perturb == 0.0 else 1.0), (errs, order)
+    assert order[3] > 1.0, (errs, order)
+    assert np.all(errs[1:] < errs[:-1]), errs
