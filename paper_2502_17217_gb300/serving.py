@@ -122,6 +122,7 @@ class Server:
                     self.max_shared_footprint = max(self.max_shared_footprint, self._in_use)
                 r.t_admit = time.perf_counter()
             t = threading.Thread(target=self._work, args=(r, need), daemon=True)
+            self._workers = [w for w in self._workers if w.is_alive()]  # a long-lived server keeps no dead threads
             self._workers.append(t)
             t.start()
 
