@@ -151,6 +151,41 @@ def test_solve_parity_multigrid_and_mixed_precision():
     assert _rel(ugm, uo) <= 1e-8
 
 
+def test_smallest_mesh_and_single_level_multigrid():
+    """Degenerate sizes: the smallest 3-D block (2x2x2 cells, every cell on the boundary, one
+    ragged chunk) and a one-level hierarchy (the mesh below the coarse-solve size), where the
+    V-cycle is the exact solve J~ z = v.  Residual and Jv match the oracle, the solves match
+    it with block-Jacobi and with the multigrid in FP64 and mixed precision; a mesh without
+    cells is rejected before any device work and the context stays usable."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(2, 2, 2, (1.0, 0.5, 0.5), perturb=0.1, seed=3)
+    n = case.mesh.n_cells
+    o = O.Oracle.from_case(case)
+    s = _solver(case, pc=jfnk.PC_MG)
+    u = I.random_field(5, n, 1e-4)
+    assert _rel(s.residual(u), o.residual(u)) <= 1e-12
+    v = I.random_field(6, n, 1.0)
+    Jv, Jvo = s.jv(u, v), o.jv(u, v)
+    eps = 1e-7 * (1 + np.linalg.norm(u)) / np.linalg.norm(v)
+    tol = 1e-12 * (np.linalg.norm(o.residual(u)) / (eps * np.linalg.norm(Jvo)) + 1)
+    assert _rel(Jv, Jvo) <= tol
+    z = s.precondition(v, jfnk.PC_MG)
+    assert np.linalg.norm(o.jtilde_apply(z) - v) <= 1e-12 * np.linalg.norm(v)
+    for kw in (dict(pc=jfnk.PC_BJACOBI), dict(pc=jfnk.PC_MG), dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED)):
+        ug, uo, st, _ = _solve_both(case, **kw)
+        assert _rel(ug, uo) <= 1e-8, (kw, _rel(ug, uo))
+    m = case.mesh
+    pts = np.ascontiguousarray(m.points, np.float64)
+    fp = np.ascontiguousarray(m.face_ptr, np.int32)
+    fq = np.ascontiguousarray(m.face_pts, np.int32)
+    ow = np.ascontiguousarray(m.owner, np.int32)
+    ne = np.ascontiguousarray(m.neighbour, np.int32)
+    rc = s.L.jfnk_set_mesh(s.h, 3, m.n_points, jfnk._ptr(pts), m.n_faces, jfnk._ptr(fp), jfnk._ptr(fq),
+                           jfnk._ptr(ow), m.n_internal, jfnk._ptr(ne), 0)
+    assert rc == jfnk.EINVAL
+    assert _rel(s.residual(u), o.residual(u)) <= 1e-12
+
+
 def test_solve_parity_st_venant_kirchhoff_load_steps():
     case = _stvk(I.case_nh_beam(16, 4, 4, (1.0, 0.25, 0.25), end_uy=0.2, load_steps=2))
     ug, uo, st, _ = _solve_both(case, load_steps=2)

@@ -282,6 +282,19 @@ def test_multigrid_vcycle_is_symmetric_and_contracts(smoothed, sweeps):
     assert its_mg < its_bj
 
 
+@pytest.mark.parametrize("dims", [(2, 2, 2), (9, 5, 4)])
+def test_single_level_vcycle_is_the_exact_compact_stencil_solve(dims):
+    """A mesh at or below the coarse-solve size gives a one-level hierarchy, and the V-cycle
+    is then the direct solve with J~ (Sec. 3.1): J~ z = v to round-off, for the smallest 3-D
+    block (8 cells, all on the boundary) as well as a larger one."""
+    c = I.case_cantilever(*dims, (1.0, 0.5, 0.4), perturb=0.1, seed=3)
+    o = O.Oracle.from_case(c)
+    assert o.mg_setup(coarse_max=2000, smoothed=True, sweeps=2) == 1
+    v = I.random_field(6, c.mesh.n_cells, 1.0)
+    z = o.mg_vcycle(v)
+    assert np.linalg.norm(o.jtilde_apply(z) - v) <= 1e-13 * np.linalg.norm(v)
+
+
 def test_smoothed_aggregation_prolongation_and_strength():
     """Smoothed prolongation P = (I - omega D^-1 A) P_tent preserves the constant vector's
     image (row sums of P equal 1 - omega D^-1 (A 1)); two-level J~ coarse operators stay
