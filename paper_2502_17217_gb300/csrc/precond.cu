@@ -758,6 +758,16 @@ int pc_setup(jfnk_ctx* c)
         fprintf(stderr, "[jfnk] multigrid hierarchy (host) %8.1f ms\n",
                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
     if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
+    if (lv.size() == 1) {
+        // the only level is the finest, whose vectors are in the internal numbering: its dense
+        // inverse (built in the caller's order) is permuted to match
+        std::vector<double> p(inv.size());
+        for (int P = 0; P < nc; P++) {
+            const size_t i = (size_t)t.n2o[P] * nc;
+            for (int Q = 0; Q < nc; Q++) p[(size_t)P * nc + Q] = inv[i + t.n2o[Q]];
+        }
+        inv.swap(p);
+    }
     std::vector<HostTransfer> tr(lv.size());
     for (size_t l = 0; l + 1 < lv.size(); l++)
         make_transfer(lv[l].prp, lv[l].pcol, lv[l].pval, lv[l].n, lv[l + 1].n, l == 0 ? &t.n2o : nullptr, tr[l]);
