@@ -186,6 +186,30 @@ def test_smallest_mesh_and_single_level_multigrid():
     assert _rel(s.residual(u), o.residual(u)) <= 1e-12
 
 
+def test_one_level_multigrid_in_the_other_solver_paths():
+    """The one-level hierarchy (exact J~ solve) as the segregated method's CG preconditioner,
+    as a left preconditioner, and for a batch whose union is below the coarse-solve size:
+    each reaches the oracle's discrete solution within the displacement tolerance."""
+    from paper_2502_17217_gb300 import jfnk
+    case = I.case_cantilever(8, 3, 3, (0.6, 0.25, 0.25), perturb=0.15, seed=2)
+    o = O.Oracle.from_case(case)
+    uo, rco, _ = o.newton(rtol=1e-11)
+    assert rco == 0
+    ug, st, rc = _solver(case, pc=jfnk.PC_MG, newton_rtol=1e-10).solve_segregated()
+    assert rc == 0 and _rel(ug, uo) <= 1e-8, (rc, _rel(ug, uo))
+    ul, stl, rcl = _solver(case, pc=jfnk.PC_MG, pc_side=jfnk.PC_LEFT, newton_rtol=1e-11).solve()
+    assert rcl == 0 and _rel(ul, uo) <= 1e-8, (rcl, _rel(ul, uo))
+    cases = [I.case_cantilever(6, 3, 3, (0.5, 0.25, 0.25), perturb=0.1, seed=k) for k in range(3)]
+    cases.append(I.case_nh_beam(8, 3, 3, (1.0, 0.3, 0.3), end_uy=0.05, load_steps=1))
+    kw = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-11)
+    B = jfnk.Batch(cases, **kw)
+    u, _, rcb = B.solve()
+    assert rcb == 0
+    for k, (c, uk) in enumerate(zip(cases, B.split(u))):
+        uok, rcok, _ = O.Oracle.from_case(c).newton(rtol=1e-11)
+        assert rcok == 0 and _rel(uk, uok) <= 1e-8, (k, _rel(uk, uok))
+
+
 def test_solve_parity_st_venant_kirchhoff_load_steps():
     case = _stvk(I.case_nh_beam(16, 4, 4, (1.0, 0.25, 0.25), end_uy=0.2, load_steps=2))
     ug, uo, st, _ = _solve_both(case, load_steps=2)
