@@ -134,6 +134,7 @@ class Server:
         return self._in_use + need <= self.budget or self._running == 0
 
     def _work(self, r: Request, need: float):
+        s = None
         try:
             import torch
             torch.cuda.set_device(self.device)
@@ -142,10 +143,15 @@ class Server:
             u, st, rc = s.solve(load_steps=r.load_steps, raise_on_fail=False)
             r.u, r.stats, r.status = u, st, rc
             r.bytes = s.device_bytes()
-            s.close()
         except Exception as e:  # reported on the request, the server keeps serving
             r.error = f"{type(e).__name__}: {e}"
             r.status = -99
+        finally:
+            if s is not None:  # the request's device memory is released on every path
+                try:
+                    s.close()
+                except Exception as e:
+                    r.error = r.error or f"close: {type(e).__name__}: {e}"
         r.t_done = time.perf_counter()
         with self._lock:
             if r.bytes:

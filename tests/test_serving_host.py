@@ -20,6 +20,7 @@ class _Live:
         self.n = 0
         self.max_n = 0
         self.order = []
+        self.closed = 0
 
 
 def _case(cells, law=0, hold=0.05, fail=False, true_bpc=None):
@@ -61,7 +62,8 @@ def live(monkeypatch):
             return int(bpc * self.case.mesh.n_cells) if bpc else 0
 
         def close(self):
-            pass
+            with rec.lock:
+                rec.closed += 1
 
     monkeypatch.setattr(serving.jfnk, "Solver", FakeSolver)
     import torch
@@ -125,6 +127,7 @@ def test_failing_request_is_reported_and_the_rest_are_served(live):
     assert reqs[0].status == 0 and reqs[2].status == 0
     assert srv._in_use == 0 and srv._running == 0
     assert all(r.done.is_set() for r in reqs)
+    assert live.closed == 3  # the failed request's context is released too
 
 
 def test_poisson_stream_and_latency_summary(live):
