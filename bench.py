@@ -101,6 +101,7 @@ class ClockSampler:
         self.path = os.path.join(tempfile.gettempdir(), f"jfnk_bench_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
+        self.f = None
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -109,6 +110,12 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            if self.f:
+                self.f.close()
+                try:
+                    os.remove(self.path)
+                except OSError:
+                    pass
         return self
 
     def __exit__(self, *a):
