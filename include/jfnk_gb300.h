@@ -195,8 +195,11 @@ int jfnk_residual_noalloc(jfnk_ctx* ctx, const double* u, double* R, void* strea
 /* Jv ~ (R(u + eps v) - R(u)) / eps, eps = jv_eps_scale (1 + |u|_2) / |v|_2; Jv = 0 for v = 0
  * (Eq. JF).  Evaluates R(u) too. */
 int jfnk_jv(jfnk_ctx* ctx, const double* u, const double* v, double* Jv, int mem, void* stream);
-/* z ~ P^-1 v with P = J~ (Sec. 3.2): JFNK_PC_BJACOBI (diagonal blocks of J~), JFNK_PC_MG
- * (one V-cycle), JFNK_PC_NONE (copy).  Precision follows opt.precision. */
+/* z ~ P^-1 v with P = J~ (Sec. 3.2), i.e. J~ z ~ v: JFNK_PC_BJACOBI (diagonal blocks of J~),
+ * JFNK_PC_MG (one V-cycle; a mesh of at most opt.mg_coarse_max cells has a one-level
+ * hierarchy, and the V-cycle is then the exact solve with J~), JFNK_PC_NONE (copy).
+ * Precision follows opt.precision.  JFNK_ESTATE for JFNK_PC_MG when the context was set up
+ * with another opt.pc (the hierarchy is built at set-up only for opt.pc = JFNK_PC_MG). */
 int jfnk_precondition(jfnk_ctx* ctx, const double* v, double* z, int pc, int mem, void* stream);
 /* Newton solve (Sec. 3.2-3.3): u holds the initial guess on entry and the solution on exit;
  * n_load_steps >= 1 ramps the load factor k / n_load_steps.  Returns JFNK_OK when every load
