@@ -183,14 +183,18 @@ int jfnk_residual(jfnk_ctx* ctx, const double* u, double* R, int mem, void* stre
  * they need a residual (inside a stream capture, under a framework whose pool owns the
  * device, or in loops that must not take the synchronisation of cudaMalloc/cudaFree).  Its
  * scratch is one fixed device array of 2^21 doubles (16 MiB) that every GPU loading the
- * library keeps until the process exits; the mesh must fit in it: 15 n_cells + 3 (internal +
- * displacement faces) + 3 internal faces doubles, plus 9 n_cells for the neo-Hookean law,
- * else JFNK_EINVAL.  u, R: device arrays [n_cells][3] in the caller's numbering; the work is
- * enqueued on `stream` (NULL = the context's stream).  The context must be set up already
- * (jfnk_setup or an earlier call), else JFNK_ESTATE: this call never sets up.  All calls
- * share the array and it keeps the last call's contents (each call writes everything it
- * reads); calls that overlap on the GPU race, so serialise them.  The first call on a device
- * looks up the array's address with that device current; make it before any stream capture. */
+ * library keeps until the process exits; the mesh must fit in it: 32 + 15 n_cells +
+ * 3 (internal + displacement + symmetry faces) + 3 internal faces doubles, plus 9 n_cells for
+ * any law other than LINEAR (and for a batch mixing laws), else JFNK_EINVAL.  u, R: device
+ * (or managed) arrays [n_cells][3] of the context's device, in the caller's numbering; other
+ * pointers give JFNK_EINVAL.  The work is enqueued on `stream` (NULL = the context's stream)
+ * and the call never waits on the host; the current load factor is passed to the GPU by
+ * value, so work recorded from the call (a captured graph) keeps that factor.  The context
+ * must be set up already (jfnk_setup or an earlier call), else JFNK_ESTATE: this call never
+ * sets up.  All calls share the array and it keeps the last call's contents (each call
+ * writes everything it reads); calls that overlap on the GPU race, so serialise them.  The
+ * first call on a device looks up the array's address with that device current; make it
+ * before any stream capture. */
 int jfnk_residual_noalloc(jfnk_ctx* ctx, const double* u, double* R, void* stream);
 /* Jv ~ (R(u + eps v) - R(u)) / eps, eps = jv_eps_scale (1 + |u|_2) / |v|_2; Jv = 0 for v = 0
  * (Eq. JF).  Evaluates R(u) too. */

@@ -346,8 +346,10 @@ enum ResidualOut { OUT_R = 0, OUT_JV = 1 };
 int residual(jfnk_ctx* c, const double* u_int, double* out, int mode);
 int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate);
 int sync_load(jfnk_ctx* c);
+// load_dev: device address of the load factor the kernels read (nullptr = the context's own,
+// kept equal to c->load by sync_load)
 int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
-                  double* F, double* Fn);
+                  double* F, double* Fn, const double* load_dev = nullptr);
 // linalg.cu
 int perm_in(jfnk_ctx* c, const double* ext_aos, double* int_soa);
 int build_chunks(jfnk_ctx* c);

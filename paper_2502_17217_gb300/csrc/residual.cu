@@ -372,9 +372,10 @@ int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, cons
 }
 
 int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
-                  double* F, double* Fn)
+                  double* F, double* Fn, const double* load_dev)
 {
     const DevMesh& m = c->dm;
+    const double* load = load_dev ? load_dev : (const double*)&c->gdev->load;
     static const char* const kNames[3] = {"grad", "flux", "finish"};
     int sl[3];
     for (int q = 0; q < 3; q++) sl[q] = c->prof.enabled ? c->prof.slot(kNames[q]) : -1;
@@ -401,7 +402,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
         jfnk_prof_begin(c, sl[1]);
 #define JF_FLUX_BS(LAW_, BS_, ST_)                                                                                      \
     jfnk_launch(c, k_flux<LAW_, BS_, ST_>, dim3(nblk(m.nflux, BS_)), dim3(BS_), gate, m.ni, m.nd, m.nflux, m.nc, m.own, m.nei, \
-                m.coef, u_int, (const double*)G, (const double*)T, m.bval, (const double*)&c->gdev->load, m.fn_pos,   \
+                m.coef, u_int, (const double*)G, (const double*)T, m.bval, load, m.fn_pos,   \
                 c->mat, (const int32_t*)c->cell_prob, F, Fn)
 #define JF_FLUX(LAW_)                                                        \
     do {                                                                     \
@@ -424,7 +425,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     jfnk_prof_begin(c, sl[2]);
     jfnk_launch(c, k_finish, dim3(nblk(3L * m.nc, tu.finish_bs)), dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr,
                 (const int32_t*)m.fs_ptr, (const double*)F, m.b0,
-                                            &c->gdev->load, mode, c->Ru, c->pd, c->cell_prob, gate, u_int, (const double*)m.V,
+                load, mode, c->Ru, c->pd, c->cell_prob, gate, u_int, (const double*)m.V,
                 (const double*)(c->dyn_on ? c->dyn_rc : nullptr), c->dyn_mk, out);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);

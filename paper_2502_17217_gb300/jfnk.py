@@ -245,8 +245,19 @@ class Solver:
         return R
 
     def residual_noalloc(self, u, out=None):
-        """R(u) for torch CUDA tensors, through the entry point that allocates nothing."""
-        u = self._in(u)
+        """R(u) through the entry point that allocates nothing (jfnk_residual_noalloc).
+
+        u and out must be contiguous float64 torch CUDA tensors of shape (n_cells, 3) on the
+        context's device; anything else raises TypeError before the library is called.  With
+        out=None the result tensor is allocated here, by torch, before the call."""
+        dev = self.options.device
+        for name, a in (("u", u), ("out", out)):
+            if a is None and name == "out":
+                continue
+            if not (_is_device(a) and a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous()
+                    and tuple(a.shape) == (self.nc, 3) and a.device.index == dev):
+                raise TypeError(f"residual_noalloc: {name} must be a contiguous float64 CUDA tensor of shape "
+                                f"({self.nc}, 3) on cuda:{dev}")
         R = self._out_like(u) if out is None else out
         self._check(self.L.jfnk_residual_noalloc(self.h, _ptr(u), _ptr(R), _stream(u)))
         return R

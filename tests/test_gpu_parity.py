@@ -328,8 +328,8 @@ def test_graph_and_direct_launch_agree(pc_side):
 
 @pytest.mark.parametrize("reorth", [0, 1, 2])
 def test_programmatic_and_plain_launch_agree(reorth, monkeypatch):
-    """Kernels launched with programmatic dependent launch (the default) and plainly
-    (JFNK_PDL=0, read when a context is created) give bitwise equal solves, for every
+    """Kernels launched with programmatic dependent launch (JFNK_PDL=1, read when a context
+    is created; off by default) and plainly (JFNK_PDL=0) give bitwise equal solves, for every
     re-orthogonalisation mode (selective, always, never), graphs replayed or not."""
     from paper_2502_17217_gb300 import jfnk
     case = I.case_cantilever(30, 6, 6, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
