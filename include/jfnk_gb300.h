@@ -304,6 +304,15 @@ int jfnk_get_tuning(jfnk_ctx* ctx, int32_t* out, int n);
  * choice until the next set-up; JFNK_EINVAL (nothing changed) for a value outside the
  * candidate sets.  Both calls run a pending set-up first (its errors are returned). */
 int jfnk_set_tuning(jfnk_ctx* ctx, const int32_t* in, int n);
+/* The multigrid hierarchy built at set-up (Sec. 3.2 and 4.2: one V-cycle per Krylov iteration
+ * applies it): for level l < min(levels, max_levels), rows[l] = unknowns per displacement
+ * component, nnz_a[l] = entries of that level's operator (off-diagonal entries plus one diagonal
+ * per row; the finest level's are the J~ face couplings, 2 per internal face), nnz_p[l] =
+ * entries of the prolongation from level l + 1 to level l (0 on the coarsest level, which is
+ * solved by a dense inverse).  Host arrays of max_levels entries, any of them NULL.  Returns the
+ * number of levels (0 when the context was set up without opt.pc = JFNK_PC_MG), or a negative
+ * status (JFNK_EINVAL for max_levels < 0; set-up errors of a pending set-up). */
+int jfnk_mg_hierarchy(jfnk_ctx* ctx, int max_levels, int64_t* rows, int64_t* nnz_a, int64_t* nnz_p);
 /* Measured FP64 FMA throughput of `device` (TFLOP/s, an FMA counted as 2 flops): a full grid
  * of independent FMA chains timed with CUDA events (allocates and frees a small buffer).  The
  * residual and Arnoldi kernels are bound by this rate on GB300. */

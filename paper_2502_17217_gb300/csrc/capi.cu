@@ -847,3 +847,20 @@ int64_t jfnk_launch_count(const jfnk_ctx* c) { return c ? c->launches : 0; }
 int64_t jfnk_device_bytes(const jfnk_ctx* c) { return c ? c->dev_bytes : 0; }
 
 }  // extern "C"
+
+extern "C" int jfnk_mg_hierarchy(jfnk_ctx* c, int max_levels, int64_t* rows, int64_t* nnz_a, int64_t* nnz_p)
+{
+    if (!c || max_levels < 0) return JFNK_EINVAL;
+    if (c->dirty) {
+        const int rc = jfnk_setup(c);
+        if (rc) return rc;
+    }
+    std::vector<int64_t> r, a, p;
+    const int nl = jfnk::mg_hierarchy_info(c, r, a, p);
+    for (int l = 0; l < nl && l < max_levels; l++) {
+        if (rows) rows[l] = r[l];
+        if (nnz_a) nnz_a[l] = a[l];
+        if (nnz_p) nnz_p[l] = p[l];
+    }
+    return nl;
+}

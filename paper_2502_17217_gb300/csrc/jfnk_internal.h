@@ -385,7 +385,7 @@ int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, 
 int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z,
                  const int* gate, bool* eps_formed = nullptr);
 void mg_release(jfnk_ctx* c);
-int mg_levels_info(jfnk_ctx* c, std::vector<int>& sizes);
+int mg_hierarchy_info(jfnk_ctx* c, std::vector<int64_t>& rows, std::vector<int64_t>& nnz_a, std::vector<int64_t>& nnz_p);
 // solver.cu
 int gmres(jfnk_ctx* c, const double* b, double* x, int* its, double* relres, int* status);
 int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st);

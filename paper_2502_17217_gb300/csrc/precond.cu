@@ -578,6 +578,7 @@ struct MgDev {
         int32_t *rrp = nullptr, *rcol = nullptr;  // R = P^T: nco x n
         T* rval = nullptr;
         int ga = 32, gr = 32;                      // lanes per row of A (coarse levels) and of R
+        int64_t nnz_a = 0, nnz_p = 0;              // operator entries (with the diagonal), P entries
         T *b = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr;
     };
     std::vector<Level> L;
@@ -653,6 +654,7 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
         auto& D = M.L[l];
         const MgLevelHost& H = lv[l];
         D.n = H.n;
+        D.nnz_a = (int64_t)H.col.size();
         std::vector<double> ad(H.n), di(H.n);
         if (l == 0) {
             ad = adiag0;
@@ -674,6 +676,7 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
         D.r = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
         if (l < nl - 1) {
             D.nco = lv[l + 1].n;
+            D.nnz_p = (int64_t)tr[l].pcol.size();
             D.prp = upload_i(c, tr[l].prp);
             D.pcol = upload_i(c, tr[l].pcol);
             D.pval = upload_as<T>(c, tr[l].pval);
@@ -792,13 +795,21 @@ int pc_setup(jfnk_ctx* c)
     return JFNK_OK;
 }
 
-int mg_levels_info(jfnk_ctx* c, std::vector<int>& sizes)
+int mg_hierarchy_info(jfnk_ctx* c, std::vector<int64_t>& rows, std::vector<int64_t>& nnz_a, std::vector<int64_t>& nnz_p)
 {
     MgState& S = mg_state(c);
-    sizes.clear();
+    rows.clear();
+    nnz_a.clear();
+    nnz_p.clear();
     if (!S.ready) return 0;
-    for (auto& l : S.f.L) sizes.push_back(l.n);
-    return (int)sizes.size();
+    for (size_t l = 0; l < S.f.L.size(); l++) {
+        const auto& D = S.f.L[l];
+        rows.push_back(D.n);
+        // the finest level runs on the face coefficients: 2 couplings per internal face + diagonal
+        nnz_a.push_back(l == 0 ? 2 * (int64_t)c->dm.ni + D.n : D.nnz_a);
+        nnz_p.push_back(D.nnz_p);
+    }
+    return (int)rows.size();
 }
 
 static inline int nb(long n, int t) { return (int)std::max<long>(1, (n + t - 1) / t); }

@@ -35,6 +35,7 @@ EXPORTS = [
     "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate", "jfnk_get_tuning", "jfnk_set_tuning",
     "jfnk_solve_segregated", "jfnk_solve_dynamic", "jfnk_dynamic_reset", "jfnk_synchronize",
     "jfnk_set_mesh_hex", "jfnk_hex_patch", "jfnk_dynamic_get_state", "jfnk_dynamic_set_state",
+    "jfnk_mg_hierarchy",
 ]
 
 
@@ -111,6 +112,7 @@ def load():
         "jfnk_measure_fp64_rate": (i, [i, C.POINTER(C.c_double)]),
         "jfnk_get_tuning": (i, [vp, i32p, i]),
         "jfnk_set_tuning": (i, [vp, i32p, i]),
+        "jfnk_mg_hierarchy": (i, [vp, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -368,6 +370,16 @@ class Solver:
 
     def device_bytes(self):
         return int(self.L.jfnk_device_bytes(self.h))
+
+    def mg_hierarchy(self):
+        """Levels of the multigrid hierarchy: list of dicts rows / nnz_a / nnz_p (empty when
+        the context was set up without the multigrid preconditioner)."""
+        n = 32
+        rows, na, npv = (np.zeros(n, np.int64) for _ in range(3))
+        nl = self.L.jfnk_mg_hierarchy(self.h, n, _ptr(rows), _ptr(na), _ptr(npv))
+        if nl < 0:
+            self._check(nl)
+        return [{"rows": int(rows[l]), "nnz_a": int(na[l]), "nnz_p": int(npv[l])} for l in range(min(nl, n))]
 
     TUNING_KEYS = ("grad_bs", "flux_bs", "flux_stage", "finish_bs", "mg_bs", "tuned")
 

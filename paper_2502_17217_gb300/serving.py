@@ -40,6 +40,8 @@ class Request:
     status: int = 0
     stats: object = None
     bytes: int = 0
+    t_setup: float = 0.0  # seconds of context creation and set-up (host work and uploads)
+    t_solve: float = 0.0  # seconds of the solve call
     error: str | None = None
     done: threading.Event = field(default_factory=threading.Event)
 
@@ -138,9 +140,12 @@ class Server:
         try:
             import torch
             torch.cuda.set_device(self.device)
+            t0 = time.perf_counter()
             s = jfnk.Solver.from_case(r.case, device=self.device, **self.options)
             s.setup()
+            t1 = time.perf_counter()
             u, st, rc = s.solve(load_steps=r.load_steps, raise_on_fail=False)
+            r.t_setup, r.t_solve = t1 - t0, time.perf_counter() - t1
             r.u, r.stats, r.status = u, st, rc
             r.bytes = s.device_bytes()
         except Exception as e:  # reported on the request, the server keeps serving
