@@ -294,7 +294,7 @@ def run_ours(workload, steps, warmup, rank=0, world=1, shapes="", profile=True, 
         t_ms, jv_total = aggregate_ranks(t_ms, jv_total, dev)
     value = nc * jv_total / (t_ms / 1e3)
     kt = {}
-    prof_work = {"arnoldi_cols": 0.0, "reorth_cols": 0.0, "its": 0.0, "reorth_its": 0.0}
+    prof_work = {"arnoldi_cols": 0.0, "reorth_cols": 0.0, "its": 0.0, "reorth_its": 0.0, "res_cells": 0.0, "vc_cells": 0.0}
     if profile:
         # per-kernel times: the same solve with CUDA events on the launch stream around every
         # kernel (events cannot sit inside the captured iteration graph, so these steps launch
@@ -416,7 +416,12 @@ def arnoldi_work(s, st, workload):
     return {"arnoldi_cols": sum(3 * n * p.arnoldi_cols for p, n in per),
             "reorth_cols": sum(3 * n * p.reorth_cols for p, n in per),
             "its": sum(3 * n * p.gmres_its for p, n in per),
-            "reorth_its": sum(3 * n * p.reorth_its for p, n in per)}
+            "reorth_its": sum(3 * n * p.reorth_its for p, n in per),
+            # cells x residual evaluations (Jv, Newton and line-search residuals) and cells x
+            # V-cycles (one per Jacobian product of the right-preconditioned Arnoldi process)
+            # of the problems that took part in them
+            "res_cells": sum(n * p.residual_evals for p, n in per),
+            "vc_cells": sum(n * p.jv_products for p, n in per)}
 
 
 MG_ORACLE = dict(theta=0.4, coarse_max=1000, smoothed=True, sweeps=2)  # the solver's default hierarchy options
@@ -667,12 +672,27 @@ def kernel_totals(r, workload):
     # hierarchy (FP32 arithmetic: no FP64 flops)
     w = r["prof_work"]
     kt = r["kernels"]
-    tot = {k: (costs[k][0] * kt[k]["launches"], costs[k][1] * kt[k]["launches"]) for k in ("grad", "flux", "finish")}
+    nc = r["nc"]
+    if workload == "c4":
+        # a batch's problems outside the Arnoldi iteration skip its passes: the work is the
+        # union's cost per cell x the cells of the evaluations each problem took part in
+        units = {k: w["res_cells"] / nc for k in ("grad", "flux", "finish")}
+        vc_units = w["vc_cells"] / nc
+    else:
+        units = {k: kt[k]["launches"] for k in ("grad", "flux", "finish")}
+        vc_units = kt["pc_mg"]["launches"]
+    tot = {k: (costs[k][0] * units[k], costs[k][1] * units[k]) for k in ("grad", "flux", "finish")}
     tot["mdot"] = (2 * (w["arnoldi_cols"] + w["its"]), 4 * w["arnoldi_cols"] + 8 * w["its"])
     tot["update"] = (2 * (w["arnoldi_cols"] + 2 * w["reorth_cols"]),
                      4 * (w["arnoldi_cols"] + w["reorth_cols"]) + 16 * (w["its"] + w["reorth_its"]))
-    tot["pc_mg"] = (0.0, vcycle_bytes(r["levels"], r["sweeps"]) * kt["pc_mg"]["launches"])
+    tot["pc_mg"] = (0.0, vcycle_bytes(r["levels"], r["sweeps"]) * vc_units)
     return tot
+
+
+WORK_UNITS = ("algorithmic flops / bytes over the kernel's CUDA-event time in the profiled solves: residual passes "
+              "per cell-evaluation x (problem cells x residual evaluations it took part in), V-cycles per fine cell x "
+              "(problem cells x Jacobian products), Gram-Schmidt per basis element projected; per-launch figures are "
+              "those totals over the launches")
 
 
 def build_roofline(r, workload):
@@ -697,12 +717,12 @@ def build_roofline(r, workload):
               for k in tot if kt[k]["ms"] > 0}
     if top == "pc_mg":
         achieved = nbytes / t_s / 1e9
-        return {"kernel": "pc_mg (one V-cycle)", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+        return {"kernel": "pc_mg (one V-cycle)", "bound": "hbm", "work_units": WORK_UNITS, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": src, "traffic": traffic,
                 "algorithmic_bytes_per_launch": nbytes / launches, "avg_launch_us": t_s / launches * 1e6,
                 "fp64_measured_tflops": fp64_measured, "others": others}
     achieved = flops / t_s / 1e12
-    return {"kernel": top, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+    return {"kernel": top, "bound": "alu", "work_units": WORK_UNITS, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "fp64_measured_tflops": fp64_measured,
             "frac_of_measured_fp64": achieved / fp64_measured, "traffic": traffic,
             "algorithmic_bytes_per_launch": nbytes / launches,

@@ -240,6 +240,10 @@ int jfnk_create(jfnk_ctx** out, const jfnk_options* opt)
     // prologue to overlap, and the early-resident blocks only wait); same kernels and results
     // either way
     if (const char* v = getenv("JFNK_PDL")) c->pdl = atoi(v) != 0;
+    // a batch's problems whose Krylov cycle is done (or that left the Newton iteration) skip
+    // the residual passes and the V-cycle of each Arnoldi iteration (JFNK_SKIP_DONE=0 runs
+    // every row every time; the results are the same bit for bit, only the work differs)
+    if (const char* v = getenv("JFNK_SKIP_DONE")) c->skip_done = atoi(v) != 0;
     c->cur = c->stream;
     *out = c;
     return JFNK_OK;

@@ -151,6 +151,24 @@ struct SegSlot {
     int pad;
 };
 
+#ifdef __CUDACC__
+// Rows (cells, the owners of faces, multigrid rows) of the problems that sit out the current
+// Arnoldi iteration of a batch: the problem of each row and the per-problem flags.  A problem
+// sits out when it left the Newton iteration or finished its Krylov cycle; its rows are
+// neither read nor written.  prob == nullptr skips nothing (single problems, and every pass
+// outside the batch's Arnoldi iteration).
+struct ProbSkip {
+    const int32_t* prob;
+    const ProbDev* pd;
+    __device__ __forceinline__ bool operator()(int i) const
+    {
+        if (!prob) return false;
+        const ProbDev& P = pd[prob[i]];
+        return !P.active || P.done;
+    }
+};
+#endif
+
 // Scalars shared by all problems of a context.
 struct GlobalDev {
     int jg;           // index of the lockstep Arnoldi iteration (all active problems share it)
@@ -253,6 +271,7 @@ struct jfnk_ctx {
     jfnk::GlobalDev* gh = nullptr;       // pinned, mapped host mirror
     jfnk::GlobalDev* gh_dev = nullptr;   // device address of the mirror (kernels store to it)
     int pdl = 0;                         // launch hot-path kernels with programmatic serialisation
+    int skip_done = 1;                   // batches: problems out of the Arnoldi iteration skip its passes
     size_t ph_count = 0;                 // problems the pinned mirror can hold
     cudaGraphExec_t it_graph = nullptr;  // one captured Arnoldi iteration (replayed for every j)
     cudaEvent_t it_ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -344,12 +363,14 @@ enum ResidualOut { OUT_R = 0, OUT_JV = 1 };
 // R(u_int) into `out` (internal order); mode OUT_JV writes (R - Ru) / eps_p with each
 // problem's eps_p (and 1 / eps_p) from its ProbDev.
 int residual(jfnk_ctx* c, const double* u_int, double* out, int mode);
-int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate);
+// skip_done (batches, inside the Arnoldi iteration): the rows of problems whose cycle is done
+// or that left the Newton iteration are not evaluated (their output keeps its old contents)
+int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, bool skip_done = false);
 int sync_load(jfnk_ctx* c);
 // load_dev: device address of the load factor the kernels read (nullptr = the context's own,
 // kept equal to c->load by sync_load)
 int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
-                  double* F, double* Fn, const double* load_dev = nullptr);
+                  double* F, double* Fn, const double* load_dev = nullptr, bool skip_done = false);
 // linalg.cu
 int perm_in(jfnk_ctx* c, const double* ext_aos, double* int_soa);
 int build_chunks(jfnk_ctx* c);
@@ -379,11 +400,11 @@ int solve_dynamic(jfnk_ctx* c, int n_steps, int32_t probe_cell, double* probe, j
 bool tuning_valid(const Tuning& t);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);
-int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate);
+int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate, bool skip_done = false);
 // eps_formed (optional): asks the multigrid's last sweep to form the following Jv's eps for a
 // single problem; set to whether it did (else the caller runs the norm pass)
 int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z,
-                 const int* gate, bool* eps_formed = nullptr);
+                 const int* gate, bool* eps_formed = nullptr, bool skip_done = false);
 void mg_release(jfnk_ctx* c);
 int mg_hierarchy_info(jfnk_ctx* c, std::vector<int64_t>& rows, std::vector<int64_t>& nnz_a, std::vector<int64_t>& nnz_p);
 // solver.cu

@@ -175,13 +175,14 @@ struct LevelOp {
 // level 0 entry: b = -v (so the cycle returns z = -A^-1 v = J~^-1 v), x = omega D^-1 b.
 // v = base + (*jidx) * ld when jidx is given (the Krylov vector of the current iteration).
 template <typename TV, typename T>
-__global__ void k_mg_pre0(const int* gate, int nc, const TV* __restrict__ base, size_t ld, const int* __restrict__ jidx,
-                          const T* __restrict__ dinv, T omega, T* __restrict__ b, T* __restrict__ x)
+__global__ void k_mg_pre0(const int* gate, ProbSkip sk, int nc, const TV* __restrict__ base, size_t ld,
+                          const int* __restrict__ jidx, const T* __restrict__ dinv, T omega, T* __restrict__ b,
+                          T* __restrict__ x)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= nc) return;
+    if (P >= nc || sk(P)) return;
     const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
     const T d = omega * dinv[P];
 #pragma unroll
@@ -200,14 +201,14 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // is needed, also at the neighbours), x1 = x0 + omega D^-1 (b - A x0).  Same arithmetic, in the
 // same order, as k_mg_pre0 followed by k_mg_jacobi.
 template <typename TV, typename T>
-__global__ void k_mg_pre0_jacobi(const int* gate, LevelOp<T> op, const TV* __restrict__ base, size_t ld,
+__global__ void k_mg_pre0_jacobi(const int* gate, ProbSkip sk, LevelOp<T> op, const TV* __restrict__ base, size_t ld,
                                  const int* __restrict__ jidx, T omega, T* __restrict__ b, T* __restrict__ xo)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = op.n;
-    if (P >= nc) return;
+    if (P >= nc || sk(P)) return;
     const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
     const T dP = omega * op.dinv[P];
     T bb[3], x0[3], ax[3];
@@ -232,13 +233,13 @@ __global__ void k_mg_pre0_jacobi(const int* gate, LevelOp<T> op, const TV* __res
 }
 
 template <typename T>
-__global__ void k_mg_pre(const int* gate, int n, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
-                         T* __restrict__ x)
+__global__ void k_mg_pre(const int* gate, ProbSkip sk, int n, const T* __restrict__ dinv, T omega,
+                         const T* __restrict__ b, T* __restrict__ x)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || sk(i)) return;
     const T d = omega * dinv[i];
 #pragma unroll
     for (int k = 0; k < 3; k++) x[(size_t)k * n + i] = d * b[(size_t)k * n + i];
@@ -246,14 +247,14 @@ __global__ void k_mg_pre(const int* gate, int n, const T* __restrict__ dinv, T o
 
 // Jacobi sweep x_out = x + omega D^-1 (b - A x); zd != null writes the result as double
 template <typename T>
-__global__ void k_mg_jacobi(const int* gate, LevelOp<T> op, T omega, const T* __restrict__ b, const T* __restrict__ x,
-                            T* __restrict__ xo, double* __restrict__ zd)
+__global__ void k_mg_jacobi(const int* gate, ProbSkip sk, LevelOp<T> op, T omega, const T* __restrict__ b,
+                            const T* __restrict__ x, T* __restrict__ xo, double* __restrict__ zd)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = op.n;
-    if (i >= n) return;
+    if (i >= n || sk(i)) return;
     T ax[3];
     op.row(i, x, ax);
     const T d = omega * op.dinv[i];
@@ -323,14 +324,14 @@ __global__ void k_mg_jacobi_eps(const int* gate, LevelOp<T> op, T omega, const T
 
 // r = b - A x
 template <typename T>
-__global__ void k_mg_resid(const int* gate, LevelOp<T> op, const T* __restrict__ b, const T* __restrict__ x,
-                           T* __restrict__ r)
+__global__ void k_mg_resid(const int* gate, ProbSkip sk, LevelOp<T> op, const T* __restrict__ b,
+                           const T* __restrict__ x, T* __restrict__ r)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = op.n;
-    if (i >= n) return;
+    if (i >= n || sk(i)) return;
     T ax[3];
     op.row(i, x, ax);
 #pragma unroll
@@ -339,13 +340,14 @@ __global__ void k_mg_resid(const int* gate, LevelOp<T> op, const T* __restrict__
 
 // y = M x (add = 0) or y += M x (add = 1) for a CSR matrix with nrow rows and nx columns
 template <typename T>
-__global__ void k_mg_spmv(const int* gate, int nrow, int nx, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                          const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add)
+__global__ void k_mg_spmv(const int* gate, ProbSkip sk, int nrow, int nx, const int32_t* __restrict__ rp,
+                          const int32_t* __restrict__ col, const T* __restrict__ val, const T* __restrict__ x,
+                          T* __restrict__ y, int add)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrow) return;
+    if (i >= nrow || sk(i)) return;
     T s[3];
     csr_row<T>(i, nrow, rp, col, val, x, nx, s);
 #pragma unroll
@@ -391,18 +393,21 @@ __device__ __forceinline__ void group_row(int qa, int qb, int sub, const int32_t
 
 // y = M x (add = 0) or y += M x (add = 1)
 template <typename T, int G>
-__global__ void k_mg_spmv_grp(const int* gate, int nrow, int nx, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                              const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, int add)
+__global__ void k_mg_spmv_grp(const int* gate, ProbSkip sk, int nrow, int nx, const int32_t* __restrict__ rp,
+                              const int32_t* __restrict__ col, const T* __restrict__ val, const T* __restrict__ x,
+                              T* __restrict__ y, int add)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / G, sub = t & (G - 1);
     T s0 = 0, s1 = 0, s2 = 0;
-    if (i < nrow)  // lanes past the last row still take part in the shuffles
+    // lanes past the last row and lanes of skipped rows still take part in the shuffles
+    const bool live = i < nrow && !sk(i);
+    if (live)
         group_row<G, T>(rp[i], rp[i + 1], sub, col, val, [&](int j, int k) { return x[(size_t)k * nx + j]; }, s0, s1, s2);
     group_sum<G>(s0, s1, s2);
-    if (i < nrow && sub == 0) {
+    if (live && sub == 0) {
         if (add) { y[i] += s0; y[nrow + i] += s1; y[2 * (size_t)nrow + i] += s2; }
         else { y[i] = s0; y[nrow + i] = s1; y[2 * (size_t)nrow + i] = s2; }
     }
@@ -412,18 +417,20 @@ __global__ void k_mg_spmv_grp(const int* gate, int nrow, int nx, const int32_t* 
 // mode 0: xo = x + omega D^-1 (b - A x);  mode 1: xo = b - A x;
 // mode 2: the first sweep from x = omega D^-1 b, which is formed where it is needed (x unused)
 template <typename T, int G>
-__global__ void k_mg_csr_grp(const int* gate, int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                             const T* __restrict__ val, const T* __restrict__ dinv, T omega, const T* __restrict__ b,
-                             const T* __restrict__ x, T* __restrict__ xo, int mode)
+__global__ void k_mg_csr_grp(const int* gate, ProbSkip sk, int n, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ col, const T* __restrict__ val, const T* __restrict__ dinv,
+                             T omega, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo, int mode)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / G, sub = t & (G - 1);
     T s0 = 0, s1 = 0, s2 = 0;
-    // the row's own values, loaded ahead of the sums
+    // the row's own values, loaded ahead of the sums; lanes of skipped rows and past the last
+    // row still take part in the shuffles
     T bi0 = 0, bi1 = 0, bi2 = 0, xi0 = 0, xi1 = 0, xi2 = 0, di = 0;
-    if (i < n) {
+    const bool live = i < n && !sk(i);
+    if (live) {
         if (sub == 0) {
             bi0 = b[i]; bi1 = b[n + i]; bi2 = b[2 * (size_t)n + i];
             di = dinv[i];
@@ -437,7 +444,7 @@ __global__ void k_mg_csr_grp(const int* gate, int n, const int32_t* __restrict__
             group_row<G, T>(qa, qb, sub, col, val, [&](int j, int k) { return x[(size_t)k * n + j]; }, s0, s1, s2);
     }
     group_sum<G>(s0, s1, s2);
-    if (i < n && sub == 0) {
+    if (live && sub == 0) {
         const T r0 = bi0 - s0, r1 = bi1 - s1, r2 = bi2 - s2;
         if (mode == 1) { xo[i] = r0; xo[n + i] = r1; xo[2 * (size_t)n + i] = r2; }
         else if (mode == 2) {
@@ -454,7 +461,7 @@ __global__ void k_mg_csr_grp(const int* gate, int n, const int32_t* __restrict__
 // y = M x (add = 0) or y += M x (add = 1) for rows longer than a warp's two-entry step: one
 // block of kCoarseWarps warps per row, the warps' sums combined in shared memory
 template <typename T>
-__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_spmv_blk(const int* gate, int nrow, int nx,
+__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_spmv_blk(const int* gate, ProbSkip sk, int nrow, int nx,
                                                                    const int32_t* __restrict__ rp,
                                                                    const int32_t* __restrict__ col,
                                                                    const T* __restrict__ val, const T* __restrict__ x,
@@ -463,6 +470,7 @@ __global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_spmv_blk(const int* ga
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int i = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (sk(i)) return;  // the whole block takes one row
     __shared__ T part[3][kCoarseWarps];
     T s0 = 0, s1 = 0, s2 = 0;
     group_row<32 * kCoarseWarps, T>(rp[i], rp[i + 1], threadIdx.x, col, val,
@@ -530,12 +538,14 @@ static void launch_spmv_grp(jfnk_ctx* c, int g, long rows, A... args)
 // loaded before use, the warps' sums combined in shared memory
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_coarse(const int* gate, int n, const T* __restrict__ Ainv,
-                                                                 const T* __restrict__ b, T* __restrict__ x)
+__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_coarse(const int* gate, ProbSkip sk, int n,
+                                                                 const T* __restrict__ Ainv, const T* __restrict__ b,
+                                                                 T* __restrict__ x)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int r = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (sk(r)) return;  // the whole block takes one row
     __shared__ T part[3][kCoarseWarps];
     T s0 = 0, s1 = 0, s2 = 0;
     const T* row = Ainv + (size_t)r * n;
@@ -544,9 +554,12 @@ __global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_coarse(const int* gate
         const int k1 = k + step;
         const bool h1 = k1 < n;
         const T a0 = row[k], a1 = h1 ? row[k1] : (T)0;
-        const T b00 = b[k], b01 = b[n + k], b02 = b[2 * (size_t)n + k];
+        // rows of skipped problems hold values of an earlier cycle (or none yet): they enter
+        // as zeros, so that nothing of another problem reaches this row's sum
+        T b00 = 0, b01 = 0, b02 = 0;
+        if (!sk(k)) { b00 = b[k]; b01 = b[n + k]; b02 = b[2 * (size_t)n + k]; }
         T b10 = 0, b11 = 0, b12 = 0;
-        if (h1) { b10 = b[k1]; b11 = b[n + k1]; b12 = b[2 * (size_t)n + k1]; }
+        if (h1 && !sk(k1)) { b10 = b[k1]; b11 = b[n + k1]; b12 = b[2 * (size_t)n + k1]; }
         s0 += a0 * b00; s1 += a0 * b01; s2 += a0 * b02;
         if (h1) { s0 += a1 * b10; s1 += a1 * b11; s2 += a1 * b12; }
     }
@@ -591,6 +604,9 @@ struct MgState {
     MgDev<float> f;
     MgDev<double> d;
     bool ready = false;
+    // batches: the problem of each row of every level (level 0: the context's cell map), for
+    // skipping the problems that sit out an Arnoldi iteration; empty for single problems
+    std::vector<const int32_t*> rprob;
 };
 
 template <typename T>
@@ -674,6 +690,9 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
         D.x = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
         D.x2 = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
         D.r = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
+        T* const vecs[4] = {D.b, D.x, D.x2, D.r};
+        for (T* v : vecs)  // rows a cycle skips are read as finite values
+            if (v) JF_CUDA(c, cudaMemsetAsync(v, 0, sizeof(T) * 3 * (size_t)H.n, c->cur ? c->cur : c->stream));
         if (l < nl - 1) {
             D.nco = lv[l + 1].n;
             D.nnz_p = (int64_t)tr[l].pcol.size();
@@ -784,6 +803,34 @@ int pc_setup(jfnk_ctx* c)
     if (rc) return rc;
     rc = mg_upload<double>(c, S.d, lv, inv, jc, sc, adiag0, tr);
     if (rc) return rc;
+    // batches: the problem of every row of every level.  Aggregates never join cells of two
+    // problems (the problems share no face, so no coupling), so each coarse row inherits the
+    // problem of the rows aggregated into it.
+    S.rprob.clear();
+    if (c->nprob > 1) {
+        std::vector<int32_t> cur(nc, -1);  // level 0 in the caller's order
+        for (int p = 0; p < c->nprob; p++)
+            for (int P = c->prob_c0[p]; P < c->prob_c1[p]; P++) cur[t.n2o[P]] = p;
+        std::vector<const int32_t*> rp{(const int32_t*)c->cell_prob};
+        bool ok = true;
+        for (size_t l = 0; ok && l + 1 < lv.size(); l++) {
+            std::vector<int32_t> nxt(lv[l + 1].n, -1);
+            ok = (int)lv[l].agg.size() == lv[l].n;
+            for (int i = 0; ok && i < lv[l].n; i++) {
+                const int a = lv[l].agg[i];
+                ok = a >= 0 && a < lv[l + 1].n && cur[i] >= 0 && (nxt[a] < 0 || nxt[a] == cur[i]);
+                if (ok) nxt[a] = cur[i];
+            }
+            for (int r = 0; ok && r < lv[l + 1].n; r++) ok = nxt[r] >= 0;
+            if (ok) {
+                const int32_t* d = upload_i(c, nxt);
+                if (!d) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
+                rp.push_back(d);
+                cur.swap(nxt);
+            }
+        }
+        if (ok) S.rprob = rp;  // else every row of every level is always evaluated
+    }
     c->mg_coarse_n = lv.back().n;
     if (getenv("JFNK_VERBOSE")) {
         for (size_t l = 0; l < lv.size(); l++)
@@ -835,8 +882,11 @@ static LevelOp<T> level_op(const jfnk_ctx* c, const MgDev<T>& M, int l)
 
 template <typename T, typename TV>
 static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const int* jidx, double* z, const int* gate,
-                  bool* eps_formed)
+                  bool* eps_formed, bool skip_done)
 {
+    const MgState& S = mg_state(c);
+    const bool skip = skip_done && c->nprob > 1 && !S.rprob.empty();
+    auto sk = [&](int l) { return ProbSkip{skip ? S.rprob[l] : nullptr, c->pd}; };
     const bool pf = c->prof.enabled && c->prof.detail;
     const int s_sm = pf ? c->prof.slot("mg_smooth") : -1, s_re = pf ? c->prof.slot("mg_resid") : -1;
     const int s_rs = pf ? c->prof.slot("mg_restrict") : -1, s_pr = pf ? c->prof.slot("mg_prolong") : -1;
@@ -847,9 +897,9 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     const int bs = c->tune.mg_bs;  // rows per block of the thread-per-row kernels
     if (nl == 1) {
         auto& D = M.L[0];
-        jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, vbase, ld, jidx, D.dinv, (T)0, D.b, D.x2);
+        jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), D.n, vbase, ld, jidx, D.dinv, (T)0, D.b, D.x2);
         JF_LAUNCHED(c);
-        jfnk_launch(c, k_mg_coarse<T>, dim3(D.n), dim3(32 * kCoarseWarps), gate, D.n, M.Ainv, D.b, D.x);
+        jfnk_launch(c, k_mg_coarse<T>, dim3(D.n), dim3(32 * kCoarseWarps), gate, sk(0), D.n, M.Ainv, D.b, D.x);
         JF_LAUNCHED(c);
         jfnk_launch(c, k_copy_to_double<T>, dim3(nb(3L * D.n, 256)), dim3(256), gate, 3 * (size_t)D.n, D.x, z);
         JF_LAUNCHED(c);
@@ -862,31 +912,31 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         jfnk_prof_begin(c, s_sm);
         // the entry and the first sweep are one kernel when there are two or more sweeps
         if (sweeps >= 2) {
-            if (l == 0) jfnk_launch(c, k_mg_pre0_jacobi<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, vbase, ld, jidx, omega, D.b, D.x);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+            if (l == 0) jfnk_launch(c, k_mg_pre0_jacobi<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), op, vbase, ld, jidx, omega, D.b, D.x);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, sk(l), D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                    (const T*)D.dinv, omega, (const T*)D.b, (const T*)nullptr, D.x, 2);
         } else {
-            if (l == 0) jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, vbase, ld, jidx, D.dinv, omega, D.b, D.x);
-            else jfnk_launch(c, k_mg_pre<T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, D.dinv, omega, D.b, D.x);
+            if (l == 0) jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), D.n, vbase, ld, jidx, D.dinv, omega, D.b, D.x);
+            else jfnk_launch(c, k_mg_pre<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(l), D.n, D.dinv, omega, D.b, D.x);
         }
         JF_LAUNCHED(c);
         for (int sw = (sweeps >= 2 ? 2 : 1); sw < sweeps; sw++) {
-            if (l == 0) jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, D.b, D.x, D.x2, nullptr);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+            if (l == 0) jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), op, omega, D.b, D.x, D.x2, nullptr);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, sk(l), D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                    (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
             JF_LAUNCHED(c);
             std::swap(D.x, D.x2);
         }
         jfnk_prof_end(c, s_sm);
         jfnk_prof_begin(c, s_re);
-        if (l == 0) jfnk_launch(c, k_mg_resid<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, D.b, D.x, D.r);
-        else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+        if (l == 0) jfnk_launch(c, k_mg_resid<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), op, D.b, D.x, D.r);
+        else launch_csr_grp<T>(c, D.ga, D.n, gate, sk(l), D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.r, 1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_re);
         auto& Cn = M.L[l + 1];
         jfnk_prof_begin(c, s_rs);
-        launch_spmv_grp<T>(c, D.gr, D.nco, gate, D.nco, D.n, (const int32_t*)D.rrp, (const int32_t*)D.rcol, (const T*)D.rval,
+        launch_spmv_grp<T>(c, D.gr, D.nco, gate, sk(l + 1), D.nco, D.n, (const int32_t*)D.rrp, (const int32_t*)D.rcol, (const T*)D.rval,
                            (const T*)D.r, Cn.b, 0);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_rs);
@@ -894,7 +944,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     {
         auto& Dc = M.L[nl - 1];
         jfnk_prof_begin(c, s_co);
-        jfnk_launch(c, k_mg_coarse<T>, dim3(Dc.n), dim3(32 * kCoarseWarps), gate, Dc.n, M.Ainv, Dc.b, Dc.x);
+        jfnk_launch(c, k_mg_coarse<T>, dim3(Dc.n), dim3(32 * kCoarseWarps), gate, sk(nl - 1), Dc.n, M.Ainv, Dc.b, Dc.x);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_co);
     }
@@ -904,7 +954,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         auto& Cn = M.L[l + 1];
         const LevelOp<T> op = level_op<T>(c, M, l);
         jfnk_prof_begin(c, s_pr);
-        jfnk_launch(c, k_mg_spmv<T>, dim3(nb(D.n, bs)), dim3(bs), gate, D.n, Cn.n, D.prp, D.pcol, D.pval, Cn.x, D.x, 1);
+        jfnk_launch(c, k_mg_spmv<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(l), D.n, Cn.n, D.prp, D.pcol, D.pval, Cn.x, D.x, 1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_pr);
         jfnk_prof_begin(c, s_sm);
@@ -915,8 +965,8 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
                 jfnk_launch(c, k_mg_jacobi_eps<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, (const T*)D.b, (const T*)D.x, z, E);
                 *eps_formed = true;
             } else if (l == 0)
-                jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, D.b, D.x, D.x2, last ? z : nullptr);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+                jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), op, omega, D.b, D.x, D.x2, last ? z : nullptr);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, sk(l), D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                    (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
             JF_LAUNCHED(c);
             if (!last) std::swap(D.x, D.x2);
@@ -928,7 +978,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
 
 // z = P^-1 v with v = vbase + (*jidx) * ld (jidx given) or vbase; v double or float; gate may be null
 int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z, const int* gate,
-                 bool* eps_formed)
+                 bool* eps_formed, bool skip_done)
 {
     if (eps_formed) *eps_formed = false;
     // the multigrid's last sweep forms the Jv step of a single problem (batches keep the norm pass)
@@ -961,10 +1011,10 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
         MgState& S = mg_state(c);
         if (!S.ready) return jfnk_fail(c, JFNK_ESTATE, "multigrid preconditioner not set up (options.pc must be JFNK_PC_MG at set-up)");
         int rc;
-        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)vbase, ld, jidx, z, gate, want_eps)
-                                  : vcycle<float, double>(c, S.f, (const double*)vbase, ld, jidx, z, gate, want_eps);
-        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)vbase, ld, jidx, z, gate, want_eps)
-                             : vcycle<double, double>(c, S.d, (const double*)vbase, ld, jidx, z, gate, want_eps);
+        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)vbase, ld, jidx, z, gate, want_eps, skip_done)
+                                  : vcycle<float, double>(c, S.f, (const double*)vbase, ld, jidx, z, gate, want_eps, skip_done);
+        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)vbase, ld, jidx, z, gate, want_eps, skip_done)
+                             : vcycle<double, double>(c, S.d, (const double*)vbase, ld, jidx, z, gate, want_eps, skip_done);
         if (rc) return rc;
     } else {
         if (v_is_float) jfnk_launch(c, k_copy_vec<float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, z);
@@ -975,9 +1025,9 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
     return JFNK_OK;
 }
 
-int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate)
+int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate, bool skip_done)
 {
-    return pc_apply_dev(c, pc, v, 0, nullptr, v_is_float, z, gate);
+    return pc_apply_dev(c, pc, v, 0, nullptr, v_is_float, z, gate, nullptr, skip_done);
 }
 
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z) { return pc_apply_any(c, pc, v, 0, z, nullptr); }

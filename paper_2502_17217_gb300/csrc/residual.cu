@@ -25,12 +25,12 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
                                               const double* __restrict__ sell_l, int n_slots,
                                               const double* __restrict__ u, double* __restrict__ G,
                                               double* __restrict__ T, MatDev mat, const int32_t* __restrict__ cell_prob,
-                                              const double* __restrict__ sym_n, int nsy)
+                                              const double* __restrict__ sym_n, int nsy, ProbSkip sk)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= nc) return;
+    if (P >= nc || sk(P)) return;
     const int s = P >> 5, lane = P & 31, base = sell_off[s], w = sell_w[s];
     const double u0 = u[P], u1 = u[nc + P], u2 = u[2 * nc + P];
     double g[9];
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
                                              const double* __restrict__ T, const double* __restrict__ bval,
                                              const double* __restrict__ load_dev, const int32_t* __restrict__ fn_pos,
                                              MatDev mat, const int32_t* __restrict__ cell_prob,
-                                             double* __restrict__ F, double* __restrict__ Fn)
+                                             double* __restrict__ F, double* __restrict__ Fn, ProbSkip sk)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
@@ -178,6 +178,14 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
     __shared__ double st[(STAGE && kT) ? 9 : 1][(STAGE && kT) ? BS : 1];
     const int f0 = blockIdx.x * BS;
     const int f = f0 + threadIdx.x;
+    if (sk.prob) {
+        // each face class (internal, displacement, symmetry) is owner-sorted and problems hold
+        // contiguous cell ranges: a block within one class whose first and last faces belong
+        // to one skipped problem has nothing to do (uniform exit, before the staging barrier)
+        const int fl = min(f0 + BS, nflux) - 1;
+        const int ca = f0 < ni ? 0 : (f0 < ni + nd ? 1 : 2), cb = fl < ni ? 0 : (fl < ni + nd ? 1 : 2);
+        if (ca == cb && sk.prob[own[f0]] == sk.prob[own[fl]] && sk(own[f0])) return;
+    }
     int Pw = 0;
     if (STAGE) {
         Pw = own[min(f0, nflux - 1)];
@@ -190,7 +198,7 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
             }
         __syncthreads();
     }
-    if (f >= nflux) return;
+    if (f >= nflux || sk(own[f])) return;
     if (f >= ni + nd) {
         // symmetry face (Eq. symm read as the mirror mean (T_P + R T_P R) / 2; Rhie-Chow with the
         // mirror neighbour at 2 delta n): t = Gamma [n.T_P.n - alpha Kbar ((n.u_P) / delta + n.G_P.n)]
@@ -322,13 +330,15 @@ __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int d
                                                 const double* __restrict__ Ru, const ProbDev* __restrict__ pd,
                                                 const int32_t* __restrict__ cell_prob, const int* __restrict__ gate,
                                                 const double* __restrict__ u, const double* __restrict__ vol,
-                                                const double* __restrict__ rc, double mk, double* __restrict__ out)
+                                                const double* __restrict__ rc, double mk, double* __restrict__ out,
+                                                ProbSkip sk)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= 3 * (int64_t)nc) return;
     const int k = (int)(t / nc), P = (int)(t - (int64_t)k * nc);
+    if (sk(P)) return;
     const size_t e = (size_t)k * nc + P;
     if (dim == 2 && k == 2) {
         out[e] = 0.0;
@@ -366,16 +376,17 @@ int sync_load(jfnk_ctx* c)
     return JFNK_OK;
 }
 
-int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate)
+int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, bool skip_done)
 {
-    return residual_bufs(c, u_int, out, mode, gate, c->G, c->T, c->F, c->Fn);
+    return residual_bufs(c, u_int, out, mode, gate, c->G, c->T, c->F, c->Fn, nullptr, skip_done);
 }
 
 int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
-                  double* F, double* Fn, const double* load_dev)
+                  double* F, double* Fn, const double* load_dev, bool skip_done)
 {
     const DevMesh& m = c->dm;
     const double* load = load_dev ? load_dev : (const double*)&c->gdev->load;
+    const ProbSkip sk{(skip_done && c->nprob > 1) ? (const int32_t*)c->cell_prob : nullptr, c->pd};
     static const char* const kNames[3] = {"grad", "flux", "finish"};
     int sl[3];
     for (int q = 0; q < 3; q++) sl[q] = c->prof.enabled ? c->prof.slot(kNames[q]) : -1;
@@ -384,7 +395,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
 #define JF_GRAD_BS(LAW_, BS_)                                                                                   \
     jfnk_launch(c, k_grad<LAW_, BS_>, dim3(nblk(m.nc, BS_)), dim3(BS_), gate, m.nc, m.dim, m.sell_off, m.sell_w, \
                 m.sell_nbr, m.sell_l, m.n_slots, u_int, G, T, c->mat, (const int32_t*)c->cell_prob,   \
-                (const double*)m.sym_n, m.nsy)
+                (const double*)m.sym_n, m.nsy, sk)
 #define JF_GRAD(LAW_)                                     \
     do {                                                  \
         if (tu.grad_bs == 64) JF_GRAD_BS(LAW_, 64);       \
@@ -403,7 +414,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
 #define JF_FLUX_BS(LAW_, BS_, ST_)                                                                                      \
     jfnk_launch(c, k_flux<LAW_, BS_, ST_>, dim3(nblk(m.nflux, BS_)), dim3(BS_), gate, m.ni, m.nd, m.nflux, m.nc, m.own, m.nei, \
                 m.coef, u_int, (const double*)G, (const double*)T, m.bval, load, m.fn_pos,   \
-                c->mat, (const int32_t*)c->cell_prob, F, Fn)
+                c->mat, (const int32_t*)c->cell_prob, F, Fn, sk)
 #define JF_FLUX(LAW_)                                                        \
     do {                                                                     \
         if (tu.flux_bs == 128) {                                             \
@@ -426,7 +437,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     jfnk_launch(c, k_finish, dim3(nblk(3L * m.nc, tu.finish_bs)), dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr,
                 (const int32_t*)m.fs_ptr, (const double*)F, m.b0,
                 load, mode, c->Ru, c->pd, c->cell_prob, gate, u_int, (const double*)m.V,
-                (const double*)(c->dyn_on ? c->dyn_rc : nullptr), c->dyn_mk, out);
+                (const double*)(c->dyn_on ? c->dyn_rc : nullptr), c->dyn_mk, out, sk);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);
     return JFNK_OK;

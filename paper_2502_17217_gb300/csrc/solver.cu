@@ -68,17 +68,21 @@ static int enqueue_iteration(jfnk_ctx* c)
     int rc;
     if (left_pc(c)) {
         if ((rc = perturb_basis(c, c->u, c->w))) return rc;
-        if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate))) return rc;
-        if ((rc = pc_apply_any(c, c->opt.pc, c->wk, 0, c->z, gate))) return rc;
+        if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate, c->skip_done != 0))) return rc;
+        if ((rc = pc_apply_any(c, c->opt.pc, c->wk, 0, c->z, gate, c->skip_done != 0))) return rc;
         if ((rc = arnoldi_orthogonalise(c, c->z))) return rc;
         JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
         return JFNK_OK;
     }
     bool eps_formed = false;
-    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate, &eps_formed))) return rc;
+    // a batch's problems whose cycle is done (or that left the Newton iteration) sit out the
+    // preconditioner and the residual passes as they sit out the vector kernels
+    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate, &eps_formed,
+                          c->skip_done != 0)))
+        return rc;
     if (!eps_formed && (rc = pnorm(c, c->z, 1, true))) return rc;
     if ((rc = perturb(c, c->u, c->z, c->w, true))) return rc;
-    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate))) return rc;
+    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate, c->skip_done != 0))) return rc;
     if ((rc = arnoldi_orthogonalise(c, c->wk))) return rc;
     JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
     return JFNK_OK;

@@ -102,3 +102,31 @@ def test_batch_segregated_bitwise_equals_alone():
         assert rca == 0
         assert np.array_equal(uk, ua), k
         assert ps.newton_its == sta.newton_its and ps.gmres_its == sta.gmres_its
+
+
+@pytest.mark.parametrize("pc", ["mg_mixed", "bjacobi_left"])
+def test_skipping_problems_out_of_the_iteration_changes_no_bit(pc, monkeypatch):
+    """In a batch, the problems whose Krylov cycle is done (or that left the Newton iteration)
+    skip the residual passes and the V-cycle of each Arnoldi iteration; the problems that run
+    get the same arithmetic.  Solves with skipping (the default) and without it
+    (JFNK_SKIP_DONE=0, read when a context is created) are bitwise equal, with the same
+    iteration counts, for the multigrid in mixed precision and for left-preconditioned
+    block-Jacobi."""
+    from paper_2502_17217_gb300 import jfnk
+    cases = _mix()
+    if pc == "mg_mixed":
+        kw = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-10, mg_coarse_max=50)
+    else:
+        kw = dict(pc=jfnk.PC_BJACOBI, newton_rtol=1e-10, pc_side=jfnk.PC_LEFT)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("JFNK_SKIP_DONE", flag)
+        B = jfnk.Batch(cases, **kw)
+        u, st, rc = B.solve()
+        assert rc == 0
+        out.append((u, [(p.gmres_its, p.newton_its, p.jv_products) for p in B.problem_stats()]))
+        B.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    # the problems converge at different iteration counts, so some did sit out iterations
+    assert len({its for its, _, _ in out[0][1]}) > 1
