@@ -617,9 +617,9 @@ def serving_record(args):
     plain_u, t_seq, lat_seq = sequential(fp64)
     _, t_seq_mixed, _ = sequential(mixed)
 
-    def served(rate, opts):
+    def served(rate, opts, mode="contexts"):
         reqs, wall, srv = serving.serve_stream(cases, rate_per_s=rate, seed=int(rate), load_steps=steps, max_slots=8,
-                                               **opts)
+                                               mode=mode, **opts)
         summ = serving.summarize(reqs, wall)
         err = max(float(np.linalg.norm(r.u - up) / max(np.linalg.norm(up), 1e-300)) if r.u is not None else float("inf")
                   for r, up in zip(reqs, plain_u))
@@ -632,6 +632,7 @@ def serving_record(args):
     rate_list = [float(x) for x in args.rates.split(",")]
     for rate in rate_list:
         rates[str(int(rate))] = served(rate, mixed)
+    lockstep = {str(int(rate)): served(rate, mixed, mode="lockstep") for rate in rate_list}
     served_fp64 = served(max(rate_list), fp64)
     best = max(v["solves_per_s"] for v in rates.values())
     seq = len(reqs_def) / t_seq
@@ -642,7 +643,10 @@ def serving_record(args):
                        "served": "continuous admission by HBM footprint, 8 slots, one context and stream per request, "
                                  "MG FP32 + FP32 basis (mixed)",
                        "baseline": "the same requests solved one after another (set-up included)"},
-            "rates": rates, "served_fp64_at_max_rate": served_fp64,
+            "rates": rates, "lockstep_rates": lockstep, "served_fp64_at_max_rate": served_fp64,
+            "modes": {"rates": "contexts: one context and stream per request, up to 8 at once",
+                      "lockstep_rates": "lockstep: queued requests with the same load steps concatenated into one "
+                                        "batch (one index space and iteration graph), up to 8 batches at once"},
             "sequential_fp64_solves_per_s": seq, "sequential_fp64_p50_latency_s": float(np.percentile(lat_seq, 50)),
             "sequential_mixed_solves_per_s": seq_mixed,
             "speedup_vs_sequential_fp64": best / seq,

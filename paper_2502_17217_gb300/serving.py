@@ -1,13 +1,22 @@
-"""Solve-request server on one GPU: continuous admission by HBM footprint, concurrent slots.
+"""Solve-request server on one GPU: continuous admission by HBM footprint.
 
 Requests (a mesh + boundary conditions + material, and a number of load steps) arrive at any
-time.  The dispatcher admits queued requests in arrival order as soon as a slot is free and
-the request's device footprint fits the memory budget; each admitted request gets its own
-context (mesh, state, Krylov basis and preconditioner resident on the device for its whole
-life) and its own CUDA stream, and runs its Newton-Krylov solve in a slot worker.  Requests
-admitted while others are running overlap with them on the device.  A request's arithmetic
-never depends on the others (separate contexts), so its result is the same alone and in the
-mix.  Latency is completion time minus arrival time (queueing, set-up and solve).
+time and queue in arrival order.  Two ways of putting them on the device:
+
+  * mode "contexts" (default): a queued request is admitted as soon as a slot is free and its
+    device footprint fits the memory budget; it gets its own context (mesh, state, Krylov
+    basis and preconditioner resident on the device for its whole life) and its own CUDA
+    stream, and runs its Newton-Krylov solve in a slot worker.  Requests admitted while
+    others run overlap with them on the device, kernel by kernel; each starts as soon as it is
+    admitted and retires as soon as it converges.
+  * mode "lockstep": when a batch slot is free, the queued requests with the head request's
+    number of load steps that fit the budget are concatenated into one batch (one index space,
+    one iteration graph for all of them, each problem with its own Newton loop and Krylov
+    scalars) and solved together; requests that arrive meanwhile wait for the next batch.
+
+A request's arithmetic never depends on the others (separate contexts, or per-problem scalars
+in a batch), so its result is the same alone and in the mix.  Latency is completion time minus
+arrival time (queueing, set-up and solve).
 
 The footprint of a request is estimated as bytes-per-cell x cells; the server starts from a
 conservative figure per law and replaces it with the largest measured ratio
@@ -55,10 +64,18 @@ class Request:
 
 
 class Server:
-    """Continuous-batching JFNK solve server (one GPU)."""
+    """Continuous-admission JFNK solve server (one GPU).  mode "contexts": one context and
+    stream per request, up to max_slots at once; mode "lockstep": batches of queued requests,
+    up to max_slots batches at once."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: float | None = None, max_slots: int = 8, **options):
+    MODES = ("contexts", "lockstep")
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: float | None = None, max_slots: int = 8,
+                 mode: str = "contexts", **options):
+        if mode not in self.MODES:
+            raise ValueError(f"mode must be one of {self.MODES}")
         self.device = device
+        self.mode = mode
         self.options = dict(options)
         self.max_slots = max_slots
         if hbm_budget_bytes is None:
@@ -70,7 +87,8 @@ class Server:
         self._queue: collections.deque[Request] = collections.deque()
         self._lock = threading.Condition()
         self._in_use = 0.0
-        self._running = 0
+        self._running = 0   # slot workers (requests, or batches in lockstep mode)
+        self._inflight = 0  # requests on the device
         self._stop = False
         self._workers: list[threading.Thread] = []
         self.completed: list[Request] = []
@@ -115,15 +133,33 @@ class Server:
                     return
                 if not self._admissible():
                     continue
-                r = self._queue.popleft()
-                need = self.footprint(r.case)
+                group = [self._queue.popleft()]
+                need = self.footprint(group[0].case)
+                if self.mode == "lockstep":
+                    # the queued requests with the head's load steps that still fit, in order
+                    keep = collections.deque()
+                    while self._queue:
+                        q = self._queue.popleft()
+                        nq = self.footprint(q.case)
+                        if q.load_steps == group[0].load_steps and self._in_use + need + nq <= self.budget:
+                            group.append(q)
+                            need += nq
+                        else:
+                            keep.append(q)
+                    self._queue = keep
                 self._in_use += need
                 self._running += 1
-                self.max_concurrent = max(self.max_concurrent, self._running)
-                if self._running > 1:
+                self._inflight += len(group)
+                self.max_concurrent = max(self.max_concurrent, self._inflight)
+                if self._inflight > 1:
                     self.max_shared_footprint = max(self.max_shared_footprint, self._in_use)
-                r.t_admit = time.perf_counter()
-            t = threading.Thread(target=self._work, args=(r, need), daemon=True)
+                now = time.perf_counter()
+                for r in group:
+                    r.t_admit = now
+            if self.mode == "lockstep":
+                t = threading.Thread(target=self._work_batch, args=(group, need), daemon=True)
+            else:
+                t = threading.Thread(target=self._work, args=(group[0], need), daemon=True)
             self._workers = [w for w in self._workers if w.is_alive()]  # a long-lived server keeps no dead threads
             self._workers.append(t)
             t.start()
@@ -158,15 +194,57 @@ class Server:
                 except Exception as e:
                     r.error = r.error or f"close: {type(e).__name__}: {e}"
         r.t_done = time.perf_counter()
+        self._retire([r], need)
+
+    def _retire(self, group, need: float):
         with self._lock:
-            if r.bytes:
-                law = r.case.material.law
-                self.bpc[law] = max(self.bpc[law] if law in self.bpc else 0.0, r.bytes / r.cells)
+            for r in group:
+                if r.bytes:
+                    law = r.case.material.law
+                    self.bpc[law] = max(self.bpc[law] if law in self.bpc else 0.0, r.bytes / r.cells)
+                self.completed.append(r)
             self._in_use -= need
             self._running -= 1
-            self.completed.append(r)
+            self._inflight -= len(group)
             self._lock.notify_all()
-        r.done.set()
+        for r in group:
+            r.done.set()
+
+    def _work_batch(self, group, need: float):
+        """Lockstep mode: the group solved as one batch; each request gets its own part of the
+        solution, its own statistics and an equal share of the batch's device bytes."""
+        b = None
+        try:
+            import torch
+            torch.cuda.set_device(self.device)
+            t0 = time.perf_counter()
+            b = jfnk.Batch([r.case for r in group], device=self.device, **self.options)
+            b.setup()
+            t1 = time.perf_counter()
+            u, st, rc = b.solve(load_steps=group[0].load_steps, raise_on_fail=False)
+            t2 = time.perf_counter()
+            per = b.problem_stats()
+            total = b.device_bytes()
+            cells = sum(r.cells for r in group)
+            for r, uk, ps in zip(group, b.split(u), per):
+                r.u, r.stats, r.status = np.array(uk), ps, ps.status
+                r.t_setup, r.t_solve = t1 - t0, t2 - t1
+                r.bytes = int(total * r.cells / max(1, cells))
+        except Exception as e:  # reported on every request of the batch, the server keeps serving
+            for r in group:
+                r.error = f"{type(e).__name__}: {e}"
+                r.status = -99
+        finally:
+            if b is not None:
+                try:
+                    b.close()
+                except Exception as e:
+                    for r in group:
+                        r.error = r.error or f"close: {type(e).__name__}: {e}"
+        now = time.perf_counter()
+        for r in group:
+            r.t_done = now
+        self._retire(group, need)
 
 
 def serve_stream(cases, rate_per_s: float, seed: int = 0, load_steps=None, **server_kw):

@@ -68,3 +68,30 @@ def test_served_results_under_contention_with_load_steps():
         ua, sta, rc = jfnk.Solver.from_case(c, **opts).solve(load_steps=st)
         assert rc == 0 and sta.load_steps_done == st
         assert np.array_equal(r.u, ua)
+
+
+@pytest.mark.parametrize("mode", ["contexts", "lockstep"])
+def test_served_results_match_the_oracle(mode):
+    """Every served request (Poisson arrivals, Hooke and neo-Hookean with two load steps,
+    mixed precision, multigrid) against the oracle's FP64 solve of that request, both to
+    |R| <= 1e-10 |R0| per load step: relative difference <= 1e-8.  In lockstep mode the
+    requests run as concatenated batches; in contexts mode each in its own context."""
+    import oracle as O
+    from paper_2502_17217_gb300 import jfnk, serving
+    reqs_def = I.serving_requests(8, lo=500, hi=4000, seed=9, frac_nh=0.4)
+    opts = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, mg_coarse_max=50, newton_rtol=1e-10)
+    cases = [c for c, _ in reqs_def]
+    steps = [s for _, s in reqs_def]
+    reqs, wall, srv = serving.serve_stream(cases, rate_per_s=500.0, seed=3, load_steps=steps, max_slots=4, mode=mode,
+                                           **opts)
+    bad = [(k, r.status, r.error, r.cells) for k, r in enumerate(reqs) if r.status != 0]
+    assert not bad, bad
+    if mode == "lockstep":
+        assert srv.max_concurrent > 1  # some requests shared a batch
+    for k, (r, (c, st)) in enumerate(zip(reqs, reqs_def)):
+        o = O.Oracle.from_case(c)
+        o.mg_setup(theta=0.4, coarse_max=50, smoothed=True, sweeps=2)
+        uo, rco, _ = o.newton(load_steps=st, rtol=1e-10, pc=O.PC_MG, m=30, aug=2)
+        assert rco == 0
+        err = np.linalg.norm(r.u - uo) / np.linalg.norm(uo)
+        assert err <= 1e-8, (k, mode, c.name, err)

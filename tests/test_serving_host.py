@@ -143,3 +143,78 @@ def test_poisson_stream_and_latency_summary(live):
     # arrivals follow the seeded gaps: submission times are increasing
     t = [r.t_arrival for r in reqs]
     assert all(x < y for x, y in zip(t, t[1:]))
+
+
+@pytest.fixture
+def batches(monkeypatch):
+    """A fake batch in place of jfnk.Batch: records each batch's requests, sleeps, returns a
+    solution whose rows carry the problem's cell count (so each request's part can be checked)."""
+    made = []
+
+    class FakeBatch:
+        def __init__(self, cases, **kw):
+            self.cases = list(cases)
+            self.sizes = [c.mesh.n_cells for c in self.cases]
+            made.append(self)
+
+        def setup(self):
+            pass
+
+        def solve(self, load_steps=1, raise_on_fail=True):
+            time.sleep(max(c.hold for c in self.cases))
+            if any(c.fail for c in self.cases):
+                raise RuntimeError("planted batch failure")
+            self.load_steps = load_steps
+            u = np.concatenate([np.full((n, 3), float(n)) for n in self.sizes])
+            return u, SimpleNamespace(), 0
+
+        def problem_stats(self):
+            return [SimpleNamespace(status=0, load_steps_done=self.load_steps) for _ in self.cases]
+
+        def split(self, u):
+            off = np.concatenate([[0], np.cumsum(self.sizes)])
+            return [u[off[k]:off[k + 1]] for k in range(len(self.sizes))]
+
+        def device_bytes(self):
+            return 0
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(serving.jfnk, "Batch", FakeBatch)
+    import torch
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    return made
+
+
+def test_lockstep_mode_groups_queued_requests_by_load_steps_and_budget(batches):
+    """Requests queued while a batch runs form the next batch: only those with the head
+    request's load steps, and only while their footprints fit the budget, in arrival order;
+    each request receives its own part of the batch's solution."""
+    bpc = serving.DEFAULT_BYTES_PER_CELL[0]
+    srv = serving.Server(hbm_budget_bytes=1000 * bpc, max_slots=1, mode="lockstep")
+    first = srv.submit(_case(100, hold=0.2))  # runs alone while the rest queue up
+    time.sleep(0.05)
+    rest = [srv.submit(_case(n, hold=0.01), load_steps=ls) for n, ls in
+            [(200, 1), (300, 2), (250, 1), (600, 1), (150, 2)]]
+    srv.drain()
+    srv.close()
+    groups = [[c.mesh.n_cells for c in b.cases] for b in batches]
+    assert groups[0] == [100]
+    # after the first batch: the head (200 cells, 1 step) with the next 1-step request that
+    # fits (250); 600 would exceed the budget (200 + 250 + 600 > 1000 cells' worth)
+    assert groups[1] == [200, 250]
+    assert sorted(map(tuple, groups[2:])) == sorted([(300, 150), (600,)])
+    for r in [first] + rest:
+        assert r.status == 0 and np.all(r.u == r.cells)
+    assert srv._in_use == 0 and srv._running == 0 and srv._inflight == 0
+
+
+def test_lockstep_batch_failure_is_reported_on_each_of_its_requests(batches):
+    srv = serving.Server(hbm_budget_bytes=1e15, max_slots=2, mode="lockstep")
+    reqs = [srv.submit(_case(100, hold=0.05, fail=(k == 1))) for k in range(2)]
+    srv.drain()
+    srv.close()
+    bad = [r for r in reqs if r.status == -99]
+    assert bad and all("planted batch failure" in r.error for r in bad)
+    assert all(r.done.is_set() for r in reqs)
