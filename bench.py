@@ -65,6 +65,9 @@ def workload_case(name="c2"):
 
 
 DRAM_BYTES_PER_LAUNCH = {"c2": {"update": 16.04e6, "mdot": 16.57e6, "flux": 30.90e6}}
+# the batched workload: DRAM bytes per evaluated cell (read + write, one ncu capture on its first
+# 96 problems, 1.31 M cells, every row evaluated), scaled by the cells a launch evaluates
+DRAM_BYTES_PER_CELL = {"c4": {"pc_mg": 558.0, "flux": 506.2, "grad": 242.9, "finish": 259.8}}
 # FP64 thread instructions (DFMA + DADD + DMUL) per launch, from ncu's per-cycle instruction
 # rates x elapsed cycles of the same capture (k_flux: 47 per internal face, 231,600 of them)
 FP64_INSTR_PER_LAUNCH = {"c2": {"flux": 10.90e6}}
@@ -225,10 +228,13 @@ def aggregate_ranks(t_ms, units, device):
     return float(t.item()), float(u.item())
 
 
-def make_solver(workload, dev, **extra):
-    """The solver (or batch) of a workload with the benchmark's options; returns (s, case)."""
+def make_solver(workload, dev, members=0, **extra):
+    """The solver (or batch) of a workload with the benchmark's options; returns (s, case).
+    members > 0 keeps the first `members` problems of the batched workload (profiling runs)."""
     from paper_2502_17217_gb300 import jfnk
     case = workload_case(workload)
+    if workload == "c4" and members > 0:
+        case = case[:members]
     opts = dict(device=dev.index, pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-8, gmres_restart=30,
                 gmres_eta=1e-3, **extra)
     if workload == "c4":
@@ -556,7 +562,7 @@ def run_for_ncu(args):
     g.build()
     dev = torch.device("cuda", 0)
     extra = dict(autotune=0) if args.shapes else {}
-    s, case, _ = make_solver(args.workload, dev, **extra)
+    s, case, _ = make_solver(args.workload, dev, members=args.members, **extra)
     if args.shapes:  # with --shapes the autotuner is off, so a capture's launch count starts at the solve
         s.set_tuning(*[int(v) for v in args.shapes.split(",")])
     for _ in range(args.warmup + args.steps):
@@ -713,6 +719,10 @@ def build_roofline(r, workload):
     flops, nbytes = tot[top]
     fp64_measured = _j.measure_fp64_rate(0)
     traffic = DRAM_BYTES_PER_LAUNCH.get(workload, {}).get(top)
+    per_cell = DRAM_BYTES_PER_CELL.get(workload, {}).get(top)
+    if per_cell is not None:
+        cells = r["prof_work"]["vc_cells"] if top == "pc_mg" else r["prof_work"]["res_cells"]
+        traffic = per_cell * cells / launches
     profiled = sum(kt[q]["ms"] for q in ("grad", "flux", "finish", "mdot", "update", "pc_mg"))
     others = {k: {"tflops": tot[k][0] / (kt[k]["ms"] / 1e3) / 1e12, "gbs": tot[k][1] / (kt[k]["ms"] / 1e3) / 1e9,
                   "hbm_frac": tot[k][1] / (kt[k]["ms"] / 1e3) / 1e9 / hbm_peak,
@@ -768,6 +778,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="config 5 alone: Poisson request stream, served solves/s and p50/p99")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--members", type=int, default=0, help="with --ncu and the batched workload: its first N "
+                    "problems only (a smaller case for counter captures)")
     ap.add_argument("--e2e-steps", type=int, default=5, help="solves in the end-to-end figure (at most --steps)")
     ap.add_argument("--shapes", default="", help="launch shapes instead of the autotuner's: grad_bs,flux_bs,"
                     "flux_stage,finish_bs,mg_bs (jfnk_set_tuning)")
