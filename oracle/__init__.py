@@ -73,6 +73,8 @@ def lib():
             "orc_segregated": (i, [vp, vp, i, d, d, i, d, i, i, vp]),
             "orc_set_dynamics": (i, [vp, d, d]),
             "orc_dynamic": (i, [vp, vp, i, d, d, i, i, i, d, i, vp, i, vp]),
+            "orc_set_updated_lagrangian": (i, [vp, i]),
+            "orc_ul_state": (None, [vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
@@ -235,6 +237,18 @@ class Oracle:
         rc = lib().orc_lgmres(self.h, _p(u), _p(Ru), _p(b), _p(x), m, aug, eta, max_restarts, pc, C.byref(its),
                               C.byref(rel))
         return x, rc, its.value, rel.value
+
+    def set_updated_lagrangian(self, on=True):
+        """App. A updated-Lagrangian form (neo-Hookean, 3-D): newton() then solves each load
+        step for the increment on the last converged configuration and returns the total
+        displacement; the mesh is left in the final configuration (geometry() shows it)."""
+        self._check(lib().orc_set_updated_lagrangian(self.h, 1 if on else 0))
+
+    def ul_state(self):
+        """Total deformation gradient of the last converged step, [n_cells, 3, 3]."""
+        F = np.zeros((self.nc, 3, 3))
+        lib().orc_ul_state(self.h, _p(F))
+        return F
 
     def set_dynamics(self, rho, dt):
         """Inertia with density rho and time step dt (BDF2, from rest); before mg_setup."""

@@ -51,6 +51,14 @@ struct orc_problem {
     int dynamic;
     double rho, dt;
     double *dyn_ut, *dyn_utm1, *dyn_vt, *dyn_vtm1, *dyn_at, *dyn_c; /* [nc][3] */
+    /* updated-Lagrangian form (App. A, Eq. momentum_UL): the points of the reference mesh,
+       the total deformation gradient of the last converged load step per cell and that
+       step's load factor; the mesh (pts, geometry) is the last converged configuration */
+    int ul;
+    double* ul_pts0;  /* [np][3] */
+    double* ul_F;     /* [nc][3][3], F_ij */
+    double* ul_u;     /* [nc][3] displacement of the last converged step, u_n */
+    double* ul_G;     /* [nc][3][3] its least-squares gradient on the updated mesh */
     char err[256];
 };
 
@@ -149,6 +157,7 @@ void orc_destroy(orc_problem* p)
     free(p->pts); free(p->fptr); free(p->fpts); free(p->own); free(p->nei); free(p->btype); free(p->bval);
     free(p->cfptr); free(p->cf); free(p->Sf); free(p->Cf); free(p->V); free(p->C); free(p->Ginv); free(p->fb);
     free(p->dyn_ut); free(p->dyn_utm1); free(p->dyn_vt); free(p->dyn_vtm1); free(p->dyn_at); free(p->dyn_c);
+    free(p->ul_pts0); free(p->ul_F); free(p->ul_u); free(p->ul_G);
     free(p);
 }
 
@@ -436,6 +445,27 @@ void orc_gradient(const orc_problem* p, const double* u, double* grad)
  * Linear elasticity (Eq. linearElastic): sigma = mu grad u + mu grad u^T + lambda tr(grad u) I.
  * Neo-Hookean (Eq. neoHook): F = I + (grad u)^T, J = det F, b = F F^T, bbar = J^-2/3 b,
  * sigma = mu/J dev(bbar) + kappa/2 (J^2 - 1)/J I. */
+/* App. B neo-Hookean Cauchy stress of the deformation gradient F (J = det F):
+ * sigma = mu / J dev(J^-2/3 F F^T) + kappa / 2 (J^2 - 1) / J I */
+static void nh_cauchy(const orc_problem* p, const double* F, double J, double* s)
+{
+    double b[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; k++) acc += F[3 * i + k] * F[3 * j + k];
+            b[3 * i + j] = acc;
+        }
+    double Jm23 = pow(J, -2.0 / 3.0);
+    double trb = Jm23 * (b[0] + b[4] + b[8]);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double bbar = Jm23 * b[3 * i + j];
+            double dev = bbar - (i == j ? trb / 3.0 : 0.0);
+            s[3 * i + j] = p->mu / J * dev + (i == j ? 0.5 * p->kappa * (J * J - 1.0) / J : 0.0);
+        }
+}
+
 void orc_cauchy_stress(const orc_problem* p, const double* g, double* s)
 {
     if (p->law == ORC_LAW_LINEAR) {
@@ -444,7 +474,7 @@ void orc_cauchy_stress(const orc_problem* p, const double* g, double* s)
             for (int j = 0; j < 3; j++) s[3 * i + j] = p->mu * (g[3 * i + j] + g[3 * j + i]) + (i == j ? p->lam * tr : 0.0);
         return;
     }
-    double F[9], b[9];
+    double F[9];
     for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++) F[3 * i + j] = (i == j ? 1.0 : 0.0) + g[3 * j + i];
     double J = det33(F);
@@ -475,20 +505,7 @@ void orc_cauchy_stress(const orc_problem* p, const double* g, double* s)
             }
         return;
     }
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) {
-            double acc = 0.0;
-            for (int k = 0; k < 3; k++) acc += F[3 * i + k] * F[3 * j + k];
-            b[3 * i + j] = acc;
-        }
-    double Jm23 = pow(J, -2.0 / 3.0);
-    double trb = Jm23 * (b[0] + b[4] + b[8]);
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) {
-            double bbar = Jm23 * b[3 * i + j];
-            double dev = bbar - (i == j ? trb / 3.0 : 0.0);
-            s[3 * i + j] = p->mu / J * dev + (i == j ? 0.5 * p->kappa * (J * J - 1.0) / J : 0.0);
-        }
+    nh_cauchy(p, F, J, s);
 }
 
 /* The tensor T_P whose contraction with an area vector gives the face force of cell P:
@@ -496,6 +513,35 @@ void orc_cauchy_stress(const orc_problem* p, const double* g, double* s)
  * (J F^-T . n_o) . sigma = n_o . (J F^-1 . sigma), so T = J F^-1 . sigma. */
 void orc_traction_operator(const orc_problem* p, const double* grad, double* T)
 {
+    if (p->ul) {
+        /* updated Lagrangian (Eq. momentum_UL): grad is the gradient of the displacement on
+           the updated mesh, so grad - G_n is that of the increment since the last converged
+           step, f = I + (grad - G_n)^T, F = f F_n, and (j f^-T . n_u) . sigma =
+           n_u . (j f^-1 . sigma), so T = j f^-1 . sigma(F) */
+        for (int P = 0; P < p->nc; P++) {
+            const double* g = grad + 9 * P;
+            const double* Gn = p->ul_G + 9 * P;
+            const double* Fn = p->ul_F + 9 * P;
+            double f[9], fi[9], F[9], sg[9];
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) f[3 * i + j] = (i == j ? 1.0 : 0.0) + (g[3 * j + i] - Gn[3 * j + i]);
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; k++) acc += f[3 * i + k] * Fn[3 * k + j];
+                    F[3 * i + j] = acc;
+                }
+            nh_cauchy(p, F, det33(F), sg);
+            double jf = inv33(f, fi);
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; k++) acc += fi[3 * i + k] * sg[3 * k + j];
+                    T[9 * P + 3 * i + j] = jf * acc;
+                }
+        }
+        return;
+    }
     for (int P = 0; P < p->nc; P++) {
         const double* g = grad + 9 * P;
         double s[9];
@@ -1512,6 +1558,128 @@ int orc_segregated(orc_problem* p, double* u, int n_load_steps, double rtol, dou
  * specified): s = 1, 1/2, 1/4, ... (at most 10 halvings), accepted when
  * |R(u + s du)| <= (1 - 1e-4 s) |R(u)|.  Converged when |R| <= max(atol, rtol |R(u0)|),
  * |R(u0)| taken at the start of each load step; stol = 0. */
+/* ------------------------------------------------------------------ App. A, updated Lagrangian
+ * Eq. momentum_UL writes the balance on the configuration reached at the last converged load
+ * step: the mesh there is the updated one (points moved with the displacement), f = I +
+ * [grad (du)]^T is the relative deformation gradient of the increment du since that step
+ * (gradient on the updated mesh), j = det f, and the surface force of a face is
+ * (j f^-T . n_u) . sigma = n_u . (j f^-1 . sigma), sigma the Cauchy stress of the total
+ * deformation F = f F_n, F_n the total deformation gradient of the last converged step.
+ * Readings (the appendix gives the balance only):
+ *  - the unknown stays the total displacement u = u_n + du (cell values): the gradient of du
+ *    on the updated mesh is grad u - G_n, G_n the gradient of u_n on that mesh; the Rhie-Chow
+ *    term of Eq. RhieChow acts on u, as in the total-Lagrangian form, with differences and
+ *    gradients taken on the updated mesh (stabilising only the increment would leave the
+ *    stabilisation of the earlier steps out of the balance: the two forms would then differ
+ *    at first order, not by discretisation error);
+ *  - j f^-1 sigma is interpolated to the faces like the total-Lagrangian operator;
+ *    displacement faces prescribe the total displacement; tractions are per unit area and
+ *    body forces per unit volume of the updated configuration;
+ *  - after a step converges, every mesh point moves by the mean, over the cells sharing it,
+ *    of the increment extrapolated from the cell centre with the cell gradient,
+ *    du_P + (x_v - x_P) . (grad du)_P (exact for increments linear in space), the geometry
+ *    and least-squares tensors are recomputed on the moved points, F_n <- f F_n, u_n <- u
+ *    and G_n is the gradient of u_n on the moved mesh.
+ * The preconditioner keeps the approximate Jacobian of the reference mesh when it is a
+ * multigrid hierarchy (built once); block-Jacobi reads the current geometry.  Neo-Hookean
+ * 3-D problems without symmetry faces and without inertia only. */
+int orc_set_updated_lagrangian(orc_problem* p, int on)
+{
+    if (on) {
+        if (p->law != ORC_LAW_NEOHOOKEAN || p->dim != 3 || p->dynamic) {
+            snprintf(p->err, sizeof p->err, "updated Lagrangian: neo-Hookean 3-D static problems only");
+            return -1;
+        }
+        for (int b = 0; b < p->nf - p->ni; b++)
+            if (p->btype[b] == ORC_BC_SYMM) {
+                snprintf(p->err, sizeof p->err, "updated Lagrangian: symmetry faces are not supported");
+                return -1;
+            }
+        if (!p->ul_pts0) {
+            p->ul_pts0 = (double*)xcalloc((size_t)p->np * 3, sizeof(double));
+            memcpy(p->ul_pts0, p->pts, sizeof(double) * 3 * (size_t)p->np);
+        }
+        if (!p->ul_F) p->ul_F = (double*)xcalloc((size_t)p->nc * 9, sizeof(double));
+        if (!p->ul_u) p->ul_u = (double*)xcalloc((size_t)p->nc * 3, sizeof(double));
+        if (!p->ul_G) p->ul_G = (double*)xcalloc((size_t)p->nc * 9, sizeof(double));
+    }
+    /* back to the reference configuration */
+    p->ul = 0;
+    if (p->ul_pts0) memcpy(p->pts, p->ul_pts0, sizeof(double) * 3 * (size_t)p->np);
+    if (p->ul_F)
+        for (int P = 0; P < p->nc; P++)
+            for (int q = 0; q < 9; q++) p->ul_F[9 * P + q] = (q % 4 == 0) ? 1.0 : 0.0;
+    if (p->ul_u) memset(p->ul_u, 0, sizeof(double) * 3 * (size_t)p->nc);
+    if (p->ul_G) memset(p->ul_G, 0, sizeof(double) * 9 * (size_t)p->nc);
+    p->ul = on ? 1 : 0;
+    return orc_prepare(p);
+}
+
+/* total deformation gradient of the last converged step, [nc][3][3] (identity before any) */
+void orc_ul_state(const orc_problem* p, double* F)
+{
+    for (int P = 0; P < p->nc; P++)
+        for (int q = 0; q < 9; q++) F[9 * P + q] = p->ul ? p->ul_F[9 * P + q] : ((q % 4 == 0) ? 1.0 : 0.0);
+}
+
+/* the end of a converged load step at displacement u: F_n <- f F_n, the points moved by the
+   increment, the geometry rebuilt, u_n <- u and G_n its gradient on the moved mesh */
+static int ul_advance(orc_problem* p, const double* u)
+{
+    int nc = p->nc, np = p->np;
+    double* grad = (double*)xcalloc((size_t)nc * 9, sizeof(double));
+    double* du = (double*)xcalloc((size_t)nc * 3, sizeof(double));
+    orc_gradient(p, u, grad);
+    for (int P = 0; P < nc; P++) {
+        for (int q = 0; q < 9; q++) grad[9 * P + q] -= p->ul_G[9 * P + q];  /* gradient of the increment */
+        for (int c = 0; c < 3; c++) du[3 * P + c] = u[3 * P + c] - p->ul_u[3 * P + c];
+        const double* g = grad + 9 * P;
+        double* Fn = p->ul_F + 9 * P;
+        double f[9], F[9];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) f[3 * i + j] = (i == j ? 1.0 : 0.0) + g[3 * j + i];
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double acc = 0.0;
+                for (int k = 0; k < 3; k++) acc += f[3 * i + k] * Fn[3 * k + j];
+                F[3 * i + j] = acc;
+            }
+        memcpy(Fn, F, sizeof F);
+    }
+    /* point increments: mean over the cells sharing the point of du_P + (x_v - x_P) . grad du_P */
+    double* dp = (double*)xcalloc((size_t)np * 3, sizeof(double));
+    int* cnt = (int*)xcalloc((size_t)np, sizeof(int));
+    int* mark = (int*)xcalloc((size_t)np, sizeof(int));
+    for (int v = 0; v < np; v++) mark[v] = -1;
+    for (int P = 0; P < nc; P++) {
+        const double* g = grad + 9 * P;
+        for (int k = p->cfptr[P]; k < p->cfptr[P + 1]; k++) {
+            int f = p->cf[k];
+            for (int q = p->fptr[f]; q < p->fptr[f + 1]; q++) {
+                int v = p->fpts[q];
+                if (mark[v] == P) continue;
+                mark[v] = P;
+                double r[3];
+                for (int c = 0; c < 3; c++) r[c] = p->pts[3 * v + c] - p->C[3 * P + c];
+                for (int j = 0; j < 3; j++) {
+                    double e = du[3 * P + j];
+                    for (int i = 0; i < 3; i++) e += r[i] * g[3 * i + j];
+                    dp[3 * v + j] += e;
+                }
+                cnt[v]++;
+            }
+        }
+    }
+    for (int v = 0; v < np; v++)
+        if (cnt[v] > 0)
+            for (int c = 0; c < 3; c++) p->pts[3 * v + c] += dp[3 * v + c] / cnt[v];
+    free(grad); free(du); free(dp); free(cnt); free(mark);
+    if (orc_prepare(p)) return -1;
+    memcpy(p->ul_u, u, sizeof(double) * 3 * (size_t)nc);
+    orc_gradient(p, p->ul_u, p->ul_G);
+    return 0;
+}
+
 int orc_newton(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_newton,
                int m, double eta, int pc, orc_stats* st)
 {
@@ -1534,6 +1702,9 @@ int orc_newton_ex(orc_problem* p, double* u, int n_load_steps, double rtol, doub
     int status = 0;
     if (p->dim == 2)
         for (int P = 0; P < p->nc; P++) u[3 * P + 2] = 0.0;
+    /* updated Lagrangian: every solve starts from the reference configuration, with u as the
+       initial guess of the first step; each converged step moves the mesh */
+    if (p->ul && orc_set_updated_lagrangian(p, 1)) { free(R); free(b); free(du); free(ut); free(Rt); return -4; }
     for (int step = 1; step <= n_load_steps && status == 0; step++) {
         orc_set_load_factor(p, (double)step / n_load_steps);
         orc_residual(p, u, R);
@@ -1567,6 +1738,7 @@ int orc_newton_ex(orc_problem* p, double* u, int n_load_steps, double rtol, doub
         }
         st->final_rel_res = (r0 > 0.0) ? rn / r0 : 0.0;
         if (!conv && status == 0) status = -2;
+        if (p->ul && status == 0 && ul_advance(p, u)) status = -4;
     }
     st->status = status;
     free(R); free(b); free(du); free(ut); free(Rt);

@@ -90,6 +90,14 @@ int orc_newton(orc_problem* p, double* u, int n_load_steps, double rtol, double 
 int orc_newton_ex(orc_problem* p, double* u, int n_load_steps, double rtol, double atol, int max_newton,
                   int m, int kaug, double eta, int pc, orc_stats* stats);
 /* dynamics: density > 0 enables the inertia term (BDF2, from rest); set before the multigrid */
+/* App. A updated-Lagrangian form (neo-Hookean, 3-D, static, no symmetry faces): on = 1 switches
+ * it on (and resets to the reference configuration), 0 back to total Lagrangian.  orc_newton
+ * then evaluates each load step on the configuration of the last converged one (the mesh moved
+ * with the displacement); u stays the total displacement.  Every call starts from the
+ * reference configuration and leaves the mesh in the final one.  Returns -1 (orc_error) for
+ * unsupported problems. */
+int orc_set_updated_lagrangian(orc_problem* p, int on);
+void orc_ul_state(const orc_problem* p, double* F /* [nc][3][3] total deformation gradient */);
 int orc_set_dynamics(orc_problem* p, double rho, double dt);
 /* n_steps time steps of dt from the stored state; u returns the last displacement; probe
  * (if not NULL) receives the displacement of probe_cell after each step [n_steps][3] */
