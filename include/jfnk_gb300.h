@@ -51,6 +51,8 @@ extern "C" {
 /* ---- enumerations ---------------------------------------------------------------------- */
 enum { JFNK_BC_DISP = 0, JFNK_BC_TRAC = 1, JFNK_BC_SYMM = 2, JFNK_BC_EMPTY = 3 };
 enum { JFNK_LAW_LINEAR = 0, JFNK_LAW_NEOHOOKEAN = 1, JFNK_LAW_STVK = 2 };
+/* App. A: the two nonlinear-geometry forms of the momentum balance */
+enum { JFNK_FORM_TOTAL_LAGRANGIAN = 0, JFNK_FORM_UPDATED_LAGRANGIAN = 1 };
 enum { JFNK_PC_NONE = 0, JFNK_PC_BJACOBI = 1, JFNK_PC_MG = 2 };
 enum { JFNK_MEM_HOST = 0, JFNK_MEM_DEVICE = 1 };
 /* FP64: everything in double.  MIXED: preconditioner (matrix, smoother, V-cycle) and the
@@ -167,6 +169,23 @@ int jfnk_set_patch(jfnk_ctx* ctx, int32_t first_face, int32_t n_faces, int bc_ty
  * NEOHOOKEAN (total Lagrangian, Eq. momentum_TL): p1 = mu, p2 = kappa.
  * STVK (St. Venant-Kirchhoff, total Lagrangian): p1 = E, p2 = nu.  Kbar = 4/3 mu + kappa. */
 int jfnk_set_material(jfnk_ctx* ctx, int law, double p1, double p2);
+/* App. A, Eq. momentum_TL (default) or Eq. momentum_UL.  In the updated-Lagrangian form each
+ * load step of jfnk_solve is evaluated on the configuration of the last converged one: the mesh
+ * points move with the displacement after every converged step (each point by the mean, over
+ * the cells sharing it, of the cell's increment extrapolated with the cell gradient), the
+ * geometry, least-squares vectors and face coefficients are rebuilt from the moved points, and
+ * the face force is n_u . (j f^-1 sigma) with f = I + [grad (du)]^T the relative deformation
+ * gradient of the increment du on the updated mesh, j = det f, sigma the Cauchy stress of
+ * F = f F_n.  The unknown stays the total displacement (u of jfnk_solve), on which the
+ * Rhie-Chow term acts as in the total-Lagrangian form; tractions and body forces are per unit
+ * area and volume of the updated configuration.  A multigrid preconditioner keeps the
+ * hierarchy of the reference configuration; block-Jacobi uses the current one.  Every
+ * jfnk_solve starts from the reference configuration (u is the first step's initial guess) and
+ * leaves the context in the final one (jfnk_get_geometry then gives the deformed mesh).
+ * Updated Lagrangian needs one neo-Hookean 3-D problem without symmetry faces and without
+ * inertia (else JFNK_EINVAL at set-up) and the Newton-Krylov solver (jfnk_solve_segregated
+ * gives JFNK_ESTATE).  Takes effect at the next set-up. */
+int jfnk_set_formulation(jfnk_ctx* ctx, int formulation);
 /* Body force per unit volume [n_cells][3] (host, copied), NULL = none (Eq. volume_integral). */
 int jfnk_set_body_force(jfnk_ctx* ctx, const double* fb);
 /* Load factor lambda multiplying prescribed displacements, tractions and body forces. */

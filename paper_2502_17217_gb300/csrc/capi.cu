@@ -136,6 +136,8 @@ static void free_device(jfnk_ctx* c)
     c->Zaug = c->AZaug = c->rprev = c->dcorr = nullptr;
     c->pd = nullptr;
     c->gdev = nullptr;
+    c->ul_pts0 = c->ul_F = c->ul_un = c->ul_Gn = nullptr;
+    c->ul_pc_ptr = c->ul_pc_cell = nullptr;
     c->ch_beg = nullptr;
     c->ch_len = c->ch_prob = c->pch_beg = c->pch_cnt = c->cell_prob = c->pmask = nullptr;
     c->mat = MatDev{};
@@ -484,6 +486,12 @@ int jfnk_setup(jfnk_ctx* c)
     clk.lap("problems and materials");
     std::string e = jfnk::build_topology(c->hm, c->opt.renumber != 0, c->topo, c->is_batch ? &group : nullptr);
     if (!e.empty()) return jfnk_fail(c, JFNK_EINVAL, e);
+    if (c->form == JFNK_FORM_UPDATED_LAGRANGIAN) {
+        if (c->is_batch || c->law_mode != 1 || c->hm.dim != 3 || c->topo.nsy > 0 || c->opt.density > 0)
+            return jfnk_fail(c, JFNK_EINVAL,
+                             "updated Lagrangian: one neo-Hookean 3-D problem without symmetry faces and without inertia");
+        c->law_mode = 3;  // the neo-Hookean operator of the updated-Lagrangian form
+    }
     clk.lap("topology (host)");
     const int nc = c->hm.nc;
     // problems' internal cell ranges and the internal cell -> problem map
@@ -557,6 +565,7 @@ int jfnk_setup(jfnk_ctx* c)
     c->pmask_h = c->pmask_h_store.data();
     rc = jfnk::dynamics_setup(c);
     if (rc) return rc;
+    if (c->form == JFNK_FORM_UPDATED_LAGRANGIAN && (rc = jfnk::ul_setup(c))) return rc;
     clk.lap("work vectors");
     rc = jfnk::pc_setup(c);
     if (rc) return rc;
@@ -728,6 +737,8 @@ int jfnk_solve_method(jfnk_ctx* c, double* u, int mem, int n_load_steps, jfnk_st
     jfnk_stats local;
     jfnk_stats* st = stats ? stats : &local;
     std::memset(st, 0, sizeof *st);
+    if (method == 1 && c->law_mode == 3)
+        return jfnk_fail(c, JFNK_ESTATE, "the updated-Lagrangian form is solved by the Newton-Krylov method only");
     if ((rc = load_vec(c, u, mem, c->u))) return rc;
     const double saved_load = c->load;
     int status = method == 1 ? jfnk::segregated(c, n_load_steps, st) : jfnk::newton(c, n_load_steps, st);

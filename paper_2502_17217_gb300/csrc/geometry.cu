@@ -11,6 +11,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cstring>
+
 #include "device_common.cuh"
 #include "jfnk_internal.h"
 
@@ -446,6 +448,38 @@ int setup_material_coefficients(jfnk_ctx* c)
         JF_LAUNCHED(c);
     }
     JF_CUDA(c, cudaStreamSynchronize(s));
+    return JFNK_OK;
+}
+
+int update_geometry(jfnk_ctx* c)
+{
+    DevMesh& m = c->dm;
+    cudaStream_t s = c->cur ? c->cur : c->stream;
+    const int nc = m.nc, nf = m.nf;
+    JF_CUDA(c, cudaMemsetAsync(m.err, 0, sizeof(int32_t), s));
+    k_face_geom<<<blocks(nf, 256), 256, 0, s>>>(nf, m.fptr, m.fpts, m.pts, m.Sf, m.Cf);
+    JF_LAUNCHED(c);
+    k_cell_geom<<<blocks(nc, 256), 256, 0, s>>>(nc, nf, m.ca_ptr, m.ca_face, m.fptr, m.fpts, m.pts, m.Cf, m.V, m.C, m.err);
+    JF_LAUNCHED(c);
+    k_cell_ls<<<blocks(nc, 128), 128, 0, s>>>(nc, nf, m.dim, m.sell_off, m.sell_w, m.sell_nbr, m.sell_face, m.Sf, m.Cf,
+                                              m.C, m.n_slots, m.sell_l, m.err);
+    JF_LAUNCHED(c);
+    if (m.nflux > 0) {
+        k_flux_coef<<<blocks(m.nflux, 256), 256, 0, s>>>(m.ni, m.nd, m.nflux, m.nf, m.nc, c->mat, c->cell_prob, m.own,
+                                                         m.nei, m.Sf, m.Cf, m.C, m.coef, m.jt_c);
+        JF_LAUNCHED(c);
+    }
+    k_cell_b0<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.nf, m.ni, m.nd, m.ft_ptr, m.Sf, m.bval, m.V, m.fb, m.dim, m.b0);
+    JF_LAUNCHED(c);
+    k_jt_diag<<<blocks(m.nc, 256), 256, 0, s>>>(m.nc, m.fo_ptr, m.fn_ptr, m.fn_face, m.fd_ptr, m.jt_c, m.V, 0.0,
+                                                 m.jt_diag, m.jt_dinv, m.jt_dinv_f);
+    JF_LAUNCHED(c);
+    int err = 0;
+    JF_CUDA(c, cudaMemcpyAsync(c->scal_h + 2, m.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    JF_CUDA(c, cudaStreamSynchronize(s));
+    std::memcpy(&err, c->scal_h + 2, sizeof(int));
+    if (err == 1) return jfnk_fail(c, JFNK_EINVAL, "a cell has a non-positive volume in the updated configuration");
+    if (err == 2) return jfnk_fail(c, JFNK_EINVAL, "singular least-squares tensor in the updated configuration");
     return JFNK_OK;
 }
 

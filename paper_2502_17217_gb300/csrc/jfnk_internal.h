@@ -231,7 +231,13 @@ struct jfnk_ctx {
     std::vector<ProblemDef> batch;       // problems of a batch, in the order added
     std::vector<int32_t> prob_first_cell;// caller numbering: first cell of each problem
     std::vector<double> mat_host;        // [6][nprob]: law, mu, lam, kappa, Kbar(alpha), Kbar(alpha_pc)
-    int law_mode = 0;                    // 0 all Hooke, 1 all neo-Hookean, 2 mixed
+    int law_mode = 0;                    // 0 all Hooke, 1 all neo-Hookean, 2 mixed, 3 neo-Hookean updated Lagrangian
+    // updated-Lagrangian form (App. A): formulation flag, and on the device the reference
+    // points, the last converged step's total deformation gradient [9][nc], displacement
+    // [3][nc] and its gradient on the updated mesh [9][nc], and the point -> cell lists
+    int form = 0;
+    double *ul_pts0 = nullptr, *ul_F = nullptr, *ul_un = nullptr, *ul_Gn = nullptr;
+    int32_t *ul_pc_ptr = nullptr, *ul_pc_cell = nullptr;
     MatDev mat{};                        // device copies
     std::vector<jfnk_stats> pstats;      // per-problem statistics of the last solve
     int32_t* pmask = nullptr;            // device [nprob]
@@ -372,6 +378,16 @@ int sync_load(jfnk_ctx* c);
 int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
                   double* F, double* Fn, const double* load_dev = nullptr, bool skip_done = false);
 // linalg.cu
+// least-squares gradient alone of u_int into Gout [9][nc] (no stress, no gating)
+int gradient_only(jfnk_ctx* c, const double* u_int, double* Gout);
+// geometry.cu: face and cell geometry, least-squares vectors, face coefficients, the constant
+// load part and the approximate Jacobian's diagonal recomputed from the device points (the
+// updated-Lagrangian configuration), on the call's stream; JFNK_EINVAL for an inverted cell
+int update_geometry(jfnk_ctx* c);
+// updated_lagrangian.cu
+int ul_setup(jfnk_ctx* c);    // allocations, point -> cell lists, reference state
+int ul_reset(jfnk_ctx* c);    // back to the reference configuration
+int ul_advance(jfnk_ctx* c);  // the end of a converged load step at displacement c->u
 int perm_in(jfnk_ctx* c, const double* ext_aos, double* int_soa);
 int build_chunks(jfnk_ctx* c);
 int perm_out(jfnk_ctx* c, const double* int_soa, double* ext_aos);

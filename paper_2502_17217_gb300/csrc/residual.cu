@@ -18,6 +18,7 @@
 namespace jfnk {
 
 constexpr int kGradUnroll = 6;  // hexahedra have up to 6 internal neighbours
+constexpr int kLawUpdated = 3;  // neo-Hookean in the updated-Lagrangian form
 
 template <int LAW, int BS>
 __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int nc, int dim, const int32_t* __restrict__ sell_off,
@@ -25,7 +26,8 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
                                               const double* __restrict__ sell_l, int n_slots,
                                               const double* __restrict__ u, double* __restrict__ G,
                                               double* __restrict__ T, MatDev mat, const int32_t* __restrict__ cell_prob,
-                                              const double* __restrict__ sym_n, int nsy, ProbSkip sk)
+                                              const double* __restrict__ sym_n, int nsy, ProbSkip sk,
+                                              const double* __restrict__ ul_Gn, const double* __restrict__ ul_F)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
@@ -92,8 +94,67 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
     }
 #pragma unroll
     for (int q = 0; q < 9; q++) G[(size_t)q * nc + P] = g[q];
-    const int pr = (LAW == JFNK_LAW_LINEAR) ? 0 : cell_prob[P];
-    if (LAW == 2 && mat.law[pr] == JFNK_LAW_STVK) {
+    const int pr = (LAW == JFNK_LAW_LINEAR || LAW == kLawUpdated) ? 0 : cell_prob[P];
+    if (LAW == kLawUpdated) {
+        // updated Lagrangian (App. A, Eq. momentum_UL), neo-Hookean: g is the gradient of the
+        // displacement on the updated mesh and Gn that of the last converged step's, so the
+        // increment's relative deformation gradient is f = I + (g - Gn)^T; the total one is
+        // F = f Fn; the operator is T = j f^-1 sigma(F) = adj(f) sigma(F) with the Cauchy stress
+        // sigma = mu J^-5/3 (b - tr(b)/3 I) + kappa/2 (J - 1/J) I, b = F F^T, J = det F
+        const double mu = mat.mu[0], kappa = mat.kappa[0];
+        double f[9], Fn[9], F[9];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) f[3 * i + j] = (i == j ? 1.0 : 0.0) + (g[3 * j + i] - ul_Gn[(size_t)(3 * j + i) * nc + P]);
+#pragma unroll
+        for (int q = 0; q < 9; q++) Fn[q] = ul_F[(size_t)q * nc + P];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                double a = f[3 * i] * Fn[j];
+                a = fma(f[3 * i + 1], Fn[3 + j], a);
+                a = fma(f[3 * i + 2], Fn[6 + j], a);
+                F[3 * i + j] = a;
+            }
+        const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                         F[2] * (F[3] * F[7] - F[4] * F[6]);
+        double bb[9];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                double a = F[3 * i] * F[3 * j];
+                a = fma(F[3 * i + 1], F[3 * j + 1], a);
+                a = fma(F[3 * i + 2], F[3 * j + 2], a);
+                bb[3 * i + j] = a;
+            }
+        // one reciprocal cube root r3 = J^-1/3 gives J^-5/3 = r3^5 and 1/J = r3^3 (an inverted
+        // cell, J <= 0, has no stress: NaN, which the line search rejects)
+        const double r3 = (J > 0.0) ? rcbrt(J) : __longlong_as_double(0x7ff8000000000000LL);
+        const double r32 = r3 * r3;
+        const double rJ = r32 * r3;
+        const double cdev = mu * r32 * rJ;                                  // mu J^-5/3
+        const double cvol = 0.5 * kappa * (J - rJ) - cdev * (bb[0] + bb[4] + bb[8]) * (1.0 / 3.0);
+        double sg[9];
+#pragma unroll
+        for (int q = 0; q < 9; q++) sg[q] = cdev * bb[q] + ((q % 4 == 0) ? cvol : 0.0);
+        // adj(f) = j f^-1 (cofactors)
+        const double A00 = f[4] * f[8] - f[5] * f[7], A01 = f[2] * f[7] - f[1] * f[8], A02 = f[1] * f[5] - f[2] * f[4];
+        const double A10 = f[5] * f[6] - f[3] * f[8], A11 = f[0] * f[8] - f[2] * f[6], A12 = f[2] * f[3] - f[0] * f[5];
+        const double A20 = f[3] * f[7] - f[4] * f[6], A21 = f[1] * f[6] - f[0] * f[7], A22 = f[0] * f[4] - f[1] * f[3];
+        const double A[9] = {A00, A01, A02, A10, A11, A12, A20, A21, A22};
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                double t = A[3 * i] * sg[j];
+                t = fma(A[3 * i + 1], sg[3 + j], t);
+                t = fma(A[3 * i + 2], sg[6 + j], t);
+                T[(size_t)(3 * i + j) * nc + P] = t;
+            }
+    } else if (LAW == 2 && mat.law[pr] == JFNK_LAW_STVK) {
         // St. Venant-Kirchhoff (App. B): E = (G + G^T + G G^T) / 2, S = 2 mu E + lambda tr(E) I;
         // the total-Lagrangian operator J F^-1 sigma with sigma = F S F^T / J is S F^T
         // (F = I + G^T, so (S F^T)_ij = S_ij + sum_k S_ik G_kj)
@@ -395,7 +456,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
 #define JF_GRAD_BS(LAW_, BS_)                                                                                   \
     jfnk_launch(c, k_grad<LAW_, BS_>, dim3(nblk(m.nc, BS_)), dim3(BS_), gate, m.nc, m.dim, m.sell_off, m.sell_w, \
                 m.sell_nbr, m.sell_l, m.n_slots, u_int, G, T, c->mat, (const int32_t*)c->cell_prob,   \
-                (const double*)m.sym_n, m.nsy, sk)
+                (const double*)m.sym_n, m.nsy, sk, (const double*)c->ul_Gn, (const double*)c->ul_F)
 #define JF_GRAD(LAW_)                                     \
     do {                                                  \
         if (tu.grad_bs == 64) JF_GRAD_BS(LAW_, 64);       \
@@ -404,6 +465,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     } while (0)
     if (c->law_mode == 0) JF_GRAD(JFNK_LAW_LINEAR);
     else if (c->law_mode == 1) JF_GRAD(JFNK_LAW_NEOHOOKEAN);
+    else if (c->law_mode == kLawUpdated) JF_GRAD(kLawUpdated);
     else JF_GRAD(2);
 #undef JF_GRAD
 #undef JF_GRAD_BS
@@ -427,6 +489,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     } while (0)
         if (c->law_mode == 0) JF_FLUX(JFNK_LAW_LINEAR);
         else if (c->law_mode == 1) JF_FLUX(JFNK_LAW_NEOHOOKEAN);
+        else if (c->law_mode == kLawUpdated) JF_FLUX(kLawUpdated);
         else JF_FLUX(2);
 #undef JF_FLUX
 #undef JF_FLUX_BS
@@ -440,6 +503,17 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
                 (const double*)(c->dyn_on ? c->dyn_rc : nullptr), c->dyn_mk, out, sk);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);
+    return JFNK_OK;
+}
+
+int gradient_only(jfnk_ctx* c, const double* u_int, double* Gout)
+{
+    const DevMesh& m = c->dm;
+    jfnk_launch(c, k_grad<JFNK_LAW_LINEAR, 128>, dim3(nblk(m.nc, 128)), dim3(128), (const int*)nullptr, m.nc, m.dim,
+                m.sell_off, m.sell_w, m.sell_nbr, m.sell_l, m.n_slots, u_int, Gout, (double*)nullptr, c->mat,
+                (const int32_t*)c->cell_prob, (const double*)m.sym_n, m.nsy, ProbSkip{nullptr, c->pd},
+                (const double*)nullptr, (const double*)nullptr);
+    JF_LAUNCHED(c);
     return JFNK_OK;
 }
 

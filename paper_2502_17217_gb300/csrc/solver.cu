@@ -272,7 +272,13 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
     if ((rc = write_problem_doubles(c, offsetof(ProbDev, n_cols)))) return rc;
     if ((rc = write_problem_doubles(c, offsetof(ProbDev, n_rcols)))) return rc;
     if ((rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
+    const bool ul = c->law_mode == 3;  // updated Lagrangian: from the reference configuration
+    if (ul && (rc = ul_reset(c))) return rc;
     for (int step = 1; step <= n_load_steps; step++) {
+        if (ul && step > 1) {
+            if (status[0] != JFNK_OK) break;
+            if ((rc = ul_advance(c))) return rc;  // the last step converged: move the mesh
+        }
         c->load = (double)step / n_load_steps;
         if ((rc = sync_load(c))) return rc;
         if ((rc = residual(c, c->u, c->Ru, OUT_R))) return rc;
@@ -356,6 +362,7 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
             S[p].final_abs_res = rn[p];
         }
     }
+    if (ul && status[0] == JFNK_OK && (rc = ul_advance(c))) return rc;  // the final configuration
     if ((rc = read_problems(c))) return rc;
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     // aggregate: maximum Newton count, sums of Krylov counts, worst status and residual

@@ -24,6 +24,7 @@ PC_NONE, PC_BJACOBI, PC_MG = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 PC_RIGHT, PC_LEFT = 0, 1
+FORM_TOTAL_LAGRANGIAN, FORM_UPDATED_LAGRANGIAN = 0, 1
 
 # every function declared in include/jfnk_gb300.h
 EXPORTS = [
@@ -35,7 +36,7 @@ EXPORTS = [
     "jfnk_batch_problem_cells", "jfnk_batch_stats", "jfnk_measure_fp64_rate", "jfnk_get_tuning", "jfnk_set_tuning",
     "jfnk_solve_segregated", "jfnk_solve_dynamic", "jfnk_dynamic_reset", "jfnk_synchronize",
     "jfnk_set_mesh_hex", "jfnk_hex_patch", "jfnk_dynamic_get_state", "jfnk_dynamic_set_state",
-    "jfnk_mg_hierarchy",
+    "jfnk_mg_hierarchy", "jfnk_set_formulation",
 ]
 
 
@@ -113,6 +114,7 @@ def load():
         "jfnk_get_tuning": (i, [vp, i32p, i]),
         "jfnk_set_tuning": (i, [vp, i32p, i]),
         "jfnk_mg_hierarchy": (i, [vp, i, vp, vp, vp]),
+        "jfnk_set_formulation": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -214,6 +216,10 @@ class Solver:
 
     def set_load_factor(self, lam):
         self._check(self.L.jfnk_set_load_factor(self.h, float(lam)))
+
+    def set_formulation(self, form):
+        """FORM_TOTAL_LAGRANGIAN (default) or FORM_UPDATED_LAGRANGIAN (App. A); next set-up."""
+        self._check(self.L.jfnk_set_formulation(self.h, int(form)))
 
     def set_options(self, **kw):
         for k, v in kw.items():
