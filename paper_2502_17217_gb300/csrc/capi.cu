@@ -528,6 +528,8 @@ int jfnk_setup(jfnk_ctx* c)
     for (double** p : vecs) {
         *p = (double*)jfnk_dalloc(c, sizeof(double) * v3);
         if (!*p) return jfnk_fail(c, JFNK_ENOMEM, "device allocation of work vectors failed");
+        // a batch's problems that sit a pass out keep their old values: start from zeros
+        JF_CUDA(c, cudaMemsetAsync(*p, 0, sizeof(double) * v3, c->stream));
     }
     c->G = (double*)jfnk_dalloc(c, sizeof(double) * 9 * (size_t)nc);
     c->T = (double*)jfnk_dalloc(c, sizeof(double) * (c->law_mode != 0 ? 9 * (size_t)nc : 1));

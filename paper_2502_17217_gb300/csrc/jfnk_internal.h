@@ -160,11 +160,12 @@ struct SegSlot {
 struct ProbSkip {
     const int32_t* prob;
     const ProbDev* pd;
+    int cycle = 1;  // 1: also the problems whose Krylov cycle is done (inside the Arnoldi iteration)
     __device__ __forceinline__ bool operator()(int i) const
     {
         if (!prob) return false;
         const ProbDev& P = pd[prob[i]];
-        return !P.active || P.done;
+        return !P.active || (cycle && P.done);
     }
 };
 #endif
@@ -368,15 +369,18 @@ int setup_material_coefficients(jfnk_ctx* c);
 enum ResidualOut { OUT_R = 0, OUT_JV = 1 };
 // R(u_int) into `out` (internal order); mode OUT_JV writes (R - Ru) / eps_p with each
 // problem's eps_p (and 1 / eps_p) from its ProbDev.
-int residual(jfnk_ctx* c, const double* u_int, double* out, int mode);
-// skip_done (batches, inside the Arnoldi iteration): the rows of problems whose cycle is done
-// or that left the Newton iteration are not evaluated (their output keeps its old contents)
-int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, bool skip_done = false);
+// skip (batches): SKIP_NONE evaluates every row; SKIP_CYCLE (inside the Arnoldi iteration)
+// leaves out the rows of problems whose cycle is done or that are not active; SKIP_INACTIVE
+// (restarts, cycle ends, line-search trials) those of problems that are not active.  Rows
+// left out keep their old contents.
+enum SkipMode { SKIP_NONE = 0, SKIP_CYCLE = 1, SKIP_INACTIVE = 2 };
+int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, int skip = SKIP_NONE);
+int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, int skip = SKIP_NONE);
 int sync_load(jfnk_ctx* c);
 // load_dev: device address of the load factor the kernels read (nullptr = the context's own,
 // kept equal to c->load by sync_load)
 int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
-                  double* F, double* Fn, const double* load_dev = nullptr, bool skip_done = false);
+                  double* F, double* Fn, const double* load_dev = nullptr, int skip = SKIP_NONE);
 // linalg.cu
 // least-squares gradient alone of u_int into Gout [9][nc] (no stress, no gating)
 int gradient_only(jfnk_ctx* c, const double* u_int, double* Gout);
@@ -404,6 +408,8 @@ int cycle_solution(jfnk_ctx* c, double* out, int ncols);  // out = sum_{i < min(
 // loose GMRES (linalg.cu): kept correction l (0 = newest) of `na`, slots in a ring
 int aug_store(jfnk_ctx* c, int slot, const double* r);     // slot <- dcorr / |dcorr_p|, (rprev - r) / |dcorr_p|
 int aug_load(jfnk_ctx* c, int slot, double* w);            // w <- J z of slot (gated on `all done`)
+// x += d for the active problems only
+int add_active(jfnk_ctx* c, const double* d, double* x);
 int aug_add(jfnk_ctx* c, const int* slots, int na, int ncols, const double* z, double* out);
 int line_trial(jfnk_ctx* c, const double* u, const double* x, double* w);       // w = u + s_p x (active)
 int accept_masked(jfnk_ctx* c, const int32_t* mask_dev, double* u, const double* w, double* Ru, const double* R);
@@ -416,11 +422,11 @@ int solve_dynamic(jfnk_ctx* c, int n_steps, int32_t probe_cell, double* probe, j
 bool tuning_valid(const Tuning& t);
 // z = P^-1 v (v, z internal SoA double); pc = JFNK_PC_*
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z);
-int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate, bool skip_done = false);
+int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate, int skip = SKIP_NONE);
 // eps_formed (optional): asks the multigrid's last sweep to form the following Jv's eps for a
 // single problem; set to whether it did (else the caller runs the norm pass)
 int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z,
-                 const int* gate, bool* eps_formed = nullptr, bool skip_done = false);
+                 const int* gate, bool* eps_formed = nullptr, int skip = SKIP_NONE);
 void mg_release(jfnk_ctx* c);
 int mg_hierarchy_info(jfnk_ctx* c, std::vector<int64_t>& rows, std::vector<int64_t>& nnz_a, std::vector<int64_t>& nnz_p);
 // solver.cu

@@ -560,11 +560,24 @@ __global__ void __launch_bounds__(kChunkThreads) k_aug_add(Chunks ch, const Prob
     __syncthreads();
     const int64_t b0 = ch.beg[c];
     const int len = ch.len[c];
+    // a problem out of the iteration gets no correction (its zin may be a pass it sat out)
     for (int q = threadIdx.x; q < len; q += kChunkThreads) {
-        double a = zin[b0 + q];
+        double a = P.active ? zin[b0 + q] : 0.0;
         for (int l = 0; l < na; l++) a = fma(ya[l], Z.z[l][b0 + q], a);
         out[b0 + q] = a;
     }
+}
+
+// x += d for the problems that are active (the others' d may be a pass they sat out)
+__global__ void __launch_bounds__(kChunkThreads) k_add_active(Chunks ch, const ProbDev* __restrict__ pd,
+                                                             const double* __restrict__ d, double* __restrict__ x)
+{
+    JF_PDL_ENTRY();
+    const int c = blockIdx.x;
+    if (!pd[ch.prob[c]].active) return;
+    const int64_t b0 = ch.beg[c];
+    const int len = ch.len[c];
+    for (int q = threadIdx.x; q < len; q += kChunkThreads) x[b0 + q] += d[b0 + q];
 }
 
 __global__ void k_f2d(size_t n, const float* __restrict__ in, double* __restrict__ out)
@@ -757,6 +770,13 @@ int aug_load(jfnk_ctx* c, int slot, double* w)
     const size_t v3 = 3 * (size_t)c->dm.nc;
     jfnk_launch(c, k_aug_load, dim3(gsz(v3)), dim3(256), v3, (const double*)(c->AZaug + (size_t)slot * v3),
                 (const GlobalDev*)c->gdev, w);
+    JF_LAUNCHED(c);
+    return JFNK_OK;
+}
+
+int add_active(jfnk_ctx* c, const double* d, double* x)
+{
+    jfnk_launch(c, k_add_active, dim3(c->n_chunks), dim3(kChunkThreads), chunks(c), (const ProbDev*)c->pd, d, x);
     JF_LAUNCHED(c);
     return JFNK_OK;
 }

@@ -830,6 +830,8 @@ int pc_setup(jfnk_ctx* c)
             }
         }
         if (ok) S.rprob = rp;  // else every row of every level is always evaluated
+        if (getenv("JFNK_VERBOSE"))
+            fprintf(stderr, "[jfnk] multigrid row -> problem maps: %s (%zu levels)\n", ok ? "built" : "not built", rp.size());
     }
     c->mg_coarse_n = lv.back().n;
     if (getenv("JFNK_VERBOSE")) {
@@ -882,11 +884,12 @@ static LevelOp<T> level_op(const jfnk_ctx* c, const MgDev<T>& M, int l)
 
 template <typename T, typename TV>
 static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const int* jidx, double* z, const int* gate,
-                  bool* eps_formed, bool skip_done)
+                  bool* eps_formed, int skip_mode)
 {
     const MgState& S = mg_state(c);
-    const bool skip = skip_done && c->nprob > 1 && !S.rprob.empty();
-    auto sk = [&](int l) { return ProbSkip{skip ? S.rprob[l] : nullptr, c->pd}; };
+    const bool skip = skip_mode != SKIP_NONE && c->nprob > 1 && c->skip_done && !S.rprob.empty();
+    const int cyc = skip_mode == SKIP_CYCLE ? 1 : 0;
+    auto sk = [&](int l) { return ProbSkip{skip ? S.rprob[l] : nullptr, c->pd, cyc}; };
     const bool pf = c->prof.enabled && c->prof.detail;
     const int s_sm = pf ? c->prof.slot("mg_smooth") : -1, s_re = pf ? c->prof.slot("mg_resid") : -1;
     const int s_rs = pf ? c->prof.slot("mg_restrict") : -1, s_pr = pf ? c->prof.slot("mg_prolong") : -1;
@@ -978,7 +981,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
 
 // z = P^-1 v with v = vbase + (*jidx) * ld (jidx given) or vbase; v double or float; gate may be null
 int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* jidx, int v_is_float, double* z, const int* gate,
-                 bool* eps_formed, bool skip_done)
+                 bool* eps_formed, int skip)
 {
     if (eps_formed) *eps_formed = false;
     // the multigrid's last sweep forms the Jv step of a single problem (batches keep the norm pass)
@@ -1011,10 +1014,10 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
         MgState& S = mg_state(c);
         if (!S.ready) return jfnk_fail(c, JFNK_ESTATE, "multigrid preconditioner not set up (options.pc must be JFNK_PC_MG at set-up)");
         int rc;
-        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)vbase, ld, jidx, z, gate, want_eps, skip_done)
-                                  : vcycle<float, double>(c, S.f, (const double*)vbase, ld, jidx, z, gate, want_eps, skip_done);
-        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)vbase, ld, jidx, z, gate, want_eps, skip_done)
-                             : vcycle<double, double>(c, S.d, (const double*)vbase, ld, jidx, z, gate, want_eps, skip_done);
+        if (fp32) rc = v_is_float ? vcycle<float, float>(c, S.f, (const float*)vbase, ld, jidx, z, gate, want_eps, skip)
+                                  : vcycle<float, double>(c, S.f, (const double*)vbase, ld, jidx, z, gate, want_eps, skip);
+        else rc = v_is_float ? vcycle<double, float>(c, S.d, (const float*)vbase, ld, jidx, z, gate, want_eps, skip)
+                             : vcycle<double, double>(c, S.d, (const double*)vbase, ld, jidx, z, gate, want_eps, skip);
         if (rc) return rc;
     } else {
         if (v_is_float) jfnk_launch(c, k_copy_vec<float>, dim3(nb(nc, 256)), dim3(256), gate, nc, (const float*)vbase, ld, jidx, z);
@@ -1025,9 +1028,9 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
     return JFNK_OK;
 }
 
-int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate, bool skip_done)
+int pc_apply_any(jfnk_ctx* c, int pc, const void* v, int v_is_float, double* z, const int* gate, int skip)
 {
-    return pc_apply_dev(c, pc, v, 0, nullptr, v_is_float, z, gate, nullptr, skip_done);
+    return pc_apply_dev(c, pc, v, 0, nullptr, v_is_float, z, gate, nullptr, skip);
 }
 
 int pc_apply(jfnk_ctx* c, int pc, const double* v, double* z) { return pc_apply_any(c, pc, v, 0, z, nullptr); }

@@ -437,17 +437,18 @@ int sync_load(jfnk_ctx* c)
     return JFNK_OK;
 }
 
-int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, bool skip_done)
+int residual_gated(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, int skip)
 {
-    return residual_bufs(c, u_int, out, mode, gate, c->G, c->T, c->F, c->Fn, nullptr, skip_done);
+    return residual_bufs(c, u_int, out, mode, gate, c->G, c->T, c->F, c->Fn, nullptr, skip);
 }
 
 int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const int* gate, double* G, double* T,
-                  double* F, double* Fn, const double* load_dev, bool skip_done)
+                  double* F, double* Fn, const double* load_dev, int skip)
 {
     const DevMesh& m = c->dm;
     const double* load = load_dev ? load_dev : (const double*)&c->gdev->load;
-    const ProbSkip sk{(skip_done && c->nprob > 1) ? (const int32_t*)c->cell_prob : nullptr, c->pd};
+    const ProbSkip sk{(skip != SKIP_NONE && c->nprob > 1 && c->skip_done) ? (const int32_t*)c->cell_prob : nullptr, c->pd,
+                      skip == SKIP_CYCLE ? 1 : 0};
     static const char* const kNames[3] = {"grad", "flux", "finish"};
     int sl[3];
     for (int q = 0; q < 3; q++) sl[q] = c->prof.enabled ? c->prof.slot(kNames[q]) : -1;
@@ -517,11 +518,11 @@ int gradient_only(jfnk_ctx* c, const double* u_int, double* Gout)
     return JFNK_OK;
 }
 
-int residual(jfnk_ctx* c, const double* u_int, double* out, int mode)
+int residual(jfnk_ctx* c, const double* u_int, double* out, int mode, int skip)
 {
     int rc = sync_load(c);
     if (rc) return rc;
-    return residual_gated(c, u_int, out, mode, nullptr);
+    return residual_gated(c, u_int, out, mode, nullptr, skip);
 }
 
 }  // namespace jfnk

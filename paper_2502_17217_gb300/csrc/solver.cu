@@ -54,7 +54,7 @@ static int jv_direction(jfnk_ctx* c, const double* x, double* out)
 {
     int rc = pnorm(c, x, 1, false);
     if (!rc) rc = perturb(c, c->u, x, c->w, false);
-    if (!rc) rc = residual(c, c->w, out, OUT_JV);
+    if (!rc) rc = residual(c, c->w, out, OUT_JV, SKIP_INACTIVE);  // restarts: the problems still iterating
     return rc;
 }
 
@@ -68,8 +68,8 @@ static int enqueue_iteration(jfnk_ctx* c)
     int rc;
     if (left_pc(c)) {
         if ((rc = perturb_basis(c, c->u, c->w))) return rc;
-        if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate, c->skip_done != 0))) return rc;
-        if ((rc = pc_apply_any(c, c->opt.pc, c->wk, 0, c->z, gate, c->skip_done != 0))) return rc;
+        if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate, SKIP_CYCLE))) return rc;
+        if ((rc = pc_apply_any(c, c->opt.pc, c->wk, 0, c->z, gate, SKIP_CYCLE))) return rc;
         if ((rc = arnoldi_orthogonalise(c, c->z))) return rc;
         JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
         return JFNK_OK;
@@ -77,12 +77,11 @@ static int enqueue_iteration(jfnk_ctx* c)
     bool eps_formed = false;
     // a batch's problems whose cycle is done (or that left the Newton iteration) sit out the
     // preconditioner and the residual passes as they sit out the vector kernels
-    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate, &eps_formed,
-                          c->skip_done != 0)))
+    if ((rc = pc_apply_dev(c, c->opt.pc, c->V, c->V_ld, &c->gdev->jg, c->V_is_float, c->z, gate, &eps_formed, SKIP_CYCLE)))
         return rc;
     if (!eps_formed && (rc = pnorm(c, c->z, 1, true))) return rc;
     if ((rc = perturb(c, c->u, c->z, c->w, true))) return rc;
-    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate, c->skip_done != 0))) return rc;
+    if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate, SKIP_CYCLE))) return rc;
     if ((rc = arnoldi_orthogonalise(c, c->wk))) return rc;
     JF_CUDA(c, cudaMemcpyAsync(c->gh, c->gdev, sizeof(GlobalDev), cudaMemcpyDeviceToHost, c->cur));
     return JFNK_OK;
@@ -179,7 +178,7 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
         } else {
             if ((rc = jv_direction(c, x, c->tmp))) return rc;
             if ((rc = axpby(c, n, 1.0, b, -1.0, c->tmp, left ? c->z : c->wk))) return rc;
-            if (left && (rc = pc_apply_any(c, c->opt.pc, c->z, 0, c->wk, nullptr))) return rc;
+            if (left && (rc = pc_apply_any(c, c->opt.pc, c->z, 0, c->wk, nullptr, SKIP_INACTIVE))) return rc;
             for (int p = 0; p < P; p++) jvs[p] += act[p];
         }
         // left: the Arnoldi vectors have unit norm, so eps_p = s (1 + |u_p|) for the whole cycle
@@ -220,14 +219,16 @@ int gmres_batch(jfnk_ctx* c, const double* b, double* x, std::vector<int>& its, 
             // the Krylov part of the correction: P^-1 (V y) (right) or V y (left)
             const double* dk = c->tmp;
             if (!left) {
-                if ((rc = pc_apply_any(c, c->opt.pc, c->tmp, 0, c->z, nullptr))) return rc;
+                if ((rc = pc_apply_any(c, c->opt.pc, c->tmp, 0, c->z, nullptr, SKIP_INACTIVE))) return rc;
                 dk = c->z;
             }
+            // the correction reaches the problems of this cycle only: the others sat the
+            // preconditioner out, so their part of dk is stale
             if (kaug > 0) {
                 if ((rc = aug_add(c, slots, na, mk, dk, c->dcorr))) return rc;
-                if ((rc = axpby(c, n, 1.0, x, 1.0, c->dcorr, x))) return rc;
+                if ((rc = add_active(c, c->dcorr, x))) return rc;
                 have_d = true;
-            } else if ((rc = axpby(c, n, 1.0, x, 1.0, dk, x))) {
+            } else if ((rc = add_active(c, dk, x))) {
                 return rc;
             }
         }
@@ -324,7 +325,7 @@ int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st)
                 if ((rc = write_problem_ints(c, offsetof(ProbDev, active)))) return rc;
                 if ((rc = write_problem_doubles(c, offsetof(ProbDev, step)))) return rc;
                 if ((rc = line_trial(c, c->u, c->x, c->w))) return rc;
-                if ((rc = residual(c, c->w, c->R, OUT_R))) return rc;
+                if ((rc = residual(c, c->w, c->R, OUT_R, SKIP_INACTIVE))) return rc;  // the trial problems
                 if ((rc = pnorm(c, c->R, 0, false))) return rc;
                 if ((rc = read_problems(c))) return rc;
                 bool any = false;
