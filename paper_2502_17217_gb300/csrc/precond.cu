@@ -799,9 +799,9 @@ int pc_setup(jfnk_ctx* c)
     std::vector<double> sc(std::max<size_t>(1, t.sell_nbr.size()), 0.0);
     for (size_t q = 0; q < t.sell_nbr.size(); q++)
         if (t.sell_nbr[q] >= 0 && t.sell_nbr[q] < nc) sc[q] = jc[t.sell_face[q]];
-    rc = mg_upload<float>(c, S.f, lv, inv, jc, sc, adiag0, tr);
-    if (rc) return rc;
-    rc = mg_upload<double>(c, S.d, lv, inv, jc, sc, adiag0, tr);
+    // the hierarchy in the precision the V-cycle runs in (a change of precision sets up again)
+    if (c->opt.precision == JFNK_PREC_MIXED) rc = mg_upload<float>(c, S.f, lv, inv, jc, sc, adiag0, tr);
+    else rc = mg_upload<double>(c, S.d, lv, inv, jc, sc, adiag0, tr);
     if (rc) return rc;
     // batches: the problem of every row of every level.  Aggregates never join cells of two
     // problems (the problems share no face, so no coupling), so each coarse row inherits the
@@ -851,13 +851,17 @@ int mg_hierarchy_info(jfnk_ctx* c, std::vector<int64_t>& rows, std::vector<int64
     nnz_a.clear();
     nnz_p.clear();
     if (!S.ready) return 0;
-    for (size_t l = 0; l < S.f.L.size(); l++) {
-        const auto& D = S.f.L[l];
-        rows.push_back(D.n);
-        // the finest level runs on the face coefficients: 2 couplings per internal face + diagonal
-        nnz_a.push_back(l == 0 ? 2 * (int64_t)c->dm.ni + D.n : D.nnz_a);
-        nnz_p.push_back(D.nnz_p);
-    }
+    auto collect = [&](const auto& L) {
+        for (size_t l = 0; l < L.size(); l++) {
+            const auto& D = L[l];
+            rows.push_back(D.n);
+            // the finest level runs on the face coefficients: 2 couplings per internal face + diagonal
+            nnz_a.push_back(l == 0 ? 2 * (int64_t)c->dm.ni + D.n : D.nnz_a);
+            nnz_p.push_back(D.nnz_p);
+        }
+    };
+    if (!S.f.L.empty()) collect(S.f.L);
+    else collect(S.d.L);
     return (int)rows.size();
 }
 

@@ -4,9 +4,11 @@
 // kernel; plus the aggregation multigrid hierarchy on -J~.  Runs once per mesh (off the hot
 // path); everything it builds is uploaded and used by the kernels.
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <numeric>
 #include <thread>
 
@@ -373,7 +375,9 @@ static void galerkin(const MgLevelHost& F, int nco, MgLevelHost& Cl)
     Cl.rp.assign(nco + 1, 0);
     Cl.col.clear();
     Cl.val.clear();
-    const int grain = 1024, nb = (nco + grain - 1) / grain;
+    // about 64 blocks of coarse rows: a coarse level has few rows but dense ones (each sums
+    // over hundreds of fine rows), so even a small level is split across the threads
+    const int grain = std::max(1, std::min(1024, nco / 64)), nb = (nco + grain - 1) / grain;
     std::vector<std::vector<int32_t>> bcol(nb);
     std::vector<std::vector<double>> bval(nb);
     std::vector<int32_t> len(nco, 0);
@@ -417,17 +421,30 @@ std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels,
     levels.clear();
     levels.push_back(std::move(fine));
     const int cap = max_levels > 0 ? max_levels : 25;
+    const bool verbose = getenv("JFNK_VERBOSE") != nullptr;
+    auto ms_since = [](std::chrono::steady_clock::time_point t0) {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    };
     while ((int)levels.size() < cap && levels.back().n > coarse_max) {
         MgLevelHost& F = levels.back();
         std::vector<int32_t> agg;
+        auto t0 = std::chrono::steady_clock::now();
         int nco = aggregate(F, theta, agg);
+        const double t_agg = ms_since(t0);
         if (nco > 0.9 * F.n) break;
         F.agg = agg;
+        t0 = std::chrono::steady_clock::now();
         smoothed_prolongation(F, agg, nco, smoothed, F.prp, F.pcol, F.pval);
+        const double t_p = ms_since(t0);
         MgLevelHost Cl;
+        t0 = std::chrono::steady_clock::now();
         galerkin(F, nco, Cl);
+        if (verbose)
+            fprintf(stderr, "[jfnk]   level %zu -> %d rows: aggregation %.1f ms, prolongation %.1f ms, Galerkin %.1f ms\n",
+                    levels.size() - 1, nco, t_agg, t_p, ms_since(t0));
         levels.push_back(std::move(Cl));
     }
+    const auto t_inv = std::chrono::steady_clock::now();
     // explicit inverse of the coarsest matrix via its Cholesky factor.  The inner products run
     // with four partial sums (independent chains for the host's FP pipes)
     const MgLevelHost& Lc = levels.back();
@@ -485,6 +502,7 @@ std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels,
             }
         }
     });
+    if (verbose) fprintf(stderr, "[jfnk]   coarsest %d rows: dense inverse %.1f ms\n", n, ms_since(t_inv));
     return "";
 }
 

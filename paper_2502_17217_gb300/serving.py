@@ -77,6 +77,9 @@ class Server:
         self.device = device
         self.mode = mode
         self.options = dict(options)
+        # a served request is solved once: the launch-shape autotuner's timing runs would cost
+        # more than they save (the shapes never change the results)
+        self.options.setdefault("autotune", 0)
         self.max_slots = max_slots
         if hbm_budget_bytes is None:
             import torch
