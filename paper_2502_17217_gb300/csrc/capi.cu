@@ -127,6 +127,7 @@ static void free_device(jfnk_ctx* c)
     c->seg_state = nullptr;
     c->load_on_device = -1.0;
     jfnk::mg_release(c);
+    jfnk::rowmap_release(c);
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
     c->dev_bytes = 0;
@@ -570,6 +571,8 @@ int jfnk_setup(jfnk_ctx* c)
     if (c->form == JFNK_FORM_UPDATED_LAGRANGIAN && (rc = jfnk::ul_setup(c))) return rc;
     clk.lap("work vectors");
     rc = jfnk::pc_setup(c);
+    if (rc) return rc;
+    rc = jfnk::rowmap_setup(c);
     if (rc) return rc;
     clk.lap("preconditioner");
     // every upload and zero-fill above is ordered on the context's stream

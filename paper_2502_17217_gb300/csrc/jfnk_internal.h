@@ -168,6 +168,62 @@ struct ProbSkip {
         return !P.active || (cycle && P.done);
     }
 };
+
+// Rows of one index space (cells, faces, the rows of a multigrid level) that a launch visits.
+// Identity (pre == nullptr): rows [0, n).  Compacted (batches, passes that leave problems
+// out): the runs of consecutive rows of the problems taking part, concatenated in row order;
+// virtual row v of run k (pre[k] <= v < pre[k + 1]) is row first[k] + v - pre[k].  The
+// kernels loop over virtual rows with a grid stride, so rows of the problems that sit a pass
+// out cost neither a block nor a load, and the rows a pass evaluates are the same as with
+// per-row skipping: the results are bitwise equal.
+struct RowMap {
+    const int32_t* pre = nullptr;    // [runs + 1] rows before each run taking part
+    const int32_t* first = nullptr;  // [runs] first row of each run taking part
+    const int32_t* hdr = nullptr;    // {runs taking part, rows taking part}
+    int n = 0;                       // rows of the space (identity)
+    __device__ __forceinline__ int total() const { return pre ? __ldg(hdr + 1) : n; }
+    // run of virtual row v (0 <= v < total()), by bisection
+    __device__ __forceinline__ int run_of(int v) const
+    {
+        int lo = 0, hi = __ldg(hdr);
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(pre + mid) <= v) lo = mid;
+            else hi = mid;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ int row(int v) const
+    {
+        if (!pre) return v;
+        const int k = run_of(v);
+        return __ldg(first + k) + (v - __ldg(pre + k));
+    }
+    // row(v) from a hint k, the run of a virtual row at or before v (v < total()): a few
+    // steps forward, else bisection
+    __device__ __forceinline__ int row_from(int v, int k) const
+    {
+        if (!pre) return v;
+        if (v >= __ldg(pre + k)) {
+#pragma unroll 1
+            for (int s = 0; s < 4; s++, k++)
+                if (__ldg(pre + k + 1) > v) return __ldg(first + k) + (v - __ldg(pre + k));
+        }
+        return row(v);
+    }
+};
+
+// Row of virtual row v for a converged warp whose lanes take rows at or after vw (the
+// warp's first row, warp-uniform): lane 0 bisects for vw's run, the lanes step on from it
+// (rows of one run are contiguous, so most lanes take no step).  Returns 0 for v >= tot.
+__device__ __forceinline__ int warp_row(const RowMap& rm, int v, int vw, int tot)
+{
+    if (!rm.pre) return v;
+    int k = 0;
+    if ((threadIdx.x & 31) == 0 && vw < tot) k = rm.run_of(vw);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    return v < tot ? rm.row_from(v, k) : 0;
+}
 #endif
 
 // Scalars shared by all problems of a context.
@@ -287,6 +343,9 @@ struct jfnk_ctx {
     double* scal_h = nullptr;            // pinned [16]
     // multigrid (precond.cu owns the hierarchy object)
     void* mgs = nullptr;
+    // compacted launches of a batch (rowmap.cu owns the object): runs of rows per problem of
+    // every index space, and the runs of the problems taking part in the current pass
+    void* rmaps = nullptr;
     int mg_coarse_n = 0;
     bool mg_ready = false;
     int64_t launches = 0;
@@ -429,6 +488,27 @@ int pc_apply_dev(jfnk_ctx* c, int pc, const void* vbase, size_t ld, const int* j
                  const int* gate, bool* eps_formed = nullptr, int skip = SKIP_NONE);
 void mg_release(jfnk_ctx* c);
 int mg_hierarchy_info(jfnk_ctx* c, std::vector<int64_t>& rows, std::vector<int64_t>& nnz_a, std::vector<int64_t>& nnz_p);
+// rowmap.cu: index spaces of compacted launches (batches with skipping): cells (also the
+// finest multigrid level), faces (the residual's flux faces), and multigrid level l >= 1
+enum MapSpace { SPACE_CELLS = 0, SPACE_FACES = 1 };
+inline int space_of_level(int l) { return l == 0 ? SPACE_CELLS : 1 + l; }
+// runs of rows per problem of every space (after the multigrid set-up; nothing for one problem)
+int rowmap_setup(jfnk_ctx* c);
+void rowmap_release(jfnk_ctx* c);
+// compacts the runs of the problems taking part in passes of skip mode `skip` (SKIP_CYCLE or
+// SKIP_INACTIVE) on the call's stream; a no-op when the context has no compacted spaces
+int rowmap_build(jfnk_ctx* c, int skip);
+#ifdef __CUDACC__
+// the rows a pass of mode `skip` visits in `space` of n rows (identity unless compacted)
+RowMap rowmap(const jfnk_ctx* c, int space, int skip, int n);
+// blocks of a grid-stride launch of kernel fn (bs threads, `per_block` units of work each)
+// over units_all units: every unit once for identity maps, else at most `waves` times the
+// blocks the SMs hold at once (the FP64-bound residual passes measured fastest with 4 waves,
+// the latency-bound V-cycle and cell sums with 1)
+int rowmap_blocks(jfnk_ctx* c, const void* fn, int bs, long units_all, long per_block, const RowMap& rm, int waves = 1);
+#endif
+// precond.cu: the problem of every row of multigrid levels >= 1 (host, batches)
+const std::vector<std::vector<int32_t>>* mg_level_problems(jfnk_ctx* c);
 // solver.cu
 int gmres(jfnk_ctx* c, const double* b, double* x, int* its, double* relres, int* status);
 int newton(jfnk_ctx* c, int n_load_steps, jfnk_stats* st);

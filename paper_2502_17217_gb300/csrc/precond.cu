@@ -172,24 +172,67 @@ struct LevelOp {
     }
 };
 
+// Vectors of the coarse levels, and the finest level's residual, are interleaved: row i holds
+// (x, y, z, 0) in p[4i .. 4i+3], so that a gathered row is one 16-byte load (FP32; two in FP64)
+// instead of three loads from three arrays, each touching its own 32-byte sector.  The finest
+// level's b and x stay component-major [3][n] like the Krylov vectors they come from and go to.
+__device__ __forceinline__ void ld3(const float* __restrict__ p, int i, float& a, float& b, float& c)
+{
+    const float4 v = reinterpret_cast<const float4*>(p)[i];
+    a = v.x; b = v.y; c = v.z;
+}
+__device__ __forceinline__ void ld3(const double* __restrict__ p, int i, double& a, double& b, double& c)
+{
+    const double2 v = reinterpret_cast<const double2*>(p)[2 * i];
+    a = v.x; b = v.y; c = p[4 * (size_t)i + 2];
+}
+__device__ __forceinline__ void st3(float* __restrict__ p, int i, float a, float b, float c)
+{
+    reinterpret_cast<float4*>(p)[i] = make_float4(a, b, c, 0.0f);
+}
+__device__ __forceinline__ void st3(double* __restrict__ p, int i, double a, double b, double c)
+{
+    reinterpret_cast<double2*>(p)[2 * i] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[2 * i + 1] = make_double2(c, 0.0);
+}
+// component-major [3][n] access with the same signature
+template <typename T>
+__device__ __forceinline__ void ld3_soa(const T* __restrict__ p, size_t n, int i, T& a, T& b, T& c)
+{
+    a = p[i]; b = p[n + i]; c = p[2 * n + i];
+}
+template <typename T>
+__device__ __forceinline__ void st3_soa(T* __restrict__ p, size_t n, int i, T a, T b, T c)
+{
+    p[i] = a; p[n + i] = b; p[2 * n + i] = c;
+}
+
 // level 0 entry: b = -v (so the cycle returns z = -A^-1 v = J~^-1 v), x = omega D^-1 b.
 // v = base + (*jidx) * ld when jidx is given (the Krylov vector of the current iteration).
+// Every thread-per-row kernel below walks the rows of its row map with a grid stride (one
+// round on the identity map's full grid; a persistent grid over the compacted rows of a
+// batch's problems taking part), warp by warp so that each warp finds its rows together.
+#define JF_ROWS(rm, i)                                                                              \
+    for (int w_ = blockIdx.x * blockDim.x + (int)(threadIdx.x & ~31u), tot_ = (rm).total(); w_ < tot_; \
+         w_ += gridDim.x * blockDim.x)                                                              \
+        if (const int v_ = w_ + (int)(threadIdx.x & 31u), i = warp_row((rm), v_, w_, tot_); v_ < tot_)
+
 template <typename TV, typename T>
-__global__ void k_mg_pre0(const int* gate, ProbSkip sk, int nc, const TV* __restrict__ base, size_t ld,
+__global__ void k_mg_pre0(const int* gate, RowMap rm, int nc, const TV* __restrict__ base, size_t ld,
                           const int* __restrict__ jidx, const T* __restrict__ dinv, T omega, T* __restrict__ b,
                           T* __restrict__ x)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= nc || sk(P)) return;
     const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
-    const T d = omega * dinv[P];
+    JF_ROWS(rm, P) {
+        const T d = omega * dinv[P];
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const T bb = -(T)v[(size_t)k * nc + P];
-        b[(size_t)k * nc + P] = bb;
-        x[(size_t)k * nc + P] = d * bb;
+        for (int k = 0; k < 3; k++) {
+            const T bb = -(T)v[(size_t)k * nc + P];
+            b[(size_t)k * nc + P] = bb;
+            x[(size_t)k * nc + P] = d * bb;
+        }
     }
 }
 
@@ -201,68 +244,70 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // is needed, also at the neighbours), x1 = x0 + omega D^-1 (b - A x0).  Same arithmetic, in the
 // same order, as k_mg_pre0 followed by k_mg_jacobi.
 template <typename TV, typename T>
-__global__ void k_mg_pre0_jacobi(const int* gate, ProbSkip sk, LevelOp<T> op, const TV* __restrict__ base, size_t ld,
+__global__ void k_mg_pre0_jacobi(const int* gate, RowMap rm, LevelOp<T> op, const TV* __restrict__ base, size_t ld,
                                  const int* __restrict__ jidx, T omega, T* __restrict__ b, T* __restrict__ xo)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
     const int nc = op.n;
-    if (P >= nc || sk(P)) return;
     const TV* v = jidx ? base + (size_t)(*jidx) * ld : base;
-    const T dP = omega * op.dinv[P];
-    T bb[3], x0[3], ax[3];
+    JF_ROWS(rm, P) {
+        const T dP = omega * op.dinv[P];
+        T bb[3], x0[3], ax[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        bb[k] = -(T)v[(size_t)k * nc + P];
-        x0[k] = mul_rn(dP, bb[k]);
-    }
-    const T a = op.adiag[P];
+        for (int k = 0; k < 3; k++) {
+            bb[k] = -(T)v[(size_t)k * nc + P];
+            x0[k] = mul_rn(dP, bb[k]);
+        }
+        const T a = op.adiag[P];
 #pragma unroll
-    for (int k = 0; k < 3; k++) ax[k] = a * x0[k];
-    for_sell_slots<T>(P, nc, op.p0, op.p1, op.p2, op.vals, [&](int N, T cf) {
-        const T dN = omega * op.dinv[N];
+        for (int k = 0; k < 3; k++) ax[k] = a * x0[k];
+        for_sell_slots<T>(P, nc, op.p0, op.p1, op.p2, op.vals, [&](int N, T cf) {
+            const T dN = omega * op.dinv[N];
 #pragma unroll
-        for (int k = 0; k < 3; k++) ax[k] -= cf * mul_rn(dN, -(T)v[(size_t)k * nc + N]);
-    });
+            for (int k = 0; k < 3; k++) ax[k] -= cf * mul_rn(dN, -(T)v[(size_t)k * nc + N]);
+        });
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        b[(size_t)k * nc + P] = bb[k];
-        xo[(size_t)k * nc + P] = x0[k] + dP * (bb[k] - ax[k]);
+        for (int k = 0; k < 3; k++) {
+            b[(size_t)k * nc + P] = bb[k];
+            xo[(size_t)k * nc + P] = x0[k] + dP * (bb[k] - ax[k]);
+        }
     }
 }
 
 template <typename T>
-__global__ void k_mg_pre(const int* gate, ProbSkip sk, int n, const T* __restrict__ dinv, T omega,
+__global__ void k_mg_pre(const int* gate, RowMap rm, int n, const T* __restrict__ dinv, T omega,
                          const T* __restrict__ b, T* __restrict__ x)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || sk(i)) return;
-    const T d = omega * dinv[i];
-#pragma unroll
-    for (int k = 0; k < 3; k++) x[(size_t)k * n + i] = d * b[(size_t)k * n + i];
+    JF_ROWS(rm, i) {
+        const T d = omega * dinv[i];
+        T b0, b1, b2;
+        ld3(b, i, b0, b1, b2);
+        st3(x, i, d * b0, d * b1, d * b2);
+    }
+    (void)n;
 }
 
 // Jacobi sweep x_out = x + omega D^-1 (b - A x); zd != null writes the result as double
 template <typename T>
-__global__ void k_mg_jacobi(const int* gate, ProbSkip sk, LevelOp<T> op, T omega, const T* __restrict__ b,
+__global__ void k_mg_jacobi(const int* gate, RowMap rm, LevelOp<T> op, T omega, const T* __restrict__ b,
                             const T* __restrict__ x, T* __restrict__ xo, double* __restrict__ zd)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = op.n;
-    if (i >= n || sk(i)) return;
-    T ax[3];
-    op.row(i, x, ax);
-    const T d = omega * op.dinv[i];
+    JF_ROWS(rm, i) {
+        T ax[3];
+        op.row(i, x, ax);
+        const T d = omega * op.dinv[i];
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const T xn = x[(size_t)k * n + i] + d * (b[(size_t)k * n + i] - ax[k]);
-        if (zd) zd[(size_t)k * n + i] = to_f64(xn);
-        else xo[(size_t)k * n + i] = xn;
+        for (int k = 0; k < 3; k++) {
+            const T xn = x[(size_t)k * n + i] + d * (b[(size_t)k * n + i] - ax[k]);
+            if (zd) zd[(size_t)k * n + i] = to_f64(xn);
+            else xo[(size_t)k * n + i] = xn;
+        }
     }
 }
 
@@ -324,36 +369,59 @@ __global__ void k_mg_jacobi_eps(const int* gate, LevelOp<T> op, T omega, const T
 
 // r = b - A x
 template <typename T>
-__global__ void k_mg_resid(const int* gate, ProbSkip sk, LevelOp<T> op, const T* __restrict__ b,
+__global__ void k_mg_resid(const int* gate, RowMap rm, LevelOp<T> op, const T* __restrict__ b,
                            const T* __restrict__ x, T* __restrict__ r)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = op.n;
-    if (i >= n || sk(i)) return;
-    T ax[3];
-    op.row(i, x, ax);
-#pragma unroll
-    for (int k = 0; k < 3; k++) r[(size_t)k * n + i] = b[(size_t)k * n + i] - ax[k];
+    JF_ROWS(rm, i) {
+        T ax[3];
+        op.row(i, x, ax);
+        st3(r, i, b[i] - ax[0], b[n + i] - ax[1], b[2 * (size_t)n + i] - ax[2]);
+    }
 }
 
-// y = M x (add = 0) or y += M x (add = 1) for a CSR matrix with nrow rows and nx columns
-template <typename T>
-__global__ void k_mg_spmv(const int* gate, ProbSkip sk, int nrow, int nx, const int32_t* __restrict__ rp,
-                          const int32_t* __restrict__ col, const T* __restrict__ val, const T* __restrict__ x,
-                          T* __restrict__ y, int add)
+// y += P x (prolongation) for a CSR matrix with nrow rows; x interleaved (a coarse level), y
+// interleaved (AOSY) or component-major (the finest level)
+template <typename T, bool AOSY>
+__global__ void k_mg_prolong(const int* gate, RowMap rm, int nrow, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ col, const T* __restrict__ val, const T* __restrict__ x,
+                             T* __restrict__ y)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nrow || sk(i)) return;
-    T s[3];
-    csr_row<T>(i, nrow, rp, col, val, x, nx, s);
+    JF_ROWS(rm, i) {
+        T s0 = 0, s1 = 0, s2 = 0;
+        const int a = rp[i], b = rp[i + 1];
+        int js[kCsrUnroll];
+        T as[kCsrUnroll];
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        if (add) y[(size_t)k * nrow + i] += s[k];
-        else y[(size_t)k * nrow + i] = s[k];
+        for (int q = 0; q < kCsrUnroll; q++) {
+            js[q] = a + q < b ? col[a + q] : 0;
+            as[q] = a + q < b ? val[a + q] : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < kCsrUnroll; q++)
+            if (a + q < b) {
+                T x0, x1, x2;
+                ld3(x, js[q], x0, x1, x2);
+                s0 += as[q] * x0; s1 += as[q] * x1; s2 += as[q] * x2;
+            }
+        for (int q = a + kCsrUnroll; q < b; q++) {
+            T x0, x1, x2;
+            ld3(x, col[q], x0, x1, x2);
+            const T v = val[q];
+            s0 += v * x0; s1 += v * x1; s2 += v * x2;
+        }
+        T y0, y1, y2;
+        if (AOSY) {
+            ld3(y, i, y0, y1, y2);
+            st3(y, i, y0 + s0, y1 + s1, y2 + s2);
+        } else {
+            ld3_soa(y, (size_t)nrow, i, y0, y1, y2);
+            st3_soa(y, (size_t)nrow, i, y0 + s0, y1 + s1, y2 + s2);
+        }
     }
 }
 
@@ -373,7 +441,8 @@ __device__ __forceinline__ void group_sum(T& s0, T& s1, T& s2)
     }
 }
 
-// sum_q a_q xin(j_q) over the group's share of row entries [qa, qb); xin(j, k) gives component k
+// sum_q a_q xin(j_q) over the group's share of row entries [qa, qb); xin(j, x0, x1, x2)
+// gives the three components of row j
 template <int G, typename T, typename X>
 __device__ __forceinline__ void group_row(int qa, int qb, int sub, const int32_t* __restrict__ col,
                                           const T* __restrict__ val, X&& xin, T& s0, T& s1, T& s2)
@@ -383,98 +452,114 @@ __device__ __forceinline__ void group_row(int qa, int qb, int sub, const int32_t
         const bool h1 = q1 < qb;
         const int j0 = col[q], j1 = h1 ? col[q1] : j0;
         const T a0 = val[q], a1 = h1 ? val[q1] : (T)0;
-        const T x00 = xin(j0, 0), x01 = xin(j0, 1), x02 = xin(j0, 2);
+        T x00, x01, x02;
+        xin(j0, x00, x01, x02);
         T x10 = 0, x11 = 0, x12 = 0;
-        if (h1) { x10 = xin(j1, 0); x11 = xin(j1, 1); x12 = xin(j1, 2); }
+        if (h1) xin(j1, x10, x11, x12);
         s0 += a0 * x00; s1 += a0 * x01; s2 += a0 * x02;
         if (h1) { s0 += a1 * x10; s1 += a1 * x11; s2 += a1 * x12; }
     }
 }
 
-// y = M x (add = 0) or y += M x (add = 1)
+// Kernels with G lanes per row walk the row map in rounds of blockDim / G rows (a grid stride
+// whose bound is uniform over the block, so every lane takes part in every shuffle).
+#define JF_GROUP_ROUNDS(rm, G, v, vw, sub, live, tot)                                             \
+    const int tot = (rm).total();                                                                \
+    for (int base_ = blockIdx.x * blockDim.x; base_ < tot * (G); base_ += gridDim.x * blockDim.x) \
+        if (const int v = (base_ + (int)threadIdx.x) / (G), vw = (base_ + (int)(threadIdx.x & ~31u)) / (G), \
+            sub = threadIdx.x & ((G)-1); true)                                                    \
+            if (const bool live = v < tot; true)
+
+// y = R x (restriction, R = P^T) with x and y interleaved
 template <typename T, int G>
-__global__ void k_mg_spmv_grp(const int* gate, ProbSkip sk, int nrow, int nx, const int32_t* __restrict__ rp,
+__global__ void k_mg_spmv_grp(const int* gate, RowMap rm, int nrow, int nx, const int32_t* __restrict__ rp,
                               const int32_t* __restrict__ col, const T* __restrict__ val, const T* __restrict__ x,
-                              T* __restrict__ y, int add)
+                              T* __restrict__ y)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / G, sub = t & (G - 1);
-    T s0 = 0, s1 = 0, s2 = 0;
-    // lanes past the last row and lanes of skipped rows still take part in the shuffles
-    const bool live = i < nrow && !sk(i);
-    if (live)
-        group_row<G, T>(rp[i], rp[i + 1], sub, col, val, [&](int j, int k) { return x[(size_t)k * nx + j]; }, s0, s1, s2);
-    group_sum<G>(s0, s1, s2);
-    if (live && sub == 0) {
-        if (add) { y[i] += s0; y[nrow + i] += s1; y[2 * (size_t)nrow + i] += s2; }
-        else { y[i] = s0; y[nrow + i] = s1; y[2 * (size_t)nrow + i] = s2; }
+    JF_GROUP_ROUNDS(rm, G, v, vw, sub, live, tot) {
+        T s0 = 0, s1 = 0, s2 = 0;
+        // lanes past the last row still take part in the shuffles
+        const int i = warp_row(rm, v, vw, tot);
+        if (live)
+            group_row<G, T>(rp[i], rp[i + 1], sub, col, val, [&](int j, T& a, T& b, T& c) { ld3(x, j, a, b, c); }, s0, s1,
+                            s2);
+        group_sum<G>(s0, s1, s2);
+        if (live && sub == 0) st3(y, i, s0, s1, s2);
     }
+    (void)nrow; (void)nx;
 }
 
-// Jacobi sweep or residual on a coarse (CSR) level:
+// Jacobi sweep or residual on a coarse (CSR) level, vectors interleaved:
 // mode 0: xo = x + omega D^-1 (b - A x);  mode 1: xo = b - A x;
 // mode 2: the first sweep from x = omega D^-1 b, which is formed where it is needed (x unused)
 template <typename T, int G>
-__global__ void k_mg_csr_grp(const int* gate, ProbSkip sk, int n, const int32_t* __restrict__ rp,
+__global__ void k_mg_csr_grp(const int* gate, RowMap rm, int n, const int32_t* __restrict__ rp,
                              const int32_t* __restrict__ col, const T* __restrict__ val, const T* __restrict__ dinv,
                              T omega, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo, int mode)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = t / G, sub = t & (G - 1);
+    JF_GROUP_ROUNDS(rm, G, v, vw, sub, live, tot) {
     T s0 = 0, s1 = 0, s2 = 0;
-    // the row's own values, loaded ahead of the sums; lanes of skipped rows and past the last
-    // row still take part in the shuffles
+    // the row's own values, loaded ahead of the sums; lanes past the last row still take part
+    // in the shuffles
     T bi0 = 0, bi1 = 0, bi2 = 0, xi0 = 0, xi1 = 0, xi2 = 0, di = 0;
-    const bool live = i < n && !sk(i);
+    const int i = warp_row(rm, v, vw, tot);
     if (live) {
         if (sub == 0) {
-            bi0 = b[i]; bi1 = b[n + i]; bi2 = b[2 * (size_t)n + i];
+            ld3(b, i, bi0, bi1, bi2);
             di = dinv[i];
-            if (mode == 0) { xi0 = x[i]; xi1 = x[n + i]; xi2 = x[2 * (size_t)n + i]; }
+            if (mode == 0) ld3(x, i, xi0, xi1, xi2);
         }
         const int qa = rp[i], qb = rp[i + 1];
         if (mode == 2)
             group_row<G, T>(qa, qb, sub, col, val,
-                            [&](int j, int k) { return mul_rn(omega * dinv[j], b[(size_t)k * n + j]); }, s0, s1, s2);
+                            [&](int j, T& a0, T& a1, T& a2) {
+                                const T d = omega * dinv[j];
+                                ld3(b, j, a0, a1, a2);
+                                a0 = mul_rn(d, a0); a1 = mul_rn(d, a1); a2 = mul_rn(d, a2);
+                            },
+                            s0, s1, s2);
         else
-            group_row<G, T>(qa, qb, sub, col, val, [&](int j, int k) { return x[(size_t)k * n + j]; }, s0, s1, s2);
+            group_row<G, T>(qa, qb, sub, col, val, [&](int j, T& a0, T& a1, T& a2) { ld3(x, j, a0, a1, a2); }, s0, s1, s2);
     }
     group_sum<G>(s0, s1, s2);
     if (live && sub == 0) {
         const T r0 = bi0 - s0, r1 = bi1 - s1, r2 = bi2 - s2;
-        if (mode == 1) { xo[i] = r0; xo[n + i] = r1; xo[2 * (size_t)n + i] = r2; }
+        if (mode == 1) st3(xo, i, r0, r1, r2);
         else if (mode == 2) {
             const T d = omega * di;
-            xo[i] = mul_rn(d, bi0) + d * r0; xo[n + i] = mul_rn(d, bi1) + d * r1;
-            xo[2 * (size_t)n + i] = mul_rn(d, bi2) + d * r2;
+            st3(xo, i, mul_rn(d, bi0) + d * r0, mul_rn(d, bi1) + d * r1, mul_rn(d, bi2) + d * r2);
         } else {
             const T d = omega * di;
-            xo[i] = xi0 + d * r0; xo[n + i] = xi1 + d * r1; xo[2 * (size_t)n + i] = xi2 + d * r2;
+            st3(xo, i, xi0 + d * r0, xi1 + d * r1, xi2 + d * r2);
         }
     }
+    }
+    (void)n;
 }
 
-// y = M x (add = 0) or y += M x (add = 1) for rows longer than a warp's two-entry step: one
-// block of kCoarseWarps warps per row, the warps' sums combined in shared memory
+// y = R x (restriction) for rows longer than a warp's two-entry step: one block of
+// kCoarseWarps warps per row, the warps' sums combined in shared memory
 template <typename T>
-__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_spmv_blk(const int* gate, ProbSkip sk, int nrow, int nx,
+__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_spmv_blk(const int* gate, RowMap rm, int nrow, int nx,
                                                                    const int32_t* __restrict__ rp,
                                                                    const int32_t* __restrict__ col,
                                                                    const T* __restrict__ val, const T* __restrict__ x,
-                                                                   T* __restrict__ y, int add)
+                                                                   T* __restrict__ y)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int i = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (sk(i)) return;  // the whole block takes one row
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ T part[3][kCoarseWarps];
+    const int tot = rm.total();
+    for (int v = blockIdx.x; v < tot; v += gridDim.x) {  // the whole block takes one row
+    const int i = rm.row(v);
     T s0 = 0, s1 = 0, s2 = 0;
     group_row<32 * kCoarseWarps, T>(rp[i], rp[i + 1], threadIdx.x, col, val,
-                                    [&](int j, int k) { return x[(size_t)k * nx + j]; }, s0, s1, s2);
+                                    [&](int j, T& a, T& b, T& c) { ld3(x, j, a, b, c); }, s0, s1, s2);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_down_sync(0xffffffffu, s0, o);
@@ -483,14 +568,16 @@ __global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_spmv_blk(const int* ga
     }
     if (lane == 0) { part[0][wid] = s0; part[1][wid] = s1; part[2][wid] = s2; }
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (threadIdx.x < 4) {  // (x, y, z, 0) of the interleaved row
         T t = 0;
+        if (threadIdx.x < 3)
 #pragma unroll
-        for (int w = 0; w < kCoarseWarps; w++) t += part[threadIdx.x][w];
-        T* yk = y + (size_t)threadIdx.x * nrow + i;
-        if (add) *yk += t;
-        else *yk = t;
+            for (int w = 0; w < kCoarseWarps; w++) t += part[threadIdx.x][w];
+        y[4 * (size_t)i + threadIdx.x] = t;
     }
+    __syncthreads();  // part[] is refilled in the next round
+    }
+    (void)nrow; (void)nx;
 }
 
 // lanes per row for CSR rows of mean length `mean`: the power of two near half of it, 4..32,
@@ -505,48 +592,57 @@ inline int group_lanes(double mean)
 }
 
 template <typename T, typename... A>
-static void launch_csr_grp(jfnk_ctx* c, int g, long rows, A... args)
+static void launch_csr_grp(jfnk_ctx* c, int g, long rows, const int* gate, const RowMap& rm, A... args)
 {
     g = std::min(g, 32);
-    const dim3 grid((unsigned)std::max<long>(1, (rows * g + 255) / 256)), block(256);
+    auto go = [&](auto k) {
+        const dim3 grid(rowmap_blocks(c, (const void*)k, 256, rows * g, 256, rm)), block(256);
+        jfnk_launch(c, k, grid, block, gate, rm, args...);
+    };
     switch (g) {
-        case 4: jfnk_launch(c, k_mg_csr_grp<T, 4>, grid, block, args...); break;
-        case 8: jfnk_launch(c, k_mg_csr_grp<T, 8>, grid, block, args...); break;
-        case 16: jfnk_launch(c, k_mg_csr_grp<T, 16>, grid, block, args...); break;
-        default: jfnk_launch(c, k_mg_csr_grp<T, 32>, grid, block, args...); break;
+        case 4: go(k_mg_csr_grp<T, 4>); break;
+        case 8: go(k_mg_csr_grp<T, 8>); break;
+        case 16: go(k_mg_csr_grp<T, 16>); break;
+        default: go(k_mg_csr_grp<T, 32>); break;
     }
 }
 
 template <typename T, typename... A>
-static void launch_spmv_grp(jfnk_ctx* c, int g, long rows, A... args)
+static void launch_spmv_grp(jfnk_ctx* c, int g, long rows, const int* gate, const RowMap& rm, A... args)
 {
     if (g > 32) {
-        jfnk_launch(c, k_mg_spmv_blk<T>, dim3((unsigned)std::max<long>(1, rows)), dim3(32 * kCoarseWarps), args...);
+        const dim3 grid(rowmap_blocks(c, (const void*)k_mg_spmv_blk<T>, 32 * kCoarseWarps, rows, 1, rm));
+        jfnk_launch(c, k_mg_spmv_blk<T>, grid, dim3(32 * kCoarseWarps), gate, rm, args...);
         return;
     }
-    const dim3 grid((unsigned)std::max<long>(1, (rows * g + 255) / 256)), block(256);
+    auto go = [&](auto k) {
+        const dim3 grid(rowmap_blocks(c, (const void*)k, 256, rows * g, 256, rm)), block(256);
+        jfnk_launch(c, k, grid, block, gate, rm, args...);
+    };
     switch (g) {
-        case 4: jfnk_launch(c, k_mg_spmv_grp<T, 4>, grid, block, args...); break;
-        case 8: jfnk_launch(c, k_mg_spmv_grp<T, 8>, grid, block, args...); break;
-        case 16: jfnk_launch(c, k_mg_spmv_grp<T, 16>, grid, block, args...); break;
-        default: jfnk_launch(c, k_mg_spmv_grp<T, 32>, grid, block, args...); break;
+        case 4: go(k_mg_spmv_grp<T, 4>); break;
+        case 8: go(k_mg_spmv_grp<T, 8>); break;
+        case 16: go(k_mg_spmv_grp<T, 16>); break;
+        default: go(k_mg_spmv_grp<T, 32>); break;
     }
 }
 
 // coarsest level: x = A_c^-1 b with the dense (symmetric) inverse, one block of kCoarseWarps
 // warps per row, each warp a strided quarter of the row with two entries per lane and step
-// loaded before use, the warps' sums combined in shared memory
-
-template <typename T>
-__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_coarse(const int* gate, ProbSkip sk, int n,
+// loaded before use, the warps' sums combined in shared memory; b and x interleaved (AOS), or
+// component-major when the coarsest level is the finest (one-level hierarchy)
+template <typename T, bool AOS>
+__global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_coarse(const int* gate, RowMap rm, ProbSkip sk, int n,
                                                                  const T* __restrict__ Ainv, const T* __restrict__ b,
                                                                  T* __restrict__ x)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int r = blockIdx.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (sk(r)) return;  // the whole block takes one row
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __shared__ T part[3][kCoarseWarps];
+    const int tot = rm.total();
+    for (int v = blockIdx.x; v < tot; v += gridDim.x) {  // the whole block takes one row
+    const int r = rm.row(v);
     T s0 = 0, s1 = 0, s2 = 0;
     const T* row = Ainv + (size_t)r * n;
     constexpr int step = 32 * kCoarseWarps;
@@ -557,9 +653,15 @@ __global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_coarse(const int* gate
         // rows of skipped problems hold values of an earlier cycle (or none yet): they enter
         // as zeros, so that nothing of another problem reaches this row's sum
         T b00 = 0, b01 = 0, b02 = 0;
-        if (!sk(k)) { b00 = b[k]; b01 = b[n + k]; b02 = b[2 * (size_t)n + k]; }
+        if (!sk(k)) {
+            if (AOS) ld3(b, k, b00, b01, b02);
+            else ld3_soa(b, (size_t)n, k, b00, b01, b02);
+        }
         T b10 = 0, b11 = 0, b12 = 0;
-        if (h1 && !sk(k1)) { b10 = b[k1]; b11 = b[n + k1]; b12 = b[2 * (size_t)n + k1]; }
+        if (h1 && !sk(k1)) {
+            if (AOS) ld3(b, k1, b10, b11, b12);
+            else ld3_soa(b, (size_t)n, k1, b10, b11, b12);
+        }
         s0 += a0 * b00; s1 += a0 * b01; s2 += a0 * b02;
         if (h1) { s0 += a1 * b10; s1 += a1 * b11; s2 += a1 * b12; }
     }
@@ -571,11 +673,15 @@ __global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_coarse(const int* gate
     }
     if (lane == 0) { part[0][wid] = s0; part[1][wid] = s1; part[2][wid] = s2; }
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (threadIdx.x < (AOS ? 4 : 3)) {
         T t = 0;
+        if (threadIdx.x < 3)
 #pragma unroll
-        for (int w = 0; w < kCoarseWarps; w++) t += part[threadIdx.x][w];
-        x[(size_t)threadIdx.x * n + r] = t;
+            for (int w = 0; w < kCoarseWarps; w++) t += part[threadIdx.x][w];
+        if (AOS) x[4 * (size_t)r + threadIdx.x] = t;
+        else x[(size_t)threadIdx.x * n + r] = t;
+    }
+    __syncthreads();  // part[] is refilled in the next round
     }
 }
 
@@ -607,6 +713,7 @@ struct MgState {
     // batches: the problem of each row of every level (level 0: the context's cell map), for
     // skipping the problems that sit out an Arnoldi iteration; empty for single problems
     std::vector<const int32_t*> rprob;
+    std::vector<std::vector<int32_t>> rprob_host;  // levels >= 1 on the host (compacted launches)
 };
 
 template <typename T>
@@ -686,13 +793,16 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
         for (int i = 0; i < H.n; i++) di[i] = 1.0 / ad[i];
         D.adiag = upload_as<T>(c, ad);
         D.dinv = upload_as<T>(c, di);
-        D.b = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
-        D.x = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
-        D.x2 = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
-        D.r = (T*)jfnk_dalloc(c, sizeof(T) * 3 * (size_t)H.n);
+        // the finest level's b, x, x2 component-major [3][n]; its residual and every coarse
+        // level's vectors interleaved [n][4]
+        const size_t nv = (l == 0 ? 3 : 4) * (size_t)H.n, nr = 4 * (size_t)H.n;
+        D.b = (T*)jfnk_dalloc(c, sizeof(T) * nv);
+        D.x = (T*)jfnk_dalloc(c, sizeof(T) * nv);
+        D.x2 = (T*)jfnk_dalloc(c, sizeof(T) * nv);
+        D.r = (T*)jfnk_dalloc(c, sizeof(T) * nr);
         T* const vecs[4] = {D.b, D.x, D.x2, D.r};
         for (T* v : vecs)  // rows a cycle skips are read as finite values
-            if (v) JF_CUDA(c, cudaMemsetAsync(v, 0, sizeof(T) * 3 * (size_t)H.n, c->cur ? c->cur : c->stream));
+            if (v) JF_CUDA(c, cudaMemsetAsync(v, 0, sizeof(T) * (v == D.r ? nr : nv), c->cur ? c->cur : c->stream));
         if (l < nl - 1) {
             D.nco = lv[l + 1].n;
             D.nnz_p = (int64_t)tr[l].pcol.size();
@@ -807,6 +917,7 @@ int pc_setup(jfnk_ctx* c)
     // problems (the problems share no face, so no coupling), so each coarse row inherits the
     // problem of the rows aggregated into it.
     S.rprob.clear();
+    S.rprob_host.clear();
     if (c->nprob > 1) {
         std::vector<int32_t> cur(nc, -1);  // level 0 in the caller's order
         for (int p = 0; p < c->nprob; p++)
@@ -826,10 +937,12 @@ int pc_setup(jfnk_ctx* c)
                 const int32_t* d = upload_i(c, nxt);
                 if (!d) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
                 rp.push_back(d);
+                S.rprob_host.push_back(nxt);
                 cur.swap(nxt);
             }
         }
         if (ok) S.rprob = rp;  // else every row of every level is always evaluated
+        else S.rprob_host.clear();
         if (getenv("JFNK_VERBOSE"))
             fprintf(stderr, "[jfnk] multigrid row -> problem maps: %s (%zu levels)\n", ok ? "built" : "not built", rp.size());
     }
@@ -842,6 +955,12 @@ int pc_setup(jfnk_ctx* c)
     S.ready = true;
     c->mg_ready = true;
     return JFNK_OK;
+}
+
+const std::vector<std::vector<int32_t>>* mg_level_problems(jfnk_ctx* c)
+{
+    MgState& S = mg_state(c);
+    return (S.ready && !S.rprob.empty()) ? &S.rprob_host : nullptr;
 }
 
 int mg_hierarchy_info(jfnk_ctx* c, std::vector<int64_t>& rows, std::vector<int64_t>& nnz_a, std::vector<int64_t>& nnz_p)
@@ -893,7 +1012,20 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     const MgState& S = mg_state(c);
     const bool skip = skip_mode != SKIP_NONE && c->nprob > 1 && c->skip_done && !S.rprob.empty();
     const int cyc = skip_mode == SKIP_CYCLE ? 1 : 0;
+    // rows of each level the cycle visits: those of the problems taking part (compacted) when
+    // problems sit the pass out, else all; the coarse solve also zeroes the columns of the
+    // problems that sit out
+    auto rm = [&](int l) {
+        RowMap m;
+        m.n = M.L[l].n;
+        if (skip) m = rowmap(c, space_of_level(l), skip_mode, M.L[l].n);
+        return m;
+    };
     auto sk = [&](int l) { return ProbSkip{skip ? S.rprob[l] : nullptr, c->pd, cyc}; };
+    if (skip && skip_mode == SKIP_INACTIVE) {
+        const int rc = rowmap_build(c, SKIP_INACTIVE);
+        if (rc) return rc;
+    }
     const bool pf = c->prof.enabled && c->prof.detail;
     const int s_sm = pf ? c->prof.slot("mg_smooth") : -1, s_re = pf ? c->prof.slot("mg_resid") : -1;
     const int s_rs = pf ? c->prof.slot("mg_restrict") : -1, s_pr = pf ? c->prof.slot("mg_prolong") : -1;
@@ -902,11 +1034,18 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     const int nl = (int)M.L.size();
     const int sweeps = std::max(1, c->opt.mg_smooth_sweeps);
     const int bs = c->tune.mg_bs;  // rows per block of the thread-per-row kernels
+    // grid of a thread-per-row kernel over level l
+    auto rows_grid = [&](const void* k, int l, const RowMap& m) { return dim3(rowmap_blocks(c, k, bs, M.L[l].n, bs, m)); };
+    auto coarse_grid = [&](int l, const RowMap& m) {
+        return dim3(rowmap_blocks(c, (const void*)k_mg_coarse<T, true>, 32 * kCoarseWarps, M.L[l].n, 1, m));
+    };
     if (nl == 1) {
         auto& D = M.L[0];
-        jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), D.n, vbase, ld, jidx, D.dinv, (T)0, D.b, D.x2);
+        const RowMap m0 = rm(0);
+        jfnk_launch(c, k_mg_pre0<TV, T>, rows_grid((const void*)k_mg_pre0<TV, T>, 0, m0), dim3(bs), gate, m0, D.n, vbase, ld,
+                    jidx, D.dinv, (T)0, D.b, D.x2);
         JF_LAUNCHED(c);
-        jfnk_launch(c, k_mg_coarse<T>, dim3(D.n), dim3(32 * kCoarseWarps), gate, sk(0), D.n, M.Ainv, D.b, D.x);
+        jfnk_launch(c, k_mg_coarse<T, false>, coarse_grid(0, m0), dim3(32 * kCoarseWarps), gate, m0, sk(0), D.n, M.Ainv, D.b, D.x);
         JF_LAUNCHED(c);
         jfnk_launch(c, k_copy_to_double<T>, dim3(nb(3L * D.n, 256)), dim3(256), gate, 3 * (size_t)D.n, D.x, z);
         JF_LAUNCHED(c);
@@ -916,42 +1055,52 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     for (int l = 0; l < nl - 1; l++) {
         auto& D = M.L[l];
         const LevelOp<T> op = level_op<T>(c, M, l);
+        const RowMap ml = rm(l), mc = rm(l + 1);
         jfnk_prof_begin(c, s_sm);
         // the entry and the first sweep are one kernel when there are two or more sweeps
         if (sweeps >= 2) {
-            if (l == 0) jfnk_launch(c, k_mg_pre0_jacobi<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), op, vbase, ld, jidx, omega, D.b, D.x);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, sk(l), D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+            if (l == 0)
+                jfnk_launch(c, k_mg_pre0_jacobi<TV, T>, rows_grid((const void*)k_mg_pre0_jacobi<TV, T>, 0, ml), dim3(bs), gate,
+                            ml, op, vbase, ld, jidx, omega, D.b, D.x);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                    (const T*)D.dinv, omega, (const T*)D.b, (const T*)nullptr, D.x, 2);
         } else {
-            if (l == 0) jfnk_launch(c, k_mg_pre0<TV, T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), D.n, vbase, ld, jidx, D.dinv, omega, D.b, D.x);
-            else jfnk_launch(c, k_mg_pre<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(l), D.n, D.dinv, omega, D.b, D.x);
+            if (l == 0)
+                jfnk_launch(c, k_mg_pre0<TV, T>, rows_grid((const void*)k_mg_pre0<TV, T>, 0, ml), dim3(bs), gate, ml, D.n, vbase,
+                            ld, jidx, D.dinv, omega, D.b, D.x);
+            else jfnk_launch(c, k_mg_pre<T>, rows_grid((const void*)k_mg_pre<T>, l, ml), dim3(bs), gate, ml, D.n, D.dinv, omega, D.b, D.x);
         }
         JF_LAUNCHED(c);
         for (int sw = (sweeps >= 2 ? 2 : 1); sw < sweeps; sw++) {
-            if (l == 0) jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), op, omega, D.b, D.x, D.x2, nullptr);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, sk(l), D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+            if (l == 0)
+                jfnk_launch(c, k_mg_jacobi<T>, rows_grid((const void*)k_mg_jacobi<T>, 0, ml), dim3(bs), gate, ml, op, omega, D.b,
+                            D.x, D.x2, nullptr);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                    (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
             JF_LAUNCHED(c);
             std::swap(D.x, D.x2);
         }
         jfnk_prof_end(c, s_sm);
         jfnk_prof_begin(c, s_re);
-        if (l == 0) jfnk_launch(c, k_mg_resid<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), op, D.b, D.x, D.r);
-        else launch_csr_grp<T>(c, D.ga, D.n, gate, sk(l), D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+        if (l == 0)
+            jfnk_launch(c, k_mg_resid<T>, rows_grid((const void*)k_mg_resid<T>, 0, ml), dim3(bs), gate, ml, op, D.b, D.x, D.r);
+        else launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.r, 1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_re);
         auto& Cn = M.L[l + 1];
         jfnk_prof_begin(c, s_rs);
-        launch_spmv_grp<T>(c, D.gr, D.nco, gate, sk(l + 1), D.nco, D.n, (const int32_t*)D.rrp, (const int32_t*)D.rcol, (const T*)D.rval,
-                           (const T*)D.r, Cn.b, 0);
+        launch_spmv_grp<T>(c, D.gr, D.nco, gate, mc, D.nco, D.n, (const int32_t*)D.rrp, (const int32_t*)D.rcol, (const T*)D.rval,
+                           (const T*)D.r, Cn.b);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_rs);
     }
     {
         auto& Dc = M.L[nl - 1];
+        const RowMap mcn = rm(nl - 1);
         jfnk_prof_begin(c, s_co);
-        jfnk_launch(c, k_mg_coarse<T>, dim3(Dc.n), dim3(32 * kCoarseWarps), gate, sk(nl - 1), Dc.n, M.Ainv, Dc.b, Dc.x);
+        jfnk_launch(c, k_mg_coarse<T, true>, coarse_grid(nl - 1, mcn), dim3(32 * kCoarseWarps), gate, mcn, sk(nl - 1), Dc.n, M.Ainv,
+                    Dc.b, Dc.x);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_co);
     }
@@ -960,8 +1109,14 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         auto& D = M.L[l];
         auto& Cn = M.L[l + 1];
         const LevelOp<T> op = level_op<T>(c, M, l);
+        const RowMap ml = rm(l);
         jfnk_prof_begin(c, s_pr);
-        jfnk_launch(c, k_mg_spmv<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(l), D.n, Cn.n, D.prp, D.pcol, D.pval, Cn.x, D.x, 1);
+        if (l == 0)
+            jfnk_launch(c, k_mg_prolong<T, false>, rows_grid((const void*)k_mg_prolong<T, false>, l, ml), dim3(bs), gate, ml,
+                        D.n, (const int32_t*)D.prp, (const int32_t*)D.pcol, (const T*)D.pval, (const T*)Cn.x, D.x);
+        else
+            jfnk_launch(c, k_mg_prolong<T, true>, rows_grid((const void*)k_mg_prolong<T, true>, l, ml), dim3(bs), gate, ml,
+                        D.n, (const int32_t*)D.prp, (const int32_t*)D.pcol, (const T*)D.pval, (const T*)Cn.x, D.x);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_pr);
         jfnk_prof_begin(c, s_sm);
@@ -972,8 +1127,9 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
                 jfnk_launch(c, k_mg_jacobi_eps<T>, dim3(nb(D.n, bs)), dim3(bs), gate, op, omega, (const T*)D.b, (const T*)D.x, z, E);
                 *eps_formed = true;
             } else if (l == 0)
-                jfnk_launch(c, k_mg_jacobi<T>, dim3(nb(D.n, bs)), dim3(bs), gate, sk(0), op, omega, D.b, D.x, D.x2, last ? z : nullptr);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, sk(l), D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+                jfnk_launch(c, k_mg_jacobi<T>, rows_grid((const void*)k_mg_jacobi<T>, 0, ml), dim3(bs), gate, ml, op, omega, D.b,
+                            D.x, D.x2, last ? z : nullptr);
+            else launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
                                    (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
             JF_LAUNCHED(c);
             if (!last) std::swap(D.x, D.x2);

@@ -20,19 +20,16 @@ namespace jfnk {
 constexpr int kGradUnroll = 6;  // hexahedra have up to 6 internal neighbours
 constexpr int kLawUpdated = 3;  // neo-Hookean in the updated-Lagrangian form
 
-template <int LAW, int BS>
-__global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int nc, int dim, const int32_t* __restrict__ sell_off,
-                                              const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
-                                              const double* __restrict__ sell_l, int n_slots,
-                                              const double* __restrict__ u, double* __restrict__ G,
-                                              double* __restrict__ T, MatDev mat, const int32_t* __restrict__ cell_prob,
-                                              const double* __restrict__ sym_n, int nsy, ProbSkip sk,
-                                              const double* __restrict__ ul_Gn, const double* __restrict__ ul_F)
+// gradient (and traction operator) of cell P
+template <int LAW>
+__device__ __forceinline__ void grad_cell(int P, int nc, int dim, const int32_t* __restrict__ sell_off,
+                                          const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
+                                          const double* __restrict__ sell_l, int n_slots,
+                                          const double* __restrict__ u, double* __restrict__ G,
+                                          double* __restrict__ T, const MatDev& mat, const int32_t* __restrict__ cell_prob,
+                                          const double* __restrict__ sym_n, int nsy,
+                                          const double* __restrict__ ul_Gn, const double* __restrict__ ul_F)
 {
-    JF_PDL_ENTRY();
-    if (gate && *gate) return;
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= nc || sk(P)) return;
     const int s = P >> 5, lane = P & 31, base = sell_off[s], w = sell_w[s];
     const double u0 = u[P], u1 = u[nc + P], u2 = u[2 * nc + P];
     double g[9];
@@ -218,48 +215,44 @@ __global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int n
     (void)dim;
 }
 
-// STAGE = 1: the block first copies the gradients (and, neo-Hookean, the traction operators)
-// of the cell window [own[f0], own[f0] + BS) into shared memory, with coalesced loads;
-// faces are owner-sorted, so the owners of the block's faces lie in that window unless a
-// block spans the internal/boundary split or cells without faces, and those read global
-// memory.  Same arithmetic either way.
-template <int LAW, int BS, int STAGE>
-__global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int ni, int nd, int nflux, int nc, const int32_t* __restrict__ own,
-                                             const int32_t* __restrict__ nei, const double* __restrict__ coef,
-                                             const double* __restrict__ u, const double* __restrict__ G,
-                                             const double* __restrict__ T, const double* __restrict__ bval,
-                                             const double* __restrict__ load_dev, const int32_t* __restrict__ fn_pos,
-                                             MatDev mat, const int32_t* __restrict__ cell_prob,
-                                             double* __restrict__ F, double* __restrict__ Fn, ProbSkip sk)
+// the cells of the row map, one per thread (a grid stride over compacted rows)
+template <int LAW, int BS>
+__global__ void __launch_bounds__(BS) k_grad(const int* __restrict__ gate, int nc, int dim, const int32_t* __restrict__ sell_off,
+                                              const int32_t* __restrict__ sell_w, const int32_t* __restrict__ sell_nbr,
+                                              const double* __restrict__ sell_l, int n_slots,
+                                              const double* __restrict__ u, double* __restrict__ G,
+                                              double* __restrict__ T, MatDev mat, const int32_t* __restrict__ cell_prob,
+                                              const double* __restrict__ sym_n, int nsy, RowMap rm,
+                                              const double* __restrict__ ul_Gn, const double* __restrict__ ul_F)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
+    const int tot = rm.total();
+    for (int vw = blockIdx.x * BS + (int)(threadIdx.x & ~31u); vw < tot; vw += gridDim.x * BS) {  // warp-uniform
+        const int v = vw + (int)(threadIdx.x & 31u), P = warp_row(rm, v, vw, tot);
+        if (v < tot)
+            grad_cell<LAW>(P, nc, dim, sell_off, sell_w, sell_nbr, sell_l, n_slots, u, G, T, mat, cell_prob, sym_n, nsy, ul_Gn,
+                           ul_F);
+    }
+}
+
+// STAGE = 1: the block first copies the gradients (and, neo-Hookean, the traction operators)
+// of the cell window [own[f0], own[f0] + BS) into shared memory, with coalesced loads, f0
+// being the first face of the block's round; faces are owner-sorted, so the owners of the
+// block's faces lie in that window unless a block spans the internal/boundary split, cells
+// without faces or (compacted launches) two problems, and those read global memory.  Same
+// arithmetic either way.
+template <int LAW, int BS, int STAGE>
+__device__ __forceinline__ void flux_face(int f, int Pw, const double* __restrict__ sg, const double* __restrict__ st,
+                                          int ni, int nd, int nflux, int nc, const int32_t* __restrict__ own,
+                                          const int32_t* __restrict__ nei, const double* __restrict__ coef,
+                                          const double* __restrict__ u, const double* __restrict__ G,
+                                          const double* __restrict__ T, const double* __restrict__ bval,
+                                          const double* __restrict__ load_dev, const int32_t* __restrict__ fn_pos,
+                                          const MatDev& mat, const int32_t* __restrict__ cell_prob,
+                                          double* __restrict__ F, double* __restrict__ Fn)
+{
     constexpr bool kT = (LAW != JFNK_LAW_LINEAR);
-    __shared__ double sg[STAGE ? 9 : 1][STAGE ? BS : 1];
-    __shared__ double st[(STAGE && kT) ? 9 : 1][(STAGE && kT) ? BS : 1];
-    const int f0 = blockIdx.x * BS;
-    const int f = f0 + threadIdx.x;
-    if (sk.prob) {
-        // each face class (internal, displacement, symmetry) is owner-sorted and problems hold
-        // contiguous cell ranges: a block within one class whose first and last faces belong
-        // to one skipped problem has nothing to do (uniform exit, before the staging barrier)
-        const int fl = min(f0 + BS, nflux) - 1;
-        const int ca = f0 < ni ? 0 : (f0 < ni + nd ? 1 : 2), cb = fl < ni ? 0 : (fl < ni + nd ? 1 : 2);
-        if (ca == cb && sk.prob[own[f0]] == sk.prob[own[fl]] && sk(own[f0])) return;
-    }
-    int Pw = 0;
-    if (STAGE) {
-        Pw = own[min(f0, nflux - 1)];
-        const int cnt = min(BS, nc - Pw);
-#pragma unroll
-        for (int q = 0; q < 9; q++)
-            for (int k = threadIdx.x; k < cnt; k += BS) {
-                sg[q][k] = G[(size_t)q * nc + Pw + k];
-                if (kT) st[q][k] = T[(size_t)q * nc + Pw + k];
-            }
-        __syncthreads();
-    }
-    if (f >= nflux || sk(own[f])) return;
     if (f >= ni + nd) {
         // symmetry face (Eq. symm read as the mirror mean (T_P + R T_P R) / 2; Rhie-Chow with the
         // mirror neighbour at 2 delta n): t = Gamma [n.T_P.n - alpha Kbar ((n.u_P) / delta + n.G_P.n)]
@@ -305,7 +298,7 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
     double gf[9];
 #pragma unroll
     for (int q = 0; q < 9; q++) {
-        const double gp = staged ? sg[q][kp] : G[(size_t)q * nc + P];
+        const double gp = staged ? sg[q * BS + kp] : G[(size_t)q * nc + P];
         if (internal) {
             const double gn = G[(size_t)q * nc + N];
             gf[q] = fma(w, gp - gn, gn);
@@ -346,7 +339,7 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
         double tf[9];
 #pragma unroll
         for (int q = 0; q < 9; q++) {
-            const double tp = (kT && staged) ? st[q][kp] : T[(size_t)q * nc + P];
+            const double tp = (kT && staged) ? st[q * BS + kp] : T[(size_t)q * nc + P];
             if (internal) {
                 const double tn = T[(size_t)q * nc + N];
                 tf[q] = fma(w, tp - tn, tn);
@@ -375,6 +368,44 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
     }
 }
 
+template <int LAW, int BS, int STAGE>
+__global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int ni, int nd, int nflux, int nc, const int32_t* __restrict__ own,
+                                             const int32_t* __restrict__ nei, const double* __restrict__ coef,
+                                             const double* __restrict__ u, const double* __restrict__ G,
+                                             const double* __restrict__ T, const double* __restrict__ bval,
+                                             const double* __restrict__ load_dev, const int32_t* __restrict__ fn_pos,
+                                             MatDev mat, const int32_t* __restrict__ cell_prob,
+                                             double* __restrict__ F, double* __restrict__ Fn, RowMap rm)
+{
+    JF_PDL_ENTRY();
+    if (gate && *gate) return;
+    constexpr bool kT = (LAW != JFNK_LAW_LINEAR);
+    __shared__ double sg[STAGE ? 9 * BS : 1];
+    __shared__ double st[(STAGE && kT) ? 9 * BS : 1];
+    const int tot = rm.total();
+    // rounds of BS faces of the row map (a grid stride; the bound is uniform over the block)
+    for (int v0 = blockIdx.x * BS; v0 < tot; v0 += gridDim.x * BS) {
+        const int v = v0 + threadIdx.x;
+        int Pw = 0;
+        if (STAGE) {
+            Pw = own[rm.row(v0)];
+            const int cnt = min(BS, nc - Pw);
+#pragma unroll
+            for (int q = 0; q < 9; q++)
+                for (int k = threadIdx.x; k < cnt; k += BS) {
+                    sg[q * BS + k] = G[(size_t)q * nc + Pw + k];
+                    if (kT) st[q * BS + k] = T[(size_t)q * nc + Pw + k];
+                }
+            __syncthreads();
+        }
+        const int f = warp_row(rm, v, v0 + (int)(threadIdx.x & ~31u), tot);
+        if (v < tot)
+            flux_face<LAW, BS, STAGE>(f, Pw, sg, st, ni, nd, nflux, nc, own, nei, coef, u, G, T, bval, load_dev, fn_pos, mat,
+                                      cell_prob, F, Fn);
+        if (STAGE) __syncthreads();  // the window is refilled in the next round
+    }
+}
+
 // mode 0: out = R;  mode 1: out = (R - Ru) / eps_p with eps_p the Jv step of the cell's
 // problem (0 -> out = 0).  Dynamics (rc != null): the inertia term -rho Omega_P a_P of the
 // evaluated state u with the BDF2 acceleration a_P = 9/(4 dt^2) u_P + c_P (Eq. inertia2):
@@ -392,32 +423,39 @@ __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int d
                                                 const int32_t* __restrict__ cell_prob, const int* __restrict__ gate,
                                                 const double* __restrict__ u, const double* __restrict__ vol,
                                                 const double* __restrict__ rc, double mk, double* __restrict__ out,
-                                                ProbSkip sk)
+                                                RowMap rm)
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= 3 * (int64_t)nc) return;
-    const int k = (int)(t / nc), P = (int)(t - (int64_t)k * nc);
-    if (sk(P)) return;
-    const size_t e = (size_t)k * nc + P;
-    if (dim == 2 && k == 2) {
-        out[e] = 0.0;
-        return;
+    // (component, cell) pairs over the row map's cells, component-major
+    const int tot = rm.total();
+    const int64_t n3 = 3 * (int64_t)tot;
+    for (int64_t tw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); tw < n3; tw += (int64_t)gridDim.x * blockDim.x) {
+        // warp-uniform rounds; a warp that straddles two components finds the rows of the
+        // second by bisection
+        const int64_t t = tw + (threadIdx.x & 31u);
+        const int k = (int)(t / tot), kw = (int)(tw / tot);
+        const int P = warp_row(rm, (int)(t - (int64_t)k * tot), (int)(tw - (int64_t)kw * tot), tot);
+        if (t >= n3) continue;
+        const size_t e = (size_t)k * nc + P;
+        if (dim == 2 && k == 2) {
+            out[e] = 0.0;
+            continue;
+        }
+        const double* Fk = F + (size_t)k * nflux;
+        const double* Fnk = Fn + (size_t)k * ni;
+        double r = *load_dev * b0[e];
+        for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) r += Fk[f];
+        for (int q = fn_ptr[P]; q < fn_ptr[P + 1]; q++) r -= Fnk[q];
+        for (int f = fd_ptr[P]; f < fd_ptr[P + 1]; f++) r += Fk[f];
+        for (int f = fs_ptr[P]; f < fs_ptr[P + 1]; f++) r += Fk[f];
+        if (rc) r -= vol[P] * fma(mk, u[e], rc[e]);
+        if (mode == 1) {
+            const ProbDev& Q = pd[cell_prob[P]];
+            r = Q.eps == 0.0 ? 0.0 : (r - Ru[e]) * Q.ieps;  // 1 / eps, formed once per problem
+        }
+        out[e] = r;
     }
-    const double* Fk = F + (size_t)k * nflux;
-    const double* Fnk = Fn + (size_t)k * ni;
-    double r = *load_dev * b0[e];
-    for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) r += Fk[f];
-    for (int q = fn_ptr[P]; q < fn_ptr[P + 1]; q++) r -= Fnk[q];
-    for (int f = fd_ptr[P]; f < fd_ptr[P + 1]; f++) r += Fk[f];
-    for (int f = fs_ptr[P]; f < fs_ptr[P + 1]; f++) r += Fk[f];
-    if (rc) r -= vol[P] * fma(mk, u[e], rc[e]);
-    if (mode == 1) {
-        const ProbDev& Q = pd[cell_prob[P]];
-        r = Q.eps == 0.0 ? 0.0 : (r - Ru[e]) * Q.ieps;  // 1 / eps, formed once per problem
-    }
-    out[e] = r;
 }
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
@@ -447,17 +485,25 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
 {
     const DevMesh& m = c->dm;
     const double* load = load_dev ? load_dev : (const double*)&c->gdev->load;
-    const ProbSkip sk{(skip != SKIP_NONE && c->nprob > 1 && c->skip_done) ? (const int32_t*)c->cell_prob : nullptr, c->pd,
-                      skip == SKIP_CYCLE ? 1 : 0};
+    // rows of the problems taking part (compacted for a batch's passes that leave problems
+    // out; the maps of SKIP_CYCLE are built at the start of each Arnoldi iteration)
+    const bool part = skip != SKIP_NONE && c->nprob > 1 && c->skip_done;
+    if (part && skip == SKIP_INACTIVE) {
+        const int rc = rowmap_build(c, SKIP_INACTIVE);
+        if (rc) return rc;
+    }
+    const RowMap rcell = part ? rowmap(c, SPACE_CELLS, skip, m.nc) : RowMap{nullptr, nullptr, nullptr, m.nc};
+    const RowMap rface = part ? rowmap(c, SPACE_FACES, skip, m.nflux) : RowMap{nullptr, nullptr, nullptr, m.nflux};
     static const char* const kNames[3] = {"grad", "flux", "finish"};
     int sl[3];
     for (int q = 0; q < 3; q++) sl[q] = c->prof.enabled ? c->prof.slot(kNames[q]) : -1;
     jfnk_prof_begin(c, sl[0]);
     const Tuning& tu = c->tune;
 #define JF_GRAD_BS(LAW_, BS_)                                                                                   \
-    jfnk_launch(c, k_grad<LAW_, BS_>, dim3(nblk(m.nc, BS_)), dim3(BS_), gate, m.nc, m.dim, m.sell_off, m.sell_w, \
-                m.sell_nbr, m.sell_l, m.n_slots, u_int, G, T, c->mat, (const int32_t*)c->cell_prob,   \
-                (const double*)m.sym_n, m.nsy, sk, (const double*)c->ul_Gn, (const double*)c->ul_F)
+    jfnk_launch(c, k_grad<LAW_, BS_>, dim3(rowmap_blocks(c, (const void*)k_grad<LAW_, BS_>, BS_, m.nc, BS_, rcell, 4)),  \
+                dim3(BS_), gate, m.nc, m.dim, m.sell_off, m.sell_w, m.sell_nbr, m.sell_l, m.n_slots, u_int, G, T,  \
+                c->mat, (const int32_t*)c->cell_prob, (const double*)m.sym_n, m.nsy, rcell, (const double*)c->ul_Gn, \
+                (const double*)c->ul_F)
 #define JF_GRAD(LAW_)                                     \
     do {                                                  \
         if (tu.grad_bs == 64) JF_GRAD_BS(LAW_, 64);       \
@@ -475,9 +521,9 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
     if (m.nflux > 0) {
         jfnk_prof_begin(c, sl[1]);
 #define JF_FLUX_BS(LAW_, BS_, ST_)                                                                                      \
-    jfnk_launch(c, k_flux<LAW_, BS_, ST_>, dim3(nblk(m.nflux, BS_)), dim3(BS_), gate, m.ni, m.nd, m.nflux, m.nc, m.own, m.nei, \
-                m.coef, u_int, (const double*)G, (const double*)T, m.bval, load, m.fn_pos,   \
-                c->mat, (const int32_t*)c->cell_prob, F, Fn, sk)
+    jfnk_launch(c, k_flux<LAW_, BS_, ST_>, dim3(rowmap_blocks(c, (const void*)k_flux<LAW_, BS_, ST_>, BS_, m.nflux, BS_, rface, 4)), \
+                dim3(BS_), gate, m.ni, m.nd, m.nflux, m.nc, m.own, m.nei, m.coef, u_int, (const double*)G, (const double*)T, \
+                m.bval, load, m.fn_pos, c->mat, (const int32_t*)c->cell_prob, F, Fn, rface)
 #define JF_FLUX(LAW_)                                                        \
     do {                                                                     \
         if (tu.flux_bs == 128) {                                             \
@@ -498,10 +544,11 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
         jfnk_prof_end(c, sl[1]);
     }
     jfnk_prof_begin(c, sl[2]);
-    jfnk_launch(c, k_finish, dim3(nblk(3L * m.nc, tu.finish_bs)), dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr,
+    jfnk_launch(c, k_finish, dim3(rowmap_blocks(c, (const void*)k_finish, tu.finish_bs, 3L * m.nc, tu.finish_bs, rcell)),
+                dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr,
                 (const int32_t*)m.fs_ptr, (const double*)F, m.b0,
                 load, mode, c->Ru, c->pd, c->cell_prob, gate, u_int, (const double*)m.V,
-                (const double*)(c->dyn_on ? c->dyn_rc : nullptr), c->dyn_mk, out, sk);
+                (const double*)(c->dyn_on ? c->dyn_rc : nullptr), c->dyn_mk, out, rcell);
     JF_LAUNCHED(c);
     jfnk_prof_end(c, sl[2]);
     return JFNK_OK;
@@ -512,7 +559,7 @@ int gradient_only(jfnk_ctx* c, const double* u_int, double* Gout)
     const DevMesh& m = c->dm;
     jfnk_launch(c, k_grad<JFNK_LAW_LINEAR, 128>, dim3(nblk(m.nc, 128)), dim3(128), (const int*)nullptr, m.nc, m.dim,
                 m.sell_off, m.sell_w, m.sell_nbr, m.sell_l, m.n_slots, u_int, Gout, (double*)nullptr, c->mat,
-                (const int32_t*)c->cell_prob, (const double*)m.sym_n, m.nsy, ProbSkip{nullptr, c->pd},
+                (const int32_t*)c->cell_prob, (const double*)m.sym_n, m.nsy, RowMap{nullptr, nullptr, nullptr, m.nc},
                 (const double*)nullptr, (const double*)nullptr);
     JF_LAUNCHED(c);
     return JFNK_OK;

@@ -66,6 +66,9 @@ static int enqueue_iteration(jfnk_ctx* c)
 {
     const int* gate = &c->gdev->all_done;
     int rc;
+    // a batch's rows of the problems whose cycle still runs, for this iteration's compacted
+    // residual passes and V-cycle (the flags change only in the Gram-Schmidt step at its end)
+    if ((rc = rowmap_build(c, SKIP_CYCLE))) return rc;
     if (left_pc(c)) {
         if ((rc = perturb_basis(c, c->u, c->w))) return rc;
         if ((rc = residual_gated(c, c->w, c->wk, OUT_JV, gate, SKIP_CYCLE))) return rc;
