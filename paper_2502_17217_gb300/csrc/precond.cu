@@ -580,6 +580,81 @@ __global__ void __launch_bounds__(32 * kCoarseWarps) k_mg_spmv_blk(const int* ga
     (void)nrow; (void)nx;
 }
 
+// sum_k a_k xin(j_k) over the sliced-ELL row i, eight entries' indices and values loaded
+// together, then their rows gathered together, then summed in entry order
+constexpr int kSellUnrollC = 8;
+template <typename T, typename X>
+__device__ __forceinline__ void sell_row(int i, const int32_t* __restrict__ soff, const int32_t* __restrict__ sw,
+                                         const int32_t* __restrict__ scol, const T* __restrict__ sval, X&& xin, T& s0,
+                                         T& s1, T& s2)
+{
+    const int sl = i >> 5, lane = i & 31, base = soff[sl], w = sw[sl];
+    for (int k0 = 0; k0 < w; k0 += kSellUnrollC) {
+        int js[kSellUnrollC];
+        T as[kSellUnrollC], xs[kSellUnrollC][3];
+#pragma unroll
+        for (int q = 0; q < kSellUnrollC; q++) {
+            const int slot = base + 32 * (k0 + q) + lane;
+            js[q] = k0 + q < w ? scol[slot] : 0;
+            as[q] = k0 + q < w ? sval[slot] : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < kSellUnrollC; q++)
+            if (k0 + q < w) xin(js[q], xs[q][0], xs[q][1], xs[q][2]);
+#pragma unroll
+        for (int q = 0; q < kSellUnrollC; q++)
+            if (k0 + q < w) { s0 += as[q] * xs[q][0]; s1 += as[q] * xs[q][1]; s2 += as[q] * xs[q][2]; }
+    }
+}
+
+// Jacobi sweep or residual on a coarse level in sliced-ELL form, one thread per row, vectors
+// interleaved; modes as k_mg_csr_grp
+template <typename T, int mode>
+__global__ void k_mg_sell(const int* gate, RowMap rm, const int32_t* __restrict__ soff, const int32_t* __restrict__ sw,
+                          const int32_t* __restrict__ scol, const T* __restrict__ sval, const T* __restrict__ dinv, T omega,
+                          const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo)
+{
+    JF_PDL_ENTRY();
+    if (gate && *gate) return;
+    JF_ROWS(rm, i) {
+        T bi0, bi1, bi2, xi0 = 0, xi1 = 0, xi2 = 0;
+        ld3(b, i, bi0, bi1, bi2);
+        const T di = dinv[i];
+        if (mode == 0) ld3(x, i, xi0, xi1, xi2);
+        T s0 = 0, s1 = 0, s2 = 0;
+        if (mode == 2)
+            sell_row<T>(i, soff, sw, scol, sval,
+                        [&](int j, T& a0, T& a1, T& a2) {
+                            const T d = omega * dinv[j];
+                            ld3(b, j, a0, a1, a2);
+                            a0 = mul_rn(d, a0); a1 = mul_rn(d, a1); a2 = mul_rn(d, a2);
+                        },
+                        s0, s1, s2);
+        else
+            sell_row<T>(i, soff, sw, scol, sval, [&](int j, T& a0, T& a1, T& a2) { ld3(x, j, a0, a1, a2); }, s0, s1, s2);
+        const T r0 = bi0 - s0, r1 = bi1 - s1, r2 = bi2 - s2;
+        const T d = omega * di;
+        if (mode == 1) st3(xo, i, r0, r1, r2);
+        else if (mode == 2) st3(xo, i, mul_rn(d, bi0) + d * r0, mul_rn(d, bi1) + d * r1, mul_rn(d, bi2) + d * r2);
+        else st3(xo, i, xi0 + d * r0, xi1 + d * r1, xi2 + d * r2);
+    }
+}
+
+// y = R x (restriction) in sliced-ELL form, one thread per coarse row, x and y interleaved
+template <typename T>
+__global__ void k_mg_restrict_sell(const int* gate, RowMap rm, const int32_t* __restrict__ soff,
+                                   const int32_t* __restrict__ sw, const int32_t* __restrict__ scol,
+                                   const T* __restrict__ sval, const T* __restrict__ x, T* __restrict__ y)
+{
+    JF_PDL_ENTRY();
+    if (gate && *gate) return;
+    JF_ROWS(rm, i) {
+        T s0 = 0, s1 = 0, s2 = 0;
+        sell_row<T>(i, soff, sw, scol, sval, [&](int j, T& a0, T& a1, T& a2) { ld3(x, j, a0, a1, a2); }, s0, s1, s2);
+        st3(y, i, s0, s1, s2);
+    }
+}
+
 // lanes per row for CSR rows of mean length `mean`: the power of two near half of it, 4..32,
 // and 32 * kCoarseWarps (a block per row, restrictions only) for rows of more than two warp
 // steps of two entries per lane
@@ -697,6 +772,13 @@ struct MgDev {
         int32_t *rrp = nullptr, *rcol = nullptr;  // R = P^T: nco x n
         T* rval = nullptr;
         int ga = 32, gr = 32;                      // lanes per row of A (coarse levels) and of R
+        // A (coarse levels) and R in sliced-ELL form (32 rows per slice, entries slot-major,
+        // one thread per row) where their rows are short enough; the CSR arrays are then unused
+        bool a_sell = false, r_sell = false;
+        int32_t *a_soff = nullptr, *a_sw = nullptr, *a_scol = nullptr;
+        T* a_sval = nullptr;
+        int32_t *r_soff = nullptr, *r_sw = nullptr, *r_scol = nullptr;
+        T* r_sval = nullptr;
         int64_t nnz_a = 0, nnz_p = 0;              // operator entries (with the diagonal), P entries
         T *b = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr;
     };
@@ -764,12 +846,57 @@ static void make_transfer(const std::vector<int32_t>& prp, const std::vector<int
         }
 }
 
+// Sliced ELL of a CSR matrix with n rows: 32 rows per slice, the slice as wide as its longest
+// row, entry k of row i at slot off[i / 32] + 32 k + i % 32 (so a warp's loads of one entry
+// index coalesce); padding slots repeat the row's first column with a zero value.
+struct SellHost {
+    std::vector<int32_t> off, w, col;
+    std::vector<double> val;
+};
+static void csr_to_sell(int n, const std::vector<int32_t>& rp, const std::vector<int32_t>& col, const std::vector<double>& val,
+                        SellHost& S)
+{
+    const int ns = (n + 31) / 32;
+    S.off.assign(ns + 1, 0);
+    S.w.assign(ns, 0);
+    for (int sl = 0; sl < ns; sl++) {
+        int w = 0;
+        for (int i = 32 * sl; i < std::min(n, 32 * sl + 32); i++) w = std::max(w, rp[i + 1] - rp[i]);
+        S.w[sl] = w;
+        S.off[sl + 1] = S.off[sl] + 32 * w;
+    }
+    S.col.assign(std::max(1, S.off[ns]), 0);
+    S.val.assign(std::max(1, S.off[ns]), 0.0);
+    for (int i = 0; i < n; i++) {
+        const int sl = i >> 5, lane = i & 31, a = rp[i], len = rp[i + 1] - a;
+        for (int k = 0; k < S.w[sl]; k++) {
+            const int slot = S.off[sl] + 32 * k + lane;
+            S.col[slot] = len > 0 ? col[a + std::min(k, len - 1)] : 0;
+            S.val[slot] = k < len ? val[a + k] : 0.0;
+        }
+    }
+}
+// Levels of at least kSellMinRows rows whose mean row length is at most kSellMaxMean run one
+// thread per row in sliced-ELL form; smaller levels (too few threads to fill 152 SMs: the
+// 80k-cell cantilever's 10k-row level 1 ran 1.7x slower that way) and longer rows keep the
+// lane-group CSR kernels
+constexpr double kSellMaxMean = 64.0;
+constexpr int kSellMinRows = 1 << 16;
+// the row threshold, JFNK_MG_SELL_MIN_ROWS overriding it (read at set-up; tests run the
+// sliced-ELL kernels on small meshes with 0)
+static int sell_min_rows()
+{
+    const char* v = getenv("JFNK_MG_SELL_MIN_ROWS");
+    return v ? std::max(0, atoi(v)) : kSellMinRows;
+}
+
 template <typename T>
 static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& lv, const std::vector<double>& inv,
                      const std::vector<double>& jc_h, const std::vector<double>& sc_h, const std::vector<double>& adiag0,
                      const std::vector<HostTransfer>& tr)
 {
     const int nl = (int)lv.size();
+    const int sell_rows = sell_min_rows();
     M.L.assign(nl, typename MgDev<T>::Level());
     M.jc = upload_as<T>(c, jc_h);
     M.sc = upload_as<T>(c, sc_h);
@@ -785,10 +912,22 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
             for (int i = 0; i < H.n; i++)
                 for (int q = H.rp[i]; q < H.rp[i + 1]; q++)
                     if (H.col[q] == i) ad[i] = H.val[q];
-            D.rp = upload_i(c, H.rp);
-            D.col = upload_i(c, H.col);
-            D.val = upload_as<T>(c, H.val);
-            D.ga = group_lanes((double)H.col.size() / std::max(1, H.n));
+            const double mean = (double)H.col.size() / std::max(1, H.n);
+            D.a_sell = mean <= kSellMaxMean && H.n >= sell_rows;
+            if (D.a_sell) {
+                SellHost S;
+                csr_to_sell(H.n, H.rp, H.col, H.val, S);
+                D.a_soff = upload_i(c, S.off);
+                D.a_sw = upload_i(c, S.w);
+                D.a_scol = upload_i(c, S.col);
+                D.a_sval = upload_as<T>(c, S.val);
+                if (!D.a_soff || !D.a_sw || !D.a_scol || !D.a_sval) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
+            } else {
+                D.rp = upload_i(c, H.rp);
+                D.col = upload_i(c, H.col);
+                D.val = upload_as<T>(c, H.val);
+                D.ga = group_lanes(mean);
+            }
         }
         for (int i = 0; i < H.n; i++) di[i] = 1.0 / ad[i];
         D.adiag = upload_as<T>(c, ad);
@@ -809,10 +948,22 @@ static int mg_upload(jfnk_ctx* c, MgDev<T>& M, const std::vector<MgLevelHost>& l
             D.prp = upload_i(c, tr[l].prp);
             D.pcol = upload_i(c, tr[l].pcol);
             D.pval = upload_as<T>(c, tr[l].pval);
-            D.rrp = upload_i(c, tr[l].rrp);
-            D.rcol = upload_i(c, tr[l].rcol);
-            D.rval = upload_as<T>(c, tr[l].rval);
-            D.gr = group_lanes((double)tr[l].rcol.size() / std::max(1, D.nco));
+            const double mean = (double)tr[l].rcol.size() / std::max(1, D.nco);
+            D.r_sell = mean <= kSellMaxMean && D.nco >= sell_rows;
+            if (D.r_sell) {
+                SellHost S;
+                csr_to_sell(D.nco, tr[l].rrp, tr[l].rcol, tr[l].rval, S);
+                D.r_soff = upload_i(c, S.off);
+                D.r_sw = upload_i(c, S.w);
+                D.r_scol = upload_i(c, S.col);
+                D.r_sval = upload_as<T>(c, S.val);
+                if (!D.r_soff || !D.r_sw || !D.r_scol || !D.r_sval) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
+            } else {
+                D.rrp = upload_i(c, tr[l].rrp);
+                D.rcol = upload_i(c, tr[l].rcol);
+                D.rval = upload_as<T>(c, tr[l].rval);
+                D.gr = group_lanes(mean);
+            }
         }
         if (!D.adiag || !D.dinv || !D.b || !D.x || !D.x2 || !D.r) return jfnk_fail(c, JFNK_ENOMEM, "multigrid allocation failed");
     }
@@ -1039,6 +1190,17 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     auto coarse_grid = [&](int l, const RowMap& m) {
         return dim3(rowmap_blocks(c, (const void*)k_mg_coarse<T, true>, 32 * kCoarseWarps, M.L[l].n, 1, m));
     };
+    // sweep (mode 0), residual (1) or first sweep (2) of a coarse level
+    auto coarse_op = [&](int l, const RowMap& ml, const T* b, const T* x, T* xo, int mode) {
+        auto& D = M.L[l];
+        if (D.a_sell) {
+            auto k = mode == 0 ? k_mg_sell<T, 0> : (mode == 1 ? k_mg_sell<T, 1> : k_mg_sell<T, 2>);
+            jfnk_launch(c, k, rows_grid((const void*)k, l, ml), dim3(bs), gate, ml, (const int32_t*)D.a_soff,
+                        (const int32_t*)D.a_sw, (const int32_t*)D.a_scol, (const T*)D.a_sval, (const T*)D.dinv, omega, b, x, xo);
+        } else
+            launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
+                              (const T*)D.dinv, omega, b, x, xo, mode);
+    };
     if (nl == 1) {
         auto& D = M.L[0];
         const RowMap m0 = rm(0);
@@ -1062,8 +1224,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
             if (l == 0)
                 jfnk_launch(c, k_mg_pre0_jacobi<TV, T>, rows_grid((const void*)k_mg_pre0_jacobi<TV, T>, 0, ml), dim3(bs), gate,
                             ml, op, vbase, ld, jidx, omega, D.b, D.x);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
-                                   (const T*)D.dinv, omega, (const T*)D.b, (const T*)nullptr, D.x, 2);
+            else coarse_op(l, ml, D.b, nullptr, D.x, 2);
         } else {
             if (l == 0)
                 jfnk_launch(c, k_mg_pre0<TV, T>, rows_grid((const void*)k_mg_pre0<TV, T>, 0, ml), dim3(bs), gate, ml, D.n, vbase,
@@ -1075,8 +1236,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
             if (l == 0)
                 jfnk_launch(c, k_mg_jacobi<T>, rows_grid((const void*)k_mg_jacobi<T>, 0, ml), dim3(bs), gate, ml, op, omega, D.b,
                             D.x, D.x2, nullptr);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
-                                   (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
+            else coarse_op(l, ml, D.b, D.x, D.x2, 0);
             JF_LAUNCHED(c);
             std::swap(D.x, D.x2);
         }
@@ -1084,14 +1244,18 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         jfnk_prof_begin(c, s_re);
         if (l == 0)
             jfnk_launch(c, k_mg_resid<T>, rows_grid((const void*)k_mg_resid<T>, 0, ml), dim3(bs), gate, ml, op, D.b, D.x, D.r);
-        else launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
-                               (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.r, 1);
+        else coarse_op(l, ml, D.b, D.x, D.r, 1);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_re);
         auto& Cn = M.L[l + 1];
         jfnk_prof_begin(c, s_rs);
-        launch_spmv_grp<T>(c, D.gr, D.nco, gate, mc, D.nco, D.n, (const int32_t*)D.rrp, (const int32_t*)D.rcol, (const T*)D.rval,
-                           (const T*)D.r, Cn.b);
+        if (D.r_sell)
+            jfnk_launch(c, k_mg_restrict_sell<T>, rows_grid((const void*)k_mg_restrict_sell<T>, l + 1, mc), dim3(bs), gate, mc,
+                        (const int32_t*)D.r_soff, (const int32_t*)D.r_sw, (const int32_t*)D.r_scol, (const T*)D.r_sval,
+                        (const T*)D.r, Cn.b);
+        else
+            launch_spmv_grp<T>(c, D.gr, D.nco, gate, mc, D.nco, D.n, (const int32_t*)D.rrp, (const int32_t*)D.rcol,
+                               (const T*)D.rval, (const T*)D.r, Cn.b);
         JF_LAUNCHED(c);
         jfnk_prof_end(c, s_rs);
     }
@@ -1129,8 +1293,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
             } else if (l == 0)
                 jfnk_launch(c, k_mg_jacobi<T>, rows_grid((const void*)k_mg_jacobi<T>, 0, ml), dim3(bs), gate, ml, op, omega, D.b,
                             D.x, D.x2, last ? z : nullptr);
-            else launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
-                                   (const T*)D.dinv, omega, (const T*)D.b, (const T*)D.x, D.x2, 0);
+            else coarse_op(l, ml, D.b, D.x, D.x2, 0);
             JF_LAUNCHED(c);
             if (!last) std::swap(D.x, D.x2);
         }

@@ -71,8 +71,14 @@ def test_batch_solve_bitwise_equals_alone_with_block_jacobi(pc_side):
         assert per[k].gmres_its == sta.gmres_its and per[k].newton_its == sta.newton_its
 
 
-def test_batch_solve_within_tolerance_with_multigrid_mixed_precision():
+@pytest.mark.parametrize("sell", [0, 1])
+def test_batch_solve_within_tolerance_with_multigrid_mixed_precision(sell, monkeypatch):
+    """Batched mixed-precision multigrid solves agree with each problem solved alone and are
+    the oracle's discrete solution; sell = 1 runs the coarse levels and restrictions in
+    sliced-ELL form (JFNK_MG_SELL_MIN_ROWS=0), on the batch and on each problem alone."""
     from paper_2502_17217_gb300 import jfnk
+    if sell:
+        monkeypatch.setenv("JFNK_MG_SELL_MIN_ROWS", "0")
     cases = _mix()
     kw = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-11, mg_coarse_max=50)
     B = jfnk.Batch(cases, **kw)
@@ -104,17 +110,20 @@ def test_batch_segregated_bitwise_equals_alone():
         assert ps.newton_its == sta.newton_its and ps.gmres_its == sta.gmres_its
 
 
-@pytest.mark.parametrize("pc", ["mg_mixed", "bjacobi_left"])
+@pytest.mark.parametrize("pc", ["mg_mixed", "mg_mixed_sell", "bjacobi_left"])
 def test_skipping_problems_out_of_the_iteration_changes_no_bit(pc, monkeypatch):
     """In a batch, the problems whose Krylov cycle is done (or that left the Newton iteration)
-    skip the residual passes and the V-cycle of each Arnoldi iteration; the problems that run
-    get the same arithmetic.  Solves with skipping (the default) and without it
-    (JFNK_SKIP_DONE=0, read when a context is created) are bitwise equal, with the same
-    iteration counts, for the multigrid in mixed precision and for left-preconditioned
-    block-Jacobi."""
+    skip the residual passes and the V-cycle of each Arnoldi iteration: compacted launches
+    over the rows of the problems that run, which get the same arithmetic.  Solves with
+    skipping (the default) and without it (JFNK_SKIP_DONE=0, read when a context is created)
+    are bitwise equal, with the same iteration counts, for the multigrid in mixed precision
+    (coarse levels as lane-group CSR, or all in sliced-ELL form with JFNK_MG_SELL_MIN_ROWS=0)
+    and for left-preconditioned block-Jacobi."""
     from paper_2502_17217_gb300 import jfnk
     cases = _mix()
-    if pc == "mg_mixed":
+    if pc == "mg_mixed_sell":
+        monkeypatch.setenv("JFNK_MG_SELL_MIN_ROWS", "0")
+    if pc.startswith("mg_mixed"):
         kw = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, newton_rtol=1e-10, mg_coarse_max=50)
     else:
         kw = dict(pc=jfnk.PC_BJACOBI, newton_rtol=1e-10, pc_side=jfnk.PC_LEFT)

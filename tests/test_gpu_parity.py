@@ -103,12 +103,17 @@ def test_block_jacobi_parity(name):
     assert _rel(s.precondition(v, jfnk.PC_NONE), v) == 0.0
 
 
+@pytest.mark.parametrize("sell", [0, 1])
 @pytest.mark.parametrize("smoothed,sweeps", [(0, 1), (1, 2)])
 @pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 2e-5)])
-def test_multigrid_vcycle_parity(precision, tol, smoothed, sweeps):
+def test_multigrid_vcycle_parity(precision, tol, smoothed, sweeps, sell, monkeypatch):
     """Same hierarchy on both sides (aggregation in the caller's cell order, plain or smoothed
-    prolongation); FP64 V-cycle agrees to round-off, the FP32 V-cycle to single precision."""
+    prolongation); FP64 V-cycle agrees to round-off, the FP32 V-cycle to single precision.
+    sell = 1 runs every coarse level and restriction in sliced-ELL form, one thread per row
+    (the form of levels of at least 2^16 rows; JFNK_MG_SELL_MIN_ROWS=0 forces it here)."""
     from paper_2502_17217_gb300 import jfnk
+    if sell:
+        monkeypatch.setenv("JFNK_MG_SELL_MIN_ROWS", "0")
     case = I.case_cantilever(40, 8, 8, (1.0, 0.2, 0.2), perturb=0.15, seed=2)
     s = _solver(case, pc=jfnk.PC_MG, precision=precision, mg_coarse_max=200, mg_smoothed=smoothed,
                 mg_smooth_sweeps=sweeps)
