@@ -623,14 +623,15 @@ def serving_record(args):
     plain_u, t_seq, lat_seq = sequential(fp64)
     _, t_seq_mixed, _ = sequential(mixed)
 
-    def served(rate, opts, mode="contexts"):
+    def served(rate, opts, mode="contexts", setup_ahead=0):
         reqs, wall, srv = serving.serve_stream(cases, rate_per_s=rate, seed=int(rate), load_steps=steps, max_slots=8,
-                                               mode=mode, **opts)
+                                               mode=mode, setup_ahead=setup_ahead, **opts)
         summ = serving.summarize(reqs, wall)
         err = max(float(np.linalg.norm(r.u - up) / max(np.linalg.norm(up), 1e-300)) if r.u is not None else float("inf")
                   for r, up in zip(reqs, plain_u))
-        summ.update(max_concurrent=srv.max_concurrent, max_rel_diff_vs_sequential_fp64=err,
+        summ.update(max_concurrent=srv.max_concurrent, max_solving=srv.max_solving, max_rel_diff_vs_sequential_fp64=err,
                     setup_s_total=float(sum(getattr(r, "t_setup", 0.0) for r in reqs)),
+                    wait_s_total=float(sum(getattr(r, "t_wait", 0.0) for r in reqs)),
                     solve_s_total=float(sum(getattr(r, "t_solve", 0.0) for r in reqs)))
         return summ
 

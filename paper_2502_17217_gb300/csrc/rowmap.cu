@@ -3,7 +3,7 @@
 // Newton iteration, sit the residual passes and the V-cycle out.  Rather than launching every
 // row and testing each row's problem, every index space (cells, flux faces, the rows of each
 // multigrid level) is cut at set-up into runs of consecutive rows of one problem; before a
-// pass one warp per space compacts the runs of the problems taking part into a prefix table
+// pass one block per space compacts the runs of the problems taking part into a prefix table
 // (RowMap), and the pass's kernels walk those rows with a grid stride on a grid of the
 // blocks the SMs hold at once.  The rows a pass evaluates, and the arithmetic of each, are the
 // same as with per-row skipping, so results are bitwise equal; the rows left out cost nothing.
@@ -58,42 +58,53 @@ static void make_runs(int n, F&& prob, std::vector<int32_t>& first, std::vector<
     }
 }
 
-// One warp per space: the runs whose problem takes part (active, and for mode 0 with its cycle
-// still running), in row order, with the prefix of their row counts.
-__global__ void k_rowmap_build(const SpaceDev* __restrict__ sp, int nsp, const ProbDev* __restrict__ pd, int mode)
+// One block per space: the runs whose problem takes part (active, and for mode 0 with its
+// cycle still running), in row order, with the prefix of their row counts.  Each thread takes
+// a consecutive share of the runs: it counts its runs and rows taking part (independent loads),
+// the block scans the counts, and the thread writes its runs at their places.
+constexpr int kMapThreads = 256;
+
+__global__ void __launch_bounds__(kMapThreads) k_rowmap_build(const SpaceDev* __restrict__ sp, const ProbDev* __restrict__ pd,
+                                                              int mode)
 {
     JF_PDL_ENTRY();
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int s = threadIdx.x >> 5; s < nsp; s += nw) {
-        const SpaceDev S = sp[s];
-        if (!S.pre[mode]) continue;  // identity space
-        int k0 = 0, r0 = 0;
-        for (int j0 = 0; j0 < S.nrun; j0 += 32) {
-            const int j = j0 + lane;
-            int take = 0, len = 0;
-            if (j < S.nrun) {
-                const ProbDev& P = pd[S.run_prob[j]];
-                take = P.active && !(mode == 0 && P.done);
-                len = take ? S.run_len[j] : 0;
-            }
-            int ct = take, cl = len;  // inclusive scans over the warp
+    const SpaceDev S = sp[blockIdx.x];
+    if (!S.pre[mode]) return;  // identity space
+    const int n = S.nrun, per = (n + kMapThreads - 1) / kMapThreads;
+    const int j0 = min(n, (int)threadIdx.x * per), j1 = min(n, j0 + per);
+    auto takes = [&](int j) {
+        const ProbDev& P = pd[S.run_prob[j]];
+        return P.active && !(mode == 0 && P.done);
+    };
+    int cnt = 0, rows = 0;
+#pragma unroll 4
+    for (int j = j0; j < j1; j++)
+        if (takes(j)) { cnt++; rows += S.run_len[j]; }
+    // exclusive block scan of (cnt, rows)
+    __shared__ int wc[kMapThreads / 32], wr[kMapThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int ic = cnt, ir = rows;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int a = __shfl_up_sync(0xffffffffu, ct, o), b = __shfl_up_sync(0xffffffffu, cl, o);
-                if (lane >= o) { ct += a; cl += b; }
-            }
-            if (take) {
-                S.first[mode][k0 + ct - 1] = S.run_first[j];
-                S.pre[mode][k0 + ct - 1] = r0 + cl - len;
-            }
-            k0 += __shfl_sync(0xffffffffu, ct, 31);
-            r0 += __shfl_sync(0xffffffffu, cl, 31);
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, ic, o), b = __shfl_up_sync(0xffffffffu, ir, o);
+        if (lane >= o) { ic += a; ir += b; }
+    }
+    if (lane == 31) { wc[wid] = ic; wr[wid] = ir; }
+    __syncthreads();
+    int bc = 0, br = 0;
+    for (int w = 0; w < wid; w++) { bc += wc[w]; br += wr[w]; }
+    int k = bc + ic - cnt, r = br + ir - rows;
+    for (int j = j0; j < j1; j++)
+        if (takes(j)) {
+            S.first[mode][k] = S.run_first[j];
+            S.pre[mode][k] = r;
+            k++;
+            r += S.run_len[j];
         }
-        if (lane == 0) {
-            S.pre[mode][k0] = r0;
-            S.hdr[mode][0] = k0;
-            S.hdr[mode][1] = r0;
-        }
+    if (threadIdx.x == kMapThreads - 1) {  // the last thread ends at the totals
+        S.pre[mode][k] = r;
+        S.hdr[mode][0] = k;
+        S.hdr[mode][1] = r;
     }
 }
 
@@ -176,8 +187,7 @@ int rowmap_build(jfnk_ctx* c, int skip)
     const RowMaps* R = maps(c);
     if (!R || (skip != SKIP_CYCLE && skip != SKIP_INACTIVE)) return JFNK_OK;
     const int nsp = (int)R->sp.size();
-    const int warps = std::min(nsp, 32);
-    jfnk_launch(c, k_rowmap_build, dim3(1), dim3(32 * warps), (const SpaceDev*)R->dev, nsp, (const ProbDev*)c->pd,
+    jfnk_launch(c, k_rowmap_build, dim3(nsp), dim3(kMapThreads), (const SpaceDev*)R->dev, (const ProbDev*)c->pd,
                 skip == SKIP_CYCLE ? 0 : 1);
     JF_LAUNCHED(c);
     return JFNK_OK;

@@ -8,7 +8,11 @@ time and queue in arrival order.  Two ways of putting them on the device:
     basis and preconditioner resident on the device for its whole life) and its own CUDA
     stream, and runs its Newton-Krylov solve in a slot worker.  Requests admitted while
     others run overlap with them on the device, kernel by kernel; each starts as soon as it is
-    admitted and retires as soon as it converges.
+    admitted and retires as soon as it converges.  With setup_ahead = A > 0, up to A more
+    requests are admitted while every slot is busy: their contexts are created and set up
+    (topology, renumbering, aggregation and Galerkin products on the host, uploads and device
+    geometry) while the slots solve, and each takes the next free slot as soon as it is ready,
+    so that a queued request's set-up is off its critical path.
   * mode "lockstep": when a batch slot is free, the queued requests with the head request's
     number of load steps that fit the budget are concatenated into one batch (one index space,
     one iteration graph for all of them, each problem with its own Newton loop and Krylov
@@ -50,6 +54,7 @@ class Request:
     stats: object = None
     bytes: int = 0
     t_setup: float = 0.0  # seconds of context creation and set-up (host work and uploads)
+    t_wait: float = 0.0   # seconds set up and waiting for a solve slot (setup_ahead > 0)
     t_solve: float = 0.0  # seconds of the solve call
     error: str | None = None
     done: threading.Event = field(default_factory=threading.Event)
@@ -65,17 +70,21 @@ class Request:
 
 class Server:
     """Continuous-admission JFNK solve server (one GPU).  mode "contexts": one context and
-    stream per request, up to max_slots at once; mode "lockstep": batches of queued requests,
-    up to max_slots batches at once."""
+    stream per request, up to max_slots solving at once and up to setup_ahead more being set
+    up or ready; mode "lockstep": batches of queued requests, up to max_slots batches at once."""
 
     MODES = ("contexts", "lockstep")
 
     def __init__(self, device: int = 0, hbm_budget_bytes: float | None = None, max_slots: int = 8,
-                 mode: str = "contexts", **options):
+                 mode: str = "contexts", setup_ahead: int = 0, **options):
         if mode not in self.MODES:
             raise ValueError(f"mode must be one of {self.MODES}")
+        if setup_ahead < 0 or (setup_ahead and mode != "contexts"):
+            raise ValueError("setup_ahead must be >= 0, and is for mode 'contexts' only")
         self.device = device
         self.mode = mode
+        self.setup_ahead = setup_ahead
+        self._slots = threading.BoundedSemaphore(max_slots)  # solves at once (mode 'contexts')
         self.options = dict(options)
         # a served request is solved once: the launch-shape autotuner's timing runs would cost
         # more than they save (the shapes never change the results)
@@ -90,8 +99,10 @@ class Server:
         self._queue: collections.deque[Request] = collections.deque()
         self._lock = threading.Condition()
         self._in_use = 0.0
-        self._running = 0   # slot workers (requests, or batches in lockstep mode)
+        self._running = 0   # workers (requests holding a context, or batches in lockstep mode)
         self._inflight = 0  # requests on the device
+        self._solving = 0   # requests in their solve (mode 'contexts')
+        self.max_solving = 0
         self._stop = False
         self._workers: list[threading.Thread] = []
         self.completed: list[Request] = []
@@ -168,7 +179,7 @@ class Server:
             t.start()
 
     def _admissible(self) -> bool:
-        if not self._queue or self._running >= self.max_slots:
+        if not self._queue or self._running >= self.max_slots + self.setup_ahead:
             return False
         need = self.footprint(self._queue[0].case)
         # an oversized request runs alone rather than never
@@ -183,8 +194,17 @@ class Server:
             s = jfnk.Solver.from_case(r.case, device=self.device, **self.options)
             s.setup()
             t1 = time.perf_counter()
-            u, st, rc = s.solve(load_steps=r.load_steps, raise_on_fail=False)
-            r.t_setup, r.t_solve = t1 - t0, time.perf_counter() - t1
+            with self._slots:  # the next free slot (at once unless set up ahead)
+                ts = time.perf_counter()
+                with self._lock:
+                    self._solving += 1
+                    self.max_solving = max(self.max_solving, self._solving)
+                try:
+                    u, st, rc = s.solve(load_steps=r.load_steps, raise_on_fail=False)
+                finally:
+                    with self._lock:
+                        self._solving -= 1
+            r.t_setup, r.t_wait, r.t_solve = t1 - t0, ts - t1, time.perf_counter() - ts
             r.u, r.stats, r.status = u, st, rc
             r.bytes = s.device_bytes()
         except Exception as e:  # reported on the request, the server keeps serving

@@ -70,20 +70,22 @@ def test_served_results_under_contention_with_load_steps():
         assert np.array_equal(r.u, ua)
 
 
-@pytest.mark.parametrize("mode", ["contexts", "lockstep"])
+@pytest.mark.parametrize("mode", ["contexts", "contexts_ahead", "lockstep"])
 def test_served_results_match_the_oracle(mode):
     """Every served request (Poisson arrivals, Hooke and neo-Hookean with two load steps,
     mixed precision, multigrid) against the oracle's FP64 solve of that request, both to
     |R| <= 1e-10 |R0| per load step: relative difference <= 1e-8.  In lockstep mode the
-    requests run as concatenated batches; in contexts mode each in its own context."""
+    requests run as concatenated batches; in contexts mode each in its own context, with
+    (contexts_ahead) or without queued requests set up while the slots solve."""
     import oracle as O
     from paper_2502_17217_gb300 import jfnk, serving
     reqs_def = I.serving_requests(8, lo=500, hi=4000, seed=9, frac_nh=0.4)
     opts = dict(pc=jfnk.PC_MG, precision=jfnk.PREC_MIXED, mg_coarse_max=50, newton_rtol=1e-10)
     cases = [c for c, _ in reqs_def]
     steps = [s for _, s in reqs_def]
-    reqs, wall, srv = serving.serve_stream(cases, rate_per_s=500.0, seed=3, load_steps=steps, max_slots=4, mode=mode,
-                                           **opts)
+    ahead = 4 if mode == "contexts_ahead" else 0
+    reqs, wall, srv = serving.serve_stream(cases, rate_per_s=500.0, seed=3, load_steps=steps, max_slots=4,
+                                           mode="lockstep" if mode == "lockstep" else "contexts", setup_ahead=ahead, **opts)
     bad = [(k, r.status, r.error, r.cells) for k, r in enumerate(reqs) if r.status != 0]
     assert not bad, bad
     if mode == "lockstep":

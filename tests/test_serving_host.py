@@ -19,13 +19,16 @@ class _Live:
         self.lock = threading.Lock()
         self.n = 0
         self.max_n = 0
+        self.solving = 0
+        self.max_solving = 0
         self.order = []
+        self.events = []  # (time, "setup-start" | "setup-end" | "solve-start" | "solve-end", tag)
         self.closed = 0
 
 
-def _case(cells, law=0, hold=0.05, fail=False, true_bpc=None):
+def _case(cells, law=0, hold=0.05, fail=False, true_bpc=None, setup_hold=0.0, tag=None):
     return SimpleNamespace(mesh=SimpleNamespace(n_cells=cells), material=SimpleNamespace(law=law),
-                           hold=hold, fail=fail, true_bpc=true_bpc)
+                           hold=hold, fail=fail, true_bpc=true_bpc, setup_hold=setup_hold, tag=tag)
 
 
 @pytest.fixture
@@ -45,8 +48,16 @@ def live(monkeypatch):
                 rec.n += 1
                 rec.max_n = max(rec.max_n, rec.n)
                 rec.order.append(id(self.case))
+                rec.events.append((time.perf_counter(), "setup-start", self.case.tag))
+            time.sleep(self.case.setup_hold)
+            with rec.lock:
+                rec.events.append((time.perf_counter(), "setup-end", self.case.tag))
 
         def solve(self, load_steps=1, raise_on_fail=True):
+            with rec.lock:
+                rec.solving += 1
+                rec.max_solving = max(rec.max_solving, rec.solving)
+                rec.events.append((time.perf_counter(), "solve-start", self.case.tag))
             try:
                 time.sleep(self.case.hold)
                 if self.case.fail:
@@ -56,6 +67,8 @@ def live(monkeypatch):
             finally:
                 with rec.lock:
                     rec.n -= 1
+                    rec.solving -= 1
+                    rec.events.append((time.perf_counter(), "solve-end", self.case.tag))
 
         def device_bytes(self):
             bpc = self.case.true_bpc
@@ -218,3 +231,37 @@ def test_lockstep_batch_failure_is_reported_on_each_of_its_requests(batches):
     bad = [r for r in reqs if r.status == -99]
     assert bad and all("planted batch failure" in r.error for r in bad)
     assert all(r.done.is_set() for r in reqs)
+
+
+def test_setup_ahead_prepares_queued_requests_while_the_slots_solve(live):
+    """With setup_ahead = 2 and 2 slots, up to 4 requests hold a context (two solving, two
+    set up and waiting), never more than 2 solve at once, every request is served, and a
+    queued request's set-up starts before the solve ahead of it ends."""
+    cases = [_case(100, hold=0.15, setup_hold=0.05, tag=k) for k in range(8)]
+    srv, reqs = _run(cases, hbm_budget_bytes=1e15, max_slots=2, setup_ahead=2)
+    assert all(r.status == 0 and r.error is None for r in reqs)
+    assert live.max_solving == 2 and srv.max_solving == 2
+    assert srv.max_concurrent == 4 and live.max_n == 4
+    assert srv._in_use == 0 and srv._running == 0 and srv._solving == 0
+    first = {}
+    for t, what, tag in live.events:
+        first.setdefault((what, tag), t)
+    # request 2 (the first to wait) was set up while requests 0 and 1 were solving
+    assert first[("setup-end", 2)] < first[("solve-end", 0)]
+    # and a request waiting for its slot reports that wait
+    assert max(r.t_wait for r in reqs) > 0.05
+
+
+def test_setup_ahead_respects_the_memory_budget(live):
+    one = serving.DEFAULT_BYTES_PER_CELL[0] * 1000
+    srv, reqs = _run([_case(1000) for _ in range(6)], hbm_budget_bytes=2.5 * one, max_slots=1, setup_ahead=4)
+    assert all(r.status == 0 for r in reqs)
+    assert srv.max_concurrent == 2 and live.max_n == 2  # the budget, not the set-up allowance, bounds it
+    assert srv.max_solving == 1
+
+
+def test_setup_ahead_is_for_the_contexts_mode_only():
+    with pytest.raises(ValueError):
+        serving.Server(hbm_budget_bytes=1e12, mode="lockstep", setup_ahead=2)
+    with pytest.raises(ValueError):
+        serving.Server(hbm_budget_bytes=1e12, setup_ahead=-1)
