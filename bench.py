@@ -624,7 +624,7 @@ def serving_record(args):
     _, t_seq_mixed, _ = sequential(mixed)
 
     def served(rate, opts, mode="contexts", setup_ahead=0):
-        reqs, wall, srv = serving.serve_stream(cases, rate_per_s=rate, seed=int(rate), load_steps=steps, max_slots=8,
+        reqs, wall, srv = serving.serve_stream(cases, rate_per_s=rate, seed=int(rate), load_steps=steps, max_slots=args.slots,
                                                mode=mode, setup_ahead=setup_ahead, **opts)
         summ = serving.summarize(reqs, wall)
         err = max(float(np.linalg.norm(r.u - up) / max(np.linalg.norm(up), 1e-300)) if r.u is not None else float("inf")
@@ -647,13 +647,13 @@ def serving_record(args):
     return {"metric": "served solves/s", "value": best, "unit": "solves/s", "higher_is_better": True,
             "config": {"workload": "serving_poisson_logU_2k_1M_70lin_30nh", "requests": args.requests,
                        "cells_total": int(sum(c.mesh.n_cells for c in cases)),
-                       "served": "continuous admission by HBM footprint, 8 slots, one context and stream per request, "
+                       "served": f"continuous admission by HBM footprint, {args.slots} slots, one context and stream per request, "
                                  "MG FP32 + FP32 basis (mixed)",
                        "baseline": "the same requests solved one after another (set-up included)"},
             "rates": rates, "lockstep_rates": lockstep, "served_fp64_at_max_rate": served_fp64,
-            "modes": {"rates": "contexts: one context and stream per request, up to 8 at once",
+            "modes": {"rates": f"contexts: one context and stream per request, up to {args.slots} at once",
                       "lockstep_rates": "lockstep: queued requests with the same load steps concatenated into one "
-                                        "batch (one index space and iteration graph), up to 8 batches at once"},
+                                        f"batch (one index space and iteration graph), up to {args.slots} batches at once"},
             "sequential_fp64_solves_per_s": seq, "sequential_fp64_p50_latency_s": float(np.percentile(lat_seq, 50)),
             "sequential_mixed_solves_per_s": seq_mixed,
             "speedup_vs_sequential_fp64": best / seq,
@@ -779,6 +779,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="config 5 alone: Poisson request stream, served solves/s and p50/p99")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--slots", type=int, default=8, help="serving: requests (or lockstep batches) on the device at once")
     ap.add_argument("--members", type=int, default=0, help="with --ncu and the batched workload: its first N "
                     "problems only (a smaller case for counter captures)")
     ap.add_argument("--e2e-steps", type=int, default=5, help="solves in the end-to-end figure (at most --steps)")

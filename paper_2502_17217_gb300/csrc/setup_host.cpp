@@ -16,27 +16,49 @@
 
 namespace jfnk {
 
-// Runs f(lo, hi) over [0, n) in blocks of `grain` taken by up to 8 host threads (blocks are
-// handed out in order through an atomic counter, so uneven blocks balance).  Each block's
-// results depend on the block alone: the outcome is the same for any thread count.
+// Host threads of the set-up's parallel loops: the host's cores, at most 16.
+static int host_threads()
+{
+    return std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+}
+
+// Runs f(lo, hi, tid) over [0, n) in blocks of `grain` taken by up to host_threads() threads
+// (tid in [0, host_threads()); blocks are handed out in order through an atomic counter, so
+// uneven blocks balance).  Each block's results depend on the block alone: the outcome is the
+// same for any thread count.  Scratch indexed by tid is private to the block's thread.
 template <typename F>
 static void parallel_blocks(int n, int grain, F&& f)
 {
     const int nblocks = (n + grain - 1) / grain;
-    const int nt = std::max(1, std::min({nblocks, 8, (int)std::thread::hardware_concurrency()}));
+    const int nt = std::max(1, std::min(nblocks, host_threads()));
     if (nt <= 1) {
-        for (int b = 0; b < nblocks; b++) f(b * grain, std::min(n, (b + 1) * grain));
+        for (int b = 0; b < nblocks; b++) f(b * grain, std::min(n, (b + 1) * grain), 0);
         return;
     }
     std::atomic<int> next(0);
-    auto work = [&]() {
-        for (int b = next++; b < nblocks; b = next++) f(b * grain, std::min(n, (b + 1) * grain));
+    auto work = [&](int tid) {
+        for (int b = next++; b < nblocks; b = next++) f(b * grain, std::min(n, (b + 1) * grain), tid);
     };
     std::vector<std::thread> th;
-    for (int t = 1; t < nt; t++) th.emplace_back(work);
-    work();
+    for (int t = 1; t < nt; t++) th.emplace_back(work, t);
+    work(0);
     for (auto& t : th) t.join();
 }
+
+// Sparse accumulator of one host thread over nco columns: entries stamped with the row being
+// formed, so it is cleared once per use, not once per row or block.
+struct SparseAcc {
+    std::vector<double> acc;
+    std::vector<int32_t> mark;
+    std::vector<int32_t> list;
+    void init(int nco)
+    {
+        if ((int)acc.size() != nco) {
+            acc.assign(nco, 0.0);
+            mark.assign(nco, -1);
+        }
+    }
+};
 
 static std::vector<int32_t> rcm_order(int nc, const std::vector<int32_t>& aptr, const std::vector<int32_t>& adj)
 {
@@ -73,9 +95,23 @@ static std::vector<int32_t> rcm_order(int nc, const std::vector<int32_t>& aptr, 
     return order;
 }
 
+// phase times of the set-up, printed to stderr when JFNK_VERBOSE is set
+struct PhaseClock {
+    bool on = getenv("JFNK_VERBOSE") != nullptr;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void lap(const char* what)
+    {
+        if (!on) return;
+        const auto n = std::chrono::steady_clock::now();
+        fprintf(stderr, "[jfnk]   topology: %-28s %8.1f ms\n", what, std::chrono::duration<double, std::milli>(n - t).count());
+        t = n;
+    }
+};
+
 std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std::vector<int32_t>* group)
 {
     const int nc = hm.nc, ni = hm.ni, nf = hm.nf;
+    PhaseClock clk;
     t = Topology();
     t.nc = nc;
     // --- cell numbering
@@ -98,6 +134,7 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
         std::stable_sort(t.n2o.begin(), t.n2o.end(), [&](int a, int b) { return (*group)[a] < (*group)[b]; });
     t.o2n.assign(nc, -1);
     for (int i = 0; i < nc; i++) t.o2n[t.n2o[i]] = i;
+    clk.lap("cell numbering");
     // --- face order
     struct FK { int32_t a, b, src; uint8_t flip; };
     std::vector<FK> in(ni);
@@ -128,6 +165,7 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     }
     for (auto& v : bd)
         std::sort(v.begin(), v.end(), [](const FK& x, const FK& y) { return x.a != y.a ? x.a < y.a : x.src < y.src; });
+    clk.lap("face order");
     t.ni = ni;
     t.nd = (int)bd[0].size();
     t.nsy = (int)bd[1].size();
@@ -161,6 +199,7 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     int bw = 0;
     for (int f = 0; f < ni; f++) bw = std::max(bw, t.nei[f] - t.own[f]);
     t.bandwidth = bw;
+    clk.lap("face arrays");
     // --- per-cell ranges
     auto ranges = [&](int lo, int hi, std::vector<int32_t>& ptr) {
         ptr.assign(nc + 1, 0);
@@ -196,6 +235,7 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
             if (f < ni) t.ca_face[fill[t.nei[f]]++] = ~f;
         }
     }
+    clk.lap("cell face lists");
     // sliced ELL of internal neighbours (32 cells per slice), faces in increasing index
     std::vector<int32_t> cnt(nc, 0);
     for (int f = 0; f < ni; f++) { cnt[t.own[f]]++; cnt[t.nei[f]]++; }
@@ -241,6 +281,7 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     t.bval.assign((size_t)(t.nd + t.nsy + t.nt) * 3, 0.0);
     for (int f = ni; f < ni + t.nd + t.nsy + t.nt; f++)
         for (int c = 0; c < 3; c++) t.bval[(size_t)(f - ni) * 3 + c] = hm.bval[(size_t)(t.face_src[f] - ni) * 3 + c];
+    clk.lap("neighbour table, values");
     return "";
 }
 
@@ -324,9 +365,13 @@ static void smoothed_prolongation(const MgLevelHost& F, const std::vector<int32_
     std::vector<std::vector<int32_t>> bcol(nb);
     std::vector<std::vector<double>> bval(nb);
     std::vector<int32_t> len(n, 0);
-    parallel_blocks(n, grain, [&](int lo, int hi) {
-        std::vector<double> acc(nco, 0.0);
-        std::vector<int32_t> mark(nco, -1), list;
+    std::vector<SparseAcc> scratch(host_threads());
+    parallel_blocks(n, grain, [&](int lo, int hi, int tid) {
+        SparseAcc& S = scratch[tid];
+        S.init(nco);
+        auto& acc = S.acc;
+        auto& mark = S.mark;
+        auto& list = S.list;
         auto& oc = bcol[lo / grain];
         auto& ov = bval[lo / grain];
         for (int i = lo; i < hi; i++) {
@@ -381,9 +426,13 @@ static void galerkin(const MgLevelHost& F, int nco, MgLevelHost& Cl)
     std::vector<std::vector<int32_t>> bcol(nb);
     std::vector<std::vector<double>> bval(nb);
     std::vector<int32_t> len(nco, 0);
-    parallel_blocks(nco, grain, [&](int lo, int hi) {
-        std::vector<double> acc(nco, 0.0);
-        std::vector<int32_t> mark(nco, -1), list;
+    std::vector<SparseAcc> scratch(host_threads());
+    parallel_blocks(nco, grain, [&](int lo, int hi, int tid) {
+        SparseAcc& S = scratch[tid];
+        S.init(nco);
+        auto& acc = S.acc;
+        auto& mark = S.mark;
+        auto& list = S.list;
         auto& oc = bcol[lo / grain];
         auto& ov = bval[lo / grain];
         for (int I = lo; I < hi; I++) {
@@ -481,7 +530,7 @@ std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels,
     // substitution reads rows of L and of Wt contiguously), then the symmetric product, each
     // entry a contiguous dot product over the rows both columns share
     std::vector<double> Wt((size_t)n * n, 0.0);
-    parallel_blocks(n, 8, [&](int lo, int hi) {
+    parallel_blocks(n, 8, [&](int lo, int hi, int) {
         for (int c = lo; c < hi; c++) {
             double* w = Wt.data() + (size_t)c * n;
             w[c] = 1.0 / A[(size_t)c * n + c];
@@ -492,7 +541,7 @@ std::string mg_build_hierarchy(MgLevelHost&& fine, double theta, int max_levels,
         }
     });
     chol.assign((size_t)n * n, 0.0);
-    parallel_blocks(n, 8, [&](int lo, int hi) {
+    parallel_blocks(n, 8, [&](int lo, int hi, int) {
         for (int i = lo; i < hi; i++) {
             const double* wi = Wt.data() + (size_t)i * n;
             for (int j = 0; j <= i; j++) {
