@@ -412,43 +412,60 @@ int jfnk_setup(jfnk_ctx* c)
         int np = 0, nc = 0, nf = 0, ni = 0;
         for (auto& q : c->batch) { np += q.hm.np; nc += q.hm.nc; nf += q.hm.nf; ni += q.hm.ni; }
         h.np = np; h.nc = nc; h.nf = nf; h.ni = ni;
-        h.pts.reserve(3 * (size_t)np);
-        h.fptr.assign(1, 0);
+        // per problem: its first point, cell, internal face and boundary face, and the first
+        // entries of its internal and boundary faces' point lists in the union; each problem is
+        // then copied on its own host thread (internal faces of all problems first, then the
+        // boundary faces, in problem order)
+        const int P = (int)c->batch.size();
+        std::vector<int64_t> p0(P + 1, 0), c0(P + 1, 0), i0(P + 1, 0), b0(P + 1, 0), ip0(P + 1, 0), bp0(P + 1, 0);
+        for (int p = 0; p < P; p++) {
+            const jfnk::HostMesh& q = c->batch[p].hm;
+            p0[p + 1] = p0[p] + q.np;
+            c0[p + 1] = c0[p] + q.nc;
+            i0[p + 1] = i0[p] + q.ni;
+            b0[p + 1] = b0[p] + (q.nf - q.ni);
+            ip0[p + 1] = ip0[p] + q.fptr[q.ni];
+            bp0[p + 1] = bp0[p] + (q.fptr[q.nf] - q.fptr[q.ni]);
+        }
+        const int64_t nbf = b0[P], nip = ip0[P];
+        h.pts.resize(3 * (size_t)np);
+        h.fptr.resize((size_t)nf + 1);
+        h.fpts.resize((size_t)(ip0[P] + bp0[P]));
+        h.own.resize(nf);
+        h.nei.resize(ni);
+        h.btype.resize(nbf);
+        h.bval.resize(3 * (size_t)nbf);
+        group.resize(nc);
         c->fb_host.assign(3 * (size_t)nc, 0.0);
-        c->prob_first_cell.clear();
-        // internal faces of all problems first, then boundary faces
-        int poff = 0, coff = 0;
-        std::vector<int32_t> bf_src;  // (problem, face) of each boundary face, in order
-        for (size_t p = 0; p < c->batch.size(); p++) {
-            const jfnk::HostMesh& q = c->batch[p].hm;
-            c->prob_first_cell.push_back(coff);
-            h.pts.insert(h.pts.end(), q.pts.begin(), q.pts.end());
-            for (int f = 0; f < q.ni; f++) {
-                for (int k = q.fptr[f]; k < q.fptr[f + 1]; k++) h.fpts.push_back(q.fpts[k] + poff);
-                h.fptr.push_back((int32_t)h.fpts.size());
-                h.own.push_back(q.own[f] + coff);
-                h.nei.push_back(q.nei[f] + coff);
+        c->prob_first_cell.assign(P, 0);
+        h.fptr[0] = 0;
+        jfnk::host_parallel(P, 1, [&](int lo, int hi) {
+            for (int p = lo; p < hi; p++) {
+                const jfnk::HostMesh& q = c->batch[p].hm;
+                const int32_t poff = (int32_t)p0[p], coff = (int32_t)c0[p];
+                c->prob_first_cell[p] = coff;
+                std::copy(q.pts.begin(), q.pts.end(), h.pts.begin() + 3 * p0[p]);
+                for (int f = 0; f < q.ni; f++) {
+                    const int64_t F = i0[p] + f;
+                    h.own[F] = q.own[f] + coff;
+                    h.nei[F] = q.nei[f] + coff;
+                    h.fptr[F + 1] = (int32_t)(ip0[p] + q.fptr[f + 1]);
+                }
+                for (int k = 0; k < q.fptr[q.ni]; k++) h.fpts[ip0[p] + k] = q.fpts[k] + poff;
+                for (int f = q.ni; f < q.nf; f++) {
+                    const int64_t B = b0[p] + (f - q.ni), F = ni + B;
+                    h.own[F] = q.own[f] + coff;
+                    h.btype[B] = q.btype[f - q.ni];
+                    for (int k = 0; k < 3; k++) h.bval[3 * B + k] = q.bval[(size_t)(f - q.ni) * 3 + k];
+                    h.fptr[F + 1] = (int32_t)(nip + bp0[p] + (q.fptr[f + 1] - q.fptr[q.ni]));
+                }
+                for (int k = q.fptr[q.ni]; k < q.fptr[q.nf]; k++) h.fpts[nip + bp0[p] + (k - q.fptr[q.ni])] = q.fpts[k] + poff;
+                if (!c->batch[p].fb.empty())
+                    std::copy(c->batch[p].fb.begin(), c->batch[p].fb.end(), c->fb_host.begin() + 3 * (size_t)coff);
+                std::fill(group.begin() + coff, group.begin() + coff + q.nc, (int32_t)p);
             }
-            if (!c->batch[p].fb.empty())
-                std::copy(c->batch[p].fb.begin(), c->batch[p].fb.end(), c->fb_host.begin() + 3 * (size_t)coff);
-            for (int i = 0; i < q.nc; i++) group.push_back((int32_t)p);
-            mats.push_back({(double)c->batch[p].law, c->batch[p].p1, c->batch[p].p2});
-            poff += q.np;
-            coff += q.nc;
-        }
-        poff = 0; coff = 0;
-        for (size_t p = 0; p < c->batch.size(); p++) {
-            const jfnk::HostMesh& q = c->batch[p].hm;
-            for (int f = q.ni; f < q.nf; f++) {
-                for (int k = q.fptr[f]; k < q.fptr[f + 1]; k++) h.fpts.push_back(q.fpts[k] + poff);
-                h.fptr.push_back((int32_t)h.fpts.size());
-                h.own.push_back(q.own[f] + coff);
-                h.btype.push_back(q.btype[f - q.ni]);
-                for (int k = 0; k < 3; k++) h.bval.push_back(q.bval[(size_t)(f - q.ni) * 3 + k]);
-            }
-            poff += q.np;
-            coff += q.nc;
-        }
+        });
+        for (int p = 0; p < P; p++) mats.push_back({(double)c->batch[p].law, c->batch[p].p1, c->batch[p].p2});
         c->nprob = (int)c->batch.size();
     } else {
         c->nprob = 1;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -53,6 +54,11 @@ struct Topology {
     std::vector<double> bval;                // [nd + nsy + nt][3] boundary values in new face order
     int bandwidth = 0;
 };
+
+// Runs f(lo, hi) over [0, n) in blocks of `grain` on up to 16 host threads (setup_host.cpp);
+// each block's results must depend on the block alone, so the outcome does not depend on the
+// thread count.
+void host_parallel(int n, int grain, const std::function<void(int, int)>& f);
 
 // Builds the topology; returns "" on success or an error message.  With `group` (one entry
 // per input cell) the cells of each group stay contiguous, groups in increasing order.

@@ -801,7 +801,10 @@ struct MgState {
 template <typename T>
 static T* upload_as(jfnk_ctx* c, const std::vector<double>& h)
 {
-    std::vector<T> t(h.begin(), h.end());
+    std::vector<T> t(h.size());
+    host_parallel((int)h.size(), 1 << 18, [&](int lo, int hi) {
+        for (int i = lo; i < hi; i++) t[i] = (T)h[i];
+    });
     T* d = (T*)jfnk_dalloc(c, sizeof(T) * std::max<size_t>(1, t.size()));
     if (d && jfnk_upload(c, d, t.data(), sizeof(T) * t.size())) return nullptr;
     return d;
@@ -824,13 +827,19 @@ static void make_transfer(const std::vector<int32_t>& prp, const std::vector<int
 {
     // rows of P in the device numbering of this level
     t.prp.assign(n + 1, 0);
-    t.pcol.clear();
-    t.pval.clear();
     for (int i = 0; i < n; i++) {
         const int src = n2o ? (*n2o)[i] : i;
-        for (int q = prp[src]; q < prp[src + 1]; q++) { t.pcol.push_back(pcol[q]); t.pval.push_back(pval[q]); }
-        t.prp[i + 1] = (int32_t)t.pcol.size();
+        t.prp[i + 1] = t.prp[i] + (prp[src + 1] - prp[src]);
     }
+    t.pcol.resize(t.prp[n]);
+    t.pval.resize(t.prp[n]);
+    host_parallel(n, 1 << 15, [&](int lo, int hi) {
+        for (int i = lo; i < hi; i++) {
+            const int src = n2o ? (*n2o)[i] : i;
+            std::copy(pcol.begin() + prp[src], pcol.begin() + prp[src + 1], t.pcol.begin() + t.prp[i]);
+            std::copy(pval.begin() + prp[src], pval.begin() + prp[src + 1], t.pval.begin() + t.prp[i]);
+        }
+    });
     t.rrp.assign(nco + 1, 0);
     for (int q = 0; q < (int)t.pcol.size(); q++) t.rrp[t.pcol[q] + 1]++;
     for (int J = 0; J < nco; J++) t.rrp[J + 1] += t.rrp[J];
@@ -867,14 +876,16 @@ static void csr_to_sell(int n, const std::vector<int32_t>& rp, const std::vector
     }
     S.col.assign(std::max(1, S.off[ns]), 0);
     S.val.assign(std::max(1, S.off[ns]), 0.0);
-    for (int i = 0; i < n; i++) {
-        const int sl = i >> 5, lane = i & 31, a = rp[i], len = rp[i + 1] - a;
-        for (int k = 0; k < S.w[sl]; k++) {
-            const int slot = S.off[sl] + 32 * k + lane;
-            S.col[slot] = len > 0 ? col[a + std::min(k, len - 1)] : 0;
-            S.val[slot] = k < len ? val[a + k] : 0.0;
+    host_parallel(n, 1 << 15, [&](int lo, int hi) {
+        for (int i = lo; i < hi; i++) {
+            const int sl = i >> 5, lane = i & 31, a = rp[i], len = rp[i + 1] - a;
+            for (int k = 0; k < S.w[sl]; k++) {
+                const int slot = S.off[sl] + 32 * k + lane;
+                S.col[slot] = len > 0 ? col[a + std::min(k, len - 1)] : 0;
+                S.val[slot] = k < len ? val[a + k] : 0.0;
+            }
         }
-    }
+    });
 }
 // Levels of at least kSellMinRows rows whose mean row length is at most kSellMaxMean run one
 // thread per row in sliced-ELL form; smaller levels (too few threads to fill 152 SMs: the
@@ -990,6 +1001,15 @@ int pc_setup(jfnk_ctx* c)
     MgState& S = mg_state(c);
     S.ready = false;
     if (c->opt.pc != JFNK_PC_MG) return JFNK_OK;
+    // phase times, printed to stderr when JFNK_VERBOSE is set
+    const bool verbose = getenv("JFNK_VERBOSE") != nullptr;
+    auto tp = std::chrono::steady_clock::now();
+    auto lap = [&](const char* what) {
+        if (!verbose) return;
+        const auto n = std::chrono::steady_clock::now();
+        fprintf(stderr, "[jfnk]   preconditioner: %-26s %8.1f ms\n", what, std::chrono::duration<double, std::milli>(n - tp).count());
+        tp = n;
+    };
     const DevMesh& m = c->dm;
     const Topology& t = c->topo;
     const int nc = m.nc;
@@ -1002,36 +1022,45 @@ int pc_setup(jfnk_ctx* c)
     // renumbering): rows by input index, columns ascending
     MgLevelHost L0;
     L0.n = nc;
-    // CSR by counting: the diagonal and one entry per internal face on each side, then each
-    // (short) row sorted by column
+    // CSR, one host thread per block of rows: the diagonal, then one entry per internal face of
+    // the cell in increasing face index (its owned faces merged with the faces it neighbours),
+    // then each (short) row sorted by column
     L0.rp.assign(nc + 1, 0);
-    for (int i = 0; i < nc; i++) L0.rp[i + 1] = 1;
-    for (int f = 0; f < m.ni; f++) { L0.rp[t.n2o[t.own[f]] + 1]++; L0.rp[t.n2o[t.nei[f]] + 1]++; }
-    for (int i = 0; i < nc; i++) L0.rp[i + 1] += L0.rp[i];
+    for (int i = 0; i < nc; i++) {
+        const int P = t.o2n[i];
+        L0.rp[i + 1] = L0.rp[i] + 1 + (t.fo_ptr[P + 1] - t.fo_ptr[P]) + (t.fn_ptr[P + 1] - t.fn_ptr[P]);
+    }
     L0.col.assign(L0.rp[nc], 0);
     L0.val.assign(L0.rp[nc], 0.0);
-    {
-        std::vector<int32_t> fill(L0.rp.begin(), L0.rp.end() - 1);
-        for (int P = 0; P < nc; P++) {
-            const int i = t.n2o[P];
-            L0.col[fill[i]] = i;
-            L0.val[fill[i]++] = -diag[P];
+    host_parallel(nc, 1 << 15, [&](int lo, int hi) {
+        for (int i = lo; i < hi; i++) {
+            const int P = t.o2n[i];
+            int q = L0.rp[i];
+            L0.col[q] = i;
+            L0.val[q++] = -diag[P];
+            int a = t.fo_ptr[P], b = t.fn_ptr[P];
+            const int ae = t.fo_ptr[P + 1], be = t.fn_ptr[P + 1];
+            while (a < ae || b < be) {
+                int f, other;
+                if (b >= be || (a < ae && a < t.fn_face[b])) { f = a++; other = t.nei[f]; }
+                else { f = t.fn_face[b++]; other = t.own[f]; }
+                L0.col[q] = t.n2o[other];
+                L0.val[q++] = -jc[f];
+            }
         }
-        for (int f = 0; f < m.ni; f++) {
-            const int a = t.n2o[t.own[f]], b = t.n2o[t.nei[f]];
-            L0.col[fill[a]] = b; L0.val[fill[a]++] = -jc[f];
-            L0.col[fill[b]] = a; L0.val[fill[b]++] = -jc[f];
-        }
-    }
-    for (int i = 0; i < nc; i++)  // insertion sort: a handful of entries per row
-        for (int q = L0.rp[i] + 1; q < L0.rp[i + 1]; q++) {
-            const int32_t cq = L0.col[q];
-            const double vq = L0.val[q];
-            int r = q - 1;
-            for (; r >= L0.rp[i] && L0.col[r] > cq; r--) { L0.col[r + 1] = L0.col[r]; L0.val[r + 1] = L0.val[r]; }
-            L0.col[r + 1] = cq;
-            L0.val[r + 1] = vq;
-        }
+    });
+    host_parallel(nc, 1 << 15, [&](int lo, int hi) {
+        for (int i = lo; i < hi; i++)  // insertion sort: a handful of entries per row
+            for (int q = L0.rp[i] + 1; q < L0.rp[i + 1]; q++) {
+                const int32_t cq = L0.col[q];
+                const double vq = L0.val[q];
+                int r = q - 1;
+                for (; r >= L0.rp[i] && L0.col[r] > cq; r--) { L0.col[r + 1] = L0.col[r]; L0.val[r + 1] = L0.val[r]; }
+                L0.col[r + 1] = cq;
+                L0.val[r + 1] = vq;
+            }
+    });
+    lap("fine-level matrix (host)");
     std::vector<MgLevelHost> lv;
     std::vector<double> inv;
     const auto t0 = std::chrono::steady_clock::now();
@@ -1051,6 +1080,7 @@ int pc_setup(jfnk_ctx* c)
         }
         inv.swap(p);
     }
+    tp = std::chrono::steady_clock::now();
     std::vector<HostTransfer> tr(lv.size());
     for (size_t l = 0; l + 1 < lv.size(); l++)
         make_transfer(lv[l].prp, lv[l].pcol, lv[l].pval, lv[l].n, lv[l + 1].n, l == 0 ? &t.n2o : nullptr, tr[l]);
@@ -1058,15 +1088,19 @@ int pc_setup(jfnk_ctx* c)
     for (int P = 0; P < nc; P++) adiag0[P] = -diag[P];
     // fine-level coefficient of every sliced-ELL neighbour slot
     std::vector<double> sc(std::max<size_t>(1, t.sell_nbr.size()), 0.0);
-    for (size_t q = 0; q < t.sell_nbr.size(); q++)
-        if (t.sell_nbr[q] >= 0 && t.sell_nbr[q] < nc) sc[q] = jc[t.sell_face[q]];
+    host_parallel((int)t.sell_nbr.size(), 1 << 18, [&](int lo, int hi) {
+        for (int q = lo; q < hi; q++)
+            if (t.sell_nbr[q] >= 0 && t.sell_nbr[q] < nc) sc[q] = jc[t.sell_face[q]];
+    });
     // the hierarchy in the precision the V-cycle runs in (a change of precision sets up again)
+    lap("transfers, slot coefficients");
     if (c->opt.precision == JFNK_PREC_MIXED) rc = mg_upload<float>(c, S.f, lv, inv, jc, sc, adiag0, tr);
     else rc = mg_upload<double>(c, S.d, lv, inv, jc, sc, adiag0, tr);
     if (rc) return rc;
     // batches: the problem of every row of every level.  Aggregates never join cells of two
     // problems (the problems share no face, so no coupling), so each coarse row inherits the
     // problem of the rows aggregated into it.
+    lap("upload (sliced ELL, CSR)");
     S.rprob.clear();
     S.rprob_host.clear();
     if (c->nprob > 1) {
@@ -1097,6 +1131,7 @@ int pc_setup(jfnk_ctx* c)
         if (getenv("JFNK_VERBOSE"))
             fprintf(stderr, "[jfnk] multigrid row -> problem maps: %s (%zu levels)\n", ok ? "built" : "not built", rp.size());
     }
+    lap("row -> problem maps");
     c->mg_coarse_n = lv.back().n;
     if (getenv("JFNK_VERBOSE")) {
         for (size_t l = 0; l < lv.size(); l++)

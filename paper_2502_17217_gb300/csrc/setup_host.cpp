@@ -45,6 +45,11 @@ static void parallel_blocks(int n, int grain, F&& f)
     for (auto& t : th) t.join();
 }
 
+void host_parallel(int n, int grain, const std::function<void(int, int)>& f)
+{
+    parallel_blocks(n, grain, [&](int lo, int hi, int) { f(lo, hi); });
+}
+
 // Sparse accumulator of one host thread over nco columns: entries stamped with the row being
 // formed, so it is cleared once per use, not once per row or block.
 struct SparseAcc {
@@ -60,39 +65,58 @@ struct SparseAcc {
     }
 };
 
-static std::vector<int32_t> rcm_order(int nc, const std::vector<int32_t>& aptr, const std::vector<int32_t>& adj)
+// Reverse Cuthill-McKee (Cuthill & McKee 1969; George 1971) of the cells [c0, c1), whose
+// neighbours all lie in the range: breadth-first search from a minimum-degree cell of each
+// component (lowest index among equals), visiting neighbours by increasing degree (then
+// index), and the order reversed.  Adjacency in CSR form: cell v's neighbours (cell indices)
+// are adj[ap[v - c0] .. ap[v - c0 + 1]); the order (cell indices) is written to out[0, c1 - c0).
+static void rcm_range(int c0, int c1, const int32_t* ap, const int32_t* adj, int32_t* out)
 {
-    // Reverse Cuthill-McKee (Cuthill & McKee 1969; George 1971): breadth-first search from a
-    // minimum-degree cell of each component, visiting neighbours by increasing degree (then
-    // index), and the final order reversed.  Adjacency in CSR form (aptr, adj).
-    std::vector<int32_t> deg(nc);
-    for (int i = 0; i < nc; i++) deg[i] = aptr[i + 1] - aptr[i];
-    std::vector<int32_t> cand(nc);
-    std::iota(cand.begin(), cand.end(), 0);
-    std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) { return deg[a] < deg[b]; });
-    std::vector<char> seen(nc, 0);
-    std::vector<int32_t> order;
-    order.reserve(nc);
-    std::vector<int32_t> nb;
+    const int n = c1 - c0;
+    if (n <= 0) return;
+    const int32_t* aptr = ap - c0;  // indexed by cell
+    auto deg = [&](int v) { return aptr[v + 1] - aptr[v]; };
+    // candidates by increasing degree, index order among equals (a counting sort)
+    int maxd = 0;
+    for (int v = c0; v < c1; v++) maxd = std::max(maxd, deg(v));
+    std::vector<int32_t> start(maxd + 2, 0), cand(n);
+    for (int v = c0; v < c1; v++) start[deg(v) + 1]++;
+    for (int d = 0; d <= maxd; d++) start[d + 1] += start[d];
+    for (int v = c0; v < c1; v++) cand[start[deg(v)]++] = v;
+    std::vector<char> seen(n, 0);
+    int tail = 0;  // the BFS order is built in out[0, tail)
+    int32_t nb[64];
+    std::vector<int32_t> nbv;
     for (int s : cand) {
-        if (seen[s]) continue;
-        size_t head = order.size();
-        order.push_back(s);
-        seen[s] = 1;
-        while (head < order.size()) {
-            int v = order[head++];
-            nb.clear();
+        if (seen[s - c0]) continue;
+        int head = tail;
+        out[tail++] = s;
+        seen[s - c0] = 1;
+        while (head < tail) {
+            const int v = out[head++];
+            const int k = aptr[v + 1] - aptr[v];
+            int32_t* list = nb;
+            if (k > 64) {
+                nbv.resize(k);
+                list = nbv.data();
+            }
+            int m = 0;
             for (int q = aptr[v]; q < aptr[v + 1]; q++)
-                if (!seen[adj[q]]) nb.push_back(adj[q]);
-            std::sort(nb.begin(), nb.end(), [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; });
-            for (int w : nb) {
-                seen[w] = 1;
-                order.push_back(w);
+                if (!seen[adj[q] - c0]) list[m++] = adj[q];
+            // insertion sort by (degree, index): a handful of neighbours
+            for (int a = 1; a < m; a++) {
+                const int w = list[a], dw = deg(w);
+                int b = a - 1;
+                for (; b >= 0 && (deg(list[b]) > dw || (deg(list[b]) == dw && list[b] > w)); b--) list[b + 1] = list[b];
+                list[b + 1] = w;
+            }
+            for (int a = 0; a < m; a++) {
+                seen[list[a] - c0] = 1;
+                out[tail++] = list[a];
             }
         }
     }
-    std::reverse(order.begin(), order.end());
-    return order;
+    std::reverse(out, out + n);
 }
 
 // phase times of the set-up, printed to stderr when JFNK_VERBOSE is set
@@ -114,57 +138,127 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     PhaseClock clk;
     t = Topology();
     t.nc = nc;
+    // groups that are contiguous, increasing ranges of cells, each with a contiguous range of
+    // the internal faces and no face between two groups (the problems of a batch), are
+    // renumbered and have their faces ordered each on its own host thread; the results are
+    // those of single passes over all cells and faces
+    std::vector<int32_t> gfirst, gface;
+    bool grouped = group != nullptr;
+    {
+        if (grouped) {
+            for (int i = 0; i < nc && grouped; i++) {
+                const int g = (*group)[i];
+                if (i == 0 || g != (*group)[i - 1]) {
+                    grouped = i == 0 || g > (*group)[i - 1];
+                    gfirst.push_back(i);
+                }
+            }
+            gfirst.push_back(nc);
+            // face range of each group: faces in group order, each inside its group
+            const int ng = (int)gfirst.size() - 1;
+            gface.assign(ng + 1, 0);
+            int g = 0;
+            for (int f = 0; f < ni && grouped; f++) {
+                const int a = hm.own[f], b = hm.nei[f];
+                while (g < ng && a >= gfirst[g + 1]) gface[++g] = f;
+                grouped = a >= gfirst[g] && a < gfirst[g + 1] && b >= gfirst[g] && b < gfirst[g + 1];
+            }
+            while (g < ng) gface[++g] = ni;
+        }
+    }
     // --- cell numbering
     if (rcm) {
-        // cell adjacency in CSR form, each cell's neighbours in face order
-        std::vector<int32_t> aptr(nc + 1, 0), adj(2 * (size_t)ni);
-        for (int f = 0; f < ni; f++) { aptr[hm.own[f] + 1]++; aptr[hm.nei[f] + 1]++; }
-        for (int i = 0; i < nc; i++) aptr[i + 1] += aptr[i];
-        std::vector<int32_t> fill(aptr.begin(), aptr.end() - 1);
-        for (int f = 0; f < ni; f++) {
-            adj[fill[hm.own[f]]++] = hm.nei[f];
-            adj[fill[hm.nei[f]]++] = hm.own[f];
+        t.n2o.resize(nc);
+        // cell adjacency in CSR form over cells [c0, c1) from faces [f0, f1)
+        auto adjacency = [&](int c0, int c1, int f0, int f1, std::vector<int32_t>& ap, std::vector<int32_t>& adj) {
+            ap.assign(c1 - c0 + 1, 0);
+            adj.resize(2 * (size_t)(f1 - f0));
+            for (int f = f0; f < f1; f++) { ap[hm.own[f] - c0 + 1]++; ap[hm.nei[f] - c0 + 1]++; }
+            for (int i = 0; i < c1 - c0; i++) ap[i + 1] += ap[i];
+            std::vector<int32_t> fill(ap.begin(), ap.end() - 1);
+            for (int f = f0; f < f1; f++) {
+                adj[fill[hm.own[f] - c0]++] = hm.nei[f];
+                adj[fill[hm.nei[f] - c0]++] = hm.own[f];
+            }
+        };
+        if (grouped) {
+            const int ng = (int)gfirst.size() - 1;
+            parallel_blocks(ng, 1, [&](int lo, int hi, int) {
+                std::vector<int32_t> ap, adj;
+                for (int g = lo; g < hi; g++) {
+                    adjacency(gfirst[g], gfirst[g + 1], gface[g], gface[g + 1], ap, adj);
+                    rcm_range(gfirst[g], gfirst[g + 1], ap.data(), adj.data(), t.n2o.data() + gfirst[g]);
+                }
+            });
+        } else {
+            std::vector<int32_t> ap, adj;
+            adjacency(0, nc, 0, ni, ap, adj);
+            rcm_range(0, nc, ap.data(), adj.data(), t.n2o.data());
+            if (group)
+                std::stable_sort(t.n2o.begin(), t.n2o.end(), [&](int a, int b) { return (*group)[a] < (*group)[b]; });
         }
-        t.n2o = rcm_order(nc, aptr, adj);
     } else {
         t.n2o.resize(nc);
         std::iota(t.n2o.begin(), t.n2o.end(), 0);
+        if (group)
+            std::stable_sort(t.n2o.begin(), t.n2o.end(), [&](int a, int b) { return (*group)[a] < (*group)[b]; });
     }
-    if (group)
-        std::stable_sort(t.n2o.begin(), t.n2o.end(), [&](int a, int b) { return (*group)[a] < (*group)[b]; });
     t.o2n.assign(nc, -1);
     for (int i = 0; i < nc; i++) t.o2n[t.n2o[i]] = i;
     clk.lap("cell numbering");
     // --- face order
     struct FK { int32_t a, b, src; uint8_t flip; };
     std::vector<FK> in(ni);
-    for (int f = 0; f < ni; f++) {
-        int a = t.o2n[hm.own[f]], b = t.o2n[hm.nei[f]];
-        uint8_t flip = 0;
-        if (a > b) { std::swap(a, b); flip = 1; }
-        in[f] = {a, b, f, flip};
-    }
-    {
-        // order by (a, b, src): bucket by a (counting), then each short bucket by (b, src)
-        std::vector<int32_t> cnt(nc + 1, 0);
-        for (const FK& k : in) cnt[k.a + 1]++;
-        for (int i = 0; i < nc; i++) cnt[i + 1] += cnt[i];
-        std::vector<FK> out(ni);
+    parallel_blocks(ni, 1 << 16, [&](int lo, int hi, int) {
+        for (int f = lo; f < hi; f++) {
+            int a = t.o2n[hm.own[f]], b = t.o2n[hm.nei[f]];
+            uint8_t flip = 0;
+            if (a > b) { std::swap(a, b); flip = 1; }
+            in[f] = {a, b, f, flip};
+        }
+    });
+    // stable counting sort of v[f0, f1) by key a in [c0, c1) (src ascending within a key, as
+    // stored); with by_b, each key's short bucket then by b (insertion sort, stable)
+    auto sort_range = [](std::vector<FK>& v, int f0, int f1, int c0, int c1, bool by_b, std::vector<FK>& tmp) {
+        std::vector<int32_t> cnt(c1 - c0 + 1, 0);
+        for (int f = f0; f < f1; f++) cnt[v[f].a - c0 + 1]++;
+        for (int i = 0; i < c1 - c0; i++) cnt[i + 1] += cnt[i];
+        tmp.resize(f1 - f0);
         std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
-        for (const FK& k : in) out[fill[k.a]++] = k;  // stable: src ascending within a bucket
-        for (int i = 0; i < nc; i++)
-            std::sort(out.begin() + cnt[i], out.begin() + cnt[i + 1],
-                      [](const FK& x, const FK& y) { return x.b != y.b ? x.b < y.b : x.src < y.src; });
-        in.swap(out);
+        for (int f = f0; f < f1; f++) tmp[fill[v[f].a - c0]++] = v[f];
+        std::copy(tmp.begin(), tmp.end(), v.begin() + f0);
+        if (by_b)
+            for (int i = 0; i < c1 - c0; i++)
+                for (int q = f0 + cnt[i] + 1; q < f0 + cnt[i + 1]; q++) {
+                    const FK k = v[q];
+                    int r = q - 1;
+                    for (; r >= f0 + cnt[i] && v[r].b > k.b; r--) v[r + 1] = v[r];
+                    v[r + 1] = k;
+                }
+    };
+    // internal faces by (a, b, src); a group's faces keep their range (the new cell numbers of
+    // a group are the group's range)
+    if (grouped) {
+        const int ng = (int)gfirst.size() - 1;
+        parallel_blocks(ng, 1, [&](int lo, int hi, int) {
+            std::vector<FK> tmp;
+            for (int g = lo; g < hi; g++) sort_range(in, gface[g], gface[g + 1], gfirst[g], gfirst[g + 1], true, tmp);
+        });
+    } else {
+        std::vector<FK> tmp;
+        sort_range(in, 0, ni, 0, nc, true, tmp);
     }
+    auto by_owner = [&](std::vector<FK>& v) {
+        std::vector<FK> tmp;
+        sort_range(v, 0, (int)v.size(), 0, nc, false, tmp);
+    };
     std::vector<FK> bd[4];  // disp, symm, trac, empty
     for (int f = ni; f < nf; f++) {
         int bt = hm.btype[f - ni];
         int cls = bt == JFNK_BC_DISP ? 0 : (bt == JFNK_BC_SYMM ? 1 : (bt == JFNK_BC_TRAC ? 2 : 3));
         bd[cls].push_back({t.o2n[hm.own[f]], -1, f, 0});
     }
-    for (auto& v : bd)
-        std::sort(v.begin(), v.end(), [](const FK& x, const FK& y) { return x.a != y.a ? x.a < y.a : x.src < y.src; });
+    for (auto& v : bd) by_owner(v);  // (a, src): pushed in src order
     clk.lap("face order");
     t.ni = ni;
     t.nd = (int)bd[0].size();
@@ -172,30 +266,44 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     t.nt = (int)bd[2].size();
     t.ne = (int)bd[3].size();
     t.nf = nf;
-    std::vector<FK> all;
-    all.reserve(nf);
-    all.insert(all.end(), in.begin(), in.end());
-    for (auto& v : bd) all.insert(all.end(), v.begin(), v.end());
+    // face f of the new order: the internal faces, then the boundary classes
+    std::vector<const FK*> cls_base(4);
+    std::vector<int> cls_first(5, ni);
+    for (int c = 0; c < 4; c++) {
+        cls_base[c] = bd[c].data();
+        cls_first[c + 1] = cls_first[c] + (int)bd[c].size();
+    }
+    auto key = [&](int f) -> const FK& {
+        if (f < ni) return in[f];
+        int c = 0;
+        while (f >= cls_first[c + 1]) c++;
+        return cls_base[c][f - cls_first[c]];
+    };
     t.face_src.resize(nf);
     t.face_flip.resize(nf);
     t.own.resize(nf);
     t.nei.resize(ni);
     t.fptr.assign(nf + 1, 0);
-    t.fpts.clear();
-    t.fpts.reserve(hm.fpts.size());
     for (int f = 0; f < nf; f++) {
-        const FK& k = all[f];
-        t.face_src[f] = k.src;
-        t.face_flip[f] = k.flip;
-        t.own[f] = k.a;
-        if (f < ni) t.nei[f] = k.b;
-        int s0 = hm.fptr[k.src], s1 = hm.fptr[k.src + 1];
-        if (!k.flip)
-            for (int q = s0; q < s1; q++) t.fpts.push_back(hm.fpts[q]);
-        else
-            for (int q = s1 - 1; q >= s0; q--) t.fpts.push_back(hm.fpts[q]);
-        t.fptr[f + 1] = (int32_t)t.fpts.size();
+        const FK& k = key(f);
+        t.fptr[f + 1] = t.fptr[f] + (hm.fptr[k.src + 1] - hm.fptr[k.src]);
     }
+    t.fpts.resize(t.fptr[nf]);
+    parallel_blocks(nf, 1 << 16, [&](int lo, int hi, int) {
+        for (int f = lo; f < hi; f++) {
+            const FK& k = key(f);
+            t.face_src[f] = k.src;
+            t.face_flip[f] = k.flip;
+            t.own[f] = k.a;
+            if (f < ni) t.nei[f] = k.b;
+            const int s0 = hm.fptr[k.src], s1 = hm.fptr[k.src + 1];
+            int32_t* o = t.fpts.data() + t.fptr[f];
+            if (!k.flip)
+                for (int q = s0; q < s1; q++) *o++ = hm.fpts[q];
+            else
+                for (int q = s1 - 1; q >= s0; q--) *o++ = hm.fpts[q];
+        }
+    });
     int bw = 0;
     for (int f = 0; f < ni; f++) bw = std::max(bw, t.nei[f] - t.own[f]);
     t.bandwidth = bw;
@@ -220,21 +328,31 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
         std::vector<int32_t> fill(t.fn_ptr.begin(), t.fn_ptr.end() - 1);
         for (int f = 0; f < ni; f++) t.fn_face[fill[t.nei[f]]++] = f;
     }
-    // all faces of each cell (geometry): owner side f, neighbour side ~f, by face index
+    // all faces of each cell (geometry): owner side f, neighbour side ~f, by face index: the
+    // cell's owned and neighbouring internal faces merged by index, then its boundary faces
+    // (each class owner-sorted, classes in face order)
+    std::vector<int32_t> fe_ptr;
+    ranges(ni + t.nd + t.nsy + t.nt, nf, fe_ptr);
     t.ca_ptr.assign(nc + 1, 0);
-    for (int f = 0; f < nf; f++) {
-        t.ca_ptr[t.own[f] + 1]++;
-        if (f < ni) t.ca_ptr[t.nei[f] + 1]++;
-    }
-    for (int P = 0; P < nc; P++) t.ca_ptr[P + 1] += t.ca_ptr[P];
+    for (int P = 0; P < nc; P++)
+        t.ca_ptr[P + 1] = t.ca_ptr[P] + (t.fo_ptr[P + 1] - t.fo_ptr[P]) + (t.fn_ptr[P + 1] - t.fn_ptr[P]) +
+                          (t.fd_ptr[P + 1] - t.fd_ptr[P]) + (t.fs_ptr[P + 1] - t.fs_ptr[P]) +
+                          (t.ft_ptr[P + 1] - t.ft_ptr[P]) + (fe_ptr[P + 1] - fe_ptr[P]);
     t.ca_face.resize(t.ca_ptr[nc]);
-    {
-        std::vector<int32_t> fill(t.ca_ptr.begin(), t.ca_ptr.end() - 1);
-        for (int f = 0; f < nf; f++) {
-            t.ca_face[fill[t.own[f]]++] = f;
-            if (f < ni) t.ca_face[fill[t.nei[f]]++] = ~f;
+    parallel_blocks(nc, 1 << 15, [&](int lo, int hi, int) {
+        for (int P = lo; P < hi; P++) {
+            int32_t* o = t.ca_face.data() + t.ca_ptr[P];
+            int a = t.fo_ptr[P], b = t.fn_ptr[P];
+            const int ae = t.fo_ptr[P + 1], be = t.fn_ptr[P + 1];
+            while (a < ae || b < be) {
+                if (b >= be || (a < ae && a < t.fn_face[b])) *o++ = a++;
+                else *o++ = ~t.fn_face[b++];
+            }
+            const std::vector<int32_t>* bp[4] = {&t.fd_ptr, &t.fs_ptr, &t.ft_ptr, &fe_ptr};
+            for (const auto* p : bp)
+                for (int f = (*p)[P]; f < (*p)[P + 1]; f++) *o++ = f;
         }
-    }
+    });
     clk.lap("cell face lists");
     // sliced ELL of internal neighbours (32 cells per slice), faces in increasing index
     std::vector<int32_t> cnt(nc, 0);
@@ -255,28 +373,30 @@ std::string build_topology(const HostMesh& hm, bool rcm, Topology& t, const std:
     t.n_slots = off;
     t.sell_nbr.assign(off, -1);
     t.sell_face.assign(off, -1);
-    std::vector<int32_t> k(nc, 0);
     // walk each cell's internal faces in increasing face index: merge owner and neighbour lists
-    for (int P = 0; P < nc; P++) {
-        int a = t.fo_ptr[P], ae = t.fo_ptr[P + 1];
-        int b = t.fn_ptr[P], be = t.fn_ptr[P + 1];
-        int s = P / 32, lane = P % 32;
-        while (a < ae || b < be) {
-            int f, N;
-            if (b >= be || (a < ae && a < t.fn_face[b])) { f = a; N = t.nei[a]; a++; }
-            else { f = t.fn_face[b]; N = t.own[f]; b++; }
-            int slot = t.sell_off[s] + 32 * k[P] + lane;
-            t.sell_nbr[slot] = N;
-            t.sell_face[slot] = f;
-            k[P]++;
+    parallel_blocks(nc, 1 << 15, [&](int lo, int hi, int) {
+        for (int P = lo; P < hi; P++) {
+            int a = t.fo_ptr[P], ae = t.fo_ptr[P + 1];
+            int b = t.fn_ptr[P], be = t.fn_ptr[P + 1];
+            const int s = P / 32, lane = P % 32;
+            int k = 0;
+            while (a < ae || b < be) {
+                int f, N;
+                if (b >= be || (a < ae && a < t.fn_face[b])) { f = a; N = t.nei[a]; a++; }
+                else { f = t.fn_face[b]; N = t.own[f]; b++; }
+                const int slot = t.sell_off[s] + 32 * k + lane;
+                t.sell_nbr[slot] = N;
+                t.sell_face[slot] = f;
+                k++;
+            }
+            for (int f = t.fs_ptr[P]; f < t.fs_ptr[P + 1]; f++) {  // mirror neighbours
+                const int slot = t.sell_off[s] + 32 * k + lane;
+                t.sell_nbr[slot] = nc + (f - ni - t.nd);
+                t.sell_face[slot] = f;
+                k++;
+            }
         }
-        for (int f = t.fs_ptr[P]; f < t.fs_ptr[P + 1]; f++) {  // mirror neighbours
-            int slot = t.sell_off[s] + 32 * k[P] + lane;
-            t.sell_nbr[slot] = nc + (f - ni - t.nd);
-            t.sell_face[slot] = f;
-            k[P]++;
-        }
-    }
+    });
     // boundary values in the new face order
     t.bval.assign((size_t)(t.nd + t.nsy + t.nt) * 3, 0.0);
     for (int f = ni; f < ni + t.nd + t.nsy + t.nt; f++)
@@ -301,13 +421,15 @@ static int aggregate(const MgLevelHost& L, double theta, std::vector<int32_t>& a
     const int n = L.n;
     agg.assign(n, -1);
     std::vector<char> strong(L.col.size(), 0);
-    for (int i = 0; i < n; i++) {
-        double mx = 0;
-        for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
-            if (L.col[q] != i) mx = std::max(mx, -L.val[q]);
-        for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
-            strong[q] = (L.col[q] != i && mx > 0 && -L.val[q] >= theta * mx * (1.0 - tie));
-    }
+    parallel_blocks(n, 1 << 14, [&](int lo, int hi, int) {
+        for (int i = lo; i < hi; i++) {
+            double mx = 0;
+            for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
+                if (L.col[q] != i) mx = std::max(mx, -L.val[q]);
+            for (int q = L.rp[i]; q < L.rp[i + 1]; q++)
+                strong[q] = (L.col[q] != i && mx > 0 && -L.val[q] >= theta * mx * (1.0 - tie));
+        }
+    });
     int na = 0;
     for (int i = 0; i < n; i++) {
         if (agg[i] >= 0) continue;
@@ -360,40 +482,45 @@ static void smoothed_prolongation(const MgLevelHost& F, const std::vector<int32_
         rho = std::max(rho, s / diag[i]);
     }
     const double omega = 4.0 / (3.0 * rho);
-    // rows in blocks, each block into its own arrays, then concatenated in row order
-    const int grain = 4096, nb = (n + grain - 1) / grain;
-    std::vector<std::vector<int32_t>> bcol(nb);
-    std::vector<std::vector<double>> bval(nb);
-    std::vector<int32_t> len(n, 0);
+    // row i of P: the aggregates of i and of its neighbours, ascending, with their weights; two
+    // passes over blocks of rows (the entry counts, then the entries at their final places),
+    // so that no thread grows arrays of its own
+    const int grain = 4096;
     std::vector<SparseAcc> scratch(host_threads());
-    parallel_blocks(n, grain, [&](int lo, int hi, int tid) {
-        SparseAcc& S = scratch[tid];
-        S.init(nco);
+    auto row = [&](SparseAcc& S, int i) {
         auto& acc = S.acc;
         auto& mark = S.mark;
         auto& list = S.list;
-        auto& oc = bcol[lo / grain];
-        auto& ov = bval[lo / grain];
+        list.clear();
+        mark[agg[i]] = i; acc[agg[i]] = 1.0; list.push_back(agg[i]);
+        for (int q = F.rp[i]; q < F.rp[i + 1]; q++) {
+            const int J = agg[F.col[q]];
+            if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list.push_back(J); }
+            acc[J] -= omega * F.val[q] / diag[i];
+        }
+        std::sort(list.begin(), list.end());
+    };
+    parallel_blocks(n, grain, [&](int lo, int hi, int tid) {
+        SparseAcc& S = scratch[tid];
+        S.init(nco);
         for (int i = lo; i < hi; i++) {
-            list.clear();
-            mark[agg[i]] = i; acc[agg[i]] = 1.0; list.push_back(agg[i]);
-            for (int q = F.rp[i]; q < F.rp[i + 1]; q++) {
-                const int J = agg[F.col[q]];
-                if (mark[J] != i) { mark[J] = i; acc[J] = 0.0; list.push_back(J); }
-                acc[J] -= omega * F.val[q] / diag[i];
-            }
-            std::sort(list.begin(), list.end());
-            for (int J : list) { oc.push_back(J); ov.push_back(acc[J]); }
-            len[i] = (int32_t)list.size();
+            row(S, i);
+            prp[i + 1] = (int32_t)S.list.size();
         }
     });
-    for (int i = 0; i < n; i++) prp[i + 1] = prp[i] + len[i];
-    pcol.reserve(prp[n]);
-    pval.reserve(prp[n]);
-    for (int b = 0; b < nb; b++) {
-        pcol.insert(pcol.end(), bcol[b].begin(), bcol[b].end());
-        pval.insert(pval.end(), bval[b].begin(), bval[b].end());
-    }
+    for (int i = 0; i < n; i++) prp[i + 1] += prp[i];
+    pcol.resize(prp[n]);
+    pval.resize(prp[n]);
+    for (auto& S : scratch) S.acc.clear(), S.mark.clear();  // stamps restart from a clean state
+    parallel_blocks(n, grain, [&](int lo, int hi, int tid) {
+        SparseAcc& S = scratch[tid];
+        S.init(nco);
+        for (int i = lo; i < hi; i++) {
+            row(S, i);
+            int o = prp[i];
+            for (int J : S.list) { pcol[o] = J; pval[o] = S.acc[J]; o++; }
+        }
+    });
 }
 
 // A_c = P^T A P, rows with ascending columns
