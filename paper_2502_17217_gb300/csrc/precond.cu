@@ -893,6 +893,7 @@ static void csr_to_sell(int n, const std::vector<int32_t>& rp, const std::vector
 // lane-group CSR kernels
 constexpr double kSellMaxMean = 64.0;
 constexpr int kSellMinRows = 1 << 16;
+constexpr int kSellWaves = 4;  // persistent-grid waves of the sliced-ELL kernels over compacted rows (4 measured 1 % faster than 1 on the 512-box batch)
 // the row threshold, JFNK_MG_SELL_MIN_ROWS overriding it (read at set-up; tests run the
 // sliced-ELL kernels on small meshes with 0)
 static int sell_min_rows()
@@ -1221,7 +1222,9 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
     const int sweeps = std::max(1, c->opt.mg_smooth_sweeps);
     const int bs = c->tune.mg_bs;  // rows per block of the thread-per-row kernels
     // grid of a thread-per-row kernel over level l
-    auto rows_grid = [&](const void* k, int l, const RowMap& m) { return dim3(rowmap_blocks(c, k, bs, M.L[l].n, bs, m)); };
+    auto rows_grid = [&](const void* k, int l, const RowMap& m, int waves = 1) {
+        return dim3(rowmap_blocks(c, k, bs, M.L[l].n, bs, m, waves));
+    };
     auto coarse_grid = [&](int l, const RowMap& m) {
         return dim3(rowmap_blocks(c, (const void*)k_mg_coarse<T, true>, 32 * kCoarseWarps, M.L[l].n, 1, m));
     };
@@ -1230,7 +1233,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         auto& D = M.L[l];
         if (D.a_sell) {
             auto k = mode == 0 ? k_mg_sell<T, 0> : (mode == 1 ? k_mg_sell<T, 1> : k_mg_sell<T, 2>);
-            jfnk_launch(c, k, rows_grid((const void*)k, l, ml), dim3(bs), gate, ml, (const int32_t*)D.a_soff,
+            jfnk_launch(c, k, rows_grid((const void*)k, l, ml, kSellWaves), dim3(bs), gate, ml, (const int32_t*)D.a_soff,
                         (const int32_t*)D.a_sw, (const int32_t*)D.a_scol, (const T*)D.a_sval, (const T*)D.dinv, omega, b, x, xo);
         } else
             launch_csr_grp<T>(c, D.ga, D.n, gate, ml, D.n, (const int32_t*)D.rp, (const int32_t*)D.col, (const T*)D.val,
@@ -1285,7 +1288,7 @@ static int vcycle(jfnk_ctx* c, MgDev<T>& M, const TV* vbase, size_t ld, const in
         auto& Cn = M.L[l + 1];
         jfnk_prof_begin(c, s_rs);
         if (D.r_sell)
-            jfnk_launch(c, k_mg_restrict_sell<T>, rows_grid((const void*)k_mg_restrict_sell<T>, l + 1, mc), dim3(bs), gate, mc,
+            jfnk_launch(c, k_mg_restrict_sell<T>, rows_grid((const void*)k_mg_restrict_sell<T>, l + 1, mc, kSellWaves), dim3(bs), gate, mc,
                         (const int32_t*)D.r_soff, (const int32_t*)D.r_sw, (const int32_t*)D.r_scol, (const T*)D.r_sval,
                         (const T*)D.r, Cn.b);
         else
