@@ -13,9 +13,12 @@
 // CUDA events over a few residual evaluations (V-cycles) after a warm-up, and keeps the
 // fastest.  The arithmetic of every kernel is the same for every shape (one thread per cell
 // or face, fixed summation order), so the choice changes timing only, never results.
+// A batch's passes run over compacted row maps on persistent grids, so a batch is timed that
+// way, with every problem taking part (the problems' flags are put back afterwards).
 // Choices are cached per (device, mesh sizes, law mix, preconditioner, precision) so that
 // contexts set up for the same mesh shape (a serving loop) do not tune again.  Meshes below
 // kTuneMinCells keep the defaults: their kernels are launch-bound and the timings noise.
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -98,9 +101,25 @@ int autotune(jfnk_ctx* c)
     c->prof.enabled = false;
     c->cur = c->stream;
     const int64_t launches = c->launches;
-    auto res = [&]() { return residual_bufs(c, c->u, c->R, OUT_R, nullptr, c->G, c->T, c->F, c->Fn); };
+    // a batch: every problem takes part in the timed passes (flags `active` and `done` of each
+    // problem, zero at set-up, set here and put back at the end)
+    const bool mapped = c->rmaps != nullptr && c->ph != nullptr;
+    auto set_flags = [&](int active) -> int {
+        for (int p = 0; p < c->nprob; p++) {
+            c->ph[p].active = active;
+            c->ph[p].done = 0;
+        }
+        for (size_t off : {offsetof(ProbDev, active), offsetof(ProbDev, done)})
+            JF_CUDA(c, cudaMemcpy2DAsync((char*)c->pd + off, sizeof(ProbDev), (const char*)c->ph + off, sizeof(ProbDev),
+                                         sizeof(int), c->nprob, cudaMemcpyHostToDevice, c->cur));
+        JF_CUDA(c, cudaStreamSynchronize(c->cur));
+        return JFNK_OK;
+    };
+    const int skip = mapped ? SKIP_INACTIVE : SKIP_NONE;
+    auto res = [&]() { return residual_bufs(c, c->u, c->R, OUT_R, nullptr, c->G, c->T, c->F, c->Fn, nullptr, skip); };
     Tuning& t = c->tune;
     int rc = sync_load(c);
+    if (!rc && mapped) rc = set_flags(1);
     // coordinate descent: each parameter over its candidates, the others held
     auto pick = [&](int* field, const int* cand, int n) {
         const int keep = *field;
@@ -141,11 +160,15 @@ int autotune(jfnk_ctx* c)
         int arg = keep;
         for (int i = 0; i < 3 && !rc; i++) {
             t.mg_bs = m_c[i];
-            const float ms = time_it(c, [&]() { return pc_apply_any(c, JFNK_PC_MG, c->R, 0, c->z, nullptr); });
+            const float ms = time_it(c, [&]() { return pc_apply_any(c, JFNK_PC_MG, c->R, 0, c->z, nullptr, skip); });
             if (ms < -1.5f) { rc = jfnk_cuda_fail(c, cudaGetLastError(), "autotune"); break; }
             if (ms >= 0.f && (best < 0.f || ms < best)) { best = ms; arg = m_c[i]; }
         }
         t.mg_bs = rc ? keep : arg;
+    }
+    if (mapped) {
+        const int rc2 = set_flags(0);
+        if (!rc) rc = rc2;
     }
     c->prof.enabled = prof;
     c->launches = launches;  // tuning launches are not the caller's work
