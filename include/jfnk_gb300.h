@@ -27,6 +27,14 @@
  *    share device scratch buffers).  Distinct contexts are independent.
  *  - Host arrays passed to set-up calls are caller-owned and copied; they may be freed on
  *    return.  The context owns every device allocation it makes.
+ *  - Environment variables (defaults in brackets): JFNK_VERBOSE [unset] prints the set-up's
+ *    phase times to stderr.  Read when a context is created, changing no bit of any result:
+ *    JFNK_SKIP_DONE [1] (0: a batch's passes evaluate every problem's rows, also those of
+ *    problems whose Krylov cycle is done) and JFNK_PDL [0] (1: programmatic dependent launch
+ *    of the hot-path kernels).  Read at set-up: JFNK_MG_SELL_MIN_ROWS [65536] (coarse
+ *    multigrid levels of at least this many rows, and rows of at most 64 entries, are stored
+ *    in sliced-ELL form and applied one thread per row, smaller levels as CSR by lane groups;
+ *    the two sum a row's entries in different orders, so the FP32 V-cycle's rounding differs).
  */
 #ifndef JFNK_GB300_H
 #define JFNK_GB300_H
