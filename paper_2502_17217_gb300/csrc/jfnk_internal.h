@@ -158,11 +158,12 @@ struct SegSlot {
 };
 
 #ifdef __CUDACC__
-// Rows (cells, the owners of faces, multigrid rows) of the problems that sit out the current
-// Arnoldi iteration of a batch: the problem of each row and the per-problem flags.  A problem
-// sits out when it left the Newton iteration or finished its Krylov cycle; its rows are
-// neither read nor written.  prob == nullptr skips nothing (single problems, and every pass
-// outside the batch's Arnoldi iteration).
+// Whether row i (of a multigrid level) belongs to a problem that sits out the current pass of
+// a batch: the problem of each row and the per-problem flags.  A problem sits out when it left
+// the Newton iteration or (inside the Arnoldi iteration) finished its Krylov cycle.  The
+// batch's coarse solve uses it to zero the columns of such problems (their rows hold values of
+// an earlier cycle); which rows the kernels visit is the row maps' business (RowMap below).
+// prob == nullptr: no problem sits out.
 struct ProbSkip {
     const int32_t* prob;
     const ProbDev* pd;
