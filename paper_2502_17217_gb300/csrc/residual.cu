@@ -414,6 +414,40 @@ __global__ void __launch_bounds__(BS) k_flux(const int* __restrict__ gate, int n
 // component coalesce: three times the threads of a per-cell pass with a third of the dependent
 // loads each (the pass is latency-bound).  Each component's sum is taken in the same order
 // as before: owner faces, neighbour faces, displacement faces, symmetry faces.
+// sums of one cell for K components: the face lists are read once for all of them, each
+// component keeps its own summation order (body force, owner faces, neighbour faces,
+// displacement faces, symmetry faces, inertia)
+template <int K>
+__device__ __forceinline__ void finish_cell(int P, int nc, int nflux, int ni, const int32_t* __restrict__ fo_ptr,
+                                            const int32_t* __restrict__ fn_ptr, const double* __restrict__ Fn,
+                                            const int32_t* __restrict__ fd_ptr, const int32_t* __restrict__ fs_ptr,
+                                            const double* __restrict__ F, const double* __restrict__ b0, double load,
+                                            const double* __restrict__ u, const double* __restrict__ vol,
+                                            const double* __restrict__ rc, double mk, double* r)
+{
+#pragma unroll
+    for (int k = 0; k < K; k++) r[k] = load * b0[(size_t)k * nc + P];
+    const int o0 = fo_ptr[P], o1 = fo_ptr[P + 1], n0 = fn_ptr[P], n1 = fn_ptr[P + 1];
+    const int d0 = fd_ptr[P], d1 = fd_ptr[P + 1], s0 = fs_ptr[P], s1 = fs_ptr[P + 1];
+    for (int f = o0; f < o1; f++)
+#pragma unroll
+        for (int k = 0; k < K; k++) r[k] += F[(size_t)k * nflux + f];
+    for (int q = n0; q < n1; q++)
+#pragma unroll
+        for (int k = 0; k < K; k++) r[k] -= Fn[(size_t)k * ni + q];
+    for (int f = d0; f < d1; f++)
+#pragma unroll
+        for (int k = 0; k < K; k++) r[k] += F[(size_t)k * nflux + f];
+    for (int f = s0; f < s1; f++)
+#pragma unroll
+        for (int k = 0; k < K; k++) r[k] += F[(size_t)k * nflux + f];
+    if (rc) {
+        const double V = vol[P];
+#pragma unroll
+        for (int k = 0; k < K; k++) r[k] -= V * fma(mk, u[(size_t)k * nc + P], rc[(size_t)k * nc + P]);
+    }
+}
+
 __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int dim, const int32_t* __restrict__ fo_ptr,
                                                 const int32_t* __restrict__ fn_ptr, const double* __restrict__ Fn,
                                                 const int32_t* __restrict__ fd_ptr, const int32_t* __restrict__ fs_ptr,
@@ -427,34 +461,29 @@ __global__ void __launch_bounds__(512) k_finish(int nc, int nflux, int ni, int d
 {
     JF_PDL_ENTRY();
     if (gate && *gate) return;
-    // (component, cell) pairs over the row map's cells, component-major
+    const double load = *load_dev;
+    // one cell per thread, all components, over the row map's cells in warp-uniform rounds
     const int tot = rm.total();
-    const int64_t n3 = 3 * (int64_t)tot;
-    for (int64_t tw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); tw < n3; tw += (int64_t)gridDim.x * blockDim.x) {
-        // warp-uniform rounds; a warp that straddles two components finds the rows of the
-        // second by bisection
-        const int64_t t = tw + (threadIdx.x & 31u);
-        const int k = (int)(t / tot), kw = (int)(tw / tot);
-        const int P = warp_row(rm, (int)(t - (int64_t)k * tot), (int)(tw - (int64_t)kw * tot), tot);
-        if (t >= n3) continue;
-        const size_t e = (size_t)k * nc + P;
-        if (dim == 2 && k == 2) {
-            out[e] = 0.0;
-            continue;
+    for (int64_t tw = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); tw < tot; tw += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)tw + (int)(threadIdx.x & 31u);
+        const int P = warp_row(rm, v, (int)tw, tot);
+        if (v >= tot) continue;
+        double r[3];
+        if (dim == 2) {
+            finish_cell<2>(P, nc, nflux, ni, fo_ptr, fn_ptr, Fn, fd_ptr, fs_ptr, F, b0, load, u, vol, rc, mk, r);
+            r[2] = 0.0;
+        } else {
+            finish_cell<3>(P, nc, nflux, ni, fo_ptr, fn_ptr, Fn, fd_ptr, fs_ptr, F, b0, load, u, vol, rc, mk, r);
         }
-        const double* Fk = F + (size_t)k * nflux;
-        const double* Fnk = Fn + (size_t)k * ni;
-        double r = *load_dev * b0[e];
-        for (int f = fo_ptr[P]; f < fo_ptr[P + 1]; f++) r += Fk[f];
-        for (int q = fn_ptr[P]; q < fn_ptr[P + 1]; q++) r -= Fnk[q];
-        for (int f = fd_ptr[P]; f < fd_ptr[P + 1]; f++) r += Fk[f];
-        for (int f = fs_ptr[P]; f < fs_ptr[P + 1]; f++) r += Fk[f];
-        if (rc) r -= vol[P] * fma(mk, u[e], rc[e]);
+        const int K = dim == 2 ? 2 : 3;
         if (mode == 1) {
             const ProbDev& Q = pd[cell_prob[P]];
-            r = Q.eps == 0.0 ? 0.0 : (r - Ru[e]) * Q.ieps;  // 1 / eps, formed once per problem
+            const double eps = Q.eps, ieps = Q.ieps;
+            for (int k = 0; k < K; k++)  // 1 / eps, formed once per problem
+                r[k] = eps == 0.0 ? 0.0 : (r[k] - Ru[(size_t)k * nc + P]) * ieps;
         }
-        out[e] = r;
+#pragma unroll
+        for (int k = 0; k < 3; k++) out[(size_t)k * nc + P] = r[k];
     }
 }
 
@@ -544,7 +573,7 @@ int residual_bufs(jfnk_ctx* c, const double* u_int, double* out, int mode, const
         jfnk_prof_end(c, sl[1]);
     }
     jfnk_prof_begin(c, sl[2]);
-    jfnk_launch(c, k_finish, dim3(rowmap_blocks(c, (const void*)k_finish, tu.finish_bs, 3L * m.nc, tu.finish_bs, rcell)),
+    jfnk_launch(c, k_finish, dim3(rowmap_blocks(c, (const void*)k_finish, tu.finish_bs, (long)m.nc, tu.finish_bs, rcell)),
                 dim3(tu.finish_bs), m.nc, m.nflux, m.ni, m.dim, m.fo_ptr, m.fn_ptr, Fn, m.fd_ptr,
                 (const int32_t*)m.fs_ptr, (const double*)F, m.b0,
                 load, mode, c->Ru, c->pd, c->cell_prob, gate, u_int, (const double*)m.V,
