@@ -10,6 +10,12 @@
  * nothing is fused or reordered for speed.  Where the paper is silent the reading taken
  * is stated at the function that uses it.
  *
+ * Parity unpinned beyond the properties the oracle's tests check: the details of the
+ * multigrid hierarchy (orc_mg_*: the aggregation is this project's reading of an algebraic
+ * multigrid, not the paper's BoomerAMG; pinned only by a hand-worked aggregation, a symmetric
+ * contracting V-cycle and the exact one-level solve) and the Krylov internals (orc_gmres,
+ * orc_lgmres: only their end results are pinned, against dense solves).
+ *
  * Only the tests, the smoke check and the CPU-baseline leg of the benchmark use this file.
  */
 #include "jfnk_oracle.h"
